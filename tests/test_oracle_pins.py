@@ -1,0 +1,378 @@
+"""Pins of the CPU oracle against results that the paper and the mathematics fix.
+
+Each test compares the oracle with something computed a *different* way:
+closed forms built from an eigendecomposition (G0, the Lindhard and
+multi-band bubbles, W of a single band, the second-order self-energy), exact
+pole sums (DLR), invariants (sum rules, filling), and a brute-force Fock-space
+expectation value for the Hartree and Fock terms.  None of these re-uses the
+oracle's own formula for the quantity under test.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import gw, lattice
+from oracle.dlr import DLR, fermi, kfun
+
+
+# ------------------------------------------------------------------ helpers
+
+def _grid_index(n, pts):
+    nn = np.asarray(n)
+    p = np.asarray(pts) % nn
+    return (p[..., 0] * nn[1] + p[..., 1]) * nn[2] + p[..., 2]
+
+
+def _eig_model(model, mu):
+    Hk = lattice.H_k(model)
+    e, U = np.linalg.eigh(Hk)
+    return e - mu, U
+
+
+def _g0_closed_form_tau(model, dlr, mu, t_rel):
+    """G0_ab(k, tau) = -sum_m U_am exp(-tau xi_m)/(1+exp(-beta xi_m)) U*_bm."""
+    xi, U = _eig_model(model, mu)
+    K = kfun(t_rel, (model.beta * xi).ravel()).reshape(len(t_rel), model.nk, model.norb)
+    return -np.einsum("kam,tkm,kbm->ktab", U, K, U.conj())
+
+
+def _pole_sum_bubble(model, dlr, mu, inu):
+    """Bubble of G0 from its Lehmann form (s_spin/N) sum_k sum_mn ...
+
+    P_{(ab),(cd)}(q, i nu) = (s/N) sum_k sum_{m,n} U_bm(k) U*_cm(k) U_dn(k') U*_an(k')
+                             (f_n(k') - f_m(k)) / (i nu + xi_n(k') - xi_m(k)),  k' = k - q.
+    Derived by inserting the eigen-decomposed G0 into the bubble and doing the tau
+    integral analytically; the 0/0 limit is -beta f (1 - f).
+    """
+    xi, U = _eig_model(model, mu)
+    f = fermi(model.beta * xi)
+    pts = lattice.grid_points(model.n)
+    no = model.norb
+    out = np.zeros((model.nk, len(inu), no * no, no * no), dtype=np.complex128)
+    for iq in range(model.nk):
+        kp = _grid_index(model.n, pts - pts[iq])            # k - q for every k
+        xm, xn = xi, xi[kp]                                  # [k, m], [k, n]
+        fm, fn = f, f[kp]
+        for j, nu in enumerate(inu):
+            den = nu + xn[:, None, :] - xm[:, :, None]       # [k, m, n]
+            num = fn[:, None, :] - fm[:, :, None]
+            small = np.abs(den) < 1e-12
+            lim = -model.beta * fm[:, :, None] * (1 - fm[:, :, None])
+            frac = np.where(small, lim, num / np.where(small, 1.0, den))
+            Ub, Ud = U, U[kp]
+            T = np.einsum("kbm,kcm,kdn,kan,kmn->abcd", Ub, Ub.conj(), Ud, Ud.conj(), frac)
+            out[iq, j] = model.s_spin * T.reshape(no * no, no * no) / model.nk
+    return out
+
+
+@pytest.fixture(scope="module")
+def square():
+    m = wl.config("square-8x8")
+    d = gw.make_dlr(m)
+    G0, mu0 = gw.g0(m, d)
+    return m, d, G0, mu0, gw.gw_step(m, d, G0)
+
+
+# ---------------------------------------------------------------- generator
+
+def test_splitmix64_published_vectors():
+    g = wl.SplitMix64(1234567)
+    assert [g.next_u64() for _ in range(3)] == [6457827717110365317, 3203168211198807973,
+                                                9817491932198370423]
+    g = wl.SplitMix64(0)
+    assert g.next_u64() == 0xE220A8397B1DCDAF
+
+
+def test_models_hermitian():
+    for name in ["square-8x8", "graphene-6x6", "five-orbital-4x3x2", "peierls-3x3"]:
+        m = wl.config(name)
+        Hk = lattice.H_k(m)
+        assert np.abs(Hk - Hk.conj().transpose(0, 2, 1)).max() < 1e-14
+        # V(-R) = V(R)^T (particle exchange) for every listed R
+        idx = {tuple(R): i for i, R in enumerate(m.V_R)}
+        for i, R in enumerate(m.V_R):
+            j = idx[tuple(-R)]
+            assert np.abs(m.V[j] - m.V[i].T).max() < 1e-15
+
+
+# --------------------------------------------------------------------- DLR
+
+@pytest.mark.parametrize("beta,Lam,eps", [(10.0, 100.0, 1e-10), (40.0, 1000.0, 1e-10),
+                                          (8.0, 60.0, 1e-10), (10.0, 300.0, 1e-12)])
+def test_dlr_reconstructs_pole_sums(beta, Lam, eps):
+    """Random pole sums with poles in [-Lambda/beta, Lambda/beta]: tau and Matsubara
+    values are exact closed forms; DLR interpolation must reproduce them to ~eps."""
+    d = DLR(beta, Lam, eps)
+    rng = np.random.default_rng(7)
+    w = rng.uniform(-Lam / beta, Lam / beta, 30)
+    c = rng.normal(size=30)
+
+    def g_tau(t_rel):   # -sum_p c_p exp(-tau w_p)/(1+exp(-beta w_p)), closed form
+        t = np.where(t_rel >= 0, t_rel, 1 + t_rel)
+        val = np.zeros(len(t))
+        for wp, cp in zip(w, c):
+            if wp >= 0:
+                val += -cp * np.exp(-t * beta * wp) / (1 + np.exp(-beta * wp))
+            else:
+                val += -cp * np.exp((1 - t) * beta * wp) / (1 + np.exp(beta * wp))
+        return val
+
+    tt = rng.uniform(-0.5, 0.5, 300)
+    ref = g_tau(tt)
+    scale = np.abs(ref).max()
+    # tau -> tau
+    coef = d.coef_from_tau(g_tau(d.t))
+    assert np.abs(d.K_tau(tt) @ coef - ref).max() <= 50 * eps * scale
+    # tau -> Matsubara (fermionic) at arbitrary n
+    n = rng.integers(-5 * int(Lam), 5 * int(Lam), 200)
+    iw = 1j * (2 * n + 1) * np.pi / beta
+    ex = (1.0 / (iw[:, None] - w[None, :])) @ c
+    assert np.abs(d.K_iw(n) @ coef - ex).max() <= 100 * eps * np.abs(ex).max()
+    # Matsubara nodes -> tau
+    giw = (1.0 / (d.iw()[:, None] - w[None, :])) @ c
+    c2 = d.coef_from_iw(giw)
+    # Matsubara-node interpolation has a larger Lebesgue constant than the tau one
+    assert np.abs(d.K_tau(tt) @ c2 - ref).max() <= 1000 * eps * scale
+    # bosonic nodes -> tau and tau -> bosonic (same real frequencies)
+    m = rng.integers(-5 * int(Lam), 5 * int(Lam), 200)
+    inu = 1j * 2 * m * np.pi / beta
+    exb = (np.tanh(beta * w / 2) / (inu[:, None] - w[None, :])) @ c
+    assert np.abs(d.K_inu(m) @ coef - exb).max() <= 100 * eps * np.abs(exb).max()
+    gb = (np.tanh(beta * w / 2) / (d.inu()[:, None] - w[None, :])) @ c
+    assert np.abs(d.K_tau(tt) @ d.coef_from_inu(gb) - ref).max() <= 1000 * eps * scale
+    # reflection K(beta - tau, w) = K(tau, -w) and beta^- value = -f
+    assert np.abs(d.K_tau_reflected() @ coef - g_tau(-d.t)).max() <= 50 * eps * scale
+
+
+def test_dlr_rank_grows_with_lambda_and_precision():
+    r1 = DLR(1.0, 100.0, 1e-10).r
+    r2 = DLR(1.0, 1000.0, 1e-10).r
+    r3 = DLR(1.0, 1000.0, 1e-12).r
+    assert 20 <= r1 < r2 < r3 <= 80
+
+
+# ---------------------------------------------------------------------- G0
+
+@pytest.mark.parametrize("name", ["square-8x8", "peierls-3x3", "five-orbital-4x3x2"])
+def test_g0_matches_closed_form(name):
+    m = wl.config(name)
+    d = gw.make_dlr(m)
+    G0, mu0 = gw.g0(m, d)
+    ref = _g0_closed_form_tau(m, d, mu0, d.t)
+    assert np.abs(G0 - ref).max() <= 1e-7
+    # G(0+) + G(beta-) = -1 and the density equals the Fermi function of H
+    c = d.coef_from_tau(np.moveaxis(G0, 1, 0))
+    g0p = np.einsum("l,lkab->kab", d.K_tau(np.array([0.0]))[0], c)
+    gbm = np.einsum("l,lkab->kab", d.K_beta(), c)
+    assert np.abs(g0p + gbm + np.eye(m.norb)[None]).max() <= 1e-7
+    xi, U = _eig_model(m, mu0)
+    n_exact = np.einsum("kam,km,kbm->kab", U, fermi(m.beta * xi), U.conj())
+    assert np.abs(-gbm - n_exact).max() <= 1e-7
+    N = m.s_spin * np.real(np.einsum("kaa->", n_exact)) / m.nk
+    assert abs(N - m.filling) <= 1e-7
+
+
+def test_half_filling_square_has_mu_zero(square):
+    m, d, G0, mu0, out = square
+    # particle-hole symmetry of the nearest-neighbour square lattice: mu0 = 0
+    assert abs(mu0) < 1e-8
+    # after one step at half filling the Hartree-Fock shift is U/2 (U n/2 * 2 - U n/2)
+    assert abs(out["mu"] - 1.0) < 1e-6
+    assert abs(out["N"] - 1.0) < 1e-11
+
+
+# --------------------------------------------------------------- the bubble
+
+def test_lindhard_single_band(square):
+    """P(q, i nu) = (s/N) sum_k (f(k-q) - f(k)) / (i nu + xi(k-q) - xi(k))."""
+    m, d, G0, mu0, out = square
+    Hk = lattice.H_k(m)
+    xi = np.real(Hk[:, 0, 0]) - mu0
+    f = fermi(m.beta * xi)
+    pts = lattice.grid_points(m.n)
+    ref = np.zeros((m.nk, d.r), dtype=np.complex128)
+    for iq in range(m.nk):
+        kq = _grid_index(m.n, pts - pts[iq])
+        for j, nu in enumerate(d.inu()):
+            den = nu + xi[kq] - xi
+            small = np.abs(den) < 1e-12
+            val = np.where(small, -m.beta * f * (1 - f), (f[kq] - f) / np.where(small, 1, den))
+            ref[iq, j] = m.s_spin * val.sum() / m.nk
+    assert np.abs(out["P_qnu"][:, :, 0, 0] - ref).max() <= 1e-8 * np.abs(ref).max()
+    # static charge response is negative, P(q, tau) = P(q, beta - tau) at half filling
+    assert np.all(ref[:, np.argmin(np.abs(d.mb))].real < 0)
+    Pq = out["P_qtau"][:, :, 0, 0]
+    c = np.linalg.solve(d.K_tau(), Pq.T)
+    assert np.abs(d.K_tau_reflected() @ c - Pq.T).max() <= 1e-8 * np.abs(Pq).max()
+
+
+@pytest.mark.parametrize("name", ["peierls-3x3", "five-orbital-4x3x2"])
+def test_multiband_bubble_lehmann(name):
+    """Orbital orientation of P pinned by the Lehmann (eigenvector) form."""
+    m = wl.config(name)
+    d = gw.make_dlr(m)
+    G0, mu0 = gw.g0(m, d)
+    cG = gw._node_axis_solve(d.K_tau(), G0)
+    GR = lattice.k_to_R(m.n, G0)
+    GreflR = lattice.k_to_R(m.n, gw._node_axis_apply(d.K_tau_reflected(), cG))
+    Pq = lattice.R_to_k(m.n, gw.polarization(m, d, GR, GreflR))
+    Pqnu = gw._node_axis_apply(d.K_inu(), gw._node_axis_solve(d.K_tau(), Pq))
+    ref = _pole_sum_bubble(m, d, mu0, d.inu())
+    assert np.abs(Pqnu - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
+def test_charge_conservation_q0():
+    """sum_{a,c} P_{(aa),(cc)}(q=0, i nu != 0) = 0 (total charge commutes with H0)."""
+    m = wl.config("peierls-3x3")
+    d = gw.make_dlr(m)
+    G0, _ = gw.g0(m, d)
+    out = gw.gw_step(m, d, G0)
+    no = m.norb
+    diag = [a * no + a for a in range(no)]
+    s = out["P_qnu"][0][:, diag][:, :, diag].sum(axis=(1, 2))
+    nz = d.mb != 0
+    assert np.abs(s[nz]).max() <= 1e-8 * np.abs(out["P_qnu"]).max()
+
+
+# -------------------------------------------------------------------------- W
+
+def test_single_band_W(square):
+    """Local U, single band: W(q, i nu) = U / (1 - U P(q, i nu)) with the Lindhard P."""
+    m, d, G0, mu0, out = square
+    U = 2.0
+    P = out["P_qnu"][:, :, 0, 0]
+    ref = U / (1 - U * P)
+    assert np.abs(out["W_qnu"][:, :, 0, 0] - ref).max() <= 1e-13 * abs(U)
+    # W^C vanishes at large |nu| (P ~ 1/nu^2)
+    big = np.argmax(np.abs(d.mb))
+    assert np.abs(out["WC_qnu"][:, big]).max() < 0.05 * np.abs(out["WC_qnu"]).max()
+
+
+def test_W_dyson_residual():
+    m = wl.config("five-orbital-4x3x2")
+    d = gw.make_dlr(m)
+    G0, _ = gw.g0(m, d)
+    out = gw.gw_step(m, d, G0)
+    Vq = lattice.V_q(m)
+    W, P = out["W_qnu"], out["P_qnu"]
+    res = W - Vq[:, None] - np.einsum("qAB,qnBC,qnCD->qnAD", Vq, P, W)
+    assert np.abs(res).max() <= 1e-12 * np.abs(Vq).max()
+
+
+# ------------------------------------------------------------ self-energy
+
+def _second_order_sigma(model, dlr, mu):
+    """Sigma^(2)_{ad}(k, tau) = -(1/N) sum_q sum_bc G0_bc(k-q, tau) [V P0 V]_(ab),(cd)(q, tau)
+
+    with G0 and P0(q, tau) = -(s/N) sum_k' G0(k', tau) (x) G0(k'-q, beta - tau)
+    from the exact exponentials of the eigendecomposition (no DLR)."""
+    no = model.norb
+    Gt = _g0_closed_form_tau(model, dlr, mu, dlr.t)            # [k, t, a, b]
+    Gb = _g0_closed_form_tau(model, dlr, mu, -dlr.t)           # at beta - tau
+    pts = lattice.grid_points(model.n)
+    Vq = lattice.V_q(model).reshape(model.nk, no, no, no, no)
+    P0 = np.zeros((model.nk, dlr.r, no, no, no, no), dtype=np.complex128)
+    for iq in range(model.nk):
+        kq = _grid_index(model.n, pts - pts[iq])
+        P0[iq] = -model.s_spin * np.einsum("ktbc,ktda->tabcd", Gt, Gb[kq]) / model.nk
+    VPV = np.einsum("qabef,qtefgh,qghcd->qtabcd", Vq, P0, Vq)
+    S = np.zeros((model.nk, dlr.r, no, no), dtype=np.complex128)
+    for ik in range(model.nk):
+        kmq = _grid_index(model.n, pts[ik] - pts)               # k - q for every q
+        S[ik] = -np.einsum("qtbc,qtabcd->tad", Gt[kmq], VPV) / model.nk
+    return S
+
+
+@pytest.mark.parametrize("name", ["square-1x1", "peierls-3x3"])
+def test_second_order_self_energy(name):
+    """Sigma^C(lam V) = lam^2 Sigma^(2) + O(lam^3); Richardson in lam removes lam^3."""
+    base = wl.config(name)
+    d = gw.make_dlr(base)
+    G0, mu0 = gw.g0(base, d)
+
+    def sig(lam):
+        m = wl.config(name)
+        m.V = base.V * lam
+        return gw.gw_step(m, d, G0)["sigc_ktau"]
+
+    lam = 1e-4      # the expansion parameter is lam * |V| * beta, not lam
+    s1, s2 = sig(lam), sig(2 * lam)
+    est = (8 * s1 - s2) / (4 * lam ** 2)
+    ref = _second_order_sigma(base, d, mu0)
+    assert np.abs(est - ref).max() <= 1e-5 * np.abs(ref).max()
+
+
+def test_sum_rule_after_step(square):
+    m, d, G0, mu0, out = square
+    c = gw._node_axis_solve(d.K_tau(), out["G_ktau"])
+    g0p = np.einsum("l,kl...->k...", d.K_tau(np.array([0.0]))[0], c)
+    gbm = np.einsum("l,kl...->k...", d.K_beta(), c)
+    assert np.abs(g0p + gbm + np.eye(m.norb)[None]).max() <= 1e-7
+
+
+# ------------------------------------------------- Hartree-Fock, brute force
+
+def _fock_space_energy(V, C, no):
+    """<Phi| (1/2) sum V_{(il),(jk)} c+_is c+_js' c_ks' c_ls |Phi> by brute force.
+
+    Spin orbitals (x, s) -> mode 2x + s; Jordan-Wigner matrices on 2^(2 no) states;
+    |Phi> = prod_o (sum_x C_xo c+_x,up) prod_o (sum_x C_xo c+_x,dn) |0>.
+    """
+    nm = 2 * no
+    dim = 1 << nm
+
+    def ann(mode):
+        A = np.zeros((dim, dim))
+        for st in range(dim):
+            if st >> mode & 1:
+                sign = (-1) ** bin(st & ((1 << mode) - 1)).count("1")
+                A[st ^ (1 << mode), st] = sign
+        return A
+
+    c = [ann(mm) for mm in range(nm)]
+    cd = [a.T for a in c]
+    vac = np.zeros(dim, dtype=np.complex128)
+    vac[0] = 1
+    phi = vac
+    for s in (0, 1):
+        for o in range(C.shape[1]):
+            op = sum(C[x, o] * cd[2 * x + s] for x in range(no))
+            phi = op @ phi
+    E = 0.0
+    for i, l, j, k in itertools.product(range(no), repeat=4):
+        v = V[i * no + l, j * no + k]
+        if v == 0:
+            continue
+        for s, sp in itertools.product((0, 1), repeat=2):
+            op = cd[2 * i + s] @ cd[2 * j + sp] @ c[2 * k + sp] @ c[2 * l + s]
+            E += 0.5 * v * np.vdot(phi, op @ phi)
+    return E / np.vdot(phi, phi)
+
+
+def test_hartree_fock_fock_space():
+    """E_HF = (s/2) Tr[(Sigma^H + Sigma^F) n] equals the exact <Phi|H_int|Phi> for
+    Slater determinants, with a random complex interaction of the right symmetry."""
+    no = 3
+    rng = np.random.default_rng(3)
+    npair = no * no
+    V = rng.normal(size=(npair, npair)) + 1j * rng.normal(size=(npair, npair))
+    sw = V.T                                              # particle exchange
+    V = 0.5 * (V + sw)
+    herm = np.zeros_like(V)                               # V_(il),(jk)* = V_(li),(kj)
+    for i, l, j, k in itertools.product(range(no), repeat=4):
+        herm[i * no + l, j * no + k] = np.conj(V[l * no + i, k * no + j])
+    V = 0.5 * (V + herm)
+    m = wl.Model("cluster", (1, 1, 1), no, np.zeros((0, 3), np.int64),
+                 np.zeros((0, no, no), complex), np.zeros(no), np.zeros((1, 3), np.int64),
+                 V[None], 1.0, 10.0, 1e-10, 1.0)
+    for nocc in (1, 2):
+        for trial in range(2):
+            Q, _ = np.linalg.qr(rng.normal(size=(no, no)) + 1j * rng.normal(size=(no, no)))
+            C = Q[:, :nocc]
+            n = C @ C.conj().T                      # n_xy = <c+_y c_x> per spin
+            sig_h, sig_f = gw.hartree_fock(m, n[None])
+            E_hf = 0.5 * m.s_spin * np.trace((sig_h + sig_f[0]) @ n)
+            E_ex = _fock_space_energy(V, C, no)
+            assert abs(E_hf - E_ex) <= 1e-12 * max(1.0, abs(E_ex))
