@@ -1,0 +1,186 @@
+/*
+ * qa.h -- C ABI of the GB300 GW-iteration library (libqa.so).
+ *
+ * One call of qa_gw_step performs one self-consistent GW iteration on a
+ * k-grid with a discrete-Lehmann-representation (DLR) imaginary-time grid,
+ * as described in the QAssemble paper (arXiv 2604.22223), Sec. "GW
+ * self-consistency" and Fig. 3(b):
+ *
+ *   G(k,tau) -> G(R,tau)                 lattice FFT, Eq. (k<->R transform)
+ *   P(R,tau) = -s G(R,tau) G(-R,beta-tau) bubble, Eq. (polarizability)
+ *   P(q,tau) -> P(q,i nu)                DLR transform (ref. Kaye et al. 2022)
+ *   W = V + V P W,  W^C = W - V          Dyson, Eq. (screened Coulomb)
+ *   W^C(q,i nu) -> W^C(R,tau)            DLR + FFT
+ *   Sigma^C(R,tau) = -G(R,tau) W^C(R,tau) Eq. (GW self-energy)
+ *   Sigma^H, Sigma^F from n = -G(beta^-) Eqs. (Hartree, Fock self-energy)
+ *   G(k,i w) = [i w + mu - H - Sigma]^-1  Eq. (Dyson for G), mu bisection
+ *
+ * Conventions (all arrays complex = interleaved (re, im) doubles unless noted):
+ *   * k-grid (N1,N2,N3), Gamma-centred; linear index (i1*N2 + i2)*N3 + i3.
+ *     The same index labels real-space cells R (j_d in [0, N_d)).
+ *   * Orbital index a in [0, norb); pair index A = (a,b) -> a*norb + b;
+ *     npair = norb*norb.
+ *   * H_ab(R) = <a,R|H|b,0> = -t_ab(R) + delta_{R0} delta_ab eps_a.
+ *     X(k) = sum_R exp(-i k.R) X(R) (cell gauge), X(i w) = int_0^beta exp(+i w tau) X(tau).
+ *   * V_{(ab),(cd)}(R): interaction in the pair basis, paper V_ijkl = V_{(il),(jk)},
+ *     pair (ab) on cell R, pair (cd) on cell 0.
+ *   * Green's function arrays ("G layout"): [r][norb][norb][N_k] complex128,
+ *     k fastest, at the r DLR imaginary-time nodes tau_j (qa_get_grid).
+ *
+ * Memory and execution:
+ *   * qa_create copies every input; it touches no GPU and allocates no device
+ *     memory.  The caller then obtains qa_workspace_size bytes of device
+ *     memory (e.g. from PyTorch's allocator) and hands it over with qa_bind,
+ *     which uploads the tables and builds G0.  The context owns nothing on the
+ *     device; the workspace must outlive the context's use.
+ *   * Device pointers passed to calls are borrowed for the duration of the call.
+ *   * All GPU work is enqueued on the caller's stream (cudaStream_t passed as
+ *     void*; NULL = legacy default stream).  Calls that return host scalars
+ *     (mu, densities, status) synchronise that stream before returning.
+ *   * Every call returns a status code; no call aborts or traps.  Device-side
+ *     failures (a singular Dyson pivot, a non-finite value) are reported
+ *     through a device error word read back at the end of the call.
+ *
+ * Limits: 1 <= norb <= 5 (npair <= 25 fits one warp per Dyson system);
+ *         N_k * 16 bytes (FP64) or * 8 bytes (mixed) must fit the FFT's
+ *         shared-memory tile (N_k <= 12288); 1 <= r <= 128.
+ */
+#ifndef QA_H
+#define QA_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+enum {
+  QA_OK = 0,
+  QA_EINVAL = 1,      /* bad argument, size or layout                       */
+  QA_ENOMEM = 2,      /* workspace too small                                */
+  QA_ESINGULAR = 3,   /* a Dyson pivot below threshold (first index in stats) */
+  QA_ENOCONV = 4,     /* chemical-potential search did not converge          */
+  QA_ERANGE = 5,      /* non-finite values or spectrum outside the DLR window */
+  QA_ETIMEOUT = 6,    /* a bounded device wait ran out                       */
+  QA_ECUDA = 7,       /* a CUDA runtime call failed                          */
+  QA_ESTATE = 8       /* call out of order (e.g. step before qa_bind)        */
+};
+
+/* arithmetic of the GPU path */
+enum {
+  QA_FP64 = 0,        /* complex128 storage and FP64 arithmetic everywhere   */
+  QA_MIXED = 1        /* complex64 storage of P, W^C and the G/Sigma stages,
+                         FP32 arithmetic; FP64 kept for the DLR matrices, the
+                         chemical potential and density accumulation         */
+};
+
+typedef struct qa_ctx qa_ctx;
+
+/* Crystal: the k-grid and the orbital count (paper Sec. "Crystal"). */
+typedef struct {
+  int n[3];           /* N1, N2, N3 >= 1                                      */
+  int norb;           /* orbitals per cell (basis sites x orbitals merged)    */
+  int nspin;          /* spin degeneracy s (2 = paramagnetic spin-1/2)        */
+} qa_lattice;
+
+/* One-body part H0[t, eps] (paper Eq. for the many-body Hamiltonian, first term). */
+typedef struct {
+  int nR;             /* number of listed lattice vectors                     */
+  const int* R;       /* [nR][3] integer lattice vectors; both R and -R listed */
+  const double* t;    /* [nR][norb][norb] complex: t_ab(R), H(R) = -t(R)       */
+  const double* eps;  /* [norb] real on-site energies                          */
+} qa_hoppings;
+
+/* Two-body part (paper Eq. for the many-body Hamiltonian, second term). */
+typedef struct {
+  int nR;             /* number of listed lattice vectors                     */
+  const int* R;       /* [nR][3]                                              */
+  const double* V;    /* [nR][npair][npair] complex V_{(ab),(cd)}(R)           */
+} qa_interaction;
+
+/* Per-step report. */
+typedef struct {
+  double mu;            /* chemical potential after the step                   */
+  double N;             /* electrons per cell at mu                            */
+  int mu_evals;         /* density evaluations used by the mu search           */
+  int status;           /* QA_OK or the first error code seen                  */
+  long long first_bad;  /* first failing system index (nu*N_k + q) or -1       */
+  int launches;         /* kernels this call launched                          */
+  float stage_ms[16];   /* per-stage GPU times when timing is enabled          */
+} qa_step_stats;
+
+/* qa_create: validate and copy the problem (paper Sec. "Results": Crystal, DLR,
+ * H0, V), build the DLR grid (Lambda = beta*omega_max dimensionless, eps = DLR
+ * tolerance; Kaye, Chen & Parcollet 2022) and the FFT plans on the host.
+ * filling = electrons per cell (both spins).  precision = QA_FP64 or QA_MIXED.
+ * Returns QA_EINVAL for sizes outside the limits above or a non-Hermitian H.
+ * *out receives a new context (free with qa_destroy). */
+int qa_create(const qa_lattice* lat, const qa_hoppings* hop, const qa_interaction* inter,
+              double beta, double Lambda, double eps, double filling, int precision,
+              qa_ctx** out);
+
+/* Bytes of device workspace qa_bind needs (tables, intermediates, G0). */
+int qa_workspace_size(const qa_ctx* ctx, size_t* bytes);
+
+/* Attach a device workspace (>= qa_workspace_size bytes, 256-byte aligned),
+ * upload tables, build H(k), V(q) and the noninteracting G0 at the mu0 that
+ * gives the filling (paper Eqs. for G0; "G0 class").  Synchronises `stream`. */
+int qa_bind(qa_ctx* ctx, void* workspace, size_t bytes, void* stream);
+
+/* DLR grid: r nodes; x = beta*omega_l (dimensionless real poles) [r];
+ * t_rel = tau_j/beta in relative format (t>1/2 stored as t-1) [r];
+ * nf = fermionic Matsubara integers n (w_n=(2n+1)pi/beta) [r];
+ * mb = bosonic Matsubara integers m (nu_m = 2 m pi/beta) [r].
+ * Any output pointer may be NULL. */
+int qa_get_grid(const qa_ctx* ctx, int* r, double* x, double* t_rel, int* nf, int* mb);
+
+/* Host-side plan tables (no GPU needed): minus_R [N_k] = linear index of the
+ * cell -R mod N for every cell R; fft_pos [N1+N2+N3] = per axis, the
+ * in-place position of frequency f after the mixed-radix stages; fft_nfac [3]
+ * radix counts; fft_fac [3][16] radices in stage order.  Any pointer may be NULL. */
+int qa_get_plan(const qa_ctx* ctx, int* minus_R, int* fft_pos, int* fft_nfac, int* fft_fac);
+
+/* Sizes: N_k, norb, r.  Any pointer may be NULL. */
+int qa_get_sizes(const qa_ctx* ctx, int* nk, int* norb, int* r);
+
+/* One GW iteration (paper Fig. 3(b)).
+ *   G_in   device, G layout, complex128; NULL = the context's G0.
+ *   G_out  device, G layout, complex128 (may equal G_in): the new G(k, tau_j).
+ *   mu_out host, new chemical potential;  n_out host [norb][norb] complex,
+ *          local density matrix n(R=0) = -G(R=0, beta^-) of the new G.
+ * Intermediates (P, W^C, Sigma^C, Sigma^HF) stay in the workspace; read them
+ * with qa_get.  Returns QA_ESINGULAR / QA_ENOCONV / QA_ERANGE on failure. */
+int qa_gw_step(qa_ctx* ctx, const void* G_in, void* G_out, double* mu_out, double* n_out,
+               qa_step_stats* stats, void* stream);
+
+/* Density of a G in G layout (device): n_out [norb][norb] complex local density
+ * matrix -G(R=0, beta^-), *N_total = s * Tr n (electrons per cell). */
+int qa_density(qa_ctx* ctx, const void* G, double* n_out, double* N_total, void* stream);
+
+/* Intermediates of the last step / of qa_bind, copied to dst (host or device):
+ * element type complex128 for QA_FP64 and complex64 for QA_MIXED, except where
+ * noted.  bytes must equal the array size. */
+enum {
+  QA_P_QNU = 1,       /* P(q, i nu_m)        [r][npair][npair][N_k]           */
+  QA_WC_RTAU = 2,     /* W^C(R, tau_j)       [r][npair][npair][N_k]           */
+  QA_SIGC_KTAU = 3,   /* Sigma^C(k, tau_j)   [r][norb][norb][N_k]             */
+  QA_SIGC_KIW = 4,    /* Sigma^C(k, i w_n)   [r][norb][norb][N_k]             */
+  QA_SIGHF_K = 5,     /* Sigma^H + Sigma^F   [N_k][norb][norb], complex128    */
+  QA_G0 = 6,          /* G0(k, tau_j)        G layout, complex128             */
+  QA_HK = 7,          /* H(k)                [N_k][norb][norb], complex128    */
+  QA_MU0 = 8          /* mu0 of G0, one double                                */
+};
+int qa_get(const qa_ctx* ctx, int which, void* dst, size_t bytes, void* stream);
+
+/* Enable per-stage CUDA-event timing in qa_step_stats (0/1). */
+int qa_set_timing(qa_ctx* ctx, int enable);
+
+void qa_destroy(qa_ctx* ctx);
+const char* qa_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QA_H */

@@ -224,3 +224,49 @@ def gw_step(model, dlr: DLR, Gtau: np.ndarray) -> dict:
     out.update(mu=mu, N=N, mu_iterations=nit, G_kiw=Giw, G_ktau=Gnew, n_k=nk_out,
                n_local=nk_out.sum(axis=0) / model.nk)
     return out
+
+
+def reflected(model, dlr: DLR, Gtau: np.ndarray) -> np.ndarray:
+    """G(k, beta - tau_j) from G(k, tau_j) through the DLR coefficients."""
+    return _node_axis_apply(dlr.K_tau_reflected(), _node_axis_solve(dlr.K_tau(), Gtau))
+
+
+def _k_minus(model, iq: int) -> np.ndarray:
+    """Linear index of k - q for every k (q given by its index)."""
+    pts = lattice.grid_points(model.n)
+    nn = np.asarray(model.n)
+    kq = (pts - pts[iq]) % nn
+    return (kq[:, 0] * nn[1] + kq[:, 1]) * nn[2] + kq[:, 2]
+
+
+def polarization_at_q(model, dlr: DLR, Gtau: np.ndarray, iq: int, Grefl=None) -> np.ndarray:
+    """P(q, i nu_m) for one q by the explicit k-sum of the bubble.
+
+    P_{(ab),(cd)}(q, tau) = sum_R exp(-i q.R) P(R, tau)
+                          = -(s_spin/N_k) sum_k G_{bc}(k, tau) G_{da}(k - q, beta - tau),
+    then the DLR tau -> i nu transform.  Used for sampled checks on grids
+    where the full R-space evaluation is too large.  Returns [r, npair, npair].
+    """
+    no = model.norb
+    if Grefl is None:
+        Grefl = reflected(model, dlr, Gtau)
+    P = -model.s_spin * np.einsum("ktbc,ktda->tabcd", Gtau, Grefl[_k_minus(model, iq)]) / model.nk
+    P = P.reshape(dlr.r, no * no, no * no)
+    c = np.linalg.solve(dlr.K_tau(), P.reshape(dlr.r, -1))
+    return (dlr.K_inu() @ c).reshape(dlr.r, no * no, no * no)
+
+
+def self_energy_at_k(model, Gtau: np.ndarray, WCq_tau: np.ndarray, ik: int) -> np.ndarray:
+    """Sigma^C(k, tau_j) for one k by the explicit q-sum (convolution form).
+
+    Sigma^C_{ad}(k, tau) = sum_R exp(-i k.R) Sigma^C_{ad}(R, tau)
+                         = -(1/N_k) sum_q sum_bc G_{bc}(k - q, tau) W^C_{(ab),(cd)}(q, tau).
+    WCq_tau: [N_k, r, npair, npair].  Returns [r, norb, norb].
+    """
+    no = model.norb
+    pts = lattice.grid_points(model.n)
+    nn = np.asarray(model.n)
+    kq = (pts[ik] - pts) % nn
+    kq = (kq[:, 0] * nn[1] + kq[:, 1]) * nn[2] + kq[:, 2]
+    W6 = WCq_tau.reshape(WCq_tau.shape[0], WCq_tau.shape[1], no, no, no, no)
+    return -np.einsum("qtbc,qtabcd->tad", Gtau[kq], W6) / model.nk

@@ -1,0 +1,710 @@
+// C ABI of libqa: problem validation, the host planner (DLR grid, FFT plans,
+// index maps), device workspace layout, and the stage sequence of one GW
+// iteration (paper Fig. 3(b)).  Every arithmetic step of the iteration runs
+// in the CUDA kernels of qa_*.cu; the host only orders launches and runs the
+// scalar chemical-potential search on device-computed densities.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/qa.h"
+#include "qa_internal.h"
+
+using cd = std::complex<double>;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct DevTables {          // DLR matrices in one precision (complex)
+  void* Trefl = nullptr;
+  void* Ttn = nullptr;
+  void* Tnt = nullptr;
+  void* Ttw = nullptr;
+  void* Twt = nullptr;
+  void* dtau = nullptr;
+  void* dw = nullptr;
+};
+
+}  // namespace
+
+struct qa_ctx {
+  // problem
+  int n[3] = {1, 1, 1};
+  int nk = 1, norb = 1, npair = 1, nspin = 2, r = 0, precision = QA_FP64;
+  double beta = 1, Lambda = 1, eps = 1e-10, filling = 1;
+  std::vector<int> hopR;          // [nH][3]
+  std::vector<cd> hopH;           // [nH][norb][norb], H(R)
+  std::vector<int> vR;            // [nV + 1][3], last = R 0 (for the Hartree density)
+  std::vector<cd> vV;             // [nV][npair][npair]
+  int nH = 0, nV = 0;
+  qa::DlrGrid grid;
+  qa::DlrMatrices mats;
+  qa::FftAxisPlan ax[3];
+  std::vector<int> pos[3];
+  std::vector<int> mR;            // -R map
+  // device
+  bool bound = false;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  DevTables t64, t32;
+  double* d_iw = nullptr;
+  void* d_tw64 = nullptr;
+  void* d_tw32 = nullptr;
+  int* d_pos = nullptr;
+  int* d_mR = nullptr;
+  int* d_hR = nullptr;
+  double2* d_hH = nullptr;
+  int* d_vR = nullptr;
+  double2* d_vV = nullptr;
+  double2* d_Hk = nullptr;
+  void* d_Vq = nullptr;
+  double2* d_G0 = nullptr;
+  void* d_Gk = nullptr;       // G_in in the compute precision (mixed only)
+  void* d_Grefl = nullptr;    // G(k, beta-tau) then G(-R..) in place
+  void* d_GR = nullptr;
+  double2* d_nk = nullptr;    // [norb^2][N_k] FP64 density of G_in
+  double2* d_nR = nullptr;    // [nV+1][norb^2]
+  double2* d_sigFR = nullptr; // [nV+1][norb^2]
+  double2* d_SigHF = nullptr; // [N_k][norb^2]
+  void* d_SigC = nullptr;     // Sigma^C(R,tau) -> (k,tau)
+  void* d_SigIw = nullptr;    // Sigma^C(k, i w)
+  void* d_Giw = nullptr;      // G(k, i w) (sized for FP64)
+  void* d_Gt = nullptr;       // G(k, tau) / n(k) scratch (sized for FP64)
+  void* d_P = nullptr;
+  void* d_W = nullptr;
+  double* d_part = nullptr;
+  double* d_red = nullptr;
+  int* d_err = nullptr;
+  long long* d_bad = nullptr;
+  double2* d_nloc = nullptr;
+  qa::FftDev fft64{}, fft32{};
+  int nblocks_g = 1;
+  double mu0 = 0.0, mu = 0.0;
+  bool have_mu = false;
+  bool timing = false;
+  int launches = 0;           // kernels launched by the current call
+};
+
+namespace {
+
+#define QA_TRY(x)                                   \
+  do {                                              \
+    cudaError_t e__ = (x);                          \
+    if (e__ != cudaSuccess) return QA_ECUDA;        \
+  } while (0)
+
+// a launcher call that enqueues `n` kernels
+#define QA_LAUNCH(c, n, x)                          \
+  do {                                              \
+    QA_TRY(x);                                      \
+    (c)->launches += (n);                           \
+  } while (0)
+
+bool small_primes_only(int L) {
+  for (int p = 2; p <= L; ++p)
+    while (L % p == 0) {
+      if (p > 13) return false;
+      L /= p;
+    }
+  return true;
+}
+
+int grid_index(const qa_ctx* c, int i1, int i2, int i3) {
+  return (i1 * c->n[1] + i2) * c->n[2] + i3;
+}
+
+// layout of the workspace; when `base` is null only sizes are accumulated
+size_t layout(qa_ctx* c, char* base) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> void* {
+    void* p = base ? base + off : nullptr;
+    off += align_up(bytes);
+    return p;
+  };
+  const size_t r = c->r, nk = c->nk, no2 = static_cast<size_t>(c->norb) * c->norb,
+               np2 = static_cast<size_t>(c->npair) * c->npair;
+  const size_t es = c->precision == QA_FP64 ? 16 : 8;   // big/compute element size
+  const size_t rr = r * r;
+  for (DevTables* t : {&c->t64, &c->t32}) {
+    const size_t e = (t == &c->t64) ? 16 : 8;
+    t->Trefl = take(rr * e);
+    t->Ttn = take(rr * e);
+    t->Tnt = take(rr * e);
+    t->Ttw = take(rr * e);
+    t->Twt = take(rr * e);
+    t->dtau = take(r * e);
+    t->dw = take(r * e);
+  }
+  const size_t ntw = c->n[0] + c->n[1] + c->n[2];
+  c->d_iw = static_cast<double*>(take(r * 8));
+  c->d_tw64 = take(ntw * 16);
+  c->d_tw32 = take(ntw * 8);
+  c->d_pos = static_cast<int*>(take(ntw * 4));
+  c->d_mR = static_cast<int*>(take(nk * 4));
+  c->d_hR = static_cast<int*>(take(std::max(1, c->nH) * 12));
+  c->d_hH = static_cast<double2*>(take(std::max(1, c->nH) * no2 * 16));
+  c->d_vR = static_cast<int*>(take((c->nV + 1) * 12));
+  c->d_vV = static_cast<double2*>(take(std::max(1, c->nV) * np2 * 16));
+  c->d_Hk = static_cast<double2*>(take(nk * no2 * 16));
+  c->d_Vq = take(nk * np2 * es);
+  c->d_G0 = static_cast<double2*>(take(r * no2 * nk * 16));
+  c->d_Gk = take(r * no2 * nk * es);
+  c->d_Grefl = take(r * no2 * nk * es);
+  c->d_GR = take(r * no2 * nk * es);
+  c->d_nk = static_cast<double2*>(take(no2 * nk * 16));
+  c->d_nR = static_cast<double2*>(take((c->nV + 1) * no2 * 16));
+  c->d_sigFR = static_cast<double2*>(take((c->nV + 1) * no2 * 16));
+  c->d_SigHF = static_cast<double2*>(take(nk * no2 * 16));
+  c->d_SigC = take(r * no2 * nk * es);
+  c->d_SigIw = take(r * no2 * nk * es);
+  c->d_Giw = take(r * no2 * nk * 16);
+  c->d_Gt = take(r * no2 * nk * 16);
+  // big tensors last; P must also hold the FP64 V(q) staging of qa_bind
+  c->d_P = take(std::max(r * np2 * nk * es, nk * np2 * 16));
+  c->d_W = take(r * np2 * nk * es);
+  c->nblocks_g = qa::dyson_g_blocks(c->r, c->nk);
+  c->d_part = static_cast<double*>(take(2 * static_cast<size_t>(c->nblocks_g) * 8));
+  c->d_red = static_cast<double*>(take(2 * 8));
+  c->d_err = static_cast<int*>(take(4));
+  c->d_bad = static_cast<long long*>(take(8));
+  c->d_nloc = static_cast<double2*>(take(no2 * 16));
+  return off;
+}
+
+template <typename T>
+cudaError_t upload_c(void* dst, const std::vector<cd>& src, cudaStream_t st) {
+  if (sizeof(T) == 8) {
+    return cudaMemcpyAsync(dst, src.data(), src.size() * 16, cudaMemcpyHostToDevice, st);
+  }
+  std::vector<float> f(2 * src.size());
+  for (size_t i = 0; i < src.size(); ++i) {
+    f[2 * i] = static_cast<float>(src[i].real());
+    f[2 * i + 1] = static_cast<float>(src[i].imag());
+  }
+  cudaError_t e = cudaMemcpyAsync(dst, f.data(), f.size() * 4, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(st);   // f goes out of scope
+}
+
+// Density and derivative at mu.  Result: N(mu), dN/dmu.
+template <typename T>
+int eval_density(qa_ctx* c, const double2* SigHF, const void* SigIw, const DevTables& tab,
+                 double mu, double* N, double* dN, cudaStream_t st) {
+  QA_LAUNCH(c, 1, qa::launch_dyson_g<T>(c->d_Hk, SigHF, SigIw, tab.dw, c->d_iw, mu, c->r, c->norb, c->nk,
+                               nullptr, c->d_part, c->nblocks_g, 0, c->d_err, st));
+  QA_LAUNCH(c, 1, qa::launch_reduce_pairs(c->d_part, c->nblocks_g, 0, c->d_red, st));
+  double h[2];
+  QA_TRY(cudaMemcpyAsync(h, c->d_red, 16, cudaMemcpyDeviceToHost, st));
+  QA_TRY(cudaStreamSynchronize(st));
+  *N = c->nspin * h[0] / c->nk;
+  *dN = -c->nspin * h[1] / c->nk;
+  return QA_OK;
+}
+
+// Chemical potential: bisection on N(mu) = filling, with Newton steps taken
+// whenever they stay inside the current bracket (N is increasing in mu).
+template <typename T>
+int mu_search(qa_ctx* c, const double2* SigHF, const void* SigIw, const DevTables& tab,
+              double mu_start, double* mu_out, double* N_out, int* evals, cudaStream_t st) {
+  QA_LAUNCH(c, 1, qa::launch_norm_bound<T>(c->d_Hk, SigHF, SigIw, c->r, c->norb, c->nk, c->d_part,
+                                  c->nblocks_g, st));
+  QA_LAUNCH(c, 1, qa::launch_reduce_pairs(c->d_part, c->nblocks_g, 1, c->d_red, st));
+  double h[2];
+  QA_TRY(cudaMemcpyAsync(h, c->d_red, 16, cudaMemcpyDeviceToHost, st));
+  QA_TRY(cudaStreamSynchronize(st));
+  if (!std::isfinite(h[0])) return QA_ERANGE;
+  const double wid = h[0] + 1.0 + 10.0 / c->beta;
+  double lo = -wid, hi = wid;
+  const double target = c->filling;
+  const bool fp64 = sizeof(T) == 8;
+  const double tolN = (fp64 ? 1e-12 : 1e-9) * std::max(1.0, target);
+  const double tolB = fp64 ? 2e-13 : 1e-10;
+  double mu = (std::isfinite(mu_start) && mu_start > lo && mu_start < hi) ? mu_start : 0.5 * (lo + hi);
+  double N = 0, dN = 0;
+  double dx = hi - lo, dxold = dx;
+  int it = 0;
+  for (; it < 200; ++it) {
+    int rc = eval_density<T>(c, SigHF, SigIw, tab, mu, &N, &dN, st);
+    if (rc != QA_OK) return rc;
+    if (!std::isfinite(N)) return QA_ERANGE;
+    const double f = N - target;
+    if (std::fabs(f) <= tolN) break;
+    if (f < 0) lo = mu; else hi = mu;
+    if (hi - lo <= tolB) {
+      mu = 0.5 * (lo + hi);
+      rc = eval_density<T>(c, SigHF, SigIw, tab, mu, &N, &dN, st);
+      ++it;
+      if (rc != QA_OK) return rc;
+      break;
+    }
+    // Newton step when it stays inside the bracket and at least halves the
+    // previous step (safeguarded Newton, "rtsafe"); bisection otherwise.
+    const double cand = mu - f / dN;
+    if (!(dN > 0) || !std::isfinite(cand) || cand <= lo || cand >= hi ||
+        std::fabs(2.0 * f) > std::fabs(dxold * dN)) {
+      dxold = dx;
+      dx = 0.5 * (hi - lo);
+      mu = lo + dx;
+    } else {
+      dxold = dx;
+      dx = f / dN;
+      mu = cand;
+    }
+  }
+  *evals = it + 1;
+  *mu_out = mu;
+  *N_out = N;
+  if (it >= 200) return QA_ENOCONV;
+  return QA_OK;
+}
+
+int check_err(qa_ctx* c, qa_step_stats* stats, cudaStream_t st) {
+  int herr = 0;
+  long long hbad = -1;
+  QA_TRY(cudaMemcpyAsync(&herr, c->d_err, 4, cudaMemcpyDeviceToHost, st));
+  QA_TRY(cudaMemcpyAsync(&hbad, c->d_bad, 8, cudaMemcpyDeviceToHost, st));
+  QA_TRY(cudaStreamSynchronize(st));
+  if (stats) {
+    stats->status = herr;
+    stats->first_bad = herr ? hbad : -1;
+  }
+  return herr;
+}
+
+int reset_err(qa_ctx* c, cudaStream_t st) {
+  QA_TRY(cudaMemsetAsync(c->d_err, 0, 4, st));
+  QA_TRY(cudaMemsetAsync(c->d_bad, 0x7f, 8, st));
+  return QA_OK;
+}
+
+// G(k,tau) = Twt G(k, i w) at mu, and the local density matrix.
+template <typename T>
+int finish_g(qa_ctx* c, const double2* SigHF, const void* SigIw, const DevTables& tab, double mu,
+             void* G_out_c128, double* n_out, cudaStream_t st) {
+  const long long ncol = static_cast<long long>(c->norb) * c->norb * c->nk;
+  QA_LAUNCH(c, 1, qa::launch_dyson_g<T>(c->d_Hk, SigHF, SigIw, tab.dw, c->d_iw, mu, c->r, c->norb, c->nk,
+                               c->d_Giw, c->d_part, c->nblocks_g, 1, c->d_err, st));
+  if (sizeof(T) == 8) {
+    QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Twt, c->r, c->r, c->d_Giw, G_out_c128, ncol, st));
+  } else {
+    QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Twt, c->r, c->r, c->d_Giw, c->d_Gt, ncol, st));
+    QA_LAUNCH(c, 1, qa::launch_c64_to_c128(static_cast<const float2*>(c->d_Gt),
+                                  static_cast<double2*>(G_out_c128), ncol * c->r, st));
+  }
+  if (n_out) {
+    // n(k) = sum_n dw_n G(k, i w_n), then its k-average (n(R = 0))
+    QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.dw, 1, c->r, c->d_Giw, c->d_Gt, ncol, st));
+    QA_LAUNCH(c, 1, qa::launch_k_average<T>(c->d_Gt, c->norb * c->norb, c->nk, c->d_nloc, st));
+    QA_TRY(cudaMemcpyAsync(n_out, c->d_nloc, static_cast<size_t>(c->norb) * c->norb * 16,
+                           cudaMemcpyDeviceToHost, st));
+    QA_TRY(cudaStreamSynchronize(st));
+  }
+  return QA_OK;
+}
+
+struct StageTimer {
+  qa_ctx* c;
+  cudaStream_t st;
+  cudaEvent_t ev[17];
+  int n = 0;
+  bool on;
+  StageTimer(qa_ctx* cc, cudaStream_t s) : c(cc), st(s), on(cc->timing) {
+    if (on)
+      for (auto& e : ev) cudaEventCreate(&e);
+    mark();
+  }
+  void mark() {
+    if (on && n < 17) cudaEventRecord(ev[n++], st);
+  }
+  void finish(qa_step_stats* stats) {
+    if (!on) return;
+    cudaEventSynchronize(ev[n - 1]);
+    for (int i = 0; i + 1 < n && i < 16; ++i) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+      if (stats) stats->stage_ms[i] = ms;
+    }
+  }
+  ~StageTimer() {
+    if (on)
+      for (auto& e : ev) cudaEventDestroy(e);
+  }
+};
+
+template <typename T>
+int gw_step_impl(qa_ctx* c, const void* G_in, void* G_out, double* mu_out, double* n_out,
+                 qa_step_stats* stats, cudaStream_t st) {
+  const DevTables& tab = sizeof(T) == 8 ? c->t64 : c->t32;
+  const qa::FftDev& fft = sizeof(T) == 8 ? c->fft64 : c->fft32;
+  const int r = c->r, no2 = c->norb * c->norb, nk = c->nk, np2 = c->npair * c->npair;
+  const long long ncs = static_cast<long long>(no2) * nk;     // small-tensor columns
+  const long long ncb = static_cast<long long>(np2) * nk;     // big-tensor columns
+  const double2* Gin = static_cast<const double2*>(G_in ? G_in : c->d_G0);
+  c->launches = 0;
+  if (int rc = reset_err(c, st)) return rc;
+  StageTimer tm(c, st);
+  // n(k) = -G(k, beta^-) of the input, Hartree and Fock (FP64)
+  QA_LAUNCH(c, 1, qa::launch_dlr_apply<double>(c->t64.dtau, 1, r, Gin, c->d_nk, ncs, st));
+  QA_LAUNCH(c, 1, qa::launch_density_R(c->d_nk, c->d_vR, c->nV + 1, no2, nullptr, nk, c->n[0], c->n[1],
+                              c->n[2], c->d_nR, st));
+  QA_LAUNCH(c, 2, qa::launch_hf(c->d_vV, c->d_nR, c->d_vR, c->nV, c->norb, c->nspin, nullptr, nk, c->n[0],
+                       c->n[1], c->n[2], c->d_sigFR, c->d_SigHF, st));
+  tm.mark();  // 0: HF
+  // G in compute precision, G(k, beta - tau), real-space G
+  const void* Gk = Gin;
+  if (sizeof(T) == 4) {
+    QA_LAUNCH(c, 1, qa::launch_c128_to_c64(Gin, static_cast<float2*>(c->d_Gk), ncs * r, st));
+    Gk = c->d_Gk;
+  }
+  QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Trefl, r, r, Gk, c->d_Grefl, ncs, st));
+  QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, +1, Gk, c->d_GR, ncs / nk * r, st));
+  QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, +1, c->d_Grefl, c->d_Grefl, ncs / nk * r, st));
+  tm.mark();  // 1: G -> R
+  QA_LAUNCH(c, 1, qa::launch_bubble<T>(c->d_GR, c->d_Grefl, c->d_mR, c->d_P, r, c->norb, nk, c->nspin, st));
+  tm.mark();  // 2: bubble
+  QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, -1, c->d_P, c->d_P, ncb / nk * r, st));
+  tm.mark();  // 3: FFT R -> q
+  QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Ttn, r, r, c->d_P, c->d_P, ncb, st));
+  tm.mark();  // 4: DLR tau -> nu
+  QA_LAUNCH(c, 1, qa::launch_dyson_w<T>(c->d_P, c->d_Vq, c->d_W, r, c->npair, nk, c->d_err, c->d_bad, st));
+  tm.mark();  // 5: Dyson W
+  QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Tnt, r, r, c->d_W, c->d_W, ncb, st));
+  tm.mark();  // 6: DLR nu -> tau
+  QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, +1, c->d_W, c->d_W, ncb / nk * r, st));
+  tm.mark();  // 7: FFT q -> R
+  QA_LAUNCH(c, 1, qa::launch_sigma<T>(c->d_GR, c->d_W, c->d_SigC, r, c->norb, nk, st));
+  tm.mark();  // 8: Sigma contraction
+  QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, -1, c->d_SigC, c->d_SigC, ncs / nk * r, st));
+  QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Ttw, r, r, c->d_SigC, c->d_SigIw, ncs, st));
+  tm.mark();  // 9: Sigma -> (k, i w)
+  double mu = 0, N = 0;
+  int evals = 0;
+  int rc = mu_search<T>(c, c->d_SigHF, c->d_SigIw, tab, c->have_mu ? c->mu : c->mu0, &mu, &N,
+                        &evals, st);
+  if (rc != QA_OK) return rc;
+  tm.mark();  // 10: mu search
+  rc = finish_g<T>(c, c->d_SigHF, c->d_SigIw, tab, mu, G_out, n_out, st);
+  if (rc != QA_OK) return rc;
+  tm.mark();  // 11: Dyson G + G(tau)
+  tm.finish(stats);
+  c->mu = mu;
+  c->have_mu = true;
+  if (mu_out) *mu_out = mu;
+  if (stats) {
+    stats->mu = mu;
+    stats->N = N;
+    stats->mu_evals = evals;
+    stats->launches = c->launches;
+  }
+  int herr = check_err(c, stats, st);
+  return herr;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* qa_strerror(int s) {
+  switch (s) {
+    case QA_OK: return "ok";
+    case QA_EINVAL: return "invalid argument";
+    case QA_ENOMEM: return "workspace too small";
+    case QA_ESINGULAR: return "singular Dyson pivot";
+    case QA_ENOCONV: return "chemical potential search did not converge";
+    case QA_ERANGE: return "non-finite value or spectrum outside the DLR window";
+    case QA_ETIMEOUT: return "device wait timed out";
+    case QA_ECUDA: return "CUDA runtime error";
+    case QA_ESTATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+int qa_create(const qa_lattice* lat, const qa_hoppings* hop, const qa_interaction* inter,
+              double beta, double Lambda, double eps, double filling, int precision,
+              qa_ctx** out) {
+  if (!lat || !hop || !inter || !out) return QA_EINVAL;
+  *out = nullptr;
+  if (precision != QA_FP64 && precision != QA_MIXED) return QA_EINVAL;
+  if (lat->norb < 1 || lat->norb > 5 || lat->nspin < 1) return QA_EINVAL;
+  long long nk = 1;
+  for (int d = 0; d < 3; ++d) {
+    if (lat->n[d] < 1 || lat->n[d] > 4096 || !small_primes_only(lat->n[d])) return QA_EINVAL;
+    nk *= lat->n[d];
+  }
+  if (nk > 12288) return QA_EINVAL;
+  if (!(beta > 0) || !(Lambda > 1) || !(eps > 0 && eps < 1)) return QA_EINVAL;
+  if (!(filling > 0) || !(filling < static_cast<double>(lat->nspin) * lat->norb)) return QA_EINVAL;
+  if (hop->nR < 0 || inter->nR < 0) return QA_EINVAL;
+  if ((hop->nR > 0 && (!hop->R || !hop->t)) || (inter->nR > 0 && (!inter->R || !inter->V)))
+    return QA_EINVAL;
+  qa_ctx* c = new (std::nothrow) qa_ctx();
+  if (!c) return QA_ENOMEM;
+  c->n[0] = lat->n[0]; c->n[1] = lat->n[1]; c->n[2] = lat->n[2];
+  c->nk = static_cast<int>(nk);
+  c->norb = lat->norb;
+  c->npair = lat->norb * lat->norb;
+  c->nspin = lat->nspin;
+  c->beta = beta; c->Lambda = Lambda; c->eps = eps; c->filling = filling;
+  c->precision = precision;
+  const int no = c->norb, no2 = no * no, np2 = c->npair * c->npair;
+  // H(R) = -t(R), plus eps on R = 0
+  bool have0 = false;
+  for (int i = 0; i < hop->nR; ++i) {
+    for (int d = 0; d < 3; ++d) c->hopR.push_back(hop->R[3 * i + d]);
+    bool zero = hop->R[3 * i] == 0 && hop->R[3 * i + 1] == 0 && hop->R[3 * i + 2] == 0;
+    for (int e = 0; e < no2; ++e) {
+      cd v(-hop->t[2 * (static_cast<size_t>(i) * no2 + e)], -hop->t[2 * (static_cast<size_t>(i) * no2 + e) + 1]);
+      if (zero && e / no == e % no && hop->eps) v += hop->eps[e / no];
+      c->hopH.push_back(v);
+    }
+    have0 |= zero;
+  }
+  if (!have0) {
+    c->hopR.insert(c->hopR.end(), {0, 0, 0});
+    for (int e = 0; e < no2; ++e)
+      c->hopH.push_back(cd(e / no == e % no && hop->eps ? hop->eps[e / no] : 0.0, 0.0));
+  }
+  c->nH = static_cast<int>(c->hopR.size() / 3);
+  // Hermiticity: H(-R) = H(R)^dagger for every listed R
+  double scale = 0;
+  for (const cd& v : c->hopH) scale = std::max(scale, std::abs(v));
+  for (int i = 0; i < c->nH; ++i) {
+    int j = -1;
+    for (int k = 0; k < c->nH; ++k)
+      if (c->hopR[3 * k] == -c->hopR[3 * i] && c->hopR[3 * k + 1] == -c->hopR[3 * i + 1] &&
+          c->hopR[3 * k + 2] == -c->hopR[3 * i + 2]) { j = k; break; }
+    if (j < 0) { delete c; return QA_EINVAL; }
+    for (int a = 0; a < no; ++a)
+      for (int b = 0; b < no; ++b) {
+        cd x = c->hopH[static_cast<size_t>(i) * no2 + a * no + b];
+        cd y = c->hopH[static_cast<size_t>(j) * no2 + b * no + a];
+        if (std::abs(x - std::conj(y)) > 1e-12 * std::max(1.0, scale)) { delete c; return QA_EINVAL; }
+      }
+  }
+  c->nV = inter->nR;
+  for (int i = 0; i < c->nV; ++i) {
+    for (int d = 0; d < 3; ++d) c->vR.push_back(inter->R[3 * i + d]);
+    for (int e = 0; e < np2; ++e)
+      c->vV.push_back(cd(inter->V[2 * (static_cast<size_t>(i) * np2 + e)],
+                         inter->V[2 * (static_cast<size_t>(i) * np2 + e) + 1]));
+  }
+  c->vR.insert(c->vR.end(), {0, 0, 0});
+  for (const cd& v : c->vV)
+    if (!std::isfinite(v.real()) || !std::isfinite(v.imag())) { delete c; return QA_EINVAL; }
+  for (const cd& v : c->hopH)
+    if (!std::isfinite(v.real()) || !std::isfinite(v.imag())) { delete c; return QA_EINVAL; }
+  // DLR grid and transform matrices
+  if (qa::build_dlr(Lambda, eps, &c->grid) != 0) { delete c; return QA_EINVAL; }
+  c->r = c->grid.r;
+  qa::build_dlr_matrices(c->grid, beta, &c->mats);
+  // FFT plans and the -R map
+  for (int d = 0; d < 3; ++d) qa::plan_fft_axis(c->n[d], &c->ax[d], &c->pos[d]);
+  c->mR.resize(c->nk);
+  for (int i1 = 0; i1 < c->n[0]; ++i1)
+    for (int i2 = 0; i2 < c->n[1]; ++i2)
+      for (int i3 = 0; i3 < c->n[2]; ++i3)
+        c->mR[grid_index(c, i1, i2, i3)] =
+            grid_index(c, (c->n[0] - i1) % c->n[0], (c->n[1] - i2) % c->n[1], (c->n[2] - i3) % c->n[2]);
+  *out = c;
+  return QA_OK;
+}
+
+int qa_workspace_size(const qa_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return QA_EINVAL;
+  *bytes = layout(const_cast<qa_ctx*>(c), nullptr) + kAlign;
+  return QA_OK;
+}
+
+int qa_bind(qa_ctx* c, void* workspace, size_t bytes, void* stream) {
+  if (!c || !workspace) return QA_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  size_t need = layout(c, nullptr);
+  char* base = static_cast<char*>(workspace);
+  size_t shift = (kAlign - reinterpret_cast<uintptr_t>(base) % kAlign) % kAlign;
+  if (bytes < need + shift) return QA_ENOMEM;
+  c->ws = base + shift;
+  c->ws_bytes = bytes - shift;
+  layout(c, c->ws);
+  const int r = c->r;
+  // DLR tables
+  const qa::DlrMatrices& m = c->mats;
+  std::vector<cd> iw_c;
+  QA_TRY(upload_c<double>(c->t64.Trefl, m.Trefl, st));
+  QA_TRY(upload_c<double>(c->t64.Ttn, m.Ttn, st));
+  QA_TRY(upload_c<double>(c->t64.Tnt, m.Tnt, st));
+  QA_TRY(upload_c<double>(c->t64.Ttw, m.Ttw, st));
+  QA_TRY(upload_c<double>(c->t64.Twt, m.Twt, st));
+  QA_TRY(upload_c<double>(c->t64.dtau, m.dtau, st));
+  QA_TRY(upload_c<double>(c->t64.dw, m.dw, st));
+  QA_TRY(upload_c<float>(c->t32.Trefl, m.Trefl, st));
+  QA_TRY(upload_c<float>(c->t32.Ttn, m.Ttn, st));
+  QA_TRY(upload_c<float>(c->t32.Tnt, m.Tnt, st));
+  QA_TRY(upload_c<float>(c->t32.Ttw, m.Ttw, st));
+  QA_TRY(upload_c<float>(c->t32.Twt, m.Twt, st));
+  QA_TRY(upload_c<float>(c->t32.dtau, m.dtau, st));
+  QA_TRY(upload_c<float>(c->t32.dw, m.dw, st));
+  QA_TRY(cudaMemcpyAsync(c->d_iw, m.iw.data(), r * 8, cudaMemcpyHostToDevice, st));
+  // FFT twiddles exp(-2 pi i m / L) per axis, and digit-reversal tables
+  std::vector<cd> tw;
+  std::vector<int> pos;
+  for (int d = 0; d < 3; ++d) {
+    c->fft64.n[d] = c->fft32.n[d] = c->n[d];
+    c->fft64.nfac[d] = c->fft32.nfac[d] = c->ax[d].nfac;
+    for (int s = 0; s < qa::kMaxFac; ++s) c->fft64.fac[d][s] = c->fft32.fac[d][s] = c->ax[d].fac[s];
+    c->fft64.tw_off[d] = c->fft32.tw_off[d] = static_cast<int>(tw.size());
+    c->fft64.pos_off[d] = c->fft32.pos_off[d] = static_cast<int>(pos.size());
+    const long double two_pi = 6.283185307179586476925286766559005768L;
+    for (int k = 0; k < c->n[d]; ++k) {
+      long double ang = -two_pi * k / c->n[d];
+      tw.push_back(cd(static_cast<double>(std::cos(ang)), static_cast<double>(std::sin(ang))));
+    }
+    pos.insert(pos.end(), c->pos[d].begin(), c->pos[d].end());
+  }
+  QA_TRY(upload_c<double>(c->d_tw64, tw, st));
+  QA_TRY(upload_c<float>(c->d_tw32, tw, st));
+  QA_TRY(cudaMemcpyAsync(c->d_pos, pos.data(), pos.size() * 4, cudaMemcpyHostToDevice, st));
+  c->fft64.tw = c->d_tw64;
+  c->fft32.tw = c->d_tw32;
+  c->fft64.pos = c->fft32.pos = c->d_pos;
+  QA_TRY(cudaMemcpyAsync(c->d_mR, c->mR.data(), c->nk * 4, cudaMemcpyHostToDevice, st));
+  QA_TRY(cudaMemcpyAsync(c->d_hR, c->hopR.data(), c->hopR.size() * 4, cudaMemcpyHostToDevice, st));
+  QA_TRY(upload_c<double>(c->d_hH, c->hopH, st));
+  QA_TRY(cudaMemcpyAsync(c->d_vR, c->vR.data(), c->vR.size() * 4, cudaMemcpyHostToDevice, st));
+  if (c->nV > 0) QA_TRY(upload_c<double>(c->d_vV, c->vV, st));
+  // H(k), V(q)
+  const int no2 = c->norb * c->norb, np2 = c->npair * c->npair;
+  QA_LAUNCH(c, 1, qa::launch_ft_table(c->d_hR, c->d_hH, c->nH, no2, nullptr, c->nk, c->n[0], c->n[1],
+                             c->n[2], c->d_Hk, st));
+  if (c->precision == QA_FP64) {
+    QA_LAUNCH(c, 1, qa::launch_ft_table(c->d_vR, c->d_vV, c->nV, np2, nullptr, c->nk, c->n[0], c->n[1],
+                               c->n[2], static_cast<double2*>(c->d_Vq), st));
+  } else {
+    QA_LAUNCH(c, 1, qa::launch_ft_table(c->d_vR, c->d_vV, c->nV, np2, nullptr, c->nk, c->n[0], c->n[1],
+                               c->n[2], static_cast<double2*>(c->d_P), st));
+    QA_LAUNCH(c, 1, qa::launch_c128_to_c64(static_cast<const double2*>(c->d_P),
+                                  static_cast<float2*>(c->d_Vq),
+                                  static_cast<long long>(c->nk) * np2, st));
+  }
+  // G0 at mu0 (always FP64)
+  if (int rc = reset_err(c, st)) return rc;
+  double mu0 = 0, N0 = 0;
+  int ev = 0;
+  int rc = mu_search<double>(c, nullptr, nullptr, c->t64, 0.0, &mu0, &N0, &ev, st);
+  if (rc != QA_OK) return rc;
+  rc = finish_g<double>(c, nullptr, nullptr, c->t64, mu0, c->d_G0, nullptr, st);
+  if (rc != QA_OK) return rc;
+  QA_TRY(cudaStreamSynchronize(st));
+  rc = check_err(c, nullptr, st);
+  if (rc != QA_OK) return rc;
+  c->mu0 = mu0;
+  c->have_mu = false;
+  c->bound = true;
+  return QA_OK;
+}
+
+int qa_get_grid(const qa_ctx* c, int* r, double* x, double* t_rel, int* nf, int* mb) {
+  if (!c) return QA_EINVAL;
+  if (r) *r = c->r;
+  for (int i = 0; i < c->r; ++i) {
+    if (x) x[i] = c->grid.x[i];
+    if (t_rel) t_rel[i] = c->grid.t[i];
+    if (nf) nf[i] = c->grid.nf[i];
+    if (mb) mb[i] = c->grid.mb[i];
+  }
+  return QA_OK;
+}
+
+int qa_get_plan(const qa_ctx* c, int* minus_R, int* fft_pos, int* fft_nfac, int* fft_fac) {
+  if (!c) return QA_EINVAL;
+  if (minus_R) std::memcpy(minus_R, c->mR.data(), c->mR.size() * 4);
+  int off = 0;
+  for (int d = 0; d < 3; ++d) {
+    if (fft_pos) std::memcpy(fft_pos + off, c->pos[d].data(), c->pos[d].size() * 4);
+    off += c->n[d];
+    if (fft_nfac) fft_nfac[d] = c->ax[d].nfac;
+    if (fft_fac)
+      for (int s = 0; s < qa::kMaxFac; ++s) fft_fac[d * qa::kMaxFac + s] = c->ax[d].fac[s];
+  }
+  return QA_OK;
+}
+
+int qa_get_sizes(const qa_ctx* c, int* nk, int* norb, int* r) {
+  if (!c) return QA_EINVAL;
+  if (nk) *nk = c->nk;
+  if (norb) *norb = c->norb;
+  if (r) *r = c->r;
+  return QA_OK;
+}
+
+int qa_set_timing(qa_ctx* c, int enable) {
+  if (!c) return QA_EINVAL;
+  c->timing = enable != 0;
+  return QA_OK;
+}
+
+int qa_gw_step(qa_ctx* c, const void* G_in, void* G_out, double* mu_out, double* n_out,
+               qa_step_stats* stats, void* stream) {
+  if (!c || !G_out) return QA_EINVAL;
+  if (!c->bound) return QA_ESTATE;
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (c->precision == QA_FP64) return gw_step_impl<double>(c, G_in, G_out, mu_out, n_out, stats, st);
+  return gw_step_impl<float>(c, G_in, G_out, mu_out, n_out, stats, st);
+}
+
+int qa_density(qa_ctx* c, const void* G, double* n_out, double* N_total, void* stream) {
+  if (!c || !G) return QA_EINVAL;
+  if (!c->bound) return QA_ESTATE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int no2 = c->norb * c->norb;
+  QA_LAUNCH(c, 1, qa::launch_dlr_apply<double>(c->t64.dtau, 1, c->r, G, c->d_nk,
+                                      static_cast<long long>(no2) * c->nk, st));
+  QA_LAUNCH(c, 1, qa::launch_k_average<double>(c->d_nk, no2, c->nk, c->d_nloc, st));
+  std::vector<double> h(2 * no2);
+  QA_TRY(cudaMemcpyAsync(h.data(), c->d_nloc, no2 * 16, cudaMemcpyDeviceToHost, st));
+  QA_TRY(cudaStreamSynchronize(st));
+  double tr = 0;
+  for (int a = 0; a < c->norb; ++a) tr += h[2 * (a * c->norb + a)];
+  if (n_out) std::memcpy(n_out, h.data(), h.size() * 8);
+  if (N_total) *N_total = c->nspin * tr;
+  return QA_OK;
+}
+
+int qa_get(const qa_ctx* c, int which, void* dst, size_t bytes, void* stream) {
+  if (!c || !dst) return QA_EINVAL;
+  if (!c->bound) return QA_ESTATE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t es = c->precision == QA_FP64 ? 16 : 8;
+  const size_t r = c->r, nk = c->nk, no2 = static_cast<size_t>(c->norb) * c->norb,
+               np2 = static_cast<size_t>(c->npair) * c->npair;
+  const void* src = nullptr;
+  size_t need = 0;
+  switch (which) {
+    case QA_P_QNU: src = c->d_P; need = r * np2 * nk * es; break;
+    case QA_WC_RTAU: src = c->d_W; need = r * np2 * nk * es; break;
+    case QA_SIGC_KTAU: src = c->d_SigC; need = r * no2 * nk * es; break;
+    case QA_SIGC_KIW: src = c->d_SigIw; need = r * no2 * nk * es; break;
+    case QA_SIGHF_K: src = c->d_SigHF; need = nk * no2 * 16; break;
+    case QA_G0: src = c->d_G0; need = r * no2 * nk * 16; break;
+    case QA_HK: src = c->d_Hk; need = nk * no2 * 16; break;
+    case QA_MU0:
+      if (bytes != 8) return QA_EINVAL;
+      std::memcpy(dst, &c->mu0, 8);
+      return QA_OK;
+    default: return QA_EINVAL;
+  }
+  if (bytes != need) return QA_EINVAL;
+  QA_TRY(cudaMemcpyAsync(dst, src, need, cudaMemcpyDefault, st));
+  QA_TRY(cudaStreamSynchronize(st));
+  return QA_OK;
+}
+
+void qa_destroy(qa_ctx* c) { delete c; }
+
+}  // extern "C"

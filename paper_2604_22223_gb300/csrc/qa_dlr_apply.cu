@@ -1,0 +1,78 @@
+// DLR node-to-node transforms (Kaye, Chen & Parcollet 2022, as used by the
+// paper's FLatDyn/BLatDyn "Fourier transforms between Matsubara frequency and
+// imaginary time"): out[j][c] = sum_l T[j][l] in[l][c] for every column c of
+// a node-major array (c runs over orbital pairs and lattice points).
+//
+// Each block stages TILE columns x r nodes in shared memory (one HBM read),
+// then every thread produces RB output rows of one column from registers.
+// The tile is fully loaded before any write, so in == out is allowed.
+#include "qa_common.cuh"
+
+namespace qa {
+namespace {
+
+template <typename T, int TILE, int RB>
+__global__ void __launch_bounds__(256) dlr_apply_kernel(const cplx<T>* __restrict__ Tm, int rows_out,
+                                                        int r, const cplx<T>* in, cplx<T>* out,
+                                                        long long ncol) {
+  using V = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* xs = reinterpret_cast<V*>(smem_raw);  // [r][TILE]
+  const long long c0 = static_cast<long long>(blockIdx.x) * TILE;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < r * TILE; i += blockDim.x) {
+    int l = i / TILE, c = i - l * TILE;
+    long long col = c0 + c;
+    xs[i] = col < ncol ? in[static_cast<long long>(l) * ncol + col] : cmk<V>(0, 0);
+  }
+  __syncthreads();
+  const int c = tid % TILE;
+  const int g = tid / TILE;
+  const int G = blockDim.x / TILE;
+  const long long col = c0 + c;
+  for (int j0 = g * RB; j0 < rows_out; j0 += G * RB) {
+    V acc[RB];
+#pragma unroll
+    for (int b = 0; b < RB; ++b) acc[b] = cmk<V>(0, 0);
+    for (int l = 0; l < r; ++l) {
+      V x = xs[l * TILE + c];
+#pragma unroll
+      for (int b = 0; b < RB; ++b) {
+        int j = j0 + b;
+        V t = j < rows_out ? __ldg(&Tm[static_cast<size_t>(j) * r + l]) : cmk<V>(0, 0);
+        acc[b] = cfma(t, x, acc[b]);
+      }
+    }
+    if (col < ncol) {
+#pragma unroll
+      for (int b = 0; b < RB; ++b)
+        if (j0 + b < rows_out) out[static_cast<long long>(j0 + b) * ncol + col] = acc[b];
+    }
+  }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_dlr_apply(const void* Tm, int rows_out, int r, const void* in, void* out,
+                             long long ncol, cudaStream_t st) {
+  if (ncol <= 0 || rows_out <= 0) return cudaSuccess;
+  constexpr int TILE = sizeof(T) == 8 ? 32 : 64;
+  constexpr int RB = 4;
+  size_t smem = static_cast<size_t>(r) * TILE * sizeof(cplx<T>);
+  auto fn = &dlr_apply_kernel<T, TILE, RB>;
+  cudaError_t e = set_smem(reinterpret_cast<const void*>(fn), smem);
+  if (e != cudaSuccess) return e;
+  long long nblk = (ncol + TILE - 1) / TILE;
+  fn<<<static_cast<unsigned>(nblk), 256, smem, st>>>(reinterpret_cast<const cplx<T>*>(Tm), rows_out,
+                                                     r, reinterpret_cast<const cplx<T>*>(in),
+                                                     reinterpret_cast<cplx<T>*>(out), ncol);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_dlr_apply<double>(const void*, int, int, const void*, void*, long long,
+                                              cudaStream_t);
+template cudaError_t launch_dlr_apply<float>(const void*, int, int, const void*, void*, long long,
+                                             cudaStream_t);
+
+}  // namespace qa

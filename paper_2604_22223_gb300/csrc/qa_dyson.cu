@@ -1,0 +1,369 @@
+// Batched Dyson solves.
+//
+// Screened interaction (paper Eq. for W): W = V + V P W per (q, i nu_m) in the
+// pair basis, so (1 - V P) W = V and W^C = W - V.  One warp owns one
+// npair x npair system: the matrices sit in shared memory, lane i owns row i
+// during the elimination, the pivot is chosen with warp shuffles (largest
+// |a_ic|, ties to the lowest row), and lane j owns column j of the
+// right-hand side during back substitution.  The FP32 variant solves for
+// W^C directly with the right-hand side V P V, which avoids the cancellation
+// of W - V when the screening is weak.
+//
+// Green's function (paper Eq. for the full Green's function):
+// G(k, i w_n) = (i w_n + mu - H(k) - Sigma^HF(k) - Sigma^C(k, i w_n))^-1 per
+// (n, k), one thread per system, Gauss-Jordan with partial pivoting in
+// registers.  The density N(mu) = (s/N_k) sum_{k,n} Re(dw_n Tr G) and its
+// derivative -(s/N_k) sum Re(dw_n Tr G^2) are accumulated in FP64.
+#include "qa_common.cuh"
+
+namespace qa {
+namespace {
+
+constexpr int kMaxPair = 25;
+constexpr int kWarpsW = 4;
+
+template <typename T> struct Tiny;
+template <> struct Tiny<double> { static constexpr double v = 1e-26; };   // |pivot|^2
+template <> struct Tiny<float> { static constexpr float v = 1e-12f; };
+
+__device__ void report(int* err, long long* first_bad, int code, long long idx) {
+  atomicCAS(err, 0, code);
+  if (first_bad) atomicMin(reinterpret_cast<unsigned long long*>(first_bad),
+                           static_cast<unsigned long long>(idx));
+}
+
+template <typename T, bool VPV>
+__global__ void __launch_bounds__(kWarpsW * 32) dyson_w_kernel(const cplx<T>* __restrict__ P,
+                                                               const cplx<T>* __restrict__ Vq,
+                                                               cplx<T>* WC, int n, int nk,
+                                                               int* err, long long* first_bad) {
+  using V = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int q = blockIdx.x * kWarpsW + w;
+  const int nu = blockIdx.y;
+  if (q >= nk) return;                  // whole warp leaves; no block barriers below
+  const int ld = n + 1;
+  V* A = reinterpret_cast<V*>(smem_raw) + static_cast<size_t>(w) * 2 * n * ld;
+  V* Bm = A + n * ld;
+  const size_t nn = static_cast<size_t>(n) * n;
+  const V* Pq = P + static_cast<size_t>(nu) * nn * nk + q;
+  const V* Vqq = Vq + static_cast<size_t>(q) * nn;
+  for (int e = lane; e < n * n; e += 32) {
+    int i = e / n, j = e - i * n;
+    A[i * ld + j] = Pq[static_cast<size_t>(e) * nk];
+    Bm[i * ld + j] = Vqq[e];
+  }
+  __syncwarp();
+  // row `lane` of V P (and of V P V)
+  V vp[kMaxPair];
+  V rhs[VPV ? kMaxPair : 1];
+  if (lane < n) {
+#pragma unroll
+    for (int j = 0; j < kMaxPair; ++j) {
+      if (j < n) {
+        V acc = cmk<V>(0, 0);
+        for (int m = 0; m < n; ++m) acc = cfma(Bm[lane * ld + m], A[m * ld + j], acc);
+        vp[j] = acc;
+      }
+    }
+    if (VPV) {
+#pragma unroll
+      for (int j = 0; j < kMaxPair; ++j) {
+        if (j < n) {
+          V acc = cmk<V>(0, 0);
+#pragma unroll
+          for (int m = 0; m < kMaxPair; ++m)
+            if (m < n) acc = cfma(vp[m], Bm[m * ld + j], acc);
+          rhs[VPV ? j : 0] = acc;
+        }
+      }
+    }
+  }
+  __syncwarp();
+  if (lane < n) {
+#pragma unroll
+    for (int j = 0; j < kMaxPair; ++j) {
+      if (j < n) {
+        V a = cmk<V>(j == lane ? 1.0 : 0.0, 0.0);
+        A[lane * ld + j] = csub(a, vp[j]);
+        if (VPV) Bm[lane * ld + j] = rhs[VPV ? j : 0];
+      }
+    }
+  }
+  __syncwarp();
+  bool singular = false;
+  for (int c = 0; c < n; ++c) {
+    T val = (lane >= c && lane < n) ? cabs2(A[lane * ld + c]) : static_cast<T>(-1);
+    int idx = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      T ov = __shfl_xor_sync(0xffffffffu, val, o);
+      int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+      if (ov > val || (ov == val && oi < idx)) { val = ov; idx = oi; }
+    }
+    const int p = idx;
+    if (val < Tiny<T>::v || !(val == val)) singular = true;
+    if (p != c && lane < n) {
+      if (lane >= c) {
+        V tmp = A[c * ld + lane]; A[c * ld + lane] = A[p * ld + lane]; A[p * ld + lane] = tmp;
+      }
+      V tmp = Bm[c * ld + lane]; Bm[c * ld + lane] = Bm[p * ld + lane]; Bm[p * ld + lane] = tmp;
+    }
+    __syncwarp();
+    if (lane > c && lane < n) {
+      V l = cmul(A[lane * ld + c], cinv(A[c * ld + c]));
+      for (int j = c + 1; j < n; ++j) A[lane * ld + j] = cfms(l, A[c * ld + j], A[lane * ld + j]);
+      for (int j = 0; j < n; ++j) Bm[lane * ld + j] = cfms(l, Bm[c * ld + j], Bm[lane * ld + j]);
+    }
+    __syncwarp();
+  }
+  if (lane < n) {
+    for (int c = n - 1; c >= 0; --c) {
+      V x = Bm[c * ld + lane];
+      for (int m = c + 1; m < n; ++m) x = cfms(A[c * ld + m], Bm[m * ld + lane], x);
+      Bm[c * ld + lane] = cmul(x, cinv(A[c * ld + c]));
+    }
+  }
+  __syncwarp();
+  V* out = WC + static_cast<size_t>(nu) * nn * nk + q;
+  for (int e = lane; e < n * n; e += 32) {
+    int i = e / n, j = e - i * n;
+    V x = Bm[i * ld + j];
+    if (!VPV) x = csub(x, Vqq[e]);
+    out[static_cast<size_t>(e) * nk] = x;
+  }
+  if (singular && lane == 0) report(err, first_bad, QA_ESINGULAR_CODE, static_cast<long long>(nu) * nk + q);
+}
+
+// ------------------------------------------------------------------ Dyson G
+
+template <typename T, int NO>
+__global__ void __launch_bounds__(256) dyson_g_kernel(const double2* __restrict__ Hk,
+                                                      const double2* __restrict__ SigHF,
+                                                      const cplx<T>* __restrict__ SigIw,
+                                                      const cplx<T>* __restrict__ dw,
+                                                      const double* __restrict__ iw, double mu,
+                                                      int r, int nk, cplx<T>* Giw, double* part,
+                                                      int mode, int* err) {
+  using V = cplx<T>;
+  __shared__ double sh[64];
+  const long long total = static_cast<long long>(r) * nk;
+  double s1 = 0.0, s2 = 0.0;
+  bool bad = false;
+  for (long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
+       idx += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int n = static_cast<int>(idx / nk);
+    const int k = static_cast<int>(idx - static_cast<long long>(n) * nk);
+    V a[NO][NO], b[NO][NO];
+#pragma unroll
+    for (int i = 0; i < NO; ++i)
+#pragma unroll
+      for (int j = 0; j < NO; ++j) {
+        double2 h = Hk[static_cast<size_t>(k) * NO * NO + i * NO + j];
+        if (SigHF) {
+          double2 s = SigHF[static_cast<size_t>(k) * NO * NO + i * NO + j];
+          h.x += s.x; h.y += s.y;
+        }
+        V m = from_d2<V>(make_double2(-h.x, -h.y));
+        if (SigIw) m = csub(m, SigIw[(static_cast<size_t>(n) * NO * NO + i * NO + j) * nk + k]);
+        if (i == j) { m.x += static_cast<T>(mu); m.y += static_cast<T>(iw[n]); }
+        a[i][j] = m;
+        b[i][j] = cmk<V>(i == j ? 1.0 : 0.0, 0.0);
+      }
+    // Gauss-Jordan with partial pivoting; all indices compile-time
+#pragma unroll
+    for (int c = 0; c < NO; ++c) {
+      int p = c;
+      T best = cabs2(a[c][c]);
+#pragma unroll
+      for (int i = c + 1; i < NO; ++i) {
+        T v = cabs2(a[i][c]);
+        if (v > best) { best = v; p = i; }
+      }
+      if (!(best > static_cast<T>(0))) bad = true;
+#pragma unroll
+      for (int i = c + 1; i < NO; ++i) {
+        if (i == p) {
+#pragma unroll
+          for (int j = 0; j < NO; ++j) {
+            V t1 = a[c][j]; a[c][j] = a[i][j]; a[i][j] = t1;
+            V t2 = b[c][j]; b[c][j] = b[i][j]; b[i][j] = t2;
+          }
+        }
+      }
+      V inv = cinv(a[c][c]);
+#pragma unroll
+      for (int j = 0; j < NO; ++j) { a[c][j] = cmul(a[c][j], inv); b[c][j] = cmul(b[c][j], inv); }
+#pragma unroll
+      for (int i = 0; i < NO; ++i) {
+        if (i == c) continue;
+        V f = a[i][c];
+#pragma unroll
+        for (int j = 0; j < NO; ++j) {
+          a[i][j] = cfms(f, a[c][j], a[i][j]);
+          b[i][j] = cfms(f, b[c][j], b[i][j]);
+        }
+      }
+    }
+    // b = G(k, i w_n)
+    double2 tr = make_double2(0, 0), tr2 = make_double2(0, 0);
+#pragma unroll
+    for (int i = 0; i < NO; ++i) {
+      double2 d = to_c64d(b[i][i]);
+      tr.x += d.x; tr.y += d.y;
+#pragma unroll
+      for (int j = 0; j < NO; ++j) {
+        double2 x = to_c64d(b[i][j]), y = to_c64d(b[j][i]);
+        tr2.x += x.x * y.x - x.y * y.y;
+        tr2.y += x.x * y.y + x.y * y.x;
+      }
+    }
+    double2 wn = to_c64d(dw[n]);
+    s1 += wn.x * tr.x - wn.y * tr.y;
+    s2 += wn.x * tr2.x - wn.y * tr2.y;
+    if (mode == 1) {
+#pragma unroll
+      for (int i = 0; i < NO; ++i)
+#pragma unroll
+        for (int j = 0; j < NO; ++j) Giw[(static_cast<size_t>(n) * NO * NO + i * NO + j) * nk + k] = b[i][j];
+    }
+  }
+  if (bad) atomicCAS(err, 0, QA_ESINGULAR_CODE);
+  block_sum2(s1, s2, sh);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = s1;
+    part[2 * blockIdx.x + 1] = s2;
+  }
+}
+
+template <typename T, int NO>
+__global__ void __launch_bounds__(256) norm_bound_kernel(const double2* __restrict__ Hk,
+                                                         const double2* __restrict__ SigHF,
+                                                         const cplx<T>* __restrict__ SigIw, int r,
+                                                         int nk, double* part) {
+  __shared__ double sh[32];
+  const long long total = static_cast<long long>(r) * nk;
+  double best = 0.0;
+  for (long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
+       idx += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int n = static_cast<int>(idx / nk);
+    const int k = static_cast<int>(idx - static_cast<long long>(n) * nk);
+#pragma unroll
+    for (int i = 0; i < NO; ++i) {
+      double rs = 0.0;
+#pragma unroll
+      for (int j = 0; j < NO; ++j) {
+        double2 h = Hk[static_cast<size_t>(k) * NO * NO + i * NO + j];
+        if (SigHF) {
+          double2 s = SigHF[static_cast<size_t>(k) * NO * NO + i * NO + j];
+          h.x += s.x; h.y += s.y;
+        }
+        if (SigIw) {
+          double2 s = to_c64d(SigIw[(static_cast<size_t>(n) * NO * NO + i * NO + j) * nk + k]);
+          h.x += s.x; h.y += s.y;
+        }
+        rs += sqrt(h.x * h.x + h.y * h.y);
+      }
+      best = fmax(best, rs);
+    }
+  }
+  best = block_max(best, sh);
+  if (threadIdx.x == 0) { part[2 * blockIdx.x] = best; part[2 * blockIdx.x + 1] = 0.0; }
+}
+
+__global__ void reduce_pairs_kernel(const double* part, int n, int op_max, double* out) {
+  __shared__ double sh[64];
+  double a = op_max ? 0.0 : 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    if (op_max) { a = fmax(a, part[2 * i]); b = fmax(b, part[2 * i + 1]); }
+    else { a += part[2 * i]; b += part[2 * i + 1]; }
+  }
+  if (op_max) {
+    a = block_max(a, sh);
+    __syncthreads();
+    b = block_max(b, sh);
+  } else {
+    block_sum2(a, b, sh);
+  }
+  if (threadIdx.x == 0) { out[0] = a; out[1] = b; }
+}
+
+}  // namespace
+
+int dyson_g_blocks(int r, int nk) {
+  long long total = static_cast<long long>(r) * nk;
+  long long b = (total + 255) / 256;
+  return static_cast<int>(b < 1216 ? (b < 1 ? 1 : b) : 1216);   // 8 per SM on 152 SMs
+}
+
+template <typename T>
+cudaError_t launch_dyson_w(const void* P, const void* Vq, void* WC, int r, int npair, int nk,
+                           int* err, long long* first_bad, cudaStream_t st) {
+  if (npair > kMaxPair) return cudaErrorInvalidValue;
+  constexpr bool vpv = sizeof(T) == 4;
+  size_t smem = static_cast<size_t>(kWarpsW) * 2 * npair * (npair + 1) * sizeof(cplx<T>);
+  auto fn = &dyson_w_kernel<T, vpv>;
+  cudaError_t e = set_smem(reinterpret_cast<const void*>(fn), smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((nk + kWarpsW - 1) / kWarpsW, r);
+  fn<<<grid, kWarpsW * 32, smem, st>>>(reinterpret_cast<const cplx<T>*>(P),
+                                       reinterpret_cast<const cplx<T>*>(Vq),
+                                       reinterpret_cast<cplx<T>*>(WC), npair, nk, err, first_bad);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_dyson_g(const double2* Hk, const double2* SigHF, const void* SigIw,
+                           const void* dw, const double* iw, double mu, int r, int norb, int nk,
+                           void* Giw, double* part, int nblocks, int mode, int* err,
+                           cudaStream_t st) {
+  auto s = reinterpret_cast<const cplx<T>*>(SigIw);
+  auto d = reinterpret_cast<const cplx<T>*>(dw);
+  auto g = reinterpret_cast<cplx<T>*>(Giw);
+  switch (norb) {
+#define QA_CASE(NO) \
+    case NO: dyson_g_kernel<T, NO><<<nblocks, 256, 0, st>>>(Hk, SigHF, s, d, iw, mu, r, nk, g, part, mode, err); break;
+    QA_CASE(1) QA_CASE(2) QA_CASE(3) QA_CASE(4) QA_CASE(5)
+#undef QA_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_norm_bound(const double2* Hk, const double2* SigHF, const void* SigIw, int r,
+                              int norb, int nk, double* part, int nblocks, cudaStream_t st) {
+  auto s = reinterpret_cast<const cplx<T>*>(SigIw);
+  switch (norb) {
+#define QA_CASE(NO) \
+    case NO: norm_bound_kernel<T, NO><<<nblocks, 256, 0, st>>>(Hk, SigHF, s, r, nk, part); break;
+    QA_CASE(1) QA_CASE(2) QA_CASE(3) QA_CASE(4) QA_CASE(5)
+#undef QA_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_pairs(const double* part, int n, int op_max, double* out,
+                                cudaStream_t st) {
+  reduce_pairs_kernel<<<1, 256, 0, st>>>(part, n, op_max, out);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_dyson_w<double>(const void*, const void*, void*, int, int, int, int*,
+                                            long long*, cudaStream_t);
+template cudaError_t launch_dyson_w<float>(const void*, const void*, void*, int, int, int, int*,
+                                           long long*, cudaStream_t);
+template cudaError_t launch_dyson_g<double>(const double2*, const double2*, const void*,
+                                            const void*, const double*, double, int, int, int,
+                                            void*, double*, int, int, int*, cudaStream_t);
+template cudaError_t launch_dyson_g<float>(const double2*, const double2*, const void*, const void*,
+                                           const double*, double, int, int, int, void*, double*,
+                                           int, int, int*, cudaStream_t);
+template cudaError_t launch_norm_bound<double>(const double2*, const double2*, const void*, int,
+                                               int, int, double*, int, cudaStream_t);
+template cudaError_t launch_norm_bound<float>(const double2*, const double2*, const void*, int, int,
+                                              int, double*, int, cudaStream_t);
+
+}  // namespace qa

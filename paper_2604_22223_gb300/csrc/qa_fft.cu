@@ -1,0 +1,140 @@
+// Batched 3-D lattice FFT in shared memory (paper Eq. for the k <-> R
+// transform; "implemented using fast Fourier transform algorithms").
+//
+// One block owns `lpb` whole lines of N_k = N1*N2*N3 points (k fastest,
+// C order over (i1, i2, i3)).  The line is staged in shared memory once,
+// transformed axis by axis with in-place mixed-radix decimation-in-frequency
+// stages (radices 4, 2, 3, 5, 7, ... from the host plan), and written back
+// through the plan's digit-reversal tables, so each line costs one HBM read
+// and one HBM write.
+#include "qa_common.cuh"
+
+namespace qa {
+namespace {
+
+constexpr int kMaxRadix = 13;
+
+template <typename V>
+__device__ __forceinline__ V tw_get(const V* tw, int idx, int sign) {
+  V w = tw[idx];
+  if (sign > 0) w.y = -w.y;
+  return w;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) fft3d_kernel(FftDev p, int sign, const cplx<T>* in,
+                                                    cplx<T>* out, int nk, int lpb, long long nlines) {
+  using V = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* buf = reinterpret_cast<V*>(smem_raw);
+  V* tws = buf + static_cast<size_t>(lpb) * nk;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  const long long line0 = static_cast<long long>(blockIdx.x) * lpb;
+  const int nl = static_cast<int>(min(static_cast<long long>(lpb), nlines - line0));
+  const int ntw = p.n[0] + p.n[1] + p.n[2];
+  const V* twg = reinterpret_cast<const V*>(p.tw);
+  for (int i = tid; i < ntw; i += bd) tws[i] = twg[i];
+  const V* src = in + line0 * nk;
+  for (int i = tid; i < nl * nk; i += bd) buf[i] = src[i];
+  __syncthreads();
+
+  const int stride[3] = {p.n[1] * p.n[2], p.n[2], 1};
+  for (int d = 0; d < 3; ++d) {
+    const int L = p.n[d];
+    if (L == 1) continue;
+    const int S = stride[d];
+    const V* tw = tws + p.tw_off[d];
+    int Ls = L;
+    for (int s = 0; s < p.nfac[d]; ++s) {
+      const int rad = p.fac[d][s];
+      const int Lp = Ls / rad;
+      const int per_line = nk / rad;
+      const int nbf = nl * per_line;
+      const int nblk = L / Ls;
+      const int tstep = L / Ls;        // twiddle stride for w_Ls
+      const int pstep = L / rad;       // twiddle stride for w_rad
+      for (int b = tid; b < nbf; b += bd) {
+        int line = b / per_line;
+        int rem = b - line * per_line;
+        int o_lo = rem % S; rem /= S;
+        int jp = rem % Lp; rem /= Lp;
+        int blk = rem % nblk;
+        int o_hi = rem / nblk;
+        V* base = buf + static_cast<size_t>(line) * nk + static_cast<size_t>(o_hi) * L * S +
+                  static_cast<size_t>(blk * Ls + jp) * S + o_lo;
+        const int es = Lp * S;
+        if (rad == 2) {
+          V x0 = base[0], x1 = base[es];
+          V y0 = cadd(x0, x1), y1 = csub(x0, x1);
+          base[0] = y0;
+          base[es] = cmul(y1, tw_get(tw, (jp * tstep) % L, sign));
+        } else if (rad == 4) {
+          V x0 = base[0], x1 = base[es], x2 = base[2 * es], x3 = base[3 * es];
+          V a0 = cadd(x0, x2), a1 = csub(x0, x2), b0 = cadd(x1, x3), b1 = csub(x1, x3);
+          // -i*b1 for the forward sign, +i*b1 for the inverse
+          V jb1 = sign < 0 ? cmk<V>(b1.y, -b1.x) : cmk<V>(-b1.y, b1.x);
+          V y0 = cadd(a0, b0), y1 = cadd(a1, jb1), y2 = csub(a0, b0), y3 = csub(a1, jb1);
+          base[0] = y0;
+          base[es] = cmul(y1, tw_get(tw, (jp * tstep) % L, sign));
+          base[2 * es] = cmul(y2, tw_get(tw, (2 * jp * tstep) % L, sign));
+          base[3 * es] = cmul(y3, tw_get(tw, (3 * jp * tstep) % L, sign));
+        } else {
+          V x[kMaxRadix];
+#pragma unroll
+          for (int j = 0; j < kMaxRadix; ++j)
+            if (j < rad) x[j] = base[j * es];
+          for (int k1 = 0; k1 < rad; ++k1) {
+            V acc = x[0];
+            for (int j1 = 1; j1 < rad; ++j1)
+              acc = cfma(x[j1], tw_get(tw, ((j1 * k1) % rad) * pstep, sign), acc);
+            base[k1 * es] = k1 == 0 ? acc : cmul(acc, tw_get(tw, (jp * k1 * tstep) % L, sign));
+          }
+        }
+      }
+      __syncthreads();
+      Ls = Lp;
+    }
+  }
+  const int* pos0 = p.pos + p.pos_off[0];
+  const int* pos1 = p.pos + p.pos_off[1];
+  const int* pos2 = p.pos + p.pos_off[2];
+  const T scale = sign > 0 ? static_cast<T>(1.0 / nk) : static_cast<T>(1);
+  V* dst = out + line0 * nk;
+  for (int i = tid; i < nl * nk; i += bd) {
+    int line = i / nk, k = i - line * nk;
+    int k3 = k % p.n[2], k2 = (k / p.n[2]) % p.n[1], k1 = k / (p.n[2] * p.n[1]);
+    int s_idx = (pos0[k1] * p.n[1] + pos1[k2]) * p.n[2] + pos2[k3];
+    V v = buf[static_cast<size_t>(line) * nk + s_idx];
+    v.x *= scale;
+    v.y *= scale;
+    dst[i] = v;
+  }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_fft3d(const FftDev& plan, int sign, const void* in, void* out, long long nlines,
+                         cudaStream_t st) {
+  if (nlines <= 0) return cudaSuccess;
+  const int nk = plan.n[0] * plan.n[1] * plan.n[2];
+  // lines per block: keep the tile near 16 KB for small grids
+  int lpb = 1;
+  while (lpb * 2 * nk * static_cast<int>(sizeof(cplx<T>)) <= 16384 && lpb * 2 <= 64) lpb *= 2;
+  size_t smem = (static_cast<size_t>(lpb) * nk + plan.n[0] + plan.n[1] + plan.n[2]) * sizeof(cplx<T>);
+  cudaError_t e = set_smem(reinterpret_cast<const void*>(&fft3d_kernel<T>), smem);
+  if (e != cudaSuccess) return e;
+  long long nblk = (nlines + lpb - 1) / lpb;
+  int threads = nk * lpb >= 2048 ? 512 : 256;
+  fft3d_kernel<T><<<static_cast<unsigned>(nblk), threads, smem, st>>>(
+      plan, sign, reinterpret_cast<const cplx<T>*>(in), reinterpret_cast<cplx<T>*>(out), nk, lpb,
+      nlines);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_fft3d<double>(const FftDev&, int, const void*, void*, long long,
+                                          cudaStream_t);
+template cudaError_t launch_fft3d<float>(const FftDev&, int, const void*, void*, long long,
+                                         cudaStream_t);
+
+}  // namespace qa

@@ -1,0 +1,139 @@
+// Internal declarations shared by the host planner (qa_api.cpp, qa_dlr.cpp)
+// and the CUDA kernels (qa_*.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <complex>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+namespace qa {
+
+// Device-side copy of the public status code for a singular pivot.
+constexpr int QA_ESINGULAR_CODE = 3;
+
+// ------------------------------------------------------------------- DLR
+// Discrete Lehmann representation (Kaye, Chen & Parcollet, PRB 105, 235115
+// (2022)); dimensionless real poles x_l = beta*omega_l, imaginary-time nodes
+// t_j = tau_j/beta in relative format (t > 1/2 stored as t - 1), fermionic
+// and bosonic Matsubara integers.
+struct DlrGrid {
+  int r = 0;
+  std::vector<double> x, t;
+  std::vector<int> nf, mb;
+};
+int build_dlr(double Lambda, double eps, DlrGrid* out);
+
+// Transform matrices composed in extended precision on the host, physical
+// units, row-major [rows][r], complex interleaved as std::complex<double>.
+struct DlrMatrices {
+  std::vector<std::complex<double>> Trefl;  // G(k, beta - tau_j) from G(k, tau)
+  std::vector<std::complex<double>> Ttn;    // tau -> i nu (bosonic)
+  std::vector<std::complex<double>> Tnt;    // i nu -> tau
+  std::vector<std::complex<double>> Ttw;    // tau -> i w (fermionic)
+  std::vector<std::complex<double>> Twt;    // i w -> tau
+  std::vector<std::complex<double>> dtau;   // n = sum_j dtau_j G(tau_j)
+  std::vector<std::complex<double>> dw;     // n = sum_n dw_n G(i w_n)
+  std::vector<double> iw;                   // w_n values (imaginary parts)
+};
+void build_dlr_matrices(const DlrGrid& g, double beta, DlrMatrices* m);
+
+// ------------------------------------------------------------------- FFT
+// Mixed-radix decimation-in-frequency plan for one axis of length L: the
+// radices in stage order, and pos[f] = position of frequency f after the
+// in-place stages (a mixed-radix digit reversal).
+struct FftAxisPlan {
+  int L = 1;
+  int nfac = 0;
+  int fac[16] = {0};
+};
+void plan_fft_axis(int L, FftAxisPlan* p, std::vector<int>* pos);
+
+constexpr int kMaxFac = 16;
+
+struct FftDev {            // passed by value to the FFT kernel
+  int n[3];
+  int nfac[3];
+  int fac[3][kMaxFac];
+  int tw_off[3];           // offset of each axis' twiddle table in tw[]
+  int pos_off[3];          // offset of each axis' position table in pos[]
+  const void* tw;          // complex (precision of the kernel) exp(-2 pi i m / L)
+  const int* pos;
+};
+
+// ------------------------------------------------------------- kernels
+// All launchers enqueue on `st` and return cudaGetLastError().
+// Complex arrays are double2 (FP64) or float2 (FP32).
+
+// out[j][c] = sum_l T[j][l] in[l][c], j < rows_out, l < r, c < ncol.
+// in and out may alias (each block stages its columns before writing).
+template <typename T>
+cudaError_t launch_dlr_apply(const void* Tm, int rows_out, int r, const void* in, void* out,
+                             long long ncol, cudaStream_t st);
+
+// Batched 3-D FFT of contiguous lines of N_k points (in place allowed).
+// sign = -1: X(k) = sum_R e^{-ikR} X(R); sign = +1: (1/N_k) sum_k e^{+ikR} X(k).
+template <typename T>
+cudaError_t launch_fft3d(const FftDev& plan, int sign, const void* in, void* out, long long nlines,
+                         cudaStream_t st);
+
+// P[t][(ab)][(cd)][R] = -s G[t][b][c][R] Grefl[t][d][a][mR[R]]
+template <typename T>
+cudaError_t launch_bubble(const void* GR, const void* GreflR, const int* mR, void* P, int r,
+                          int norb, int nk, double s, cudaStream_t st);
+
+// W^C(q, i nu) from P(q, i nu) and V(q): per (nu, q) system of size npair.
+template <typename T>
+cudaError_t launch_dyson_w(const void* P, const void* Vq, void* WC, int r, int npair, int nk,
+                           int* err, long long* first_bad, cudaStream_t st);
+
+// Sigma^C[t][a][d][R] = -sum_bc G[t][b][c][R] W^C[t][(ab)][(cd)][R]
+template <typename T>
+cudaError_t launch_sigma(const void* GR, const void* WC, void* Sig, int r, int norb, int nk,
+                         cudaStream_t st);
+
+// Dyson for G at chemical potential mu.  mode 0: accumulate per-block
+// partial sums of Re(dw_n Tr G) and Re(dw_n Tr G^2) into part[2*blocks];
+// mode 1: also store G(k, i w_n) in Giw [r][norb][norb][N_k].
+// SigHF (FP64, [N_k][norb][norb]) and SigIw may be null.
+template <typename T>
+cudaError_t launch_dyson_g(const double2* Hk, const double2* SigHF, const void* SigIw,
+                           const void* dw, const double* iw, double mu, int r, int norb, int nk,
+                           void* Giw, double* part, int nblocks, int mode, int* err,
+                           cudaStream_t st);
+int dyson_g_blocks(int r, int nk);
+
+// max over (k, n) of the row-sum norm of H(k) + SigHF(k) + SigIw(k, i w_n)
+template <typename T>
+cudaError_t launch_norm_bound(const double2* Hk, const double2* SigHF, const void* SigIw, int r,
+                              int norb, int nk, double* part, int nblocks, cudaStream_t st);
+
+// Deterministic final reduction of `n` partial pairs (sum or max).
+cudaError_t launch_reduce_pairs(const double* part, int n, int op_max, double* out,
+                                cudaStream_t st);
+
+// H(k) and V(q) tables from their R lists (FP64).
+cudaError_t launch_ft_table(const int* R, const double2* XR, int nR, int msize, const int* kpts,
+                            int nk, int n1, int n2, int n3, double2* out, cudaStream_t st);
+
+// n(R_v) = (1/N_k) sum_k e^{+i k.R_v} n(k) for the interaction's R list,
+// n(k) given as [norb^2][N_k] FP64.
+cudaError_t launch_density_R(const double2* nk_, const int* R, int nRv, int norb2, const int* kpts,
+                             int nk, int n1, int n2, int n3, double2* nR_out, cudaStream_t st);
+
+// Sigma^H and Sigma^F(R_v) (one block), then Sigma^HF(k) per k.
+cudaError_t launch_hf(const double2* VR, const double2* nR_in, const int* R, int nRv, int norb,
+                      double s, const int* kpts, int nk, int n1, int n2, int n3, double2* sigF_R,
+                      double2* SigHF, cudaStream_t st);
+
+// Local average over k: out[e] = (1/N_k) sum_k x[e][k], e < m (FP64 out).
+template <typename T>
+cudaError_t launch_k_average(const void* x, int m, int nk, double2* out, cudaStream_t st);
+
+// Precision conversions.
+cudaError_t launch_c128_to_c64(const double2* in, float2* out, long long n, cudaStream_t st);
+cudaError_t launch_c64_to_c128(const float2* in, double2* out, long long n, cudaStream_t st);
+
+}  // namespace qa

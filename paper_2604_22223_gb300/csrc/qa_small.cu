@@ -1,0 +1,165 @@
+// Small FP64 kernels: lattice Fourier tables, Hartree and Fock terms,
+// k-averages and precision conversions.
+//
+// H(k) = sum_R H(R) e^{-i k.R} and V(q) = sum_R V(R) e^{-i q.R} (paper Eq. for
+// the k<->R transform, cell gauge).  Hartree (paper Eq. for Sigma^H):
+// Sigma^H_{ab} = s sum_{cd} V_{(ab),(cd)}(q=0) n_{dc}(R=0).  Fock (paper Eq. for
+// Sigma^F): Sigma^F_{ad}(R) = -sum_{bc} V_{(ab),(cd)}(R) n_{bc}(R), summed back
+// to k with e^{-i k.R}; n(R) = (1/N_k) sum_k e^{+i k.R} n(k).
+#include "qa_common.cuh"
+
+namespace qa {
+namespace {
+
+__global__ void ft_table_kernel(const int* __restrict__ R, const double2* __restrict__ XR, int nR,
+                                int msize, int nk, int n1, int n2, int n3, double2* out) {
+  const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= static_cast<long long>(nk) * msize) return;
+  const int k = static_cast<int>(idx / msize);
+  const int e = static_cast<int>(idx - static_cast<long long>(k) * msize);
+  double2 acc = make_double2(0, 0);
+  for (int v = 0; v < nR; ++v) {
+    double2 ph = lattice_phase(k, n1, n2, n3, R + 3 * v, -1);
+    acc = cfma(XR[static_cast<size_t>(v) * msize + e], ph, acc);
+  }
+  out[idx] = acc;
+}
+
+// block per (v, e)
+__global__ void density_R_kernel(const double2* __restrict__ nk_, const int* __restrict__ R,
+                                 int norb2, int nk, int n1, int n2, int n3, double2* nR) {
+  __shared__ double sh[64];
+  const int v = blockIdx.x / norb2, e = blockIdx.x % norb2;
+  double re = 0.0, im = 0.0;
+  for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+    double2 ph = lattice_phase(k, n1, n2, n3, R + 3 * v, +1);
+    double2 x = nk_[static_cast<size_t>(e) * nk + k];
+    re += x.x * ph.x - x.y * ph.y;
+    im += x.x * ph.y + x.y * ph.x;
+  }
+  block_sum2(re, im, sh);
+  if (threadIdx.x == 0) nR[blockIdx.x] = make_double2(re / nk, im / nk);
+}
+
+// one block: Sigma^F(R_v) for every v and Sigma^H (stored after them).
+// nR_in holds n(R_v) for v < nRv and n(R=0) at v = nRv.
+__global__ void hf_real_kernel(const double2* __restrict__ VR, const double2* __restrict__ nR,
+                               int nRv, int no, double s, double2* sigF_R) {
+  const int np = no * no;
+  const double2* n0 = nR + static_cast<size_t>(nRv) * np;
+  for (int o = threadIdx.x; o < (nRv + 1) * np; o += blockDim.x) {
+    const int v = o / np, e = o % np;
+    const int a = e / no, d = e % no;
+    double2 acc = make_double2(0, 0);
+    if (v < nRv) {
+      const double2* Vv = VR + static_cast<size_t>(v) * np * np;
+      const double2* nv = nR + static_cast<size_t>(v) * np;
+      for (int b = 0; b < no; ++b)
+        for (int c = 0; c < no; ++c)
+          acc = cfms(Vv[(a * no + b) * np + c * no + d], nv[b * no + c], acc);
+    } else {
+      // Hartree: (a, d) here play (a, b) of Sigma^H_ab
+      for (int w = 0; w < nRv; ++w) {
+        const double2* Vw = VR + static_cast<size_t>(w) * np * np;
+        for (int c = 0; c < no; ++c)
+          for (int dd = 0; dd < no; ++dd)
+            acc = cfma(Vw[(a * no + d) * np + c * no + dd], n0[dd * no + c], acc);
+      }
+      acc.x *= s;
+      acc.y *= s;
+    }
+    sigF_R[o] = acc;
+  }
+}
+
+__global__ void hf_k_kernel(const double2* __restrict__ sigF_R, const int* __restrict__ R, int nRv,
+                            int no, int nk, int n1, int n2, int n3, double2* SigHF) {
+  const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int np = no * no;
+  if (idx >= static_cast<long long>(nk) * np) return;
+  const int k = static_cast<int>(idx / np), e = static_cast<int>(idx % np);
+  double2 acc = sigF_R[static_cast<size_t>(nRv) * np + e];   // Sigma^H
+  for (int v = 0; v < nRv; ++v) {
+    double2 ph = lattice_phase(k, n1, n2, n3, R + 3 * v, -1);
+    acc = cfma(sigF_R[static_cast<size_t>(v) * np + e], ph, acc);
+  }
+  SigHF[idx] = acc;
+}
+
+template <typename T>
+__global__ void k_average_kernel(const cplx<T>* __restrict__ x, int nk, double2* out) {
+  __shared__ double sh[64];
+  const int e = blockIdx.x;
+  double re = 0.0, im = 0.0;
+  for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+    double2 v = to_c64d(x[static_cast<size_t>(e) * nk + k]);
+    re += v.x;
+    im += v.y;
+  }
+  block_sum2(re, im, sh);
+  if (threadIdx.x == 0) out[e] = make_double2(re / nk, im / nk);
+}
+
+__global__ void c128_to_c64_kernel(const double2* in, float2* out, long long n) {
+  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    out[i] = make_float2(static_cast<float>(in[i].x), static_cast<float>(in[i].y));
+}
+
+__global__ void c64_to_c128_kernel(const float2* in, double2* out, long long n) {
+  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    out[i] = make_double2(in[i].x, in[i].y);
+}
+
+unsigned grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  return static_cast<unsigned>(b > 4864 ? 4864 : (b < 1 ? 1 : b));
+}
+
+}  // namespace
+
+cudaError_t launch_ft_table(const int* R, const double2* XR, int nR, int msize, const int*, int nk,
+                            int n1, int n2, int n3, double2* out, cudaStream_t st) {
+  long long n = static_cast<long long>(nk) * msize;
+  ft_table_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, st>>>(R, XR, nR, msize, nk, n1,
+                                                                         n2, n3, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_density_R(const double2* nk_, const int* R, int nRv, int norb2, const int*,
+                             int nk, int n1, int n2, int n3, double2* nR_out, cudaStream_t st) {
+  density_R_kernel<<<nRv * norb2, 256, 0, st>>>(nk_, R, norb2, nk, n1, n2, n3, nR_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hf(const double2* VR, const double2* nR_in, const int* R, int nRv, int norb,
+                      double s, const int*, int nk, int n1, int n2, int n3, double2* sigF_R,
+                      double2* SigHF, cudaStream_t st) {
+  hf_real_kernel<<<1, 256, 0, st>>>(VR, nR_in, nRv, norb, s, sigF_R);
+  long long n = static_cast<long long>(nk) * norb * norb;
+  hf_k_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, st>>>(sigF_R, R, nRv, norb, nk, n1,
+                                                                     n2, n3, SigHF);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_k_average(const void* x, int m, int nk, double2* out, cudaStream_t st) {
+  k_average_kernel<T><<<m, 256, 0, st>>>(reinterpret_cast<const cplx<T>*>(x), nk, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_c128_to_c64(const double2* in, float2* out, long long n, cudaStream_t st) {
+  c128_to_c64_kernel<<<grid_for(n, 256), 256, 0, st>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_c64_to_c128(const float2* in, double2* out, long long n, cudaStream_t st) {
+  c64_to_c128_kernel<<<grid_for(n, 256), 256, 0, st>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_k_average<double>(const void*, int, int, double2*, cudaStream_t);
+template cudaError_t launch_k_average<float>(const void*, int, int, double2*, cudaStream_t);
+
+}  // namespace qa

@@ -1,0 +1,247 @@
+"""ctypes binding of libqa (argument marshalling only).
+
+Every step of the GW iteration runs in the CUDA kernels behind the C ABI in
+include/qa.h; this module converts Python/numpy/torch arguments to the
+ABI's plain pointers and sizes and raises on a non-zero status.  PyTorch
+provides the device memory (the context workspace and the G arrays) and the
+CUDA stream.  There is no CPU fallback: without the library or a GPU the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libqa.so")
+
+QA_FP64, QA_MIXED = 0, 1
+QA_P_QNU, QA_WC_RTAU, QA_SIGC_KTAU, QA_SIGC_KIW, QA_SIGHF_K, QA_G0, QA_HK, QA_MU0 = range(1, 9)
+
+EXPORTED = ["qa_create", "qa_workspace_size", "qa_bind", "qa_get_grid", "qa_get_plan",
+            "qa_get_sizes", "qa_gw_step", "qa_density", "qa_get", "qa_set_timing", "qa_destroy",
+            "qa_strerror"]
+
+STAGES = ["hartree_fock", "g_to_R", "bubble", "fft_R_to_q", "dlr_tau_to_nu", "dyson_w",
+          "dlr_nu_to_tau", "fft_q_to_R", "sigma", "sigma_to_k_iw", "mu_search", "dyson_g"]
+
+
+class QAError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__("%s failed: %s (status %d)" % (where, strerror(status), status))
+
+
+class Lattice(C.Structure):
+    _fields_ = [("n", C.c_int * 3), ("norb", C.c_int), ("nspin", C.c_int)]
+
+
+class Hoppings(C.Structure):
+    _fields_ = [("nR", C.c_int), ("R", C.POINTER(C.c_int)), ("t", C.POINTER(C.c_double)),
+                ("eps", C.POINTER(C.c_double))]
+
+
+class Interaction(C.Structure):
+    _fields_ = [("nR", C.c_int), ("R", C.POINTER(C.c_int)), ("V", C.POINTER(C.c_double))]
+
+
+class StepStats(C.Structure):
+    _fields_ = [("mu", C.c_double), ("N", C.c_double), ("mu_evals", C.c_int),
+                ("status", C.c_int), ("first_bad", C.c_longlong), ("launches", C.c_int),
+                ("stage_ms", C.c_float * 16)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libqa.so and declare the ABI; raises if it was not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libqa.so not found at %s: run paper_2604_22223_gb300.build()" % path)
+    L = C.CDLL(path)
+    vp, i, d, sz = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+    L.qa_create.argtypes = [C.POINTER(Lattice), C.POINTER(Hoppings), C.POINTER(Interaction), d, d,
+                            d, d, i, C.POINTER(vp)]
+    L.qa_workspace_size.argtypes = [vp, C.POINTER(sz)]
+    L.qa_bind.argtypes = [vp, vp, sz, vp]
+    L.qa_get_grid.argtypes = [vp, C.POINTER(i), vp, vp, vp, vp]
+    L.qa_get_plan.argtypes = [vp, vp, vp, vp, vp]
+    L.qa_get_sizes.argtypes = [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i)]
+    L.qa_gw_step.argtypes = [vp, vp, vp, C.POINTER(d), vp, C.POINTER(StepStats), vp]
+    L.qa_density.argtypes = [vp, vp, vp, C.POINTER(d), vp]
+    L.qa_get.argtypes = [vp, i, vp, sz, vp]
+    L.qa_set_timing.argtypes = [vp, i]
+    L.qa_destroy.argtypes = [vp]
+    L.qa_destroy.restype = None
+    L.qa_strerror.argtypes = [i]
+    L.qa_strerror.restype = C.c_char_p
+    for name in EXPORTED:
+        if name not in ("qa_destroy", "qa_strerror"):
+            getattr(L, name).restype = i
+    _lib = L
+    return L
+
+
+def strerror(status: int) -> str:
+    try:
+        return load().qa_strerror(status).decode()
+    except Exception:  # noqa: BLE001 - message only
+        return "status %d" % status
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise QAError(status, where)
+
+
+def _as(arr, dtype):
+    return np.ascontiguousarray(arr, dtype=dtype)
+
+
+class Problem:
+    """Host-side problem handle (qa_create): validation, DLR grid and FFT plans.
+
+    `model` provides n, norb, s_spin, hop_R, hop_t, eps, V_R, V, beta, Lambda,
+    eps_dlr and filling (see workloads.Model).  No GPU is touched.
+    """
+
+    def __init__(self, model, precision: str = "fp64"):
+        L = load()
+        self.model = model
+        self.precision = {"fp64": QA_FP64, "mixed": QA_MIXED}[precision]
+        self._keep = []
+        lat = Lattice((C.c_int * 3)(*[int(v) for v in model.n]), int(model.norb), int(model.s_spin))
+        hR = _as(model.hop_R, np.int32)
+        ht = _as(np.asarray(model.hop_t, dtype=np.complex128).view(np.float64), np.float64)
+        he = _as(model.eps, np.float64)
+        vR = _as(model.V_R, np.int32)
+        vV = _as(np.asarray(model.V, dtype=np.complex128).view(np.float64), np.float64)
+        self._keep += [hR, ht, he, vR, vV]
+        hop = Hoppings(len(hR), hR.ctypes.data_as(C.POINTER(C.c_int)),
+                       ht.ctypes.data_as(C.POINTER(C.c_double)),
+                       he.ctypes.data_as(C.POINTER(C.c_double)))
+        inter = Interaction(len(vR), vR.ctypes.data_as(C.POINTER(C.c_int)),
+                            vV.ctypes.data_as(C.POINTER(C.c_double)))
+        ctx = C.c_void_p()
+        _check(L.qa_create(C.byref(lat), C.byref(hop), C.byref(inter), float(model.beta),
+                           float(model.Lambda), float(model.eps_dlr), float(model.filling),
+                           self.precision, C.byref(ctx)), "qa_create")
+        self.ctx = ctx
+        nk, no, r = C.c_int(), C.c_int(), C.c_int()
+        _check(L.qa_get_sizes(ctx, C.byref(nk), C.byref(no), C.byref(r)), "qa_get_sizes")
+        self.nk, self.norb, self.r = nk.value, no.value, r.value
+        self.npair = self.norb * self.norb
+
+    def grid(self) -> dict:
+        r = self.r
+        x = np.zeros(r)
+        t = np.zeros(r)
+        nf = np.zeros(r, np.int32)
+        mb = np.zeros(r, np.int32)
+        rr = C.c_int()
+        _check(load().qa_get_grid(self.ctx, C.byref(rr), x.ctypes.data, t.ctypes.data,
+                                  nf.ctypes.data, mb.ctypes.data), "qa_get_grid")
+        return {"r": rr.value, "x": x, "t": t, "nf": nf, "mb": mb}
+
+    def plan(self) -> dict:
+        n = [int(v) for v in self.model.n]
+        mR = np.zeros(self.nk, np.int32)
+        pos = np.zeros(sum(n), np.int32)
+        nfac = np.zeros(3, np.int32)
+        fac = np.zeros((3, 16), np.int32)
+        _check(load().qa_get_plan(self.ctx, mR.ctypes.data, pos.ctypes.data, nfac.ctypes.data,
+                                  fac.ctypes.data), "qa_get_plan")
+        return {"minus_R": mR, "pos": pos, "nfac": nfac, "fac": fac}
+
+    def workspace_size(self) -> int:
+        b = C.c_size_t()
+        _check(load().qa_workspace_size(self.ctx, C.byref(b)), "qa_workspace_size")
+        return b.value
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            load().qa_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+class Context(Problem):
+    """A bound context: Problem + device workspace (torch) + G0 (qa_bind)."""
+
+    def __init__(self, model, precision: str = "fp64", device: str = "cuda"):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("libqa needs a CUDA GPU; no CPU fallback exists")
+        super().__init__(model, precision)
+        self.torch = torch
+        self.device = torch.device(device)
+        nbytes = self.workspace_size()
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        _check(load().qa_bind(self.ctx, self.workspace.data_ptr(), nbytes, self._stream()), "qa_bind")
+
+    def _stream(self):
+        return self.torch.cuda.current_stream(self.device).cuda_stream
+
+    @property
+    def g_shape(self):
+        return (self.r, self.norb, self.norb, self.nk)
+
+    def new_g(self):
+        return self.torch.empty(self.g_shape, dtype=self.torch.complex128, device=self.device)
+
+    def step(self, G_in=None, G_out=None, timing: bool = False):
+        """One GW iteration; returns (G_out, mu, n_local [norb, norb] complex, stats dict)."""
+        L = load()
+        if G_out is None:
+            G_out = self.new_g()
+        for G in (G_in, G_out):
+            if G is not None:
+                assert G.dtype == self.torch.complex128 and G.is_contiguous() and tuple(G.shape) == self.g_shape
+        _check(L.qa_set_timing(self.ctx, int(timing)), "qa_set_timing")
+        mu = C.c_double()
+        n = np.zeros(2 * self.norb * self.norb)
+        st = StepStats()
+        status = L.qa_gw_step(self.ctx, None if G_in is None else G_in.data_ptr(), G_out.data_ptr(),
+                              C.byref(mu), n.ctypes.data, C.byref(st), self._stream())
+        _check(status, "qa_gw_step")
+        stats = {"mu": st.mu, "N": st.N, "mu_evals": st.mu_evals, "status": st.status,
+                 "first_bad": st.first_bad, "launches": st.launches}
+        if timing:
+            stats["stage_ms"] = dict(zip(STAGES, list(st.stage_ms)[:len(STAGES)]))
+        return G_out, mu.value, n.view(np.complex128).reshape(self.norb, self.norb), stats
+
+    def density(self, G):
+        n = np.zeros(2 * self.norb * self.norb)
+        N = C.c_double()
+        _check(load().qa_density(self.ctx, G.data_ptr(), n.ctypes.data, C.byref(N), self._stream()),
+               "qa_density")
+        return n.view(np.complex128).reshape(self.norb, self.norb), N.value
+
+    def get(self, which: int):
+        """Copy an intermediate into a new device tensor (shape per include/qa.h)."""
+        torch = self.torch
+        r, no, np_, nk = self.r, self.norb, self.npair, self.nk
+        big_dt = torch.complex128 if self.precision == QA_FP64 else torch.complex64
+        shapes = {QA_P_QNU: ((r, np_, np_, nk), big_dt), QA_WC_RTAU: ((r, np_, np_, nk), big_dt),
+                  QA_SIGC_KTAU: ((r, no, no, nk), big_dt), QA_SIGC_KIW: ((r, no, no, nk), big_dt),
+                  QA_SIGHF_K: ((nk, no, no), torch.complex128),
+                  QA_G0: ((r, no, no, nk), torch.complex128), QA_HK: ((nk, no, no), torch.complex128)}
+        if which == QA_MU0:
+            v = C.c_double()
+            _check(load().qa_get(self.ctx, QA_MU0, C.addressof(v), 8, self._stream()), "qa_get")
+            return v.value
+        shape, dt = shapes[which]
+        out = torch.empty(shape, dtype=dt, device=self.device)
+        _check(load().qa_get(self.ctx, which, out.data_ptr(), out.numel() * out.element_size(),
+                             self._stream()), "qa_get")
+        return out

@@ -1,0 +1,141 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Small workloads span several FFT tiles, ragged grids (5x3x2, 6x5x1, 4x3x2), the
+degenerate 1x1x1 grid, complex hoppings and 1, 2 and 5 orbitals; each is
+compared element by element on G0, P(q, i nu), W^C(R, tau), Sigma^C(k, tau),
+Sigma^C(k, i w), Sigma^H + Sigma^F, the new G(k, tau), mu and the density.
+
+Bounds (relative max-norm error, max|gpu - oracle| / max|oracle|):
+  FP64 path : 1e-10 for every quantity (the target stated for the FP64 path).
+  mixed path: MIXED_BOUND below.  FP32 arithmetic and complex64 storage
+              (u = 6e-8) are amplified by the DLR Matsubara -> tau interpolation
+              (i nu -> tau for W^C, i w -> tau for G; Lebesgue-type constants
+              of 10-600 measured on the oracle); the worst case is the
+              degenerate 1x1x1 grid, whose W^C(tau) is dominated by one pole
+              at omega = 0.
+"""
+import functools
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import gw, lattice
+
+pytestmark = pytest.mark.gpu
+
+SMALL = ["square-8x8", "peierls-3x3", "peierls-5x3x2", "five-orbital-6x5x1", "five-orbital-4x3x2",
+         "graphene-6x6", "square-1x1"]
+FP64_BOUND = 1e-10
+MIXED_BOUND = {"P_qnu": 1e-6, "WC_Rtau": 1e-4, "sigc_ktau": 1e-4, "sigc_kiw": 1e-5,
+               "sighf": 1e-9, "G": 2e-5, "mu": 2e-5, "n": 2e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_22223_gb300 import build
+    build()
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_run(name, steps=2):
+    m = wl.config(name)
+    d = gw.make_dlr(m)
+    G0, mu0 = gw.g0(m, d)
+    outs = []
+    G = G0
+    for _ in range(steps):
+        o = gw.gw_step(m, d, G)
+        outs.append(o)
+        G = o["G_ktau"]
+    return m, d, G0, mu0, outs
+
+
+def k_last(x):
+    """oracle layout [k, node, ...] -> GPU layout [node, ..., k]."""
+    return np.moveaxis(x, 0, -1)
+
+
+def rel(gpu, ref):
+    gpu = np.asarray(gpu)
+    return float(np.abs(gpu - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+
+def gpu_arrays(ctx, qa):
+    out = {}
+    for key, which in [("P_qnu", qa.QA_P_QNU), ("WC_Rtau", qa.QA_WC_RTAU),
+                       ("sigc_ktau", qa.QA_SIGC_KTAU), ("sigc_kiw", qa.QA_SIGC_KIW),
+                       ("sighf", qa.QA_SIGHF_K)]:
+        out[key] = ctx.get(which).cpu().numpy().astype(np.complex128)
+    return out
+
+
+def compare_step(ctx, qa, m, o, G_gpu, mu, n_loc, bound):
+    arr = gpu_arrays(ctx, qa)
+    no = m.norb
+    errs = {
+        "P_qnu": rel(arr["P_qnu"], k_last(o["P_qnu"])),
+        "WC_Rtau": rel(arr["WC_Rtau"], k_last(o["WC_Rtau"])),
+        "sigc_ktau": rel(arr["sigc_ktau"], k_last(o["sigc_ktau"])),
+        "sigc_kiw": rel(arr["sigc_kiw"], k_last(o["sigc_kiw"])),
+        "sighf": rel(arr["sighf"], o["sig_hf_k"]),
+        "G": rel(G_gpu.cpu().numpy(), k_last(o["G_ktau"])),
+        "mu": abs(mu - o["mu"]) / max(1.0, abs(o["mu"])),
+        "n": rel(n_loc, o["n_local"].reshape(no, no)),
+    }
+    for k, e in errs.items():
+        b = bound if isinstance(bound, float) else bound.get(k, bound["G"])
+        assert e <= b, (k, e, b, errs)
+    return errs
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_fp64_g0(name):
+    from paper_2604_22223_gb300 import qa
+    m, d, G0, mu0, _ = oracle_run(name)
+    ctx = qa.Context(m, "fp64")
+    g = ctx.get(qa.QA_G0).cpu().numpy()
+    assert rel(g, k_last(G0)) <= FP64_BOUND
+    assert abs(ctx.get(qa.QA_MU0) - mu0) <= 1e-10 * max(1.0, abs(mu0))
+    Hk = ctx.get(qa.QA_HK).cpu().numpy()
+    assert rel(Hk, lattice.H_k(m)) <= 1e-14
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_fp64_two_steps(name):
+    from paper_2604_22223_gb300 import qa
+    m, d, G0, mu0, outs = oracle_run(name)
+    ctx = qa.Context(m, "fp64")
+    G1, mu1, n1, st = ctx.step()
+    compare_step(ctx, qa, m, outs[0], G1, mu1, n1, FP64_BOUND)
+    assert st["status"] == 0 and abs(st["N"] - m.filling) <= 1e-11
+    G2, mu2, n2, st = ctx.step(G1)
+    compare_step(ctx, qa, m, outs[1], G2, mu2, n2, FP64_BOUND)
+    # qa_density on the output agrees with the step's density
+    n_chk, N_chk = ctx.density(G2)
+    assert abs(N_chk - m.filling) <= 1e-9
+    assert np.abs(n_chk - n2).max() <= 1e-9
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_mixed_one_step(name):
+    from paper_2604_22223_gb300 import qa
+    m, d, G0, mu0, outs = oracle_run(name)
+    ctx = qa.Context(m, "mixed")
+    g = ctx.get(qa.QA_G0).cpu().numpy()
+    assert rel(g, k_last(G0)) <= FP64_BOUND        # G0 is built in FP64 in both modes
+    G1, mu1, n1, st = ctx.step()
+    compare_step(ctx, qa, m, outs[0], G1, mu1, n1, MIXED_BOUND)
+
+
+def test_in_place_step_and_timing():
+    from paper_2604_22223_gb300 import qa
+    m, d, G0, mu0, outs = oracle_run("peierls-3x3")
+    ctx = qa.Context(m, "fp64")
+    G = ctx.get(qa.QA_G0).clone()
+    G, mu, n, st = ctx.step(G, G, timing=True)     # G_out aliases G_in
+    assert rel(G.cpu().numpy(), k_last(outs[0]["G_ktau"])) <= FP64_BOUND
+    assert all(v >= 0 for v in st["stage_ms"].values())
