@@ -1,0 +1,432 @@
+#!/usr/bin/env python
+"""Benchmark: GW iterations/s on the five-orbital 32x32x8 DLR workload.
+
+One step = one full GW iteration through qa_gw_step (G -> P -> W -> Sigma ->
+Dyson -> mu -> G) on the mixed-precision path, inputs resident in HBM; the
+steps alternate between two fixed inputs, G0 and its first iteration.  The FP64 path is timed beside it.  The JSON
+line also carries the end-to-end number through the public API with host
+buffers, the per-stage times, the roofline of the dominant kernel, sampled
+clocks and the CPU oracle baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torchrun) every rank runs an independent replica of
+the workload (the iteration has no cross-GPU exchange at this size); value is
+the total iterations of all ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GW iterations/s (5-orbital, 32×32×8 k, DLR) mixed vs FP64; % of HBM roofline"
+UNIT = "GW iterations/s"
+WORKLOAD = "five-orbital-32x32x8"
+FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12     # SMs x FP32 lanes x FMA x max clock
+FP64_TFLOPS = 1.25                                      # GB300 nominal FP64 rate
+
+
+# ------------------------------------------------------------------ helpers
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d["hbm_gbs"], "src": "measured"}
+    return {"hbm_gbs": 6800.0, "src": "fallback"}
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:  # noqa: BLE001 - clocks are best effort
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait(timeout=10)
+        self.f.flush()
+        rows = [l.split(",") for l in open(self.f.name).read().strip().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def stage_costs(ctx, mixed: bool):
+    """Algorithmic bytes and flops per launch of each stage (see the design notes)."""
+    r, nk, no, npair = ctx.r, ctx.nk, ctx.norb, ctx.npair
+    es = 8 if mixed else 16
+    X = r * npair * npair * nk          # big-tensor elements
+    Y = r * no * no * nk                # small-tensor elements
+    import math
+    lg = math.log2(nk)
+    n = npair
+    fd = 8 * (n ** 3 + (n ** 3 if mixed else 0) + n ** 3 / 3 + n ** 3)   # VP, [VPV], LU, solve
+    return {
+        "bubble": (X * es + 2 * Y * es, 6 * X),
+        "fft_R_to_q": (2 * X * es, 5 * X * lg),
+        "dlr_tau_to_nu": (2 * X * es, 8 * r * X),
+        "dyson_w": (2 * X * es + nk * n * n * es, r * nk * fd),
+        "dlr_nu_to_tau": (2 * X * es, 8 * r * X),
+        "fft_q_to_R": (2 * X * es, 5 * X * lg),
+        "sigma": (X * es + 2 * Y * es, 8 * X),
+    }
+
+
+def iteration_bytes(ctx, mixed: bool):
+    """Minimum HBM bytes of one iteration: P and W^C written and read once each,
+    about six passes over the small G/Sigma tensors (complex128) and V(q)."""
+    r, nk, no, npair = ctx.r, ctx.nk, ctx.norb, ctx.npair
+    X = r * npair * npair * nk
+    Y = r * no * no * nk
+    return 4 * X * (8 if mixed else 16) + 6 * Y * 16 + nk * npair * npair * 16
+
+
+def roofline(ctx, mixed, stage_ms, pk):
+    costs = stage_costs(ctx, mixed)
+    name = max(costs, key=lambda s: stage_ms.get(s, 0.0))
+    ms = stage_ms[name]
+    b, f = costs[name]
+    alu_peak = FP32_SIMT_TFLOPS if mixed else FP64_TFLOPS
+    t_hbm = b / (pk["hbm_gbs"] * 1e9)
+    t_alu = f / (alu_peak * 1e12)
+    if t_hbm >= t_alu:
+        ach = b / (ms * 1e-3) / 1e9
+        out = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+               "peak_src": pk["src"] + " hbm_gbs"}
+    else:
+        ach = f / (ms * 1e-3) / 1e12
+        out = {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
+               "peak_src": "152 SMs x %s lanes x 2 x 2.07 GHz" % ("128 FP32" if mixed else "FP64 nominal")}
+    out["frac"] = out["achieved"] / out["peak"]
+    out["kernel"] = name
+    out["ms_per_launch"] = ms
+    out["algorithmic_bytes"] = b
+    out["algorithmic_flops"] = f
+    out["traffic"] = traffic_for(name)
+    return out
+
+
+def traffic_for(stage):
+    """DRAM bytes per launch from a committed ncu summary, if its source matches."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        ent = d.get(stage)
+        if not ent:
+            return None
+        from paper_2604_22223_gb300.builder import _stamp
+        if ent.get("stamp") != _stamp():
+            return None
+        return ent.get("dram_bytes_per_launch")
+    except Exception:  # noqa: BLE001
+        return None
+
+
+def oracle_sample(model, n_q=1, n_k=1):
+    """Time the CPU oracle on a bounded sample of the workload and extrapolate.
+
+    Per iteration the explicit-sum oracle does, for every q, the bubble k-sum,
+    the DLR transform and the W Dyson solve (polarization_at_q +
+    screened_interaction), for every k the Sigma q-sum (self_energy_at_k), and
+    ~45 density evaluations of the mu bisection.  Stand-in arrays of the
+    workload's shapes are used (cost does not depend on values)."""
+    import numpy as np
+    from oracle import gw, lattice
+    dlr = gw.make_dlr(model)
+    rng = np.random.default_rng(0)
+    nk, r, no, npair = model.nk, dlr.r, model.norb, model.npair
+    G = rng.normal(size=(nk, r, no, no)) + 1j * rng.normal(size=(nk, r, no, no))
+    t0 = time.perf_counter()
+    Grefl = gw.reflected(model, dlr, G)
+    t_shared = time.perf_counter() - t0
+    Vq = lattice.V_q(model)
+    tq = []
+    for iq in range(n_q):
+        t0 = time.perf_counter()
+        P = gw.polarization_at_q(model, dlr, G, iq, Grefl)
+        gw.screened_interaction(Vq[iq:iq + 1], P[None])
+        tq.append(time.perf_counter() - t0)
+    WC = np.zeros((nk, r, npair, npair), dtype=np.complex128)
+    tk = []
+    for ik in range(n_k):
+        t0 = time.perf_counter()
+        gw.self_energy_at_k(model, G, WC, ik)
+        tk.append(time.perf_counter() - t0)
+    del WC
+    Hk = lattice.H_k(model)
+    t0 = time.perf_counter()
+    gw.density_from_iw(dlr, gw.g_iw(dlr, Hk, 0.0))
+    t_dens = time.perf_counter() - t0
+    n_bis = 45
+    t_iter = t_shared + nk * (statistics.mean(tq) + statistics.mean(tk)) + n_bis * t_dens
+    return t_iter, {"t_q_s": statistics.mean(tq), "t_k_s": statistics.mean(tk),
+                    "t_density_s": t_dens, "t_shared_s": t_shared}
+
+
+# --------------------------------------------------------------- the arms
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def max_over_ranks(pg, value, device=None):
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def run_ours(args):
+    import torch
+    import workloads as wl
+    from paper_2604_22223_gb300 import build, qa
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build()
+    model = wl.config(WORKLOAD)
+    pk = peaks()
+
+    def timed(ctx, K, W, clocks=None):
+        """W untimed + K timed iterations.  Step i takes input G_a (= G0) or
+        G_b (= the iteration of G0) alternately, so every step is one full
+        iteration over a fixed synthetic input and the mu search starts from
+        the other input's chemical potential."""
+        Ga = ctx.get(qa.QA_G0).clone()
+        Gb = ctx.new_g()
+        Gout = ctx.new_g()
+        ctx.step(Ga, Gb)
+        for i in range(max(W - 1, 0)):
+            ctx.step(Ga if i % 2 else Gb, Gout)
+        stage = {}
+        launches = 0
+        evals = []
+        barrier(pg)
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(K):
+            _, mu, n, st = ctx.step(Ga if i % 2 else Gb, Gout, timing=True)
+            for k, v in st["stage_ms"].items():
+                stage[k] = stage.get(k, 0.0) + v
+            launches += st["launches"]
+            evals.append(st["mu_evals"])
+        e1.record()
+        torch.cuda.synchronize()
+        ck = clocks.stop() if clocks else None
+        barrier(pg)
+        ms = e0.elapsed_time(e1)
+        return ms, {k: v / K for k, v in stage.items()}, launches, evals, ck
+
+    # mixed path (headline)
+    ctx = qa.Context(model, "mixed", device=str(dev))
+    clocks = Clocks(local)
+    ms_mixed, stage_mixed, launches, evals, ck = timed(ctx, args.steps, args.warmup, clocks)
+    ms_mixed = max_over_ranks(pg, ms_mixed, dev)
+    value = world * args.steps / (ms_mixed / 1e3)
+    rl = roofline(ctx, True, stage_mixed, pk)
+    it_bytes = iteration_bytes(ctx, True)
+    # end to end through the public API with pinned host buffers
+    Gh_in = ctx.get(qa.QA_G0).cpu().pin_memory()
+    Gh_out = torch.empty_like(Gh_in).pin_memory()
+    Gd_in, Gd_out = ctx.new_g(), ctx.new_g()
+    for _ in range(2):
+        Gd_in.copy_(Gh_in, non_blocking=True)
+        ctx.step(Gd_in, Gd_out)
+        Gh_out.copy_(Gd_out, non_blocking=True)
+    torch.cuda.synchronize()
+    barrier(pg)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    K2 = max(2, args.steps // 2)
+    e0.record()
+    for _ in range(K2):
+        Gd_in.copy_(Gh_in, non_blocking=True)
+        _, mu, n, _ = ctx.step(Gd_in, Gd_out)
+        Gh_out.copy_(Gd_out, non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(pg)
+    ms_e2e = max_over_ranks(pg, e0.elapsed_time(e1), dev)
+    gbytes = Gh_in.numel() * Gh_in.element_size()
+    r, nk, no = ctx.r, ctx.nk, ctx.norb
+    del ctx, Gd_in, Gd_out
+    torch.cuda.empty_cache()
+    # FP64 path
+    ctx64 = qa.Context(model, "fp64", device=str(dev))
+    ms64, stage64, _, _, _ = timed(ctx64, args.fp64_steps, 1)
+    ms64 = max_over_ranks(pg, ms64, dev)
+    rl64 = roofline(ctx64, False, stage64, pk)
+    it_bytes64 = iteration_bytes(ctx64, False)
+    del ctx64
+    torch.cuda.empty_cache()
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        t_iter, parts = oracle_sample(model)
+        cpu = {"value": 1.0 / t_iter, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "explicit-sum FP64 oracle timed on 1 q-point (bubble k-sum + DLR + W "
+                         "Dyson), 1 k-point (Sigma q-sum) and 1 density evaluation of the "
+                         "32x32x8 workload, extrapolated to 8192 q, 8192 k and 45 bisection "
+                         "steps per iteration; numpy/OpenBLAS default threading",
+               "seconds_per_iteration": t_iter, "parts": parts}
+    ms_step = ms_mixed / args.steps
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64/f32 (mixed path; FP64 mu and density)",
+        "data": "synthetic: seeded five-orbital Hund-Hubbard model (SplitMix64), no dataset",
+        "config": {"workload": WORKLOAD, "k_grid": [32, 32, 8], "norb": no, "npair": no * no,
+                   "dlr_rank": r, "beta": 100.0, "Lambda": 1e4, "eps": 1e-12,
+                   "precision": "mixed", "l2": "no flush: per-step working set (P, W^C: 2 x %.1f GB) "
+                   "is far larger than the 129 MB L2" % (r * 625 * nk * 8 / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "iteration": {"hbm_bytes": it_bytes, "hbm_frac": it_bytes / (ms_step * 1e-3) / 1e9 / pk["hbm_gbs"],
+                      "mu_evals_per_step": statistics.mean(evals)},
+        "stage_ms": stage_mixed,
+        "fp64": {"value": world * args.fp64_steps / (ms64 / 1e3), "ms_per_step": ms64 / args.fp64_steps,
+                 "steps": args.fp64_steps, "stage_ms": stage64, "roofline": rl64,
+                 "iteration_hbm_frac": it_bytes64 / (ms64 / args.fp64_steps * 1e-3) / 1e9 / pk["hbm_gbs"]},
+        "roofline": rl,
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * K2 / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": gbytes,
+                "d2h_bytes_per_step": gbytes + 8 + no * no * 16},
+        "gpu_launches": launches,
+        "clocks": ck,
+    }
+    print(json.dumps(line))
+
+
+def run_reference(args):
+    """The CPU oracle as the reference arm (bounded samples, extrapolated)."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    import workloads as wl
+    from oracle import gw, lattice
+    model = wl.config(WORKLOAD)
+    dlr = gw.make_dlr(model)
+    rng = np.random.default_rng(0)
+    nk, r, no, npair = model.nk, dlr.r, model.norb, model.npair
+    G = rng.normal(size=(nk, r, no, no)) + 1j * rng.normal(size=(nk, r, no, no))
+    Grefl = gw.reflected(model, dlr, G)
+    Vq = lattice.V_q(model)
+    Hk = lattice.H_k(model)
+    # warm-up steps also measure the per-k Sigma cost and one density evaluation
+    WC = np.zeros((nk, r, npair, npair), dtype=np.complex128)
+    tk, td = [], []
+    for i in range(max(args.warmup, 1)):
+        t0 = time.perf_counter()
+        gw.self_energy_at_k(model, G, WC, i % nk)
+        tk.append(time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        gw.density_from_iw(dlr, gw.g_iw(dlr, Hk, 0.0))
+        td.append(time.perf_counter() - t0)
+    del WC
+    iters = []
+    for i in range(args.steps):
+        t0 = time.perf_counter()
+        P = gw.polarization_at_q(model, dlr, G, (7 * i) % nk, Grefl)
+        gw.screened_interaction(Vq[(7 * i) % nk:(7 * i) % nk + 1], P[None])
+        tq = time.perf_counter() - t0
+        iters.append(nk * (tq + statistics.mean(tk)) + 45 * statistics.mean(td))
+    t_iter = statistics.mean(iters)
+    value = 1.0 / t_iter
+    sample = ("per step: the explicit-sum FP64 oracle's bubble + DLR + W Dyson for one q-point "
+              "of the 32x32x8 workload (timed), plus the per-k Sigma q-sum and one density "
+              "evaluation timed in warm-up, extrapolated to 8192 q, 8192 k and 45 bisection steps")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_iter * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic: seeded five-orbital Hund-Hubbard model (SplitMix64), no dataset",
+        "config": {"workload": WORKLOAD, "k_grid": [32, 32, 8], "norb": no, "dlr_rank": r,
+                   "precision": "fp64 oracle"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

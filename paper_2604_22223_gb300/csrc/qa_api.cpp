@@ -207,60 +207,102 @@ int eval_density(qa_ctx* c, const double2* SigHF, const void* SigIw, const DevTa
   return QA_OK;
 }
 
-// Chemical potential: bisection on N(mu) = filling, with Newton steps taken
-// whenever they stay inside the current bracket (N is increasing in mu).
+// Chemical potential: the root of N(mu) = filling (N increases with mu).
+// A bracket is found by marching from the warm start (the previous mu) in
+// the direction of the root with growing steps, clamped to the window
+// |mu| <= max ||H + Sigma|| + 1 + 10/beta where N is empty or full; then
+// bisection with Newton steps taken when they stay inside the bracket and
+// at least halve the step before last (safeguarded Newton, "rtsafe").
+// Stop when |N - filling| <= tolN or the bracket (or, on the mixed path
+// whose FP32 density carries ~1e-6 noise, the Newton step) is below tolB.
 template <typename T>
 int mu_search(qa_ctx* c, const double2* SigHF, const void* SigIw, const DevTables& tab,
               double mu_start, double* mu_out, double* N_out, int* evals, cudaStream_t st) {
   QA_LAUNCH(c, 1, qa::launch_norm_bound<T>(c->d_Hk, SigHF, SigIw, c->r, c->norb, c->nk, c->d_part,
-                                  c->nblocks_g, st));
+                                           c->nblocks_g, st));
   QA_LAUNCH(c, 1, qa::launch_reduce_pairs(c->d_part, c->nblocks_g, 1, c->d_red, st));
   double h[2];
   QA_TRY(cudaMemcpyAsync(h, c->d_red, 16, cudaMemcpyDeviceToHost, st));
   QA_TRY(cudaStreamSynchronize(st));
   if (!std::isfinite(h[0])) return QA_ERANGE;
   const double wid = h[0] + 1.0 + 10.0 / c->beta;
-  double lo = -wid, hi = wid;
   const double target = c->filling;
   const bool fp64 = sizeof(T) == 8;
-  const double tolN = (fp64 ? 1e-12 : 1e-9) * std::max(1.0, target);
-  const double tolB = fp64 ? 2e-13 : 1e-10;
-  double mu = (std::isfinite(mu_start) && mu_start > lo && mu_start < hi) ? mu_start : 0.5 * (lo + hi);
+  const double tolN = (fp64 ? 1e-12 : 1e-6) * std::max(1.0, target);
+  auto tolB = [&](double m) { return (fp64 ? 2e-13 : 1e-9) * std::max(1.0, std::fabs(m)); };
+  int count = 0;
   double N = 0, dN = 0;
-  double dx = hi - lo, dxold = dx;
-  int it = 0;
-  for (; it < 200; ++it) {
-    int rc = eval_density<T>(c, SigHF, SigIw, tab, mu, &N, &dN, st);
+  auto ev = [&](double m, double* f, double* d) -> int {
+    int rc = eval_density<T>(c, SigHF, SigIw, tab, m, &N, &dN, st);
+    ++count;
     if (rc != QA_OK) return rc;
     if (!std::isfinite(N)) return QA_ERANGE;
-    const double f = N - target;
-    if (std::fabs(f) <= tolN) break;
-    if (f < 0) lo = mu; else hi = mu;
-    if (hi - lo <= tolB) {
-      mu = 0.5 * (lo + hi);
-      rc = eval_density<T>(c, SigHF, SigIw, tab, mu, &N, &dN, st);
-      ++it;
+    *f = N - target;
+    *d = dN;
+    return QA_OK;
+  };
+  double mu = std::isfinite(mu_start) ? std::min(std::max(mu_start, -wid), wid) : 0.0;
+  double f = 0, d = 0;
+  int rc = ev(mu, &f, &d);
+  if (rc != QA_OK) return rc;
+  double lo = mu, hi = mu;
+  if (std::fabs(f) > tolN) {
+    // march toward the root until the sign of N - filling changes
+    double step = (d > 0 && std::isfinite(f / d)) ? 1.5 * std::fabs(f / d) : 1.0;
+    step = std::min(std::max(step, 1e-6), 2.0 * wid);
+    const double dir = f < 0 ? 1.0 : -1.0;
+    double fa = f, a = mu, b = mu, fb = f, db = d;
+    for (int m = 0; m < 64; ++m) {
+      b = a + dir * step;
+      if (b > wid) b = wid;
+      if (b < -wid) b = -wid;
+      rc = ev(b, &fb, &db);
       if (rc != QA_OK) return rc;
-      break;
+      if ((fb < 0) != (fa < 0) || std::fabs(fb) <= tolN) break;
+      if (b == wid || b == -wid) return QA_ERANGE;   // filling not reachable in the window
+      a = b;
+      fa = fb;
+      step *= 4.0;
     }
-    // Newton step when it stays inside the bracket and at least halves the
-    // previous step (safeguarded Newton, "rtsafe"); bisection otherwise.
-    const double cand = mu - f / dN;
-    if (!(dN > 0) || !std::isfinite(cand) || cand <= lo || cand >= hi ||
-        std::fabs(2.0 * f) > std::fabs(dxold * dN)) {
-      dxold = dx;
-      dx = 0.5 * (hi - lo);
-      mu = lo + dx;
-    } else {
-      dxold = dx;
-      dx = f / dN;
-      mu = cand;
+    if ((fb < 0) == (fa < 0) && std::fabs(fb) > tolN) return QA_ENOCONV;
+    lo = std::min(a, b);
+    hi = std::max(a, b);
+    // continue from the end with the smaller residual
+    if (std::fabs(fb) < std::fabs(fa)) { mu = b; f = fb; d = db; }
+    else { mu = a; f = fa; }
+    double dx = hi - lo, dxold = dx;
+    for (int it = 0; it < 200 && std::fabs(f) > tolN; ++it) {
+      if (f < 0) lo = std::max(lo, mu); else hi = std::min(hi, mu);
+      if (hi - lo <= tolB(mu)) {
+        mu = 0.5 * (lo + hi);
+        rc = ev(mu, &f, &d);
+        if (rc != QA_OK) return rc;
+        break;
+      }
+      const double cand = mu - f / d;
+      if (!(d > 0) || !std::isfinite(cand) || cand <= lo || cand >= hi ||
+          std::fabs(2.0 * f) > std::fabs(dxold * d)) {
+        dxold = dx;
+        dx = 0.5 * (hi - lo);
+        mu = lo + dx;
+      } else {
+        dxold = dx;
+        dx = f / d;
+        mu = cand;
+        if (!fp64 && std::fabs(dx) <= tolB(mu)) {   // converged to the density noise
+          rc = ev(mu, &f, &d);
+          if (rc != QA_OK) return rc;
+          break;
+        }
+      }
+      rc = ev(mu, &f, &d);
+      if (rc != QA_OK) return rc;
+      if (it == 199 && std::fabs(f) > tolN) return QA_ENOCONV;
     }
   }
-  *evals = it + 1;
+  *evals = count;
   *mu_out = mu;
   *N_out = N;
-  if (it >= 200) return QA_ENOCONV;
   return QA_OK;
 }
 

@@ -274,6 +274,9 @@ def config(name: str) -> Model:
     if name == "five-orbital-32x32x8":
         return five_orbital(n=(32, 32, 8), beta=100.0, Lambda=1.0e4, eps_dlr=1e-12,
                             name="five-orbital-32x32x8")
+    if name == "five-orbital-16x16x8":      # same beta/Lambda/eps at 1/4 of the k-points
+        return five_orbital(n=(16, 16, 8), beta=100.0, Lambda=1.0e4, eps_dlr=1e-12,
+                            name="five-orbital-16x16x8")
     # small parity cases
     if name == "five-orbital-6x5x1":
         return five_orbital(n=(6, 5, 1), beta=10.0, Lambda=200.0, name="five-orbital-6x5x1")
