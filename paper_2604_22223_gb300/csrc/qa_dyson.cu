@@ -136,6 +136,135 @@ __global__ void __launch_bounds__(kWarpsW * 32) dyson_w_kernel(const cplx<T>* __
   if (singular && lane == 0) report(err, first_bad, QA_ESINGULAR_CODE, static_cast<long long>(nu) * nk + q);
 }
 
+// ------------------------------------------------- Dyson W, register rows
+// FP32 variant with the rows in registers.  A block of 8 warps takes 8
+// consecutive q at one nu, so the P / W^C tiles move through shared memory
+// with coalesced runs along q.  Lane i owns row i of A = 1 - V P and of the
+// right-hand side V P V; elimination tracks the pivot lanes instead of
+// swapping rows (the pivot row is broadcast with warp shuffles), and the
+// triangular solve runs column-parallel from shared memory.
+
+constexpr int kWarpsR = 8;
+
+template <int MAXN>
+__global__ void __launch_bounds__(kWarpsR * 32) dyson_w_reg_kernel(const float2* __restrict__ P,
+                                                                  const float2* __restrict__ Vq,
+                                                                  float2* WC, int n, int nk,
+                                                                  int* err, long long* first_bad) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nn = n * n;
+  float2* Ps = reinterpret_cast<float2*>(smem_raw);        // [kWarpsR][nn]
+  float2* Vs = Ps + kWarpsR * nn;                           // [kWarpsR][nn]
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int q0 = blockIdx.x * kWarpsR;
+  const int nu = blockIdx.y;
+  const size_t slab = static_cast<size_t>(nu) * nn * nk;
+  for (int idx = tid; idx < kWarpsR * nn; idx += blockDim.x) {
+    int e = idx / kWarpsR, ww = idx - e * kWarpsR;
+    int q = q0 + ww;
+    Ps[ww * nn + e] = q < nk ? P[slab + static_cast<size_t>(e) * nk + q] : make_float2(0.f, 0.f);
+  }
+  for (int idx = tid; idx < kWarpsR * nn; idx += blockDim.x) {
+    int ww = idx / nn, e = idx - ww * nn;
+    int q = q0 + ww;
+    Vs[idx] = q < nk ? Vq[static_cast<size_t>(q) * nn + e] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const int q = q0 + w;
+  float2* Pw = Ps + w * nn;
+  float2* Vw = Vs + w * nn;
+  float2 a[MAXN], b[MAXN];
+  const bool row = lane < n;
+  // a = row `lane` of V P
+#pragma unroll
+  for (int j = 0; j < MAXN; ++j) a[j] = make_float2(0.f, 0.f);
+  if (row) {
+    for (int m = 0; m < n; ++m) {
+      float2 v = Vw[lane * n + m];
+#pragma unroll
+      for (int j = 0; j < MAXN; ++j)
+        if (j < n) a[j] = cfma(v, Pw[m * n + j], a[j]);
+    }
+  }
+  // b = row `lane` of (V P) V
+#pragma unroll
+  for (int j = 0; j < MAXN; ++j) b[j] = make_float2(0.f, 0.f);
+  if (row) {
+#pragma unroll
+    for (int m = 0; m < MAXN; ++m) {
+      if (m < n) {
+#pragma unroll
+        for (int j = 0; j < MAXN; ++j)
+          if (j < n) b[j] = cfma(a[m], Vw[m * n + j], b[j]);
+      }
+    }
+  }
+  // a = 1 - V P
+#pragma unroll
+  for (int j = 0; j < MAXN; ++j) {
+    a[j].x = (row && j == lane ? 1.f : 0.f) - a[j].x;
+    a[j].y = -a[j].y;
+  }
+  bool used = !row;
+  int mypos = -1;
+  bool singular = false;
+#pragma unroll
+  for (int c = 0; c < MAXN; ++c) {
+    if (c < n) {
+      float val = used ? -1.f : cabs2(a[c]);
+      int idx = lane;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        float ov = __shfl_xor_sync(0xffffffffu, val, o);
+        int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+        if (ov > val || (ov == val && oi < idx)) { val = ov; idx = oi; }
+      }
+      const int p = idx;
+      if (!(val >= 1e-12f)) singular = true;
+      if (lane == p) { used = true; mypos = c; }
+      float2 apc = make_float2(__shfl_sync(0xffffffffu, a[c].x, p), __shfl_sync(0xffffffffu, a[c].y, p));
+      float2 l = used ? make_float2(0.f, 0.f) : cmul(a[c], cinv(apc));
+#pragma unroll
+      for (int j = c + 1; j < MAXN; ++j) {
+        if (j < n) {
+          float2 apj = make_float2(__shfl_sync(0xffffffffu, a[j].x, p), __shfl_sync(0xffffffffu, a[j].y, p));
+          a[j] = cfms(l, apj, a[j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < MAXN; ++j) {
+        if (j < n) {
+          float2 bpj = make_float2(__shfl_sync(0xffffffffu, b[j].x, p), __shfl_sync(0xffffffffu, b[j].y, p));
+          b[j] = cfms(l, bpj, b[j]);
+        }
+      }
+    }
+  }
+  // rows of the triangular factor to shared memory, in pivot order
+  __syncwarp();
+  if (mypos >= 0) {
+#pragma unroll
+    for (int j = 0; j < MAXN; ++j)
+      if (j < n) { Pw[mypos * n + j] = a[j]; Vw[mypos * n + j] = b[j]; }
+  }
+  __syncwarp();
+  if (row) {
+    for (int c = n - 1; c >= 0; --c) {
+      float2 x = Vw[c * n + lane];
+      for (int m = c + 1; m < n; ++m) x = cfms(Pw[c * n + m], Vw[m * n + lane], x);
+      Vw[c * n + lane] = cmul(x, cinv(Pw[c * n + c]));
+    }
+  }
+  if (singular && lane == 0 && q < nk)
+    report(err, first_bad, QA_ESINGULAR_CODE, static_cast<long long>(nu) * nk + q);
+  __syncthreads();
+  for (int idx = tid; idx < kWarpsR * nn; idx += blockDim.x) {
+    int e = idx / kWarpsR, ww = idx - e * kWarpsR;
+    int qq = q0 + ww;
+    if (qq < nk) WC[slab + static_cast<size_t>(e) * nk + qq] = Vs[ww * nn + e];
+  }
+}
+
 // ------------------------------------------------------------------ Dyson G
 
 template <typename T, int NO>
@@ -301,9 +430,21 @@ template <typename T>
 cudaError_t launch_dyson_w(const void* P, const void* Vq, void* WC, int r, int npair, int nk,
                            int* err, long long* first_bad, cudaStream_t st) {
   if (npair > kMaxPair) return cudaErrorInvalidValue;
-  constexpr bool vpv = sizeof(T) == 4;
+  if (sizeof(T) == 4) {
+    // register-row kernel: W^C = (1 - V P)^-1 V P V directly
+    size_t smem = static_cast<size_t>(2) * kWarpsR * npair * npair * sizeof(float2);
+    auto fn = npair <= 4 ? &dyson_w_reg_kernel<4> : (npair <= 9 ? &dyson_w_reg_kernel<9>
+              : (npair <= 16 ? &dyson_w_reg_kernel<16> : &dyson_w_reg_kernel<25>));
+    cudaError_t e = set_smem(reinterpret_cast<const void*>(fn), smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((nk + kWarpsR - 1) / kWarpsR, r);
+    fn<<<grid, kWarpsR * 32, smem, st>>>(reinterpret_cast<const float2*>(P),
+                                         reinterpret_cast<const float2*>(Vq),
+                                         reinterpret_cast<float2*>(WC), npair, nk, err, first_bad);
+    return cudaGetLastError();
+  }
   size_t smem = static_cast<size_t>(kWarpsW) * 2 * npair * (npair + 1) * sizeof(cplx<T>);
-  auto fn = &dyson_w_kernel<T, vpv>;
+  auto fn = &dyson_w_kernel<T, false>;
   cudaError_t e = set_smem(reinterpret_cast<const void*>(fn), smem);
   if (e != cudaSuccess) return e;
   dim3 grid((nk + kWarpsW - 1) / kWarpsW, r);

@@ -111,6 +111,117 @@ __global__ void __launch_bounds__(512) fft3d_kernel(FftDev p, int sign, const cp
   }
 }
 
+// ---------------------------------------------------------------------------
+// Register path for power-of-two axes (L <= 32, or 64 in FP32): each thread
+// owns one whole line along the current axis, loads it in bit-reversed
+// order, runs the radix-2 stages in registers with compile-time indices and
+// stores it back in natural order, so no digit-reversal pass is needed.
+// The staged line is padded by one element after every `pad` elements (pad =
+// innermost non-trivial axis length) so that threads walking the innermost
+// axis hit distinct shared-memory banks.
+
+__host__ __device__ constexpr int brev_bits(int i, int bits) {
+  int r = 0;
+  for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
+  return r;
+}
+__host__ __device__ constexpr int ilog2(int L) { return L <= 1 ? 0 : 1 + ilog2(L / 2); }
+
+template <typename V, int L>
+__device__ __forceinline__ void line_fft(V* __restrict__ buf, int base, int S, int pad,
+                                         const V* __restrict__ tw64, int sign) {
+  constexpr int B = ilog2(L);
+  V x[L];
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    int e = base + brev_bits(j, B) * S;
+    x[j] = buf[e + e / pad];
+  }
+#pragma unroll
+  for (int m = 2; m <= L; m <<= 1) {
+#pragma unroll
+    for (int k = 0; k < m / 2; ++k) {
+      V w = tw64[k * (64 / m)];
+      if (sign > 0) w.y = -w.y;
+#pragma unroll
+      for (int s0 = 0; s0 < L; s0 += m) {
+        V u = x[s0 + k];
+        V t = k == 0 ? x[s0 + k + m / 2] : cmul(w, x[s0 + k + m / 2]);
+        x[s0 + k] = cadd(u, t);
+        x[s0 + k + m / 2] = csub(u, t);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    int e = base + j * S;
+    buf[e + e / pad] = x[j];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) fft3d_reg_kernel(int n1, int n2, int n3, int sign,
+                                                        const cplx<T>* in, cplx<T>* out, int nk,
+                                                        int lpb, long long nlines, int pad) {
+  using V = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* tw = reinterpret_cast<V*>(smem_raw);               // exp(-2 pi i k / 64), k < 32
+  V* buf = tw + 32;
+  const int tid = threadIdx.x, bd = blockDim.x;
+  const int line_sz = nk + nk / pad;
+  const long long line0 = static_cast<long long>(blockIdx.x) * lpb;
+  const int nl = static_cast<int>(min(static_cast<long long>(lpb), nlines - line0));
+  if (tid < 32) {
+    double sn, cs;
+    sincospi(-tid / 32.0, &sn, &cs);
+    tw[tid] = cmk<V>(cs, sn);
+  }
+  const V* src = in + line0 * nk;
+  for (int i = tid; i < nl * nk; i += bd) {
+    int line = i / nk, e = i - line * nk;
+    buf[line * line_sz + e + e / pad] = src[i];
+  }
+  __syncthreads();
+  const int n[3] = {n1, n2, n3};
+  const int stride[3] = {n2 * n3, n3, 1};
+  for (int d = 2; d >= 0; --d) {
+    const int L = n[d];
+    if (L == 1) continue;
+    const int S = stride[d];
+    const int per_line = nk / L;
+    for (int task = tid; task < nl * per_line; task += bd) {
+      int line = task / per_line, rem = task - line * per_line;
+      int o_lo = rem % S, o_hi = rem / S;
+      V* lb = buf + line * line_sz;
+      int base = o_hi * L * S + o_lo;
+      switch (L) {
+        case 2: line_fft<V, 2>(lb, base, S, pad, tw, sign); break;
+        case 4: line_fft<V, 4>(lb, base, S, pad, tw, sign); break;
+        case 8: line_fft<V, 8>(lb, base, S, pad, tw, sign); break;
+        case 16: line_fft<V, 16>(lb, base, S, pad, tw, sign); break;
+        case 32: line_fft<V, 32>(lb, base, S, pad, tw, sign); break;
+        default:
+          if constexpr (sizeof(T) == 4) line_fft<V, 64>(lb, base, S, pad, tw, sign);
+          break;
+      }
+    }
+    __syncthreads();
+  }
+  const T scale = sign > 0 ? static_cast<T>(1.0 / nk) : static_cast<T>(1);
+  V* dst = out + line0 * nk;
+  for (int i = tid; i < nl * nk; i += bd) {
+    int line = i / nk, e = i - line * nk;
+    V v = buf[line * line_sz + e + e / pad];
+    v.x *= scale;
+    v.y *= scale;
+    dst[i] = v;
+  }
+}
+
+bool reg_axis_ok(int L, int maxL) {
+  return L >= 1 && L <= maxL && (L & (L - 1)) == 0;
+}
+
 }  // namespace
 
 template <typename T>
@@ -118,6 +229,22 @@ cudaError_t launch_fft3d(const FftDev& plan, int sign, const void* in, void* out
                          cudaStream_t st) {
   if (nlines <= 0) return cudaSuccess;
   const int nk = plan.n[0] * plan.n[1] * plan.n[2];
+  const int maxL = sizeof(T) == 4 ? 64 : 32;
+  if (reg_axis_ok(plan.n[0], maxL) && reg_axis_ok(plan.n[1], maxL) && reg_axis_ok(plan.n[2], maxL) &&
+      nk >= 2) {
+    const int pad = plan.n[2] > 1 ? plan.n[2] : (plan.n[1] > 1 ? plan.n[1] : plan.n[0]);
+    const int line_sz = nk + nk / pad;
+    int lpb = 1;
+    while (lpb * 2 * line_sz * static_cast<int>(sizeof(cplx<T>)) <= 32768 && lpb * 2 <= 64) lpb *= 2;
+    size_t smem = (static_cast<size_t>(lpb) * line_sz + 32) * sizeof(cplx<T>);
+    cudaError_t e = set_smem(reinterpret_cast<const void*>(&fft3d_reg_kernel<T>), smem);
+    if (e != cudaSuccess) return e;
+    long long nblk = (nlines + lpb - 1) / lpb;
+    fft3d_reg_kernel<T><<<static_cast<unsigned>(nblk), 256, smem, st>>>(
+        plan.n[0], plan.n[1], plan.n[2], sign, reinterpret_cast<const cplx<T>*>(in),
+        reinterpret_cast<cplx<T>*>(out), nk, lpb, nlines, pad);
+    return cudaGetLastError();
+  }
   // lines per block: keep the tile near 16 KB for small grids
   int lpb = 1;
   while (lpb * 2 * nk * static_cast<int>(sizeof(cplx<T>)) <= 16384 && lpb * 2 <= 64) lpb *= 2;
