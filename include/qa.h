@@ -158,6 +158,23 @@ int qa_gw_step(qa_ctx* ctx, const void* G_in, void* G_out, double* mu_out, doubl
  * matrix -G(R=0, beta^-), *N_total = s * Tr n (electrons per cell). */
 int qa_density(qa_ctx* ctx, const void* G, double* n_out, double* N_total, void* stream);
 
+/* qa_density_static: the result of qa_density without any device allocation.
+ * The paper has no counterpart; this entry point exists for callers that cannot
+ * call cudaMalloc (host callbacks, error handlers, plug-ins inside a framework
+ * that owns every device allocation, real-time loops where an allocation may
+ * block).  It needs only a context from qa_create (no qa_bind, no workspace) and
+ * the caller's device G (G layout, complex128).  Its scratch is a file-scope
+ * static __device__ array of 4 MiB that every GPU loading the library holds
+ * until process exit; problems with (r + norb^2 * (N_k + 1)) * 16 bytes (each
+ * part rounded up to 256) above 4 MiB are rejected with QA_ENOMEM (five orbitals
+ * fit up to N_k = 10,480).  All calls
+ * on a device share that array and it keeps the last call's contents: calls
+ * whose GPU work overlaps (other streams or threads) race and give wrong
+ * results.  The first call on a device looks up the array's address; make that
+ * call before any stream capture.  Synchronises `stream`. */
+int qa_density_static(const qa_ctx* ctx, const void* G, double* n_out, double* N_total,
+                      void* stream);
+
 /* Intermediates of the last step / of qa_bind, copied to dst (host or device):
  * element type complex128 for QA_FP64 and complex64 for QA_MIXED, except where
  * noted.  bytes must equal the array size. */

@@ -450,6 +450,19 @@ int gw_step_impl(qa_ctx* c, const void* G_in, void* G_out, double* mu_out, doubl
 
 }  // namespace
 
+namespace qa {
+int density_tables(const ::qa_ctx* c, const std::complex<double>** dtau, int* r, int* norb,
+                   int* nk, int* nspin) {
+  if (!c || c->r < 1) return QA_EINVAL;
+  *dtau = c->mats.dtau.data();
+  *r = c->r;
+  *norb = c->norb;
+  *nk = c->nk;
+  *nspin = c->nspin;
+  return QA_OK;
+}
+}  // namespace qa
+
 extern "C" {
 
 const char* qa_strerror(int s) {

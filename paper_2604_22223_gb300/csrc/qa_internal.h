@@ -9,6 +9,8 @@
 
 #include <cuda_runtime.h>
 
+struct qa_ctx;
+
 namespace qa {
 
 // Device-side copy of the public status code for a singular pivot.
@@ -131,6 +133,10 @@ cudaError_t launch_hf(const double2* VR, const double2* nR_in, const int* R, int
 // Local average over k: out[e] = (1/N_k) sum_k x[e][k], e < m (FP64 out).
 template <typename T>
 cudaError_t launch_k_average(const void* x, int m, int nk, double2* out, cudaStream_t st);
+
+// Host copies a density call needs (valid for the context's lifetime).
+int density_tables(const ::qa_ctx* ctx, const std::complex<double>** dtau, int* r, int* norb,
+                   int* nk, int* nspin);
 
 // Precision conversions.
 cudaError_t launch_c128_to_c64(const double2* in, float2* out, long long n, cudaStream_t st);

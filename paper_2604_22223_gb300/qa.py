@@ -21,8 +21,8 @@ QA_FP64, QA_MIXED = 0, 1
 QA_P_QNU, QA_WC_RTAU, QA_SIGC_KTAU, QA_SIGC_KIW, QA_SIGHF_K, QA_G0, QA_HK, QA_MU0 = range(1, 9)
 
 EXPORTED = ["qa_create", "qa_workspace_size", "qa_bind", "qa_get_grid", "qa_get_plan",
-            "qa_get_sizes", "qa_gw_step", "qa_density", "qa_get", "qa_set_timing", "qa_destroy",
-            "qa_strerror"]
+            "qa_get_sizes", "qa_gw_step", "qa_density", "qa_density_static", "qa_get",
+            "qa_set_timing", "qa_destroy", "qa_strerror"]
 
 STAGES = ["hartree_fock", "g_to_R", "bubble", "fft_R_to_q", "dlr_tau_to_nu", "dyson_w",
           "dlr_nu_to_tau", "fft_q_to_R", "sigma", "sigma_to_k_iw", "mu_search", "dyson_g"]
@@ -74,6 +74,7 @@ def load(path: str = LIB_PATH):
     L.qa_get_sizes.argtypes = [vp, C.POINTER(i), C.POINTER(i), C.POINTER(i)]
     L.qa_gw_step.argtypes = [vp, vp, vp, C.POINTER(d), vp, C.POINTER(StepStats), vp]
     L.qa_density.argtypes = [vp, vp, vp, C.POINTER(d), vp]
+    L.qa_density_static.argtypes = [vp, vp, vp, C.POINTER(d), vp]
     L.qa_get.argtypes = [vp, i, vp, sz, vp]
     L.qa_set_timing.argtypes = [vp, i]
     L.qa_destroy.argtypes = [vp]
