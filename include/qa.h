@@ -154,6 +154,37 @@ int qa_get_sizes(const qa_ctx* ctx, int* nk, int* norb, int* r);
 int qa_gw_step(qa_ctx* ctx, const void* G_in, void* G_out, double* mu_out, double* n_out,
                qa_step_stats* stats, void* stream);
 
+/* Hold the chemical potential fixed (fixed = 1: every qa_gw_step uses `mu`
+ * instead of the search; fixed = 0: search again).  The frozen-mu reading is
+ * the one the adjoint differentiates. */
+int qa_set_mu(qa_ctx* ctx, int fixed, double mu);
+
+/* Replace the hopping amplitudes, on-site energies and interaction values of a
+ * bound context (same R lists, same order as at qa_create); rebuilds H(k) and
+ * V(q) on the device.  Used for finite differences and for optimisation loops. */
+int qa_set_params(qa_ctx* ctx, const qa_hoppings* hop, const qa_interaction* inter, void* stream);
+
+/* qa_gw_backward: hand-written adjoint of one qa_gw_step at fixed chemical
+ * potential `mu` (the value the forward step used), FP64 contexts only.
+ * For a real loss L of the step's outputs the caller passes the cotangents
+ * (Xbar = dL/dRe X + i dL/dIm X, each may be NULL = zero):
+ *   Gbar_out  device, G layout complex128: cotangent of the new G(k, tau_j);
+ *   Sigbar    device, [r][norb][norb][N_k] complex128: cotangent of Sigma^C(k, tau_j);
+ *   nbar      host [norb][norb] complex: cotangent of the local density n(R=0).
+ * Outputs (each may be NULL):
+ *   Gbar_in   device, G layout complex128: cotangent of G_in (chains iterations);
+ *   grad_t    host [nR_hop][norb][norb] complex: dL/dRe t(R) + i dL/dIm t(R) per
+ *             listed hopping matrix (t(R) and t(-R) are separate entries);
+ *   grad_V    host [nR_V][npair][npair] complex: the same for V(R).
+ * The forward stages are recomputed from G_in (nothing is kept from an earlier
+ * step), so an unrolled loop checkpoints only its G's and mu's.  Adjoints:
+ * FFT -> inverse FFT, DLR map -> conjugate transpose, Dyson -> -G^H Gbar G^H,
+ * W Dyson -> Pbar = W^H Wbar W^H, Vbar = (1-VP)^-H Wbar (1+PW)^H - Wbar, reusing
+ * one LU per (q, i nu).  Synchronises `stream`. */
+int qa_gw_backward(qa_ctx* ctx, const void* G_in, double mu, const void* Gbar_out,
+                   const void* Sigbar, const double* nbar, void* Gbar_in, double* grad_t,
+                   double* grad_V, void* stream);
+
 /* Density of a G in G layout (device): n_out [norb][norb] complex local density
  * matrix -G(R=0, beta^-), *N_total = s * Tr n (electrons per cell). */
 int qa_density(qa_ctx* ctx, const void* G, double* n_out, double* N_total, void* stream);

@@ -179,8 +179,11 @@ def self_energy_c(model, GR: np.ndarray, WCR: np.ndarray) -> np.ndarray:
     return -np.einsum("Rtbc,Rtabcd->Rtad", GR, W6)
 
 
-def gw_step(model, dlr: DLR, Gtau: np.ndarray) -> dict:
-    """One G -> P -> W -> Sigma -> G iteration (paper Fig. 3(b)) from G(k, tau_j)."""
+def gw_step(model, dlr: DLR, Gtau: np.ndarray, mu_fixed=None) -> dict:
+    """One G -> P -> W -> Sigma -> G iteration (paper Fig. 3(b)) from G(k, tau_j).
+
+    mu_fixed: use this chemical potential instead of the bisection (the frozen-mu
+    reading used for gradients, where mu is held at its forward value)."""
     n = model.n
     out = {}
     # DLR coefficients of the input G; G at beta - tau_j; density n(k)
@@ -216,7 +219,11 @@ def gw_step(model, dlr: DLR, Gtau: np.ndarray) -> dict:
     out["sigc_Rtau"], out["sigc_ktau"], out["sigc_kiw"] = sigR, sigk, sigiw
     # Dyson for G and the chemical potential
     Hk = lattice.H_k(model)
-    mu, N, nit = solve_mu(model, dlr, Hk, sig_hf_k, sigiw)
+    if mu_fixed is None:
+        mu, N, nit = solve_mu(model, dlr, Hk, sig_hf_k, sigiw)
+    else:
+        mu, nit = float(mu_fixed), 0
+        N = total_density(model, density_from_iw(dlr, g_iw(dlr, Hk, mu, sig_hf_k, sigiw)))
     Giw = g_iw(dlr, Hk, mu, sig_hf_k, sigiw)
     cnew = _node_axis_solve(dlr.K_iw(), Giw)
     Gnew = _node_axis_apply(dlr.K_tau(), cnew)

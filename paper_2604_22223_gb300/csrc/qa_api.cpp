@@ -89,6 +89,21 @@ struct qa_ctx {
   bool have_mu = false;
   bool timing = false;
   int launches = 0;           // kernels launched by the current call
+  bool mu_fixed = false;      // qa_set_mu: use mu_value instead of the search
+  double mu_value = 0.0;
+  // adjoint (FP64 contexts only)
+  DevTables tH;               // conjugate transposes of the FP64 DLR matrices
+  double2* d_GRbar = nullptr;
+  double2* d_GLbar = nullptr;
+  double2* d_Sbar = nullptr;  // [norb^2][N_k]
+  double* d_Vqbar = nullptr;  // [npair^2][N_k] complex as doubles
+  double2* d_X = nullptr;     // density_R outputs
+  double2* d_VbarHF = nullptr;
+  double2* d_nbarR = nullptr;
+  double2* d_tbar = nullptr;
+  double2* d_Vbar = nullptr;
+  double2* d_nbar = nullptr;
+  int nH_user = 0;
 };
 
 namespace {
@@ -174,6 +189,26 @@ size_t layout(qa_ctx* c, char* base) {
   c->d_err = static_cast<int*>(take(4));
   c->d_bad = static_cast<long long*>(take(8));
   c->d_nloc = static_cast<double2*>(take(no2 * 16));
+  if (c->precision == QA_FP64) {
+    c->tH.Trefl = take(rr * 16);
+    c->tH.Ttn = take(rr * 16);
+    c->tH.Tnt = take(rr * 16);
+    c->tH.Ttw = take(rr * 16);
+    c->tH.Twt = take(rr * 16);
+    c->tH.dtau = take(r * 16);
+    c->d_GRbar = static_cast<double2*>(take(r * no2 * nk * 16));
+    c->d_GLbar = static_cast<double2*>(take(r * no2 * nk * 16));
+    c->d_Sbar = static_cast<double2*>(take(no2 * nk * 16));
+    c->d_Vqbar = static_cast<double*>(take(np2 * nk * 16));
+    const size_t nx = std::max({static_cast<size_t>(c->nV + 1) * no2, static_cast<size_t>(c->nH) * no2,
+                                static_cast<size_t>(std::max(1, c->nV)) * np2});
+    c->d_X = static_cast<double2*>(take(nx * 16));
+    c->d_VbarHF = static_cast<double2*>(take(std::max(1, c->nV) * np2 * 16));
+    c->d_nbarR = static_cast<double2*>(take((c->nV + 1) * no2 * 16));
+    c->d_tbar = static_cast<double2*>(take(std::max(1, c->nH) * no2 * 16));
+    c->d_Vbar = static_cast<double2*>(take(std::max(1, c->nV) * np2 * 16));
+    c->d_nbar = static_cast<double2*>(take(no2 * 16));
+  }
   return off;
 }
 
@@ -379,18 +414,17 @@ struct StageTimer {
   }
 };
 
+// Stages of one iteration up to Sigma^C(k, i w) and Sigma^HF(k) from G_in
+// (device, G layout, complex128).  Leaves G(R,tau), G(-R,beta-tau) (small),
+// P(q, i nu) (big tensor 1), W^C(R, tau) (big tensor 2), Sigma^C(k, tau),
+// Sigma^C(k, i w), Sigma^HF(k) and n(R_v) in the workspace.
 template <typename T>
-int gw_step_impl(qa_ctx* c, const void* G_in, void* G_out, double* mu_out, double* n_out,
-                 qa_step_stats* stats, cudaStream_t st) {
+int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st) {
   const DevTables& tab = sizeof(T) == 8 ? c->t64 : c->t32;
   const qa::FftDev& fft = sizeof(T) == 8 ? c->fft64 : c->fft32;
   const int r = c->r, no2 = c->norb * c->norb, nk = c->nk, np2 = c->npair * c->npair;
   const long long ncs = static_cast<long long>(no2) * nk;     // small-tensor columns
   const long long ncb = static_cast<long long>(np2) * nk;     // big-tensor columns
-  const double2* Gin = static_cast<const double2*>(G_in ? G_in : c->d_G0);
-  c->launches = 0;
-  if (int rc = reset_err(c, st)) return rc;
-  StageTimer tm(c, st);
   // n(k) = -G(k, beta^-) of the input, Hartree and Fock (FP64)
   QA_LAUNCH(c, 1, qa::launch_dlr_apply<double>(c->t64.dtau, 1, r, Gin, c->d_nk, ncs, st));
   QA_LAUNCH(c, 1, qa::launch_density_R(c->d_nk, c->d_vR, c->nV + 1, no2, nullptr, nk, c->n[0], c->n[1],
@@ -425,10 +459,30 @@ int gw_step_impl(qa_ctx* c, const void* G_in, void* G_out, double* mu_out, doubl
   QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, -1, c->d_SigC, c->d_SigC, ncs / nk * r, st));
   QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Ttw, r, r, c->d_SigC, c->d_SigIw, ncs, st));
   tm.mark();  // 9: Sigma -> (k, i w)
+  return QA_OK;
+}
+
+template <typename T>
+int gw_step_impl(qa_ctx* c, const void* G_in, void* G_out, double* mu_out, double* n_out,
+                 qa_step_stats* stats, cudaStream_t st) {
+  const DevTables& tab = sizeof(T) == 8 ? c->t64 : c->t32;
+  const double2* Gin = static_cast<const double2*>(G_in ? G_in : c->d_G0);
+  c->launches = 0;
+  if (int rc = reset_err(c, st)) return rc;
+  StageTimer tm(c, st);
+  if (int rc = forward_sigma<T>(c, Gin, tm, st)) return rc;
   double mu = 0, N = 0;
   int evals = 0;
-  int rc = mu_search<T>(c, c->d_SigHF, c->d_SigIw, tab, c->have_mu ? c->mu : c->mu0, &mu, &N,
-                        &evals, st);
+  int rc = QA_OK;
+  if (c->mu_fixed) {
+    double dN = 0;
+    mu = c->mu_value;
+    rc = eval_density<T>(c, c->d_SigHF, c->d_SigIw, tab, mu, &N, &dN, st);
+    evals = 1;
+  } else {
+    rc = mu_search<T>(c, c->d_SigHF, c->d_SigIw, tab, c->have_mu ? c->mu : c->mu0, &mu, &N,
+                      &evals, st);
+  }
   if (rc != QA_OK) return rc;
   tm.mark();  // 10: mu search
   rc = finish_g<T>(c, c->d_SigHF, c->d_SigIw, tab, mu, G_out, n_out, st);
@@ -446,6 +500,99 @@ int gw_step_impl(qa_ctx* c, const void* G_in, void* G_out, double* mu_out, doubl
   }
   int herr = check_err(c, stats, st);
   return herr;
+}
+
+// Adjoint of one iteration at fixed mu (FP64).  Recomputes the forward
+// stages from G_in (P is recomputed, not stored), then pulls the cotangents
+// back stage by stage (qa_adjoint.cu).
+int gw_backward_impl(qa_ctx* c, const double2* Gin, double mu, const double2* Gbar_out,
+                     const double2* Sigbar, const double* nbar, double2* Gbar_in, double* grad_t,
+                     double* grad_V, cudaStream_t st) {
+  const qa::FftDev& fft = c->fft64;
+  const int r = c->r, no2 = c->norb * c->norb, nk = c->nk, np2 = c->npair * c->npair;
+  const long long ncs = static_cast<long long>(no2) * nk;
+  const long long ncb = static_cast<long long>(np2) * nk;
+  const long long lines_s = static_cast<long long>(no2) * r, lines_b = static_cast<long long>(np2) * r;
+  c->launches = 0;
+  if (int rc = reset_err(c, st)) return rc;
+  bool timing = c->timing;
+  c->timing = false;
+  StageTimer tm(c, st);
+  c->timing = timing;
+  if (int rc = forward_sigma<double>(c, Gin, tm, st)) return rc;
+  double2* Giw_bar = static_cast<double2*>(c->d_Giw);
+  double2* SigIw_bar = static_cast<double2*>(c->d_Gt);
+  double2* Sig_bar = static_cast<double2*>(c->d_SigC);
+  double2* Wbig = static_cast<double2*>(c->d_W);
+  // outputs -> Gbar(k, i w)
+  if (Gbar_out) {
+    QA_LAUNCH(c, 1, qa::launch_dlr_apply<double>(c->tH.Twt, r, r, Gbar_out, Giw_bar, ncs, st));
+  } else {
+    QA_TRY(cudaMemsetAsync(Giw_bar, 0, static_cast<size_t>(ncs) * r * 16, st));
+  }
+  if (nbar) {
+    QA_TRY(cudaMemcpyAsync(c->d_nbar, nbar, no2 * 16, cudaMemcpyHostToDevice, st));
+    QA_LAUNCH(c, 1, qa::launch_add_dw_nbar(Giw_bar, static_cast<const double2*>(c->t64.dw), c->d_nbar,
+                                           r, no2, nk, st));
+  }
+  // Dyson for G
+  QA_LAUNCH(c, 1, qa::launch_dyson_g_bwd(c->d_Hk, c->d_SigHF, static_cast<const double2*>(c->d_SigIw),
+                                         c->d_iw, mu, r, c->norb, nk, Giw_bar, SigIw_bar, c->d_Sbar, st));
+  // Sigma^C(k, i w) <- Sigma^C(k, tau) <- Sigma^C(R, tau)
+  QA_LAUNCH(c, 1, qa::launch_dlr_apply<double>(c->tH.Ttw, r, r, SigIw_bar, Sig_bar, ncs, st));
+  if (Sigbar) QA_LAUNCH(c, 1, qa::launch_axpy(Sig_bar, Sigbar, 1.0, ncs * r, st));
+  QA_LAUNCH(c, 1, qa::launch_fft3d<double>(fft, +1, Sig_bar, Sig_bar, lines_s, st, 1.0));
+  // Sigma contraction: Gbar(R) and Wbar(R, tau) (in place over W^C)
+  QA_LAUNCH(c, 1, qa::launch_sigma_bwd(static_cast<const double2*>(c->d_GR), Sig_bar, Wbig, c->d_GRbar,
+                                       r, c->norb, nk, st));
+  // W^C(R, tau) <- W^C(q, tau) <- W^C(q, i nu)
+  QA_LAUNCH(c, 1, qa::launch_fft3d<double>(fft, -1, Wbig, Wbig, lines_b, st, 1.0 / nk));
+  QA_LAUNCH(c, 1, qa::launch_dlr_apply<double>(c->tH.Tnt, r, r, Wbig, Wbig, ncb, st));
+  // Dyson for W: Pbar (in place) and Vbar(q)
+  QA_TRY(cudaMemsetAsync(c->d_Vqbar, 0, static_cast<size_t>(ncb) * 16, st));
+  QA_LAUNCH(c, 1, qa::launch_dyson_w_bwd(static_cast<const double2*>(c->d_P),
+                                         static_cast<const double2*>(c->d_Vq), Wbig, c->d_Vqbar, r,
+                                         c->npair, nk, c->d_err, st));
+  // P(q, i nu) <- P(q, tau) <- P(R, tau)
+  QA_LAUNCH(c, 1, qa::launch_dlr_apply<double>(c->tH.Ttn, r, r, Wbig, Wbig, ncb, st));
+  QA_LAUNCH(c, 1, qa::launch_fft3d<double>(fft, +1, Wbig, Wbig, lines_b, st, 1.0));
+  // bubble
+  QA_LAUNCH(c, 1, qa::launch_bubble_bwd(static_cast<const double2*>(c->d_GR),
+                                        static_cast<const double2*>(c->d_Grefl), c->d_mR, Wbig,
+                                        c->d_GRbar, c->d_GLbar, r, c->norb, nk, c->nspin, st));
+  // G(R) <- G(k) and G(-R, beta - tau) <- G(k, beta - tau) <- G(k, tau)
+  QA_LAUNCH(c, 1, qa::launch_fft3d<double>(fft, -1, c->d_GRbar, c->d_GRbar, lines_s, st, 1.0 / nk));
+  QA_LAUNCH(c, 1, qa::launch_fft3d<double>(fft, -1, c->d_GLbar, c->d_GLbar, lines_s, st, 1.0 / nk));
+  double2* gin = Gbar_in ? Gbar_in : reinterpret_cast<double2*>(c->d_Gk);
+  QA_LAUNCH(c, 1, qa::launch_dlr_apply<double>(c->tH.Trefl, r, r, c->d_GLbar, gin, ncs, st));
+  QA_LAUNCH(c, 1, qa::launch_axpy(gin, c->d_GRbar, 1.0, ncs * r, st));
+  // Hartree and Fock: (H, Sigma^HF) bar -> Sigma^H bar, Sigma^F bar(R_v) -> Vbar, nbar
+  QA_LAUNCH(c, 1, qa::launch_density_R(c->d_Sbar, c->d_vR, c->nV + 1, no2, nullptr, nk, c->n[0],
+                                       c->n[1], c->n[2], c->d_X, st));
+  QA_LAUNCH(c, 1, qa::launch_hf_bwd(c->d_vV, c->d_nR, c->d_X, c->nV, c->norb, c->nspin, nk,
+                                    c->d_VbarHF, c->d_nbarR, st));
+  QA_LAUNCH(c, 1, qa::launch_nbar_k(c->d_nbarR, c->d_vR, c->nV + 1, no2, nk, c->n[0], c->n[1],
+                                    c->n[2], c->d_nk, st));
+  QA_LAUNCH(c, 1, qa::launch_dlr_apply<double>(c->tH.dtau, r, 1, c->d_nk, gin, ncs, st, 1));
+  // t(R) = -H(R): tbar(R) = -sum_k e^{+ik.R} Hbar(k)
+  QA_LAUNCH(c, 1, qa::launch_density_R(c->d_Sbar, c->d_hR, c->nH, no2, nullptr, nk, c->n[0], c->n[1],
+                                       c->n[2], c->d_tbar, st));
+  QA_LAUNCH(c, 1, qa::launch_scale(c->d_tbar, -static_cast<double>(nk), static_cast<long long>(c->nH) * no2, st));
+  // V(R): sum_q e^{+iq.R} Vbar(q) plus the Hartree/Fock part
+  if (c->nV > 0) {
+    QA_LAUNCH(c, 1, qa::launch_density_R(reinterpret_cast<const double2*>(c->d_Vqbar), c->d_vR, c->nV,
+                                         np2, nullptr, nk, c->n[0], c->n[1], c->n[2], c->d_Vbar, st));
+    QA_LAUNCH(c, 1, qa::launch_scale(c->d_Vbar, static_cast<double>(nk), static_cast<long long>(c->nV) * np2, st));
+    QA_LAUNCH(c, 1, qa::launch_axpy(c->d_Vbar, c->d_VbarHF, 1.0, static_cast<long long>(c->nV) * np2, st));
+  }
+  if (grad_t)
+    QA_TRY(cudaMemcpyAsync(grad_t, c->d_tbar, static_cast<size_t>(c->nH_user) * no2 * 16,
+                           cudaMemcpyDeviceToHost, st));
+  if (grad_V && c->nV > 0)
+    QA_TRY(cudaMemcpyAsync(grad_V, c->d_Vbar, static_cast<size_t>(c->nV) * np2 * 16,
+                           cudaMemcpyDeviceToHost, st));
+  QA_TRY(cudaStreamSynchronize(st));
+  return check_err(c, nullptr, st);
 }
 
 }  // namespace
@@ -526,6 +673,7 @@ int qa_create(const qa_lattice* lat, const qa_hoppings* hop, const qa_interactio
       c->hopH.push_back(cd(e / no == e % no && hop->eps ? hop->eps[e / no] : 0.0, 0.0));
   }
   c->nH = static_cast<int>(c->hopR.size() / 3);
+  c->nH_user = hop->nR;
   // Hermiticity: H(-R) = H(R)^dagger for every listed R
   double scale = 0;
   for (const cd& v : c->hopH) scale = std::max(scale, std::abs(v));
@@ -605,6 +753,25 @@ int qa_bind(qa_ctx* c, void* workspace, size_t bytes, void* stream) {
   QA_TRY(upload_c<float>(c->t32.dtau, m.dtau, st));
   QA_TRY(upload_c<float>(c->t32.dw, m.dw, st));
   QA_TRY(cudaMemcpyAsync(c->d_iw, m.iw.data(), r * 8, cudaMemcpyHostToDevice, st));
+  if (c->precision == QA_FP64) {
+    auto ctrans = [r](const std::vector<cd>& T) {
+      std::vector<cd> H(T.size());
+      for (int i = 0; i < r; ++i)
+        for (int j = 0; j < r; ++j) H[static_cast<size_t>(j) * r + i] = std::conj(T[static_cast<size_t>(i) * r + j]);
+      return H;
+    };
+    std::vector<cd> cdt(r);
+    for (int j = 0; j < r; ++j) cdt[j] = std::conj(m.dtau[j]);     // an r x 1 matrix
+    const std::vector<cd> h1 = ctrans(m.Trefl), h2 = ctrans(m.Ttn), h3 = ctrans(m.Tnt),
+                          h4 = ctrans(m.Ttw), h5 = ctrans(m.Twt);
+    QA_TRY(upload_c<double>(c->tH.Trefl, h1, st));
+    QA_TRY(upload_c<double>(c->tH.Ttn, h2, st));
+    QA_TRY(upload_c<double>(c->tH.Tnt, h3, st));
+    QA_TRY(upload_c<double>(c->tH.Ttw, h4, st));
+    QA_TRY(upload_c<double>(c->tH.Twt, h5, st));
+    QA_TRY(upload_c<double>(c->tH.dtau, cdt, st));
+    QA_TRY(cudaStreamSynchronize(st));
+  }
   // FFT twiddles exp(-2 pi i m / L) per axis, and digit-reversal tables
   std::vector<cd> tw;
   std::vector<int> pos;
@@ -758,6 +925,70 @@ int qa_get(const qa_ctx* c, int which, void* dst, size_t bytes, void* stream) {
   QA_TRY(cudaMemcpyAsync(dst, src, need, cudaMemcpyDefault, st));
   QA_TRY(cudaStreamSynchronize(st));
   return QA_OK;
+}
+
+int qa_set_mu(qa_ctx* c, int fixed, double mu) {
+  if (!c || !std::isfinite(mu)) return QA_EINVAL;
+  c->mu_fixed = fixed != 0;
+  c->mu_value = mu;
+  return QA_OK;
+}
+
+int qa_set_params(qa_ctx* c, const qa_hoppings* hop, const qa_interaction* inter, void* stream) {
+  if (!c || !hop || !inter) return QA_EINVAL;
+  if (!c->bound) return QA_ESTATE;
+  if (hop->nR != c->nH_user || inter->nR != c->nV) return QA_EINVAL;
+  const int no = c->norb, no2 = no * no, np2 = c->npair * c->npair;
+  for (int i = 0; i < hop->nR; ++i)
+    for (int d = 0; d < 3; ++d)
+      if (hop->R[3 * i + d] != c->hopR[3 * i + d]) return QA_EINVAL;
+  for (int i = 0; i < inter->nR; ++i)
+    for (int d = 0; d < 3; ++d)
+      if (inter->R[3 * i + d] != c->vR[3 * i + d]) return QA_EINVAL;
+  std::vector<cd> H(c->hopH.size());
+  for (int i = 0; i < c->nH; ++i) {
+    const bool user = i < hop->nR;
+    const bool zero = c->hopR[3 * i] == 0 && c->hopR[3 * i + 1] == 0 && c->hopR[3 * i + 2] == 0;
+    for (int e = 0; e < no2; ++e) {
+      cd v = user ? cd(-hop->t[2 * (static_cast<size_t>(i) * no2 + e)], -hop->t[2 * (static_cast<size_t>(i) * no2 + e) + 1])
+                  : cd(0.0, 0.0);
+      if (zero && e / no == e % no && hop->eps) v += hop->eps[e / no];
+      H[static_cast<size_t>(i) * no2 + e] = v;
+    }
+  }
+  for (const cd& v : H)
+    if (!std::isfinite(v.real()) || !std::isfinite(v.imag())) return QA_EINVAL;
+  c->hopH = H;
+  for (size_t e = 0; e < c->vV.size(); ++e)
+    c->vV[e] = cd(inter->V[2 * e], inter->V[2 * e + 1]);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  QA_TRY(upload_c<double>(c->d_hH, c->hopH, st));
+  if (c->nV > 0) QA_TRY(upload_c<double>(c->d_vV, c->vV, st));
+  QA_TRY(qa::launch_ft_table(c->d_hR, c->d_hH, c->nH, no2, nullptr, c->nk, c->n[0], c->n[1], c->n[2],
+                             c->d_Hk, st));
+  if (c->precision == QA_FP64) {
+    QA_TRY(qa::launch_ft_table(c->d_vR, c->d_vV, c->nV, np2, nullptr, c->nk, c->n[0], c->n[1],
+                               c->n[2], static_cast<double2*>(c->d_Vq), st));
+  } else {
+    QA_TRY(qa::launch_ft_table(c->d_vR, c->d_vV, c->nV, np2, nullptr, c->nk, c->n[0], c->n[1],
+                               c->n[2], static_cast<double2*>(c->d_P), st));
+    QA_TRY(qa::launch_c128_to_c64(static_cast<const double2*>(c->d_P), static_cast<float2*>(c->d_Vq),
+                                  static_cast<long long>(c->nk) * np2, st));
+  }
+  QA_TRY(cudaStreamSynchronize(st));
+  return QA_OK;
+}
+
+int qa_gw_backward(qa_ctx* c, const void* G_in, double mu, const void* Gbar_out, const void* Sigbar,
+                   const double* nbar, void* Gbar_in, double* grad_t, double* grad_V,
+                   void* stream) {
+  if (!c) return QA_EINVAL;
+  if (!c->bound) return QA_ESTATE;
+  if (c->precision != QA_FP64 || !std::isfinite(mu)) return QA_EINVAL;
+  const double2* Gin = static_cast<const double2*>(G_in ? G_in : c->d_G0);
+  return gw_backward_impl(c, Gin, mu, static_cast<const double2*>(Gbar_out),
+                          static_cast<const double2*>(Sigbar), nbar, static_cast<double2*>(Gbar_in),
+                          grad_t, grad_V, static_cast<cudaStream_t>(stream));
 }
 
 void qa_destroy(qa_ctx* c) { delete c; }

@@ -122,7 +122,14 @@ __device__ __forceinline__ double block_max(double a, double* sh) {
   return a;
 }
 
-inline cudaError_t set_smem(const void* fn, size_t bytes) {
+// Allow `bytes` of dynamic shared memory; max_carveout asks for the largest
+// shared-memory carveout (for kernels that rely on shared memory, not L1).
+inline cudaError_t set_smem(const void* fn, size_t bytes, bool max_carveout = false) {
+  if (max_carveout) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+  }
   if (bytes <= 48 * 1024) return cudaSuccess;
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               static_cast<int>(bytes));

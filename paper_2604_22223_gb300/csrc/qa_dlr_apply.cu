@@ -14,7 +14,7 @@ namespace {
 template <typename T, int TILE, int RB>
 __global__ void __launch_bounds__(256) dlr_apply_kernel(const cplx<T>* __restrict__ Tm, int rows_out,
                                                         int r, const cplx<T>* in, cplx<T>* out,
-                                                        long long ncol) {
+                                                        long long ncol, int accumulate) {
   using V = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* xs = reinterpret_cast<V*>(smem_raw);  // [r][TILE]
@@ -46,7 +46,10 @@ __global__ void __launch_bounds__(256) dlr_apply_kernel(const cplx<T>* __restric
     if (col < ncol) {
 #pragma unroll
       for (int b = 0; b < RB; ++b)
-        if (j0 + b < rows_out) out[static_cast<long long>(j0 + b) * ncol + col] = acc[b];
+        if (j0 + b < rows_out) {
+          const long long o = static_cast<long long>(j0 + b) * ncol + col;
+          out[o] = accumulate ? cadd(out[o], acc[b]) : acc[b];
+        }
     }
   }
 }
@@ -55,7 +58,7 @@ __global__ void __launch_bounds__(256) dlr_apply_kernel(const cplx<T>* __restric
 
 template <typename T>
 cudaError_t launch_dlr_apply(const void* Tm, int rows_out, int r, const void* in, void* out,
-                             long long ncol, cudaStream_t st) {
+                             long long ncol, cudaStream_t st, int accumulate) {
   if (ncol <= 0 || rows_out <= 0) return cudaSuccess;
   constexpr int TILE = sizeof(T) == 8 ? 32 : 64;
   constexpr int RB = 4;
@@ -66,13 +69,13 @@ cudaError_t launch_dlr_apply(const void* Tm, int rows_out, int r, const void* in
   long long nblk = (ncol + TILE - 1) / TILE;
   fn<<<static_cast<unsigned>(nblk), 256, smem, st>>>(reinterpret_cast<const cplx<T>*>(Tm), rows_out,
                                                      r, reinterpret_cast<const cplx<T>*>(in),
-                                                     reinterpret_cast<cplx<T>*>(out), ncol);
+                                                     reinterpret_cast<cplx<T>*>(out), ncol, accumulate);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_dlr_apply<double>(const void*, int, int, const void*, void*, long long,
-                                              cudaStream_t);
+                                              cudaStream_t, int);
 template cudaError_t launch_dlr_apply<float>(const void*, int, int, const void*, void*, long long,
-                                             cudaStream_t);
+                                             cudaStream_t, int);
 
 }  // namespace qa

@@ -23,7 +23,8 @@ __device__ __forceinline__ V tw_get(const V* tw, int idx, int sign) {
 
 template <typename T>
 __global__ void __launch_bounds__(512) fft3d_kernel(FftDev p, int sign, const cplx<T>* in,
-                                                    cplx<T>* out, int nk, int lpb, long long nlines) {
+                                                    cplx<T>* out, int nk, int lpb, long long nlines,
+                                                    T scale) {
   using V = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* buf = reinterpret_cast<V*>(smem_raw);
@@ -98,7 +99,6 @@ __global__ void __launch_bounds__(512) fft3d_kernel(FftDev p, int sign, const cp
   const int* pos0 = p.pos + p.pos_off[0];
   const int* pos1 = p.pos + p.pos_off[1];
   const int* pos2 = p.pos + p.pos_off[2];
-  const T scale = sign > 0 ? static_cast<T>(1.0 / nk) : static_cast<T>(1);
   V* dst = out + line0 * nk;
   for (int i = tid; i < nl * nk; i += bd) {
     int line = i / nk, k = i - line * nk;
@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(512) fft3d_kernel(FftDev p, int sign, const cp
 }
 
 // ---------------------------------------------------------------------------
-// Register path for power-of-two axes (L <= 32, or 64 in FP32): each thread
+// Register path for power-of-two axes (L <= 32): each thread
 // owns one whole line along the current axis, loads it in bit-reversed
 // order, runs the radix-2 stages in registers with compile-time indices and
 // stores it back in natural order, so no digit-reversal pass is needed.
@@ -160,9 +160,10 @@ __device__ __forceinline__ void line_fft(V* __restrict__ buf, int base, int S, i
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) fft3d_reg_kernel(int n1, int n2, int n3, int sign,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) fft3d_reg_kernel(int n1, int n2, int n3, int sign,
                                                         const cplx<T>* in, cplx<T>* out, int nk,
-                                                        int lpb, long long nlines, int pad) {
+                                                        int lpb, long long nlines, int pad,
+                                                        T scale) {
   using V = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* tw = reinterpret_cast<V*>(smem_raw);               // exp(-2 pi i k / 64), k < 32
@@ -200,14 +201,11 @@ __global__ void __launch_bounds__(256) fft3d_reg_kernel(int n1, int n2, int n3, 
         case 8: line_fft<V, 8>(lb, base, S, pad, tw, sign); break;
         case 16: line_fft<V, 16>(lb, base, S, pad, tw, sign); break;
         case 32: line_fft<V, 32>(lb, base, S, pad, tw, sign); break;
-        default:
-          if constexpr (sizeof(T) == 4) line_fft<V, 64>(lb, base, S, pad, tw, sign);
-          break;
+        default: break;
       }
     }
     __syncthreads();
   }
-  const T scale = sign > 0 ? static_cast<T>(1.0 / nk) : static_cast<T>(1);
   V* dst = out + line0 * nk;
   for (int i = tid; i < nl * nk; i += bd) {
     int line = i / nk, e = i - line * nk;
@@ -226,10 +224,11 @@ bool reg_axis_ok(int L, int maxL) {
 
 template <typename T>
 cudaError_t launch_fft3d(const FftDev& plan, int sign, const void* in, void* out, long long nlines,
-                         cudaStream_t st) {
+                         cudaStream_t st, double scale) {
   if (nlines <= 0) return cudaSuccess;
   const int nk = plan.n[0] * plan.n[1] * plan.n[2];
-  const int maxL = sizeof(T) == 4 ? 64 : 32;
+  const T sc = static_cast<T>(scale > 0 ? scale : (sign > 0 ? 1.0 / nk : 1.0));
+  const int maxL = 32;
   if (reg_axis_ok(plan.n[0], maxL) && reg_axis_ok(plan.n[1], maxL) && reg_axis_ok(plan.n[2], maxL) &&
       nk >= 2) {
     const int pad = plan.n[2] > 1 ? plan.n[2] : (plan.n[1] > 1 ? plan.n[1] : plan.n[0]);
@@ -237,12 +236,12 @@ cudaError_t launch_fft3d(const FftDev& plan, int sign, const void* in, void* out
     int lpb = 1;
     while (lpb * 2 * line_sz * static_cast<int>(sizeof(cplx<T>)) <= 32768 && lpb * 2 <= 64) lpb *= 2;
     size_t smem = (static_cast<size_t>(lpb) * line_sz + 32) * sizeof(cplx<T>);
-    cudaError_t e = set_smem(reinterpret_cast<const void*>(&fft3d_reg_kernel<T>), smem);
+    cudaError_t e = set_smem(reinterpret_cast<const void*>(&fft3d_reg_kernel<T>), smem, true);
     if (e != cudaSuccess) return e;
     long long nblk = (nlines + lpb - 1) / lpb;
     fft3d_reg_kernel<T><<<static_cast<unsigned>(nblk), 256, smem, st>>>(
         plan.n[0], plan.n[1], plan.n[2], sign, reinterpret_cast<const cplx<T>*>(in),
-        reinterpret_cast<cplx<T>*>(out), nk, lpb, nlines, pad);
+        reinterpret_cast<cplx<T>*>(out), nk, lpb, nlines, pad, sc);
     return cudaGetLastError();
   }
   // lines per block: keep the tile near 16 KB for small grids
@@ -255,13 +254,13 @@ cudaError_t launch_fft3d(const FftDev& plan, int sign, const void* in, void* out
   int threads = nk * lpb >= 2048 ? 512 : 256;
   fft3d_kernel<T><<<static_cast<unsigned>(nblk), threads, smem, st>>>(
       plan, sign, reinterpret_cast<const cplx<T>*>(in), reinterpret_cast<cplx<T>*>(out), nk, lpb,
-      nlines);
+      nlines, sc);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_fft3d<double>(const FftDev&, int, const void*, void*, long long,
-                                          cudaStream_t);
+                                          cudaStream_t, double);
 template cudaError_t launch_fft3d<float>(const FftDev&, int, const void*, void*, long long,
-                                         cudaStream_t);
+                                         cudaStream_t, double);
 
 }  // namespace qa

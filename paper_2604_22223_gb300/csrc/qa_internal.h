@@ -71,15 +71,17 @@ struct FftDev {            // passed by value to the FFT kernel
 
 // out[j][c] = sum_l T[j][l] in[l][c], j < rows_out, l < r, c < ncol.
 // in and out may alias (each block stages its columns before writing).
+// accumulate != 0: out[j][c] += ... (in and out must not alias then).
 template <typename T>
 cudaError_t launch_dlr_apply(const void* Tm, int rows_out, int r, const void* in, void* out,
-                             long long ncol, cudaStream_t st);
+                             long long ncol, cudaStream_t st, int accumulate = 0);
 
 // Batched 3-D FFT of contiguous lines of N_k points (in place allowed).
 // sign = -1: X(k) = sum_R e^{-ikR} X(R); sign = +1: (1/N_k) sum_k e^{+ikR} X(k).
+// scale > 0 replaces the default factor (1 for sign -1, 1/N_k for sign +1).
 template <typename T>
 cudaError_t launch_fft3d(const FftDev& plan, int sign, const void* in, void* out, long long nlines,
-                         cudaStream_t st);
+                         cudaStream_t st, double scale = 0.0);
 
 // P[t][(ab)][(cd)][R] = -s G[t][b][c][R] Grefl[t][d][a][mR[R]]
 template <typename T>
@@ -133,6 +135,27 @@ cudaError_t launch_hf(const double2* VR, const double2* nR_in, const int* R, int
 // Local average over k: out[e] = (1/N_k) sum_k x[e][k], e < m (FP64 out).
 template <typename T>
 cudaError_t launch_k_average(const void* x, int m, int nk, double2* out, cudaStream_t st);
+
+// ---- adjoint (FP64), qa_adjoint.cu
+cudaError_t launch_dyson_g_bwd(const double2* Hk, const double2* SigHF, const double2* SigIw,
+                               const double* iw, double mu, int r, int norb, int nk,
+                               const double2* Gbar_iw, double2* SigCbar_iw, double2* Sbar,
+                               cudaStream_t st);
+cudaError_t launch_sigma_bwd(const double2* GR, const double2* SigbarR, double2* W, double2* GRbar,
+                             int r, int norb, int nk, cudaStream_t st);
+cudaError_t launch_bubble_bwd(const double2* GR, const double2* GL, const int* mR,
+                              const double2* Pbar, double2* GRbar, double2* GLbar, int r, int norb,
+                              int nk, double s, cudaStream_t st);
+cudaError_t launch_dyson_w_bwd(const double2* P, const double2* Vq, double2* Wb, double* Vqbar,
+                               int r, int npair, int nk, int* err, cudaStream_t st);
+cudaError_t launch_hf_bwd(const double2* VR, const double2* nR, const double2* X, int nV, int norb,
+                          double s, int nk, double2* VbarHF, double2* nbarR, cudaStream_t st);
+cudaError_t launch_nbar_k(const double2* nbarR, const int* R, int nV1, int np, int nk, int n1,
+                          int n2, int n3, double2* nbk, cudaStream_t st);
+cudaError_t launch_add_dw_nbar(double2* Gbar_iw, const double2* dw, const double2* nbar, int r,
+                               int np, int nk, cudaStream_t st);
+cudaError_t launch_axpy(double2* y, const double2* x, double a, long long n, cudaStream_t st);
+cudaError_t launch_scale(double2* y, double a, long long n, cudaStream_t st);
 
 // Host copies a density call needs (valid for the context's lifetime).
 int density_tables(const ::qa_ctx* ctx, const std::complex<double>** dtau, int* r, int* norb,

@@ -22,7 +22,8 @@ QA_P_QNU, QA_WC_RTAU, QA_SIGC_KTAU, QA_SIGC_KIW, QA_SIGHF_K, QA_G0, QA_HK, QA_MU
 
 EXPORTED = ["qa_create", "qa_workspace_size", "qa_bind", "qa_get_grid", "qa_get_plan",
             "qa_get_sizes", "qa_gw_step", "qa_density", "qa_density_static", "qa_get",
-            "qa_set_timing", "qa_destroy", "qa_strerror"]
+            "qa_set_timing", "qa_set_mu", "qa_set_params", "qa_gw_backward", "qa_destroy",
+            "qa_strerror"]
 
 STAGES = ["hartree_fock", "g_to_R", "bubble", "fft_R_to_q", "dlr_tau_to_nu", "dyson_w",
           "dlr_nu_to_tau", "fft_q_to_R", "sigma", "sigma_to_k_iw", "mu_search", "dyson_g"]
@@ -77,6 +78,9 @@ def load(path: str = LIB_PATH):
     L.qa_density_static.argtypes = [vp, vp, vp, C.POINTER(d), vp]
     L.qa_get.argtypes = [vp, i, vp, sz, vp]
     L.qa_set_timing.argtypes = [vp, i]
+    L.qa_set_mu.argtypes = [vp, i, d]
+    L.qa_set_params.argtypes = [vp, C.POINTER(Hoppings), C.POINTER(Interaction), vp]
+    L.qa_gw_backward.argtypes = [vp, vp, d, vp, vp, vp, vp, vp, vp, vp]
     L.qa_destroy.argtypes = [vp]
     L.qa_destroy.restype = None
     L.qa_strerror.argtypes = [i]
@@ -117,17 +121,7 @@ class Problem:
         self.precision = {"fp64": QA_FP64, "mixed": QA_MIXED}[precision]
         self._keep = []
         lat = Lattice((C.c_int * 3)(*[int(v) for v in model.n]), int(model.norb), int(model.s_spin))
-        hR = _as(model.hop_R, np.int32)
-        ht = _as(np.asarray(model.hop_t, dtype=np.complex128).view(np.float64), np.float64)
-        he = _as(model.eps, np.float64)
-        vR = _as(model.V_R, np.int32)
-        vV = _as(np.asarray(model.V, dtype=np.complex128).view(np.float64), np.float64)
-        self._keep += [hR, ht, he, vR, vV]
-        hop = Hoppings(len(hR), hR.ctypes.data_as(C.POINTER(C.c_int)),
-                       ht.ctypes.data_as(C.POINTER(C.c_double)),
-                       he.ctypes.data_as(C.POINTER(C.c_double)))
-        inter = Interaction(len(vR), vR.ctypes.data_as(C.POINTER(C.c_int)),
-                            vV.ctypes.data_as(C.POINTER(C.c_double)))
+        hop, inter = self._structs(model)
         ctx = C.c_void_p()
         _check(L.qa_create(C.byref(lat), C.byref(hop), C.byref(inter), float(model.beta),
                            float(model.Lambda), float(model.eps_dlr), float(model.filling),
@@ -137,6 +131,20 @@ class Problem:
         _check(L.qa_get_sizes(ctx, C.byref(nk), C.byref(no), C.byref(r)), "qa_get_sizes")
         self.nk, self.norb, self.r = nk.value, no.value, r.value
         self.npair = self.norb * self.norb
+
+    def _structs(self, model):
+        hR = _as(model.hop_R, np.int32)
+        ht = _as(np.asarray(model.hop_t, dtype=np.complex128).view(np.float64), np.float64)
+        he = _as(model.eps, np.float64)
+        vR = _as(model.V_R, np.int32)
+        vV = _as(np.asarray(model.V, dtype=np.complex128).view(np.float64), np.float64)
+        self._keep = [hR, ht, he, vR, vV]
+        hop = Hoppings(len(hR), hR.ctypes.data_as(C.POINTER(C.c_int)),
+                       ht.ctypes.data_as(C.POINTER(C.c_double)),
+                       he.ctypes.data_as(C.POINTER(C.c_double)))
+        inter = Interaction(len(vR), vR.ctypes.data_as(C.POINTER(C.c_int)),
+                            vV.ctypes.data_as(C.POINTER(C.c_double)))
+        return hop, inter
 
     def grid(self) -> dict:
         r = self.r
@@ -220,6 +228,33 @@ class Context(Problem):
         if timing:
             stats["stage_ms"] = dict(zip(STAGES, list(st.stage_ms)[:len(STAGES)]))
         return G_out, mu.value, n.view(np.complex128).reshape(self.norb, self.norb), stats
+
+    def set_mu(self, mu=None):
+        """Hold mu fixed at `mu` for later steps (None: search again)."""
+        _check(load().qa_set_mu(self.ctx, 0 if mu is None else 1, 0.0 if mu is None else float(mu)),
+               "qa_set_mu")
+
+    def set_params(self, model):
+        """Replace t(R), eps and V(R) (same R lists as at creation)."""
+        hop, inter = self._structs(model)
+        _check(load().qa_set_params(self.ctx, C.byref(hop), C.byref(inter), self._stream()),
+               "qa_set_params")
+        self.model = model
+
+    def backward(self, G_in, mu, Gbar_out=None, Sigbar=None, nbar=None, want_gin=True):
+        """Adjoint of one step at fixed mu; returns (Gbar_in, grad_t, grad_V)."""
+        no, npair = self.norb, self.npair
+        nH, nV = len(self.model.hop_R), len(self.model.V_R)
+        gt = np.zeros(2 * nH * no * no)
+        gV = np.zeros(2 * max(nV, 1) * npair * npair)
+        Gb = self.new_g() if want_gin else None
+        nb = None if nbar is None else np.ascontiguousarray(np.asarray(nbar, np.complex128)).view(np.float64)
+        ptr = lambda t: None if t is None else t.data_ptr()
+        _check(load().qa_gw_backward(self.ctx, ptr(G_in), float(mu), ptr(Gbar_out), ptr(Sigbar),
+                                     None if nb is None else nb.ctypes.data, ptr(Gb), gt.ctypes.data,
+                                     gV.ctypes.data, self._stream()), "qa_gw_backward")
+        return (Gb, gt.view(np.complex128).reshape(nH, no, no),
+                gV.view(np.complex128)[:nV * npair * npair].reshape(nV, npair, npair))
 
     def density(self, G):
         n = np.zeros(2 * self.norb * self.norb)

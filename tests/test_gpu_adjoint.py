@@ -1,0 +1,170 @@
+"""The hand-written adjoint (qa_gw_backward) against central finite differences.
+
+Loss: L = Re<C_G, G_out> + Re<C_S, Sigma^C(k, tau)> + Re<c_n, n_local> with seeded
+random cotangents (<a, b> = sum conj(a) b), mu held at the forward value.
+Directional derivatives along seeded random directions in the hopping
+amplitudes t(R) (Hermitian pairs t(R), t(-R) moved together), in U and J of
+the Kanamori interaction, and in G_in are compared with central differences
+(h = 1e-5) of (a) the GPU FP64 forward and (b) the CPU oracle, within 1e-6
+relative.
+"""
+import copy
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import gw
+
+pytestmark = pytest.mark.gpu
+H = 1e-5
+TOL = 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_22223_gb300 import build
+    build()
+
+
+def hop_direction(model, rng):
+    """Random Hermitian-consistent perturbation of the listed t(R)."""
+    idx = {tuple(R): i for i, R in enumerate(model.hop_R)}
+    D = np.zeros_like(model.hop_t)
+    done = set()
+    for i, R in enumerate(model.hop_R):
+        if i in done:
+            continue
+        j = idx[tuple(-R)]
+        X = rng.normal(size=D.shape[1:]) + 1j * rng.normal(size=D.shape[1:])
+        if i == j:
+            X = 0.5 * (X + X.conj().T)
+            np.fill_diagonal(X, 0)
+        D[i] = X
+        D[j] = X.conj().T if i != j else X
+        done |= {i, j}
+    return D
+
+
+def kanamori_dV(model, which):
+    """dV/dU or dV/dJ of the on-site Kanamori block (U' = U - 2J)."""
+    no = model.norb
+    eU = wl.kanamori_local(no, 1.0, 0.0, 0.0)          # V_(aa),(aa)
+    eUp = wl.kanamori_local(no, 0.0, 0.0, 1.0)         # V_(aa),(cc), a != c
+    eJ = wl.kanamori_local(no, 0.0, 1.0, 0.0)          # exchange + pair hopping
+    d = eU + eUp if which == "U" else eJ - 2.0 * eUp
+    dV = np.zeros_like(model.V)
+    i0 = [i for i, R in enumerate(model.V_R) if not np.any(R)][0]
+    dV[i0] = d
+    return dV
+
+
+def perturbed(model, dt=None, dV=None, h=0.0):
+    m = copy.deepcopy(model)
+    if dt is not None:
+        m.hop_t = model.hop_t + h * dt
+    if dV is not None:
+        m.V = model.V + h * dV
+    return m
+
+
+@pytest.mark.parametrize("name", ["peierls-3x3", "five-orbital-4x3x2"])
+def test_adjoint_matches_finite_differences(name):
+    import torch
+    from paper_2604_22223_gb300 import qa
+    model = wl.config(name)
+    rng = np.random.default_rng(11)
+    ctx = qa.Context(model, "fp64")
+    G0 = ctx.get(qa.QA_G0)
+    _, mu, _, _ = ctx.step(G0)
+    ctx.set_mu(mu)                      # frozen mu for the forward evaluations below
+    shape = tuple(G0.shape)
+    CG = torch.from_numpy(rng.normal(size=shape) + 1j * rng.normal(size=shape)).cuda()
+    CS = torch.from_numpy(rng.normal(size=shape) + 1j * rng.normal(size=shape)).cuda()
+    cn = rng.normal(size=(model.norb, model.norb)) + 1j * rng.normal(size=(model.norb, model.norb))
+
+    def loss_gpu(m, G_in):
+        ctx.set_params(m)
+        G, _, n, _ = ctx.step(G_in)
+        S = ctx.get(qa.QA_SIGC_KTAU)
+        return float(torch.sum(CG.conj() * G).real + torch.sum(CS.conj() * S).real) + \
+            float(np.sum(np.conj(cn) * n).real)
+
+    Gb, gt, gV = ctx.backward(G0, mu, CG, CS, cn)
+    # directions
+    dt = hop_direction(model, rng)
+    dG = torch.from_numpy(rng.normal(size=shape) + 1j * rng.normal(size=shape)).cuda() * 1e-2
+    adj = {
+        "t": float(np.sum(np.conj(gt) * dt).real),
+        "U": float(np.sum(np.conj(gV) * kanamori_dV(model, "U")).real),
+        "J": float(np.sum(np.conj(gV) * kanamori_dV(model, "J")).real),
+        "G": float(torch.sum(Gb.conj() * dG).real),
+    }
+    fd = {
+        "t": (loss_gpu(perturbed(model, dt=dt, h=H), G0) - loss_gpu(perturbed(model, dt=dt, h=-H), G0)) / (2 * H),
+        "U": (loss_gpu(perturbed(model, dV=kanamori_dV(model, "U"), h=H), G0)
+              - loss_gpu(perturbed(model, dV=kanamori_dV(model, "U"), h=-H), G0)) / (2 * H),
+        "J": (loss_gpu(perturbed(model, dV=kanamori_dV(model, "J"), h=H), G0)
+              - loss_gpu(perturbed(model, dV=kanamori_dV(model, "J"), h=-H), G0)) / (2 * H),
+    }
+    fd["G"] = (loss_gpu(model, G0 + H * dG) - loss_gpu(model, G0 - H * dG)) / (2 * H)
+    for k in adj:
+        assert abs(adj[k] - fd[k]) <= TOL * max(1.0, abs(fd[k])), (k, adj[k], fd[k])
+
+    # the oracle's FP64 gradient by its own central differences (frozen mu)
+    d = gw.make_dlr(model)
+    G0_or, _ = gw.g0(model, d)
+    CGo = np.moveaxis(CG.cpu().numpy(), -1, 0)
+    CSo = np.moveaxis(CS.cpu().numpy(), -1, 0)
+
+    def loss_or(m):
+        o = gw.gw_step(m, d, G0_or, mu_fixed=mu)
+        return float(np.sum(np.conj(CGo) * o["G_ktau"]).real + np.sum(np.conj(CSo) * o["sigc_ktau"]).real
+                     + np.sum(np.conj(cn) * o["n_local"]).real)
+
+    fd_or_t = (loss_or(perturbed(model, dt=dt, h=H)) - loss_or(perturbed(model, dt=dt, h=-H))) / (2 * H)
+    dU = kanamori_dV(model, "U")
+    fd_or_U = (loss_or(perturbed(model, dV=dU, h=H)) - loss_or(perturbed(model, dV=dU, h=-H))) / (2 * H)
+    assert abs(adj["t"] - fd_or_t) <= TOL * max(1.0, abs(fd_or_t)), (adj["t"], fd_or_t)
+    assert abs(adj["U"] - fd_or_U) <= TOL * max(1.0, abs(fd_or_U)), (adj["U"], fd_or_U)
+
+
+def test_unrolled_autograd_density_gradient():
+    """Gradient of the density after 3 checkpointed iterations w.r.t. the hoppings,
+    through torch.autograd, against central differences of the same loop."""
+    import torch
+    from paper_2604_22223_gb300 import qa
+    from paper_2604_22223_gb300.autograd import GWStep
+    model = wl.config("peierls-3x3")
+    ctx = qa.Context(model, "fp64")
+    rng = np.random.default_rng(5)
+    cn = rng.normal(size=(model.norb, model.norb))
+    mus = []
+    G = ctx.get(qa.QA_G0)
+    for _ in range(3):                  # forward once to fix the mu of every iteration
+        G, mu, _, _ = ctx.step(G)
+        mus.append(mu)
+
+    def loop(m, grad=False):
+        ctx.set_params(m)
+        t = torch.tensor(m.hop_t, requires_grad=grad)
+        V = torch.tensor(m.V, requires_grad=grad)
+        G = ctx.get(qa.QA_G0)
+        n = None
+        for i in range(3):
+            ctx.set_mu(mus[i])
+            G, S, n = GWStep.apply(G, t, V, ctx)
+        L = torch.sum(torch.from_numpy(cn) * n.real)
+        return L, t
+
+    L, t = loop(model, grad=True)
+    L.backward()
+    dt = hop_direction(model, rng)
+    adj = float(np.sum(np.conj(t.grad.numpy()) * dt).real)
+    Lp, _ = loop(perturbed(model, dt=dt, h=H))
+    Lm, _ = loop(perturbed(model, dt=dt, h=-H))
+    fd = (float(Lp) - float(Lm)) / (2 * H)
+    assert abs(adj - fd) <= TOL * max(1.0, abs(fd)), (adj, fd)
