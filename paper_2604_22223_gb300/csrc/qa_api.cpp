@@ -7,6 +7,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -104,6 +105,11 @@ struct qa_ctx {
   double2* d_Vbar = nullptr;
   double2* d_nbar = nullptr;
   int nH_user = 0;
+  // tensor-core DLR operands (mixed contexts)
+  bool use_tc = false;
+  std::vector<uint16_t> tc_Ttn, tc_Tnt;
+  void* d_tc_Ttn = nullptr;
+  void* d_tc_Tnt = nullptr;
 };
 
 namespace {
@@ -189,6 +195,10 @@ size_t layout(qa_ctx* c, char* base) {
   c->d_err = static_cast<int*>(take(4));
   c->d_bad = static_cast<long long*>(take(8));
   c->d_nloc = static_cast<double2*>(take(no2 * 16));
+  if (c->precision == QA_MIXED && c->use_tc) {
+    c->d_tc_Ttn = take(c->tc_Ttn.size() * 2);
+    c->d_tc_Tnt = take(c->tc_Tnt.size() * 2);
+  }
   if (c->precision == QA_FP64) {
     c->tH.Trefl = take(rr * 16);
     c->tH.Ttn = take(rr * 16);
@@ -446,11 +456,17 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
   tm.mark();  // 2: bubble
   QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, -1, c->d_P, c->d_P, ncb / nk * r, st));
   tm.mark();  // 3: FFT R -> q
-  QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Ttn, r, r, c->d_P, c->d_P, ncb, st));
+  if (sizeof(T) == 4 && c->use_tc)
+    QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Ttn, r, c->d_P, c->d_P, ncb, c->d_err, st));
+  else
+    QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Ttn, r, r, c->d_P, c->d_P, ncb, st));
   tm.mark();  // 4: DLR tau -> nu
   QA_LAUNCH(c, 1, qa::launch_dyson_w<T>(c->d_P, c->d_Vq, c->d_W, r, c->npair, nk, c->d_err, c->d_bad, st));
   tm.mark();  // 5: Dyson W
-  QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Tnt, r, r, c->d_W, c->d_W, ncb, st));
+  if (sizeof(T) == 4 && c->use_tc)
+    QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Tnt, r, c->d_W, c->d_W, ncb, c->d_err, st));
+  else
+    QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Tnt, r, r, c->d_W, c->d_W, ncb, st));
   tm.mark();  // 6: DLR nu -> tau
   QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, +1, c->d_W, c->d_W, ncb / nk * r, st));
   tm.mark();  // 7: FFT q -> R
@@ -706,6 +722,14 @@ int qa_create(const qa_lattice* lat, const qa_hoppings* hop, const qa_interactio
   if (qa::build_dlr(Lambda, eps, &c->grid) != 0) { delete c; return QA_EINVAL; }
   c->r = c->grid.r;
   qa::build_dlr_matrices(c->grid, beta, &c->mats);
+  if (precision == QA_MIXED && qa::dlr_tc_supported(c->r, nullptr)) {
+    const char* env = std::getenv("QA_DLR_SIMT");
+    c->use_tc = !(env && env[0] == '1');
+    if (c->use_tc) {
+      qa::pack_dlr_tc(c->mats.Ttn.data(), c->r, &c->tc_Ttn);
+      qa::pack_dlr_tc(c->mats.Tnt.data(), c->r, &c->tc_Tnt);
+    }
+  }
   // FFT plans and the -R map
   for (int d = 0; d < 3; ++d) qa::plan_fft_axis(c->n[d], &c->ax[d], &c->pos[d]);
   c->mR.resize(c->nk);
@@ -753,6 +777,10 @@ int qa_bind(qa_ctx* c, void* workspace, size_t bytes, void* stream) {
   QA_TRY(upload_c<float>(c->t32.dtau, m.dtau, st));
   QA_TRY(upload_c<float>(c->t32.dw, m.dw, st));
   QA_TRY(cudaMemcpyAsync(c->d_iw, m.iw.data(), r * 8, cudaMemcpyHostToDevice, st));
+  if (c->use_tc) {
+    QA_TRY(cudaMemcpyAsync(c->d_tc_Ttn, c->tc_Ttn.data(), c->tc_Ttn.size() * 2, cudaMemcpyHostToDevice, st));
+    QA_TRY(cudaMemcpyAsync(c->d_tc_Tnt, c->tc_Tnt.data(), c->tc_Tnt.size() * 2, cudaMemcpyHostToDevice, st));
+  }
   if (c->precision == QA_FP64) {
     auto ctrans = [r](const std::vector<cd>& T) {
       std::vector<cd> H(T.size());

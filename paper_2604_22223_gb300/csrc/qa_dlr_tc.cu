@@ -1,0 +1,389 @@
+// DLR node transforms of the big tensors on the 5th-generation tensor cores
+// (tcgen05, sm_103a), FP32 data with split-bf16 operands and FP32 accumulation.
+//
+// The complex transform out[j][c] = sum_l T[j][l] in[l][c] of every column c
+// is one real GEMM  Y (cols x 2r) = X (cols x 2r) * Tt^T (2r x 2r), where
+// X[c][(l,re/im)] are the interleaved input values and Tt is the real
+// embedding [[Re T, -Im T], [Im T, Re T]] of T.  Every operand is split into
+// three bf16 pieces (x = x0 + x1 + x2, ~24 significant bits) and the six
+// leading cross products x_i t_j (i + j <= 2) accumulate in FP32 in tensor
+// memory, which keeps the FP32-level accuracy of the SIMT kernel.
+//
+// One persistent CTA per SM (128 threads): the three Tt pieces stay resident
+// in shared memory (K-major canonical layout, no swizzle); each 128-column
+// tile of X streams through double-buffered K-chunks of 16 (8 nodes x re/im)
+// that all threads convert to bf16 pieces while the previous chunk's six
+// MMAs run; one thread issues tcgen05.mma (M = 128, N = 2r padded to 16,
+// K = 16) into a 128 x N FP32 accumulator in TMEM; the epilogue reads it
+// back with tcgen05.ld (warp w <-> TMEM lanes 32w..32w+31, thread <-> column)
+// and stores Y in place of X.  Every mbarrier wait is bounded; on time-out
+// the kernel records QA_ETIMEOUT, waits (bounded) for its own MMAs, frees
+// TMEM and returns.
+#include <cuda_bf16.h>
+
+#include <cstring>
+#include <vector>
+
+#include "qa_common.cuh"
+
+namespace qa {
+namespace {
+
+constexpr int kTcThreads = 128;
+constexpr int kTileM = 128;
+constexpr int kChunkK = 16;
+constexpr uint32_t kTmemCols = 256;
+constexpr long long kWaitLimit = 1ll << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait; returns false on time-out
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (long long i = 0; i < kWaitLimit; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// shared-memory matrix descriptor: K-major, no swizzle; LBO = byte stride of
+// core matrices along K, SBO = byte stride along M/N (core = 8 rows x 16 B)
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((addr >> 4) & 0x3FFF);
+  d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFF) << 16;
+  d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFF) << 32;
+  d |= 1ull << 46;                                  // descriptor version for tcgen05
+  return d;                                         // base offset 0, swizzle none
+}
+
+// instruction descriptor: kind::f16 with BF16 A/B, FP32 D, both K-major
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t taddr, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(taddr),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void split3(float x, uint16_t& h0, uint16_t& h1, uint16_t& h2) {
+  __nv_bfloat16 b0 = __float2bfloat16_rn(x);
+  float r1 = x - __bfloat162float(b0);
+  __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
+  float r2 = r1 - __bfloat162float(b1);
+  __nv_bfloat16 b2 = __float2bfloat16_rn(r2);
+  h0 = __bfloat16_as_ushort(b0);
+  h1 = __bfloat16_as_ushort(b1);
+  h2 = __bfloat16_as_ushort(b2);
+}
+
+struct TcArgs {
+  const uint4* Bsplit;   // 3 pieces x Np x Kp bf16 in the canonical layout
+  int Np, Kp, r;
+  const float2* in;
+  float2* out;
+  long long ncol;
+  int* err;
+};
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+constexpr int kHalfMax = 96;            // accumulator columns per thread (Np <= 192)
+
+// 256 threads: thread (w, lane) owns TMEM lane / tile row m = 32 (w % 4) + lane
+// and half h = w / 4 of the accumulator columns and of each chunk's 8 nodes.
+// Each K-chunk's six MMAs go to a fresh accumulator (two alternate in TMEM),
+// which is drained into FP32 registers with round-to-nearest adds while the
+// next chunk's MMAs run, so the tensor core never sums more than 96 products.
+__global__ void __launch_bounds__(2 * kTcThreads, 1) dlr_tc_kernel(TcArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m = 32 * (warp & 3) + lane;
+  const int half = warp >> 2;
+  const uint32_t bpiece = static_cast<uint32_t>(a.Np) * a.Kp * 2;    // bytes of one Tt piece
+  uint8_t* Bs = smem;
+  uint8_t* As = smem + 3 * bpiece;                                    // [2 buffers][3 pieces][4096 B]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(As + 2 * 3 * kTileM * kChunkK * 2);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  __shared__ int s_abort;
+
+  for (uint32_t i = tid; i < 3 * bpiece / 16; i += blockDim.x)
+    reinterpret_cast<uint4*>(Bs)[i] = a.Bsplit[i];
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tslot)),
+                 "r"(2 * kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t taddr = *tslot;
+  const uint32_t idesc = instr_desc(kTileM, a.Np);
+  const int nchunk = a.Kp / kChunkK;
+  const uint32_t bsbo = static_cast<uint32_t>(a.Kp / 8) * 128;
+  const long long ntiles = (a.ncol + kTileM - 1) / kTileM;
+  const int nodes = a.r;
+  const int nh = a.Np / 2;                           // accumulator columns of this thread
+  const uint32_t lane_base = static_cast<uint32_t>(32 * (warp & 3)) << 16;
+  const uint32_t roff = static_cast<uint32_t>(m >> 3) * 256 + static_cast<uint32_t>(m & 7) * 16 +
+                        static_cast<uint32_t>(half) * 128;
+  long long g = 0;                                   // global chunk counter
+  bool ok = true;
+  const int pa[6] = {0, 0, 1, 0, 1, 2};
+  const int pb[6] = {0, 1, 0, 2, 1, 0};
+
+  for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const long long col = tile * kTileM + m;
+    const bool colok = col < a.ncol;
+    float acc[kHalfMax];
+#pragma unroll
+    for (int i = 0; i < kHalfMax; ++i) acc[i] = 0.f;
+    // register prefetch two chunks ahead: this thread's 4 nodes of a chunk
+    float2 xn[4], xnn[4];
+    auto load_chunk = [&](int ch, float2* dst) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int l = ch * 8 + half * 4 + e;
+        dst[e] = (colok && ch < nchunk && l < nodes) ? a.in[static_cast<long long>(l) * a.ncol + col]
+                                                     : make_float2(0.f, 0.f);
+      }
+    };
+    auto drain = [&](long long gd) {
+      // wait for chunk gd's MMAs and add its accumulator into registers
+      bool w = mbar_wait(&bar[gd & 1], static_cast<uint32_t>((gd >> 1) & 1));
+      tc_fence_after();
+      const uint32_t dcol = static_cast<uint32_t>((gd & 1) * kTmemCols + half * nh);
+#pragma unroll
+      for (int c8 = 0; c8 < kHalfMax / 8; ++c8) {
+        if (c8 * 8 < nh) {
+          float v[8];
+          tmem_ld8(taddr + lane_base + dcol + static_cast<uint32_t>(c8 * 8), v);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) acc[c8 * 8 + i] += v[i];
+        }
+      }
+      tc_fence_before();
+      return w;
+    };
+    load_chunk(0, xn);
+    load_chunk(1, xnn);
+    for (int ch = 0; ch < nchunk; ++ch, ++g) {
+      const int b = static_cast<int>(g & 1);
+      // (chunk g-2's MMAs were drained in the previous iteration, so buffer b is free)
+      float2 cur[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) { cur[e] = xn[e]; xn[e] = xnn[e]; }
+      load_chunk(ch + 2, xnn);
+      uint16_t h[3][8];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        split3(cur[e].x, h[0][2 * e], h[1][2 * e], h[2][2 * e]);
+        split3(cur[e].y, h[0][2 * e + 1], h[1][2 * e + 1], h[2][2 * e + 1]);
+      }
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        uint4 v;
+        v.x = h[p][0] | (static_cast<uint32_t>(h[p][1]) << 16);
+        v.y = h[p][2] | (static_cast<uint32_t>(h[p][3]) << 16);
+        v.z = h[p][4] | (static_cast<uint32_t>(h[p][5]) << 16);
+        v.w = h[p][6] | (static_cast<uint32_t>(h[p][7]) << 16);
+        *reinterpret_cast<uint4*>(As + (b * 3 + p) * (kTileM * kChunkK * 2) + roff) = v;
+      }
+      fence_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t dcol = static_cast<uint32_t>(b) * kTmemCols;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+          const uint32_t aaddr = smem_u32(As + (b * 3 + pa[q]) * (kTileM * kChunkK * 2));
+          const uint32_t baddr = smem_u32(Bs + pb[q] * bpiece) + static_cast<uint32_t>(ch) * 256;
+          mma_bf16(taddr + dcol, smem_desc(aaddr, 128, 256), smem_desc(baddr, 128, bsbo), idesc,
+                   q > 0 ? 1u : 0u);
+        }
+        mma_commit(&bar[b]);
+      }
+      if (ch > 0) {
+        bool w = drain(g - 1);
+        if (__syncthreads_or(!w)) { ok = false; break; }
+      }
+    }
+    if (!ok) break;
+    {
+      bool w = drain(g - 1);                         // the tile's last chunk
+      if (__syncthreads_or(!w)) { ok = false; break; }
+    }
+    if (colok) {
+#pragma unroll
+      for (int i = 0; i < kHalfMax; i += 2) {
+        const int j = (half * nh + i) >> 1;
+        if (i < nh && j < nodes)
+          a.out[static_cast<long long>(j) * a.ncol + col] = make_float2(acc[i], acc[i + 1]);
+      }
+    }
+  }
+  if (!ok && tid == 0) {
+    atomicCAS(a.err, 0, QA_ETIMEOUT_CODE);
+    s_abort = 1;
+  }
+  __syncthreads();
+  if (s_abort && g > 0) {
+    // let this CTA's own MMAs finish (bounded) before TMEM is released
+    const long long gl = g - 1;
+    mbar_wait(&bar[gl & 1], static_cast<uint32_t>((gl >> 1) & 1));
+    __syncthreads();
+  }
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr),
+                 "r"(2 * kTmemCols)
+                 : "memory");
+}
+
+uint16_t bf16_rn(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  if ((u & 0x7F800000u) == 0x7F800000u) return static_cast<uint16_t>(u >> 16);   // inf / nan
+  uint32_t rounding = 0x7FFFu + ((u >> 16) & 1u);
+  return static_cast<uint16_t>((u + rounding) >> 16);
+}
+double bf16_val(uint16_t h) {
+  uint32_t u = static_cast<uint32_t>(h) << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+}  // namespace
+
+bool dlr_tc_supported(int r, size_t* smem_bytes) {
+  const int Kp = ((2 * r + 15) / 16) * 16;
+  const size_t bytes = 3ull * Kp * Kp * 2 + 2ull * 3 * kTileM * kChunkK * 2 + 2 * 8 + 16;
+  if (smem_bytes) *smem_bytes = bytes;
+  return Kp <= 192 && bytes <= 227 * 1024;
+}
+
+// Real embedding of the complex r x r matrix T, split into three bf16 pieces,
+// laid out K-major (n = output index 2j + c', k = input index 2l + c) in the
+// canonical no-swizzle core-matrix order.  dst has 3 * Kp * Kp uint16 entries.
+void pack_dlr_tc(const std::complex<double>* T, int r, std::vector<uint16_t>* dst) {
+  const int Kp = ((2 * r + 15) / 16) * 16, Np = Kp;
+  dst->assign(3ull * Np * Kp, 0);
+  for (int n = 0; n < 2 * r; ++n)
+    for (int k = 0; k < 2 * r; ++k) {
+      const int j = n >> 1, cp = n & 1, l = k >> 1, c = k & 1;
+      const std::complex<double> t = T[static_cast<size_t>(j) * r + l];
+      double x;
+      if (cp == 0) x = c == 0 ? t.real() : -t.imag();
+      else x = c == 0 ? t.imag() : t.real();
+      const size_t off = static_cast<size_t>(n / 8) * (Kp / 8) * 64 + static_cast<size_t>(k / 8) * 64 +
+                         static_cast<size_t>(n % 8) * 8 + (k % 8);
+      double rem = x;
+      for (int p = 0; p < 3; ++p) {
+        uint16_t h = bf16_rn(static_cast<float>(rem));
+        (*dst)[static_cast<size_t>(p) * Np * Kp + off] = h;
+        rem -= bf16_val(h);
+      }
+    }
+}
+
+cudaError_t launch_dlr_tc(const void* Bsplit, int r, const void* in, void* out, long long ncol,
+                          int* err, cudaStream_t st) {
+  size_t smem = 0;
+  if (!dlr_tc_supported(r, &smem)) return cudaErrorInvalidValue;
+  if (ncol <= 0) return cudaSuccess;
+  cudaError_t e = set_smem(reinterpret_cast<const void*>(&dlr_tc_kernel), smem, true);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const long long ntiles = (ncol + kTileM - 1) / kTileM;
+  const int grid = static_cast<int>(ntiles < sms ? ntiles : sms);
+  TcArgs a;
+  a.Bsplit = reinterpret_cast<const uint4*>(Bsplit);
+  a.Kp = ((2 * r + 15) / 16) * 16;
+  a.Np = a.Kp;
+  a.r = r;
+  a.in = reinterpret_cast<const float2*>(in);
+  a.out = reinterpret_cast<float2*>(out);
+  a.ncol = ncol;
+  a.err = err;
+  dlr_tc_kernel<<<grid, 2 * kTcThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace qa

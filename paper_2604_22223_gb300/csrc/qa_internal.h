@@ -15,6 +15,7 @@ namespace qa {
 
 // Device-side copy of the public status code for a singular pivot.
 constexpr int QA_ESINGULAR_CODE = 3;
+constexpr int QA_ETIMEOUT_CODE = 6;
 
 // ------------------------------------------------------------------- DLR
 // Discrete Lehmann representation (Kaye, Chen & Parcollet, PRB 105, 235115
@@ -75,6 +76,13 @@ struct FftDev {            // passed by value to the FFT kernel
 template <typename T>
 cudaError_t launch_dlr_apply(const void* Tm, int rows_out, int r, const void* in, void* out,
                              long long ncol, cudaStream_t st, int accumulate = 0);
+
+// Tensor-core (tcgen05) DLR transform of FP32 complex columns, in place allowed.
+// Bsplit: the packed operand of pack_dlr_tc.  Supported when 2r <= 186.
+bool dlr_tc_supported(int r, size_t* smem_bytes);
+void pack_dlr_tc(const std::complex<double>* T, int r, std::vector<uint16_t>* dst);
+cudaError_t launch_dlr_tc(const void* Bsplit, int r, const void* in, void* out, long long ncol,
+                          int* err, cudaStream_t st);
 
 // Batched 3-D FFT of contiguous lines of N_k points (in place allowed).
 // sign = -1: X(k) = sum_R e^{-ikR} X(R); sign = +1: (1/N_k) sum_k e^{+ikR} X(k).
