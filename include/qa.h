@@ -102,7 +102,8 @@ typedef struct {
 /* Per-step report. */
 typedef struct {
   double mu;            /* chemical potential after the step                   */
-  double N;             /* electrons per cell at mu                            */
+  double N;             /* electrons per cell at mu (mixed path: the FP64
+                           density, linearised over the final Newton step)     */
   int mu_evals;         /* density evaluations used by the mu search           */
   int status;           /* QA_OK or the first error code seen                  */
   long long first_bad;  /* first failing system index (nu*N_k + q) or -1       */

@@ -273,8 +273,9 @@ int mu_search(qa_ctx* c, const double2* SigHF, const void* SigIw, const DevTable
   const double wid = h[0] + 1.0 + 10.0 / c->beta;
   const double target = c->filling;
   const bool fp64 = sizeof(T) == 8;
-  const double tolN = (fp64 ? 1e-12 : 1e-6) * std::max(1.0, target);
-  auto tolB = [&](double m) { return (fp64 ? 2e-13 : 1e-9) * std::max(1.0, std::fabs(m)); };
+  // FP32 densities carry ~1e-6 relative noise: stop at that level on the mixed path
+  const double tolN = (fp64 ? 1e-12 : 2e-6) * std::max(1.0, target);
+  auto tolB = [&](double m) { return (fp64 ? 2e-13 : 2e-7) * std::max(1.0, std::fabs(m)); };
   int count = 0;
   double N = 0, dN = 0;
   auto ev = [&](double m, double* f, double* d) -> int {
@@ -343,6 +344,28 @@ int mu_search(qa_ctx* c, const double2* SigHF, const void* SigIw, const DevTable
       rc = ev(mu, &f, &d);
       if (rc != QA_OK) return rc;
       if (it == 199 && std::fabs(f) > tolN) return QA_ENOCONV;
+    }
+  }
+  if (!fp64) {
+    // one FP64 evaluation at the FP32 root (FP64 inverse of the stored Sigma)
+    // and a Newton correction: removes the FP32 density noise from mu
+    QA_LAUNCH(c, 1, qa::launch_dyson_g_f64_sig32(c->d_Hk, SigHF, SigIw, c->t64.dw, c->d_iw, mu, c->r,
+                                                 c->norb, c->nk, c->d_part, c->nblocks_g, c->d_err,
+                                                 st));
+    QA_LAUNCH(c, 1, qa::launch_reduce_pairs(c->d_part, c->nblocks_g, 0, c->d_red, st));
+    double h2[2];
+    QA_TRY(cudaMemcpyAsync(h2, c->d_red, 16, cudaMemcpyDeviceToHost, st));
+    QA_TRY(cudaStreamSynchronize(st));
+    ++count;
+    const double N64 = c->nspin * h2[0] / c->nk;
+    const double d64 = -c->nspin * h2[1] / c->nk;
+    N = N64;
+    if (std::isfinite(N64) && d64 > 0) {
+      const double step = (N64 - target) / d64;
+      if (std::fabs(step) < 1e-3 * std::max(1.0, std::fabs(mu))) {
+        mu -= step;
+        N = N64 - step * d64;     // FP64 density linearised over the correction
+      }
     }
   }
   *evals = count;

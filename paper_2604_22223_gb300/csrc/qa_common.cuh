@@ -63,7 +63,7 @@ __device__ __forceinline__ double2 cinv(double2 a) {
   return make_double2(a.x * d, -a.y * d);
 }
 __device__ __forceinline__ float2 cinv(float2 a) {
-  float d = 1.0f / cabs2(a);
+  float d = __frcp_rn(cabs2(a));
   return make_float2(a.x * d, -a.y * d);
 }
 __device__ __forceinline__ double2 to_c64d(double2 a) { return a; }

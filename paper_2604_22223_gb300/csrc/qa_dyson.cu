@@ -267,10 +267,69 @@ __global__ void __launch_bounds__(kWarpsR * 32) dyson_w_reg_kernel(const float2*
 
 // ------------------------------------------------------------------ Dyson G
 
-template <typename T, int NO>
-__global__ void __launch_bounds__(256) dyson_g_kernel(const double2* __restrict__ Hk,
+// In-place Gauss-Jordan inverse with partial pivoting (row swaps recorded,
+// undone as column swaps at the end); every index is a compile-time constant.
+template <typename V, int NO>
+__device__ __forceinline__ bool gj_inverse(V (&a)[NO][NO]) {
+  bool bad = false;
+  int piv[NO];
+#pragma unroll
+  for (int c = 0; c < NO; ++c) {
+    int p = c;
+    auto best = cabs2(a[c][c]);
+#pragma unroll
+    for (int i = c + 1; i < NO; ++i) {
+      auto v = cabs2(a[i][c]);
+      if (v > best) { best = v; p = i; }
+    }
+    if (!(best > 0)) bad = true;
+    piv[c] = p;
+    // row swap c <-> p as branch-free selects (keeps the matrix in registers)
+#pragma unroll
+    for (int i = c + 1; i < NO; ++i) {
+      const bool sw = (i == p);
+#pragma unroll
+      for (int j = 0; j < NO; ++j) {
+        const V ti = a[i][j], tc = a[c][j];
+        a[c][j].x = sw ? ti.x : tc.x; a[c][j].y = sw ? ti.y : tc.y;
+        a[i][j].x = sw ? tc.x : ti.x; a[i][j].y = sw ? tc.y : ti.y;
+      }
+    }
+    const V inv = cinv(a[c][c]);
+    a[c][c] = cmk<V>(1.0, 0.0);
+#pragma unroll
+    for (int j = 0; j < NO; ++j) a[c][j] = cmul(a[c][j], inv);
+#pragma unroll
+    for (int i = 0; i < NO; ++i) {
+      if (i == c) continue;
+      const V f = a[i][c];
+      a[i][c] = cmk<V>(0.0, 0.0);
+#pragma unroll
+      for (int j = 0; j < NO; ++j) a[i][j] = cfms(f, a[c][j], a[i][j]);
+    }
+  }
+#pragma unroll
+  for (int c = NO - 1; c >= 0; --c) {
+#pragma unroll
+    for (int k = c + 1; k < NO; ++k) {
+      const bool sw = (piv[c] == k);
+#pragma unroll
+      for (int i = 0; i < NO; ++i) {
+        const V tk = a[i][k], tc = a[i][c];
+        a[i][c].x = sw ? tk.x : tc.x; a[i][c].y = sw ? tk.y : tc.y;
+        a[i][k].x = sw ? tc.x : tk.x; a[i][k].y = sw ? tc.y : tk.y;
+      }
+    }
+  }
+  return bad;
+}
+
+// T: arithmetic of the inverse; TS: storage type of Sigma^C(k, i w) (may be
+// narrower, e.g. the FP64 refinement of mu on the mixed path)
+template <typename T, int NO, typename TS = T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) dyson_g_kernel(const double2* __restrict__ Hk,
                                                       const double2* __restrict__ SigHF,
-                                                      const cplx<T>* __restrict__ SigIw,
+                                                      const cplx<TS>* __restrict__ SigIw,
                                                       const cplx<T>* __restrict__ dw,
                                                       const double* __restrict__ iw, double mu,
                                                       int r, int nk, cplx<T>* Giw, double* part,
@@ -284,7 +343,7 @@ __global__ void __launch_bounds__(256) dyson_g_kernel(const double2* __restrict_
        idx += static_cast<long long>(gridDim.x) * blockDim.x) {
     const int n = static_cast<int>(idx / nk);
     const int k = static_cast<int>(idx - static_cast<long long>(n) * nk);
-    V a[NO][NO], b[NO][NO];
+    V a[NO][NO];
 #pragma unroll
     for (int i = 0; i < NO; ++i)
 #pragma unroll
@@ -295,55 +354,21 @@ __global__ void __launch_bounds__(256) dyson_g_kernel(const double2* __restrict_
           h.x += s.x; h.y += s.y;
         }
         V m = from_d2<V>(make_double2(-h.x, -h.y));
-        if (SigIw) m = csub(m, SigIw[(static_cast<size_t>(n) * NO * NO + i * NO + j) * nk + k]);
+        if (SigIw)
+          m = csub(m, from_d2<V>(to_c64d(SigIw[(static_cast<size_t>(n) * NO * NO + i * NO + j) * nk + k])));
         if (i == j) { m.x += static_cast<T>(mu); m.y += static_cast<T>(iw[n]); }
         a[i][j] = m;
-        b[i][j] = cmk<V>(i == j ? 1.0 : 0.0, 0.0);
       }
-    // Gauss-Jordan with partial pivoting; all indices compile-time
-#pragma unroll
-    for (int c = 0; c < NO; ++c) {
-      int p = c;
-      T best = cabs2(a[c][c]);
-#pragma unroll
-      for (int i = c + 1; i < NO; ++i) {
-        T v = cabs2(a[i][c]);
-        if (v > best) { best = v; p = i; }
-      }
-      if (!(best > static_cast<T>(0))) bad = true;
-#pragma unroll
-      for (int i = c + 1; i < NO; ++i) {
-        if (i == p) {
-#pragma unroll
-          for (int j = 0; j < NO; ++j) {
-            V t1 = a[c][j]; a[c][j] = a[i][j]; a[i][j] = t1;
-            V t2 = b[c][j]; b[c][j] = b[i][j]; b[i][j] = t2;
-          }
-        }
-      }
-      V inv = cinv(a[c][c]);
-#pragma unroll
-      for (int j = 0; j < NO; ++j) { a[c][j] = cmul(a[c][j], inv); b[c][j] = cmul(b[c][j], inv); }
-#pragma unroll
-      for (int i = 0; i < NO; ++i) {
-        if (i == c) continue;
-        V f = a[i][c];
-#pragma unroll
-        for (int j = 0; j < NO; ++j) {
-          a[i][j] = cfms(f, a[c][j], a[i][j]);
-          b[i][j] = cfms(f, b[c][j], b[i][j]);
-        }
-      }
-    }
-    // b = G(k, i w_n)
+    bad |= gj_inverse<V, NO>(a);
+    // a = G(k, i w_n)
     double2 tr = make_double2(0, 0), tr2 = make_double2(0, 0);
 #pragma unroll
     for (int i = 0; i < NO; ++i) {
-      double2 d = to_c64d(b[i][i]);
+      double2 d = to_c64d(a[i][i]);
       tr.x += d.x; tr.y += d.y;
 #pragma unroll
       for (int j = 0; j < NO; ++j) {
-        double2 x = to_c64d(b[i][j]), y = to_c64d(b[j][i]);
+        double2 x = to_c64d(a[i][j]), y = to_c64d(a[j][i]);
         tr2.x += x.x * y.x - x.y * y.y;
         tr2.y += x.x * y.y + x.y * y.x;
       }
@@ -355,7 +380,7 @@ __global__ void __launch_bounds__(256) dyson_g_kernel(const double2* __restrict_
 #pragma unroll
       for (int i = 0; i < NO; ++i)
 #pragma unroll
-        for (int j = 0; j < NO; ++j) Giw[(static_cast<size_t>(n) * NO * NO + i * NO + j) * nk + k] = b[i][j];
+        for (int j = 0; j < NO; ++j) Giw[(static_cast<size_t>(n) * NO * NO + i * NO + j) * nk + k] = a[i][j];
     }
   }
   if (bad) atomicCAS(err, 0, QA_ESINGULAR_CODE);
@@ -454,22 +479,38 @@ cudaError_t launch_dyson_w(const void* P, const void* Vq, void* WC, int r, int n
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_dyson_g(const double2* Hk, const double2* SigHF, const void* SigIw,
-                           const void* dw, const double* iw, double mu, int r, int norb, int nk,
-                           void* Giw, double* part, int nblocks, int mode, int* err,
-                           cudaStream_t st) {
-  auto s = reinterpret_cast<const cplx<T>*>(SigIw);
+template <typename T, typename TS>
+cudaError_t launch_dyson_g_impl(const double2* Hk, const double2* SigHF, const void* SigIw,
+                                const void* dw, const double* iw, double mu, int r, int norb,
+                                int nk, void* Giw, double* part, int nblocks, int mode, int* err,
+                                cudaStream_t st) {
+  auto s = reinterpret_cast<const cplx<TS>*>(SigIw);
   auto d = reinterpret_cast<const cplx<T>*>(dw);
   auto g = reinterpret_cast<cplx<T>*>(Giw);
   switch (norb) {
 #define QA_CASE(NO) \
-    case NO: dyson_g_kernel<T, NO><<<nblocks, 256, 0, st>>>(Hk, SigHF, s, d, iw, mu, r, nk, g, part, mode, err); break;
+    case NO: dyson_g_kernel<T, NO, TS><<<nblocks, 256, 0, st>>>(Hk, SigHF, s, d, iw, mu, r, nk, g, part, mode, err); break;
     QA_CASE(1) QA_CASE(2) QA_CASE(3) QA_CASE(4) QA_CASE(5)
 #undef QA_CASE
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_dyson_g(const double2* Hk, const double2* SigHF, const void* SigIw,
+                           const void* dw, const double* iw, double mu, int r, int norb, int nk,
+                           void* Giw, double* part, int nblocks, int mode, int* err,
+                           cudaStream_t st) {
+  return launch_dyson_g_impl<T, T>(Hk, SigHF, SigIw, dw, iw, mu, r, norb, nk, Giw, part, nblocks,
+                                   mode, err, st);
+}
+
+cudaError_t launch_dyson_g_f64_sig32(const double2* Hk, const double2* SigHF, const void* SigIw,
+                                     const void* dw, const double* iw, double mu, int r, int norb,
+                                     int nk, double* part, int nblocks, int* err, cudaStream_t st) {
+  return launch_dyson_g_impl<double, float>(Hk, SigHF, SigIw, dw, iw, mu, r, norb, nk, nullptr,
+                                            part, nblocks, 0, err, st);
 }
 
 template <typename T>

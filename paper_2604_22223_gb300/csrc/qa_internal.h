@@ -116,6 +116,10 @@ cudaError_t launch_dyson_g(const double2* Hk, const double2* SigHF, const void* 
                            void* Giw, double* part, int nblocks, int mode, int* err,
                            cudaStream_t st);
 int dyson_g_blocks(int r, int nk);
+// FP64 density sums (mode 0) with Sigma^C(k, i w) stored as complex64.
+cudaError_t launch_dyson_g_f64_sig32(const double2* Hk, const double2* SigHF, const void* SigIw,
+                                     const void* dw, const double* iw, double mu, int r, int norb,
+                                     int nk, double* part, int nblocks, int* err, cudaStream_t st);
 
 // max over (k, n) of the row-sum norm of H(k) + SigHF(k) + SigIw(k, i w_n)
 template <typename T>

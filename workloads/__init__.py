@@ -190,7 +190,8 @@ def five_orbital(n=(16, 16, 1), seed=DEFAULT_SEED, U=3.0, J=0.6, Vnn=0.5, beta=4
     t(y) 25 (sig_nn), t(x+y) = t(x-y) 25 (sig_nnn), crystal field 5 uniforms in
     [-0.3, 0.3), then t(z) 25 (sig_nn) only when N3 > 1 (a simple-tetragonal
     stack).  t(-R) = t(R)^T.  Interaction: Kanamori (U, J, U' = U - 2J) on site,
-    density-density Vnn between nearest-neighbour cells (including +-z in 3-D).
+    density-density Vnn between in-plane nearest-neighbour cells (+-x, +-y), as in
+    the 2-D model; the stack adds interlayer hopping only.
     """
     norb = 5
     rng = SplitMix64(seed)
@@ -212,8 +213,6 @@ def five_orbital(n=(16, 16, 1), seed=DEFAULT_SEED, U=3.0, J=0.6, Vnn=0.5, beta=4
     hops = {k: np.asarray(v, dtype=np.complex128) for k, v in hops.items()}
     Vs = {(0, 0, 0): kanamori_local(norb, U, J)}
     nn = [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0)]
-    if three_d:
-        nn += [(0, 0, 1), (0, 0, -1)]
     for R in nn:
         Vs[R] = density_density(norb, np.full((norb, norb), Vnn))
     hop_R, hop_t, V_R, V = _finish(hops, Vs, norb)
