@@ -75,6 +75,13 @@ enum {
                          chemical potential and density accumulation         */
 };
 
+/* pair basis of the big tensors P(q, i nu) and W^C (qa_set_pair_basis) */
+enum {
+  QA_PAIRS_AUTO = 0,     /* reduced on QA_MIXED contexts, full on QA_FP64      */
+  QA_PAIRS_FULL = 1,     /* all npair^2 entries (the paper's product basis)    */
+  QA_PAIRS_REDUCED = 2   /* the rho^2 entries of the interaction subspace      */
+};
+
 typedef struct qa_ctx qa_ctx;
 
 /* Crystal: the k-grid and the orbital count (paper Sec. "Crystal"). */
@@ -120,6 +127,30 @@ typedef struct {
 int qa_create(const qa_lattice* lat, const qa_hoppings* hop, const qa_interaction* inter,
               double beta, double Lambda, double eps, double filling, int precision,
               qa_ctx** out);
+
+/* qa_set_pair_basis: choose the basis of the big tensors before qa_bind
+ * (QA_ESTATE afterwards; the workspace size depends on it).
+ * The interaction matrices V(R) all act inside one subspace of the pair space:
+ * the span of the columns of every V(R) and V(R)^H, of dimension rho (15 of 25
+ * pairs for Kanamori plus density-density interactions on five orbitals, 2 of
+ * 4 for a two-site density-density model).  With B an orthonormal basis of it,
+ * V(q) = B S(q) B^H, the Dyson equation W = V + V P W of the paper's screened
+ * interaction closes on Pt = B^H P B and S, and W^C = B Wt^C B^H exactly
+ * (up to rounding): the reduced basis carries rho^2 instead of npair^2 entries
+ * per (q, nu) through the bubble, both FFTs, both DLR maps and the Dyson solve.
+ * This is an exact instance of the rank reduction of the orbital-index
+ * contraction that the paper proposes for the O(N_orb^4) polarizability (Sec.
+ * "Results", five-orbital benchmark).  QA_PAIRS_REDUCED takes effect when
+ * 0 < rho < npair and the contraction term lists have at most 4096 entries;
+ * otherwise the full basis is used.  qa_gw_backward needs the full basis. */
+int qa_set_pair_basis(qa_ctx* ctx, int mode);
+
+/* The interaction subspace: *rho its dimension, *active 1 when the big tensors
+ * use it, B (may be NULL) [npair][rho] complex (interleaved doubles), the
+ * orthonormal basis (columns), real and sparse for real interactions: a
+ * component of pairs whose V columns have full rank keeps its unit vectors.
+ * Available right after qa_create (no GPU needed). */
+int qa_get_pair_basis(const qa_ctx* ctx, int* rho, int* active, double* B);
 
 /* Bytes of device workspace qa_bind needs (tables, intermediates, G0). */
 int qa_workspace_size(const qa_ctx* ctx, size_t* bytes);
@@ -181,7 +212,8 @@ int qa_set_params(qa_ctx* ctx, const qa_hoppings* hop, const qa_interaction* int
  * step), so an unrolled loop checkpoints only its G's and mu's.  Adjoints:
  * FFT -> inverse FFT, DLR map -> conjugate transpose, Dyson -> -G^H Gbar G^H,
  * W Dyson -> Pbar = W^H Wbar W^H, Vbar = (1-VP)^-H Wbar (1+PW)^H - Wbar, reusing
- * one LU per (q, i nu).  Synchronises `stream`. */
+ * one LU per (q, i nu).  Needs the full pair basis (QA_ESTATE otherwise).
+ * Synchronises `stream`. */
 int qa_gw_backward(qa_ctx* ctx, const void* G_in, double mu, const void* Gbar_out,
                    const void* Sigbar, const double* nbar, void* Gbar_in, double* grad_t,
                    double* grad_V, void* stream);
@@ -209,7 +241,9 @@ int qa_density_static(const qa_ctx* ctx, const void* G, double* n_out, double* N
 
 /* Intermediates of the last step / of qa_bind, copied to dst (host or device):
  * element type complex128 for QA_FP64 and complex64 for QA_MIXED, except where
- * noted.  bytes must equal the array size. */
+ * noted.  bytes must equal the array size.  With the reduced pair basis active
+ * (qa_get_pair_basis) the two big tensors are held and returned as
+ * B^H P B and B^H W^C B: [r][rho][rho][N_k]. */
 enum {
   QA_P_QNU = 1,       /* P(q, i nu_m)        [r][npair][npair][N_k]           */
   QA_WC_RTAU = 2,     /* W^C(R, tau_j)       [r][npair][npair][N_k]           */

@@ -110,6 +110,19 @@ struct qa_ctx {
   std::vector<uint16_t> tc_Ttn, tc_Tnt;
   void* d_tc_Ttn = nullptr;
   void* d_tc_Tnt = nullptr;
+  // pair basis of the big tensors: full (npair) or reduced (rho, qa_basis.cpp)
+  int pair_mode = QA_PAIRS_AUTO;
+  bool reduced = false;
+  int rho = 0;                    // rank of the interaction subspace
+  int nb = 1;                     // size of the big-tensor matrices (npair or rho)
+  std::vector<cd> basis;          // [npair][rho]
+  std::vector<cd> sV;             // [nV][rho][rho] = B^H V(R) B
+  qa::PairTerms tbub, tsig;
+  int* d_tbub = nullptr;          // off + idx
+  void* d_cbub = nullptr;         // coefficients (compute precision)
+  int* d_tsig = nullptr;
+  void* d_csig = nullptr;
+  double2* d_sV = nullptr;        // [nV][rho][rho] FP64
 };
 
 namespace {
@@ -140,6 +153,64 @@ int grid_index(const qa_ctx* c, int i1, int i2, int i3) {
   return (i1 * c->n[1] + i2) * c->n[2] + i3;
 }
 
+// Pair basis of the big tensors.  The interaction subspace (rank rho, basis
+// B) is found on the host; the reduced basis is used when the mode asks for it
+// (QA_PAIRS_AUTO: on the mixed path) and 0 < rho < npair with term lists that
+// fit the reduced kernels.  Then S(R) = B^H V(R) B replaces V(R) in the Dyson
+// equation for W.  With `bound` set (the workspace is laid out) the choice and
+// rho must stay as they are.
+int setup_pairs(qa_ctx* c, bool bound) {
+  std::vector<cd> B;
+  const int rho = qa::reduced_pair_basis(c->vV, c->nV, c->npair, &B);
+  qa::PairTerms tb, ts;
+  bool ok = rho > 0 && rho < c->npair;
+  if (ok) {
+    qa::pair_basis_terms(B, c->norb, rho, static_cast<double>(c->nspin), &tb, &ts);
+    ok = static_cast<int>(tb.idx.size()) <= qa::kMaxPairTerms &&
+         static_cast<int>(ts.idx.size()) <= qa::kMaxPairTerms;
+  }
+  const bool want = c->pair_mode == QA_PAIRS_REDUCED ||
+                    (c->pair_mode == QA_PAIRS_AUTO && c->precision == QA_MIXED);
+  const bool red = want && ok;
+  if (bound && (red != c->reduced || (red && rho != c->rho))) return QA_EINVAL;
+  c->rho = rho;
+  c->basis = B;
+  c->reduced = red;
+  c->nb = red ? rho : c->npair;
+  c->tbub = tb;
+  c->tsig = ts;
+  c->sV.clear();
+  if (red) {
+    const int np = c->npair;
+    c->sV.assign(static_cast<size_t>(c->nV) * rho * rho, cd(0, 0));
+    for (int v = 0; v < c->nV; ++v) {
+      const cd* X = c->vV.data() + static_cast<size_t>(v) * np * np;
+      std::vector<cd> XB(static_cast<size_t>(np) * rho, cd(0, 0));      // V(R) B
+      for (int A = 0; A < np; ++A)
+        for (int Bp = 0; Bp < np; ++Bp) {
+          const cd x = X[static_cast<size_t>(A) * np + Bp];
+          if (x == cd(0, 0)) continue;
+          for (int j = 0; j < rho; ++j) XB[static_cast<size_t>(A) * rho + j] += x * B[static_cast<size_t>(Bp) * rho + j];
+        }
+      cd* S = c->sV.data() + static_cast<size_t>(v) * rho * rho;
+      for (int A = 0; A < np; ++A)
+        for (int i = 0; i < rho; ++i) {
+          const cd bi = std::conj(B[static_cast<size_t>(A) * rho + i]);
+          if (bi == cd(0, 0)) continue;
+          for (int j = 0; j < rho; ++j) S[static_cast<size_t>(i) * rho + j] += bi * XB[static_cast<size_t>(A) * rho + j];
+        }
+    }
+  }
+  return QA_OK;
+}
+
+// Room for the reduced term lists: every list a later qa_set_params can make
+// (rho^2 outputs of at most npair^2 terms each), capped by the kernels' limit.
+size_t term_capacity(const qa_ctx* c) {
+  const size_t bound = static_cast<size_t>(c->rho) * c->rho * c->npair * c->npair;
+  return std::min(bound, static_cast<size_t>(qa::kMaxPairTerms));
+}
+
 // layout of the workspace; when `base` is null only sizes are accumulated
 size_t layout(qa_ctx* c, char* base) {
   size_t off = 0;
@@ -149,7 +220,8 @@ size_t layout(qa_ctx* c, char* base) {
     return p;
   };
   const size_t r = c->r, nk = c->nk, no2 = static_cast<size_t>(c->norb) * c->norb,
-               np2 = static_cast<size_t>(c->npair) * c->npair;
+               np2 = static_cast<size_t>(c->npair) * c->npair,
+               nb2 = static_cast<size_t>(c->nb) * c->nb;    // big-tensor matrix entries
   const size_t es = c->precision == QA_FP64 ? 16 : 8;   // big/compute element size
   const size_t rr = r * r;
   for (DevTables* t : {&c->t64, &c->t32}) {
@@ -173,7 +245,7 @@ size_t layout(qa_ctx* c, char* base) {
   c->d_vR = static_cast<int*>(take((c->nV + 1) * 12));
   c->d_vV = static_cast<double2*>(take(std::max(1, c->nV) * np2 * 16));
   c->d_Hk = static_cast<double2*>(take(nk * no2 * 16));
-  c->d_Vq = take(nk * np2 * es);
+  c->d_Vq = take(nk * nb2 * es);
   c->d_G0 = static_cast<double2*>(take(r * no2 * nk * 16));
   c->d_Gk = take(r * no2 * nk * es);
   c->d_Grefl = take(r * no2 * nk * es);
@@ -187,8 +259,8 @@ size_t layout(qa_ctx* c, char* base) {
   c->d_Giw = take(r * no2 * nk * 16);
   c->d_Gt = take(r * no2 * nk * 16);
   // big tensors last; P must also hold the FP64 V(q) staging of qa_bind
-  c->d_P = take(std::max(r * np2 * nk * es, nk * np2 * 16));
-  c->d_W = take(r * np2 * nk * es);
+  c->d_P = take(std::max(r * nb2 * nk * es, nk * nb2 * 16));
+  c->d_W = take(r * nb2 * nk * es);
   c->nblocks_g = qa::dyson_g_blocks(c->r, c->nk);
   c->d_part = static_cast<double*>(take(2 * static_cast<size_t>(c->nblocks_g) * 8));
   c->d_red = static_cast<double*>(take(2 * 8));
@@ -198,6 +270,14 @@ size_t layout(qa_ctx* c, char* base) {
   if (c->precision == QA_MIXED && c->use_tc) {
     c->d_tc_Ttn = take(c->tc_Ttn.size() * 2);
     c->d_tc_Tnt = take(c->tc_Tnt.size() * 2);
+  }
+  if (c->reduced) {
+    c->d_sV = static_cast<double2*>(take(std::max(1, c->nV) * nb2 * 16));
+    const size_t cap = term_capacity(c);
+    c->d_tbub = static_cast<int*>(take((nb2 + 1 + cap) * 4));
+    c->d_cbub = take(cap * es);
+    c->d_tsig = static_cast<int*>(take((nb2 + 1 + cap) * 4));
+    c->d_csig = take(cap * es);
   }
   if (c->precision == QA_FP64) {
     c->tH.Trefl = take(rr * 16);
@@ -235,6 +315,40 @@ cudaError_t upload_c(void* dst, const std::vector<cd>& src, cudaStream_t st) {
   cudaError_t e = cudaMemcpyAsync(dst, f.data(), f.size() * 4, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return e;
   return cudaStreamSynchronize(st);   // f goes out of scope
+}
+
+// The interaction tables of the Dyson equation for W: V(q) on the full pair
+// basis, or the term lists, S(R) = B^H V(R) B and S(q) on the reduced one.
+int upload_interaction(qa_ctx* c, cudaStream_t st) {
+  const int nb2 = c->nb * c->nb;
+  const double2* src = c->d_vV;
+  if (c->reduced) {
+    const qa::PairTerms* tl[2] = {&c->tbub, &c->tsig};
+    int* di[2] = {c->d_tbub, c->d_tsig};
+    void* dc[2] = {c->d_cbub, c->d_csig};
+    for (int k = 0; k < 2; ++k) {
+      std::vector<int> iv(tl[k]->off);
+      iv.insert(iv.end(), tl[k]->idx.begin(), tl[k]->idx.end());
+      QA_TRY(cudaMemcpyAsync(di[k], iv.data(), iv.size() * 4, cudaMemcpyHostToDevice, st));
+      QA_TRY(cudaStreamSynchronize(st));
+      if (c->precision == QA_FP64) QA_TRY(upload_c<double>(dc[k], tl[k]->coef, st));
+      else QA_TRY(upload_c<float>(dc[k], tl[k]->coef, st));
+    }
+    if (c->nV > 0) QA_TRY(upload_c<double>(c->d_sV, c->sV, st));
+    src = c->d_sV;
+  }
+  if (c->precision == QA_FP64) {
+    QA_LAUNCH(c, 1, qa::launch_ft_table(c->d_vR, src, c->nV, nb2, nullptr, c->nk, c->n[0], c->n[1],
+                                        c->n[2], static_cast<double2*>(c->d_Vq), st));
+  } else {
+    QA_LAUNCH(c, 1, qa::launch_ft_table(c->d_vR, src, c->nV, nb2, nullptr, c->nk, c->n[0], c->n[1],
+                                        c->n[2], static_cast<double2*>(c->d_P), st));
+    QA_LAUNCH(c, 1, qa::launch_c128_to_c64(static_cast<const double2*>(c->d_P),
+                                           static_cast<float2*>(c->d_Vq),
+                                           static_cast<long long>(c->nk) * nb2, st));
+  }
+  QA_TRY(cudaStreamSynchronize(st));
+  return QA_OK;
 }
 
 // Density and derivative at mu.  Result: N(mu), dN/dmu.
@@ -455,9 +569,9 @@ template <typename T>
 int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st) {
   const DevTables& tab = sizeof(T) == 8 ? c->t64 : c->t32;
   const qa::FftDev& fft = sizeof(T) == 8 ? c->fft64 : c->fft32;
-  const int r = c->r, no2 = c->norb * c->norb, nk = c->nk, np2 = c->npair * c->npair;
+  const int r = c->r, no2 = c->norb * c->norb, nk = c->nk, nb2 = c->nb * c->nb;
   const long long ncs = static_cast<long long>(no2) * nk;     // small-tensor columns
-  const long long ncb = static_cast<long long>(np2) * nk;     // big-tensor columns
+  const long long ncb = static_cast<long long>(nb2) * nk;     // big-tensor columns
   // n(k) = -G(k, beta^-) of the input, Hartree and Fock (FP64)
   QA_LAUNCH(c, 1, qa::launch_dlr_apply<double>(c->t64.dtau, 1, r, Gin, c->d_nk, ncs, st));
   QA_LAUNCH(c, 1, qa::launch_density_R(c->d_nk, c->d_vR, c->nV + 1, no2, nullptr, nk, c->n[0], c->n[1],
@@ -475,7 +589,12 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
   QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, +1, Gk, c->d_GR, ncs / nk * r, st));
   QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, +1, c->d_Grefl, c->d_Grefl, ncs / nk * r, st));
   tm.mark();  // 1: G -> R
-  QA_LAUNCH(c, 1, qa::launch_bubble<T>(c->d_GR, c->d_Grefl, c->d_mR, c->d_P, r, c->norb, nk, c->nspin, st));
+  if (c->reduced)
+    QA_LAUNCH(c, 1, qa::launch_bubble_reduced<T>(c->d_GR, c->d_Grefl, c->d_mR, c->d_tbub, c->d_cbub,
+                                                 static_cast<int>(c->tbub.idx.size()), c->d_P, r,
+                                                 c->norb, c->rho, nk, st));
+  else
+    QA_LAUNCH(c, 1, qa::launch_bubble<T>(c->d_GR, c->d_Grefl, c->d_mR, c->d_P, r, c->norb, nk, c->nspin, st));
   tm.mark();  // 2: bubble
   QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, -1, c->d_P, c->d_P, ncb / nk * r, st));
   tm.mark();  // 3: FFT R -> q
@@ -484,7 +603,7 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
   else
     QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Ttn, r, r, c->d_P, c->d_P, ncb, st));
   tm.mark();  // 4: DLR tau -> nu
-  QA_LAUNCH(c, 1, qa::launch_dyson_w<T>(c->d_P, c->d_Vq, c->d_W, r, c->npair, nk, c->d_err, c->d_bad, st));
+  QA_LAUNCH(c, 1, qa::launch_dyson_w<T>(c->d_P, c->d_Vq, c->d_W, r, c->nb, nk, c->d_err, c->d_bad, st));
   tm.mark();  // 5: Dyson W
   if (sizeof(T) == 4 && c->use_tc)
     QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Tnt, r, c->d_W, c->d_W, ncb, c->d_err, st));
@@ -493,7 +612,12 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
   tm.mark();  // 6: DLR nu -> tau
   QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, +1, c->d_W, c->d_W, ncb / nk * r, st));
   tm.mark();  // 7: FFT q -> R
-  QA_LAUNCH(c, 1, qa::launch_sigma<T>(c->d_GR, c->d_W, c->d_SigC, r, c->norb, nk, st));
+  if (c->reduced)
+    QA_LAUNCH(c, 1, qa::launch_sigma_reduced<T>(c->d_GR, c->d_W, c->d_tsig, c->d_csig,
+                                                static_cast<int>(c->tsig.idx.size()), c->d_SigC, r,
+                                                c->norb, c->rho, nk, st));
+  else
+    QA_LAUNCH(c, 1, qa::launch_sigma<T>(c->d_GR, c->d_W, c->d_SigC, r, c->norb, nk, st));
   tm.mark();  // 8: Sigma contraction
   QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, -1, c->d_SigC, c->d_SigC, ncs / nk * r, st));
   QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Ttw, r, r, c->d_SigC, c->d_SigIw, ncs, st));
@@ -741,6 +865,7 @@ int qa_create(const qa_lattice* lat, const qa_hoppings* hop, const qa_interactio
     if (!std::isfinite(v.real()) || !std::isfinite(v.imag())) { delete c; return QA_EINVAL; }
   for (const cd& v : c->hopH)
     if (!std::isfinite(v.real()) || !std::isfinite(v.imag())) { delete c; return QA_EINVAL; }
+  setup_pairs(c, false);
   // DLR grid and transform matrices
   if (qa::build_dlr(Lambda, eps, &c->grid) != 0) { delete c; return QA_EINVAL; }
   c->r = c->grid.r;
@@ -762,6 +887,22 @@ int qa_create(const qa_lattice* lat, const qa_hoppings* hop, const qa_interactio
         c->mR[grid_index(c, i1, i2, i3)] =
             grid_index(c, (c->n[0] - i1) % c->n[0], (c->n[1] - i2) % c->n[1], (c->n[2] - i3) % c->n[2]);
   *out = c;
+  return QA_OK;
+}
+
+int qa_set_pair_basis(qa_ctx* c, int mode) {
+  if (!c || (mode != QA_PAIRS_AUTO && mode != QA_PAIRS_FULL && mode != QA_PAIRS_REDUCED))
+    return QA_EINVAL;
+  if (c->bound) return QA_ESTATE;
+  c->pair_mode = mode;
+  return setup_pairs(c, false);
+}
+
+int qa_get_pair_basis(const qa_ctx* c, int* rho, int* active, double* B) {
+  if (!c) return QA_EINVAL;
+  if (rho) *rho = c->rho;
+  if (active) *active = c->reduced ? 1 : 0;
+  if (B && c->rho > 0) std::memcpy(B, c->basis.data(), c->basis.size() * 16);
   return QA_OK;
 }
 
@@ -850,20 +991,11 @@ int qa_bind(qa_ctx* c, void* workspace, size_t bytes, void* stream) {
   QA_TRY(upload_c<double>(c->d_hH, c->hopH, st));
   QA_TRY(cudaMemcpyAsync(c->d_vR, c->vR.data(), c->vR.size() * 4, cudaMemcpyHostToDevice, st));
   if (c->nV > 0) QA_TRY(upload_c<double>(c->d_vV, c->vV, st));
-  // H(k), V(q)
-  const int no2 = c->norb * c->norb, np2 = c->npair * c->npair;
+  // H(k), V(q) (or S(q) on the reduced pair basis)
+  const int no2 = c->norb * c->norb;
   QA_LAUNCH(c, 1, qa::launch_ft_table(c->d_hR, c->d_hH, c->nH, no2, nullptr, c->nk, c->n[0], c->n[1],
                              c->n[2], c->d_Hk, st));
-  if (c->precision == QA_FP64) {
-    QA_LAUNCH(c, 1, qa::launch_ft_table(c->d_vR, c->d_vV, c->nV, np2, nullptr, c->nk, c->n[0], c->n[1],
-                               c->n[2], static_cast<double2*>(c->d_Vq), st));
-  } else {
-    QA_LAUNCH(c, 1, qa::launch_ft_table(c->d_vR, c->d_vV, c->nV, np2, nullptr, c->nk, c->n[0], c->n[1],
-                               c->n[2], static_cast<double2*>(c->d_P), st));
-    QA_LAUNCH(c, 1, qa::launch_c128_to_c64(static_cast<const double2*>(c->d_P),
-                                  static_cast<float2*>(c->d_Vq),
-                                  static_cast<long long>(c->nk) * np2, st));
-  }
+  if (int rc = upload_interaction(c, st)) return rc;
   // G0 at mu0 (always FP64)
   if (int rc = reset_err(c, st)) return rc;
   double mu0 = 0, N0 = 0;
@@ -955,12 +1087,12 @@ int qa_get(const qa_ctx* c, int which, void* dst, size_t bytes, void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t es = c->precision == QA_FP64 ? 16 : 8;
   const size_t r = c->r, nk = c->nk, no2 = static_cast<size_t>(c->norb) * c->norb,
-               np2 = static_cast<size_t>(c->npair) * c->npair;
+               nb2 = static_cast<size_t>(c->nb) * c->nb;
   const void* src = nullptr;
   size_t need = 0;
   switch (which) {
-    case QA_P_QNU: src = c->d_P; need = r * np2 * nk * es; break;
-    case QA_WC_RTAU: src = c->d_W; need = r * np2 * nk * es; break;
+    case QA_P_QNU: src = c->d_P; need = r * nb2 * nk * es; break;
+    case QA_WC_RTAU: src = c->d_W; need = r * nb2 * nk * es; break;
     case QA_SIGC_KTAU: src = c->d_SigC; need = r * no2 * nk * es; break;
     case QA_SIGC_KIW: src = c->d_SigIw; need = r * no2 * nk * es; break;
     case QA_SIGHF_K: src = c->d_SigHF; need = nk * no2 * 16; break;
@@ -989,7 +1121,7 @@ int qa_set_params(qa_ctx* c, const qa_hoppings* hop, const qa_interaction* inter
   if (!c || !hop || !inter) return QA_EINVAL;
   if (!c->bound) return QA_ESTATE;
   if (hop->nR != c->nH_user || inter->nR != c->nV) return QA_EINVAL;
-  const int no = c->norb, no2 = no * no, np2 = c->npair * c->npair;
+  const int no = c->norb, no2 = no * no;
   for (int i = 0; i < hop->nR; ++i)
     for (int d = 0; d < 3; ++d)
       if (hop->R[3 * i + d] != c->hopR[3 * i + d]) return QA_EINVAL;
@@ -1009,25 +1141,24 @@ int qa_set_params(qa_ctx* c, const qa_hoppings* hop, const qa_interaction* inter
   }
   for (const cd& v : H)
     if (!std::isfinite(v.real()) || !std::isfinite(v.imag())) return QA_EINVAL;
-  c->hopH = H;
+  for (const double* v = inter->V; v < inter->V + 2 * c->vV.size(); ++v)
+    if (!std::isfinite(*v)) return QA_EINVAL;
+  std::vector<cd> oldV = c->vV;
   for (size_t e = 0; e < c->vV.size(); ++e)
     c->vV[e] = cd(inter->V[2 * e], inter->V[2 * e + 1]);
+  // the workspace keeps its pair basis: a new V must keep the basis choice and rank
+  if (setup_pairs(c, true) != QA_OK) {
+    c->vV = oldV;
+    setup_pairs(c, true);
+    return QA_EINVAL;
+  }
+  c->hopH = H;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   QA_TRY(upload_c<double>(c->d_hH, c->hopH, st));
   if (c->nV > 0) QA_TRY(upload_c<double>(c->d_vV, c->vV, st));
   QA_TRY(qa::launch_ft_table(c->d_hR, c->d_hH, c->nH, no2, nullptr, c->nk, c->n[0], c->n[1], c->n[2],
                              c->d_Hk, st));
-  if (c->precision == QA_FP64) {
-    QA_TRY(qa::launch_ft_table(c->d_vR, c->d_vV, c->nV, np2, nullptr, c->nk, c->n[0], c->n[1],
-                               c->n[2], static_cast<double2*>(c->d_Vq), st));
-  } else {
-    QA_TRY(qa::launch_ft_table(c->d_vR, c->d_vV, c->nV, np2, nullptr, c->nk, c->n[0], c->n[1],
-                               c->n[2], static_cast<double2*>(c->d_P), st));
-    QA_TRY(qa::launch_c128_to_c64(static_cast<const double2*>(c->d_P), static_cast<float2*>(c->d_Vq),
-                                  static_cast<long long>(c->nk) * np2, st));
-  }
-  QA_TRY(cudaStreamSynchronize(st));
-  return QA_OK;
+  return upload_interaction(c, st);
 }
 
 int qa_gw_backward(qa_ctx* c, const void* G_in, double mu, const void* Gbar_out, const void* Sigbar,
@@ -1036,6 +1167,7 @@ int qa_gw_backward(qa_ctx* c, const void* G_in, double mu, const void* Gbar_out,
   if (!c) return QA_EINVAL;
   if (!c->bound) return QA_ESTATE;
   if (c->precision != QA_FP64 || !std::isfinite(mu)) return QA_EINVAL;
+  if (c->reduced) return QA_ESTATE;
   const double2* Gin = static_cast<const double2*>(G_in ? G_in : c->d_G0);
   return gw_backward_impl(c, Gin, mu, static_cast<const double2*>(Gbar_out),
                           static_cast<const double2*>(Sigbar), nbar, static_cast<double2*>(Gbar_in),

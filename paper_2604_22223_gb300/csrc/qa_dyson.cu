@@ -137,56 +137,63 @@ __global__ void __launch_bounds__(kWarpsW * 32) dyson_w_kernel(const cplx<T>* __
 }
 
 // ------------------------------------------------- Dyson W, register rows
-// FP32 variant with the rows in registers.  A block of 8 warps takes 8
-// consecutive q at one nu, so the P / W^C tiles move through shared memory
-// with coalesced runs along q.  Lane i owns row i of A = 1 - V P and of the
-// right-hand side V P V; elimination tracks the pivot lanes instead of
-// swapping rows (the pivot row is broadcast with warp shuffles), and the
-// triangular solve runs column-parallel from shared memory.
+// FP32 variant with the rows in registers.  W lanes (W = next power of two
+// >= n) own one system, so a warp solves 32/W systems side by side, and a
+// block of 8 warps takes 8*32/W consecutive q at one nu: the P / W^C tiles
+// move through shared memory with coalesced runs along q.  Lane i of a
+// system owns row i of A = 1 - V P and of the right-hand side V P V;
+// elimination tracks the pivot lanes instead of swapping rows (the pivot row
+// is broadcast with width-W warp shuffles), and the triangular solve runs
+// column-parallel from shared memory.
 
 constexpr int kWarpsR = 8;
 
-template <int MAXN>
+template <int MAXN, int W>
 __global__ void __launch_bounds__(kWarpsR * 32) dyson_w_reg_kernel(const float2* __restrict__ P,
                                                                   const float2* __restrict__ Vq,
                                                                   float2* WC, int n, int nk,
                                                                   int* err, long long* first_bad) {
+  static_assert(MAXN <= W && W <= 32 && (W & (W - 1)) == 0, "system width");
+  constexpr int SPW = 32 / W;                 // systems per warp
+  constexpr int NSYS = kWarpsR * SPW;         // systems per block
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nn = n * n;
-  float2* Ps = reinterpret_cast<float2*>(smem_raw);        // [kWarpsR][nn]
-  float2* Vs = Ps + kWarpsR * nn;                           // [kWarpsR][nn]
+  float2* Ps = reinterpret_cast<float2*>(smem_raw);        // [NSYS][nn]
+  float2* Vs = Ps + NSYS * nn;                              // [NSYS][nn]
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  const int q0 = blockIdx.x * kWarpsR;
+  const int l = lane % W;                                   // row owned in the system
+  const int sys = w * SPW + lane / W;                       // system within the block
+  const int q0 = blockIdx.x * NSYS;
   const int nu = blockIdx.y;
   const size_t slab = static_cast<size_t>(nu) * nn * nk;
-  for (int idx = tid; idx < kWarpsR * nn; idx += blockDim.x) {
-    int e = idx / kWarpsR, ww = idx - e * kWarpsR;
-    int q = q0 + ww;
-    Ps[ww * nn + e] = q < nk ? P[slab + static_cast<size_t>(e) * nk + q] : make_float2(0.f, 0.f);
+  for (int idx = tid; idx < NSYS * nn; idx += blockDim.x) {
+    int e = idx / NSYS, ss = idx - e * NSYS;
+    int q = q0 + ss;
+    Ps[ss * nn + e] = q < nk ? P[slab + static_cast<size_t>(e) * nk + q] : make_float2(0.f, 0.f);
   }
-  for (int idx = tid; idx < kWarpsR * nn; idx += blockDim.x) {
-    int ww = idx / nn, e = idx - ww * nn;
-    int q = q0 + ww;
+  for (int idx = tid; idx < NSYS * nn; idx += blockDim.x) {
+    int ss = idx / nn, e = idx - ss * nn;
+    int q = q0 + ss;
     Vs[idx] = q < nk ? Vq[static_cast<size_t>(q) * nn + e] : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  const int q = q0 + w;
-  float2* Pw = Ps + w * nn;
-  float2* Vw = Vs + w * nn;
+  const int q = q0 + sys;
+  float2* Pw = Ps + sys * nn;
+  float2* Vw = Vs + sys * nn;
   float2 a[MAXN], b[MAXN];
-  const bool row = lane < n;
-  // a = row `lane` of V P
+  const bool row = l < n;
+  // a = row l of V P
 #pragma unroll
   for (int j = 0; j < MAXN; ++j) a[j] = make_float2(0.f, 0.f);
   if (row) {
     for (int m = 0; m < n; ++m) {
-      float2 v = Vw[lane * n + m];
+      float2 v = Vw[l * n + m];
 #pragma unroll
       for (int j = 0; j < MAXN; ++j)
         if (j < n) a[j] = cfma(v, Pw[m * n + j], a[j]);
     }
   }
-  // b = row `lane` of (V P) V
+  // b = row l of (V P) V
 #pragma unroll
   for (int j = 0; j < MAXN; ++j) b[j] = make_float2(0.f, 0.f);
   if (row) {
@@ -202,7 +209,7 @@ __global__ void __launch_bounds__(kWarpsR * 32) dyson_w_reg_kernel(const float2*
   // a = 1 - V P
 #pragma unroll
   for (int j = 0; j < MAXN; ++j) {
-    a[j].x = (row && j == lane ? 1.f : 0.f) - a[j].x;
+    a[j].x = (row && j == l ? 1.f : 0.f) - a[j].x;
     a[j].y = -a[j].y;
   }
   bool used = !row;
@@ -212,30 +219,34 @@ __global__ void __launch_bounds__(kWarpsR * 32) dyson_w_reg_kernel(const float2*
   for (int c = 0; c < MAXN; ++c) {
     if (c < n) {
       float val = used ? -1.f : cabs2(a[c]);
-      int idx = lane;
+      int idx = l;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
+      for (int o = W / 2; o > 0; o >>= 1) {
         float ov = __shfl_xor_sync(0xffffffffu, val, o);
         int oi = __shfl_xor_sync(0xffffffffu, idx, o);
         if (ov > val || (ov == val && oi < idx)) { val = ov; idx = oi; }
       }
-      const int p = idx;
+      const int p = idx;                      // pivot row within the system
       if (!(val >= 1e-12f)) singular = true;
-      if (lane == p) { used = true; mypos = c; }
-      float2 apc = make_float2(__shfl_sync(0xffffffffu, a[c].x, p), __shfl_sync(0xffffffffu, a[c].y, p));
-      float2 l = used ? make_float2(0.f, 0.f) : cmul(a[c], cinv(apc));
+      if (l == p) { used = true; mypos = c; }
+      float2 apc = make_float2(__shfl_sync(0xffffffffu, a[c].x, p, W),
+                               __shfl_sync(0xffffffffu, a[c].y, p, W));
+      float2 f = used ? make_float2(0.f, 0.f) : cmul(a[c], cinv(apc));
+      // a fixed range with a predicate (not j = c + 1 ..) keeps a[] in registers
 #pragma unroll
-      for (int j = c + 1; j < MAXN; ++j) {
-        if (j < n) {
-          float2 apj = make_float2(__shfl_sync(0xffffffffu, a[j].x, p), __shfl_sync(0xffffffffu, a[j].y, p));
-          a[j] = cfms(l, apj, a[j]);
+      for (int j = 1; j < MAXN; ++j) {
+        if (j > c && j < n) {
+          float2 apj = make_float2(__shfl_sync(0xffffffffu, a[j].x, p, W),
+                                   __shfl_sync(0xffffffffu, a[j].y, p, W));
+          a[j] = cfms(f, apj, a[j]);
         }
       }
 #pragma unroll
       for (int j = 0; j < MAXN; ++j) {
         if (j < n) {
-          float2 bpj = make_float2(__shfl_sync(0xffffffffu, b[j].x, p), __shfl_sync(0xffffffffu, b[j].y, p));
-          b[j] = cfms(l, bpj, b[j]);
+          float2 bpj = make_float2(__shfl_sync(0xffffffffu, b[j].x, p, W),
+                                   __shfl_sync(0xffffffffu, b[j].y, p, W));
+          b[j] = cfms(f, bpj, b[j]);
         }
       }
     }
@@ -250,19 +261,34 @@ __global__ void __launch_bounds__(kWarpsR * 32) dyson_w_reg_kernel(const float2*
   __syncwarp();
   if (row) {
     for (int c = n - 1; c >= 0; --c) {
-      float2 x = Vw[c * n + lane];
-      for (int m = c + 1; m < n; ++m) x = cfms(Pw[c * n + m], Vw[m * n + lane], x);
-      Vw[c * n + lane] = cmul(x, cinv(Pw[c * n + c]));
+      float2 x = Vw[c * n + l];
+      for (int m = c + 1; m < n; ++m) x = cfms(Pw[c * n + m], Vw[m * n + l], x);
+      Vw[c * n + l] = cmul(x, cinv(Pw[c * n + c]));
     }
   }
-  if (singular && lane == 0 && q < nk)
+  if (singular && l == 0 && q < nk)
     report(err, first_bad, QA_ESINGULAR_CODE, static_cast<long long>(nu) * nk + q);
   __syncthreads();
-  for (int idx = tid; idx < kWarpsR * nn; idx += blockDim.x) {
-    int e = idx / kWarpsR, ww = idx - e * kWarpsR;
-    int qq = q0 + ww;
-    if (qq < nk) WC[slab + static_cast<size_t>(e) * nk + qq] = Vs[ww * nn + e];
+  for (int idx = tid; idx < NSYS * nn; idx += blockDim.x) {
+    int e = idx / NSYS, ss = idx - e * NSYS;
+    int qq = q0 + ss;
+    if (qq < nk) WC[slab + static_cast<size_t>(e) * nk + qq] = Vs[ss * nn + e];
   }
+}
+
+template <int MAXN, int W>
+cudaError_t launch_dyson_w_reg(const void* P, const void* Vq, void* WC, int r, int n, int nk,
+                               int* err, long long* first_bad, cudaStream_t st) {
+  constexpr int NSYS = kWarpsR * (32 / W);
+  const size_t smem = static_cast<size_t>(2) * NSYS * n * n * sizeof(float2);
+  auto fn = &dyson_w_reg_kernel<MAXN, W>;
+  cudaError_t e = set_smem(reinterpret_cast<const void*>(fn), smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((nk + NSYS - 1) / NSYS, r);
+  fn<<<grid, kWarpsR * 32, smem, st>>>(reinterpret_cast<const float2*>(P),
+                                       reinterpret_cast<const float2*>(Vq),
+                                       reinterpret_cast<float2*>(WC), n, nk, err, first_bad);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ Dyson G
@@ -457,16 +483,10 @@ cudaError_t launch_dyson_w(const void* P, const void* Vq, void* WC, int r, int n
   if (npair > kMaxPair) return cudaErrorInvalidValue;
   if (sizeof(T) == 4) {
     // register-row kernel: W^C = (1 - V P)^-1 V P V directly
-    size_t smem = static_cast<size_t>(2) * kWarpsR * npair * npair * sizeof(float2);
-    auto fn = npair <= 4 ? &dyson_w_reg_kernel<4> : (npair <= 9 ? &dyson_w_reg_kernel<9>
-              : (npair <= 16 ? &dyson_w_reg_kernel<16> : &dyson_w_reg_kernel<25>));
-    cudaError_t e = set_smem(reinterpret_cast<const void*>(fn), smem);
-    if (e != cudaSuccess) return e;
-    dim3 grid((nk + kWarpsR - 1) / kWarpsR, r);
-    fn<<<grid, kWarpsR * 32, smem, st>>>(reinterpret_cast<const float2*>(P),
-                                         reinterpret_cast<const float2*>(Vq),
-                                         reinterpret_cast<float2*>(WC), npair, nk, err, first_bad);
-    return cudaGetLastError();
+    if (npair <= 4) return launch_dyson_w_reg<4, 4>(P, Vq, WC, r, npair, nk, err, first_bad, st);
+    if (npair <= 8) return launch_dyson_w_reg<8, 8>(P, Vq, WC, r, npair, nk, err, first_bad, st);
+    if (npair <= 16) return launch_dyson_w_reg<16, 16>(P, Vq, WC, r, npair, nk, err, first_bad, st);
+    return launch_dyson_w_reg<25, 32>(P, Vq, WC, r, npair, nk, err, first_bad, st);
   }
   size_t smem = static_cast<size_t>(kWarpsW) * 2 * npair * (npair + 1) * sizeof(cplx<T>);
   auto fn = &dyson_w_kernel<T, false>;

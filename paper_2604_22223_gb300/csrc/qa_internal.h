@@ -43,6 +43,24 @@ struct DlrMatrices {
 };
 void build_dlr_matrices(const DlrGrid& g, double beta, DlrMatrices* m);
 
+// ------------------------------------------------------------ pair basis
+// Orthonormal basis B (npair x rho, row-major [A][j]) of the subspace that the
+// interaction matrices V(R) act in (qa_basis.cpp); returns rho (0: no V).
+int reduced_pair_basis(const std::vector<std::complex<double>>& VR, int nV, int npair,
+                       std::vector<std::complex<double>>* B);
+
+// Term lists of the reduced bubble and self-energy contractions, one list per
+// reduced output entry o = i*rho + j (terms off[o] .. off[o+1]-1).
+//   bubble: Pt_ij += coef * G[idx & 255] * G^refl[idx >> 8]
+//   sigma:  Sigma[idx >> 8] += coef * G[idx & 255] * Wt_ij
+struct PairTerms {
+  std::vector<int> off;
+  std::vector<int> idx;
+  std::vector<std::complex<double>> coef;
+};
+void pair_basis_terms(const std::vector<std::complex<double>>& B, int norb, int rho, double s,
+                      PairTerms* bubble, PairTerms* sigma);
+
 // ------------------------------------------------------------------- FFT
 // Mixed-radix decimation-in-frequency plan for one axis of length L: the
 // radices in stage order, and pos[f] = position of frequency f after the
@@ -105,6 +123,20 @@ cudaError_t launch_dyson_w(const void* P, const void* Vq, void* WC, int r, int n
 template <typename T>
 cudaError_t launch_sigma(const void* GR, const void* WC, void* Sig, int r, int norb, int nk,
                          cudaStream_t st);
+
+// Reduced-basis bubble and self-energy (qa_reduced.cu).  terms: int
+// off[nout + 1] followed by int idx[nterm]; coef: cplx<T>[nterm].
+//   Pt[t][o][R] = sum_terms coef * GR[t][g1][R] * GreflR[t][g2][mR[R]]
+//   Sig[t][e][R] = sum_o sum_terms coef * GR[t][g][R] * Wt[t][o][R]
+constexpr int kMaxPairTerms = 4096;
+template <typename T>
+cudaError_t launch_bubble_reduced(const void* GR, const void* GreflR, const int* mR,
+                                  const int* terms, const void* coef, int nterm, void* Pt, int r,
+                                  int norb, int rho, int nk, cudaStream_t st);
+template <typename T>
+cudaError_t launch_sigma_reduced(const void* GR, const void* Wt, const int* terms, const void* coef,
+                                 int nterm, void* Sig, int r, int norb, int rho, int nk,
+                                 cudaStream_t st);
 
 // Dyson for G at chemical potential mu.  mode 0: accumulate per-block
 // partial sums of Re(dw_n Tr G) and Re(dw_n Tr G^2) into part[2*blocks];

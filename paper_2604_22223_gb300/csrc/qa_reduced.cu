@@ -1,0 +1,180 @@
+// Bubble and self-energy contractions in the reduced pair basis.
+//
+// With W^C = B Wt^C B^H and Pt = B^H P B (B: orthonormal basis of the
+// subspace the interaction acts in, qa_basis.cpp) the two pointwise products
+// of the iteration become, per (R, tau_j),
+//   Pt_ij  = sum_{(ab) in i, (cd) in j} conj(B_(ab)i) B_(cd)j (-s) G_bc(R) G_da(-R, beta - tau)
+//   Sigma_ad = - sum_ij Wt^C_ij sum_{(ab) in i, (cd) in j} B_(ab)i conj(B_(cd)j) G_bc(R)
+// i.e. the paper's bubble and GW self-energy equations projected on the
+// subspace.  The coefficient/index lists come from the host (one list per
+// reduced entry, uniform across threads), so each thread owns one R at one
+// tau, keeps its G (and G^refl, or its Sigma accumulators) as columns of
+// shared memory [element][thread], and reads the term lists from shared
+// memory as broadcasts.  Global traffic: the rho^2 reduced entries plus
+// the small tensors, all coalesced along R.
+#include "qa_common.cuh"
+
+namespace qa {
+namespace {
+
+template <typename T> struct RedTpb { static constexpr int v = 128; };
+template <> struct RedTpb<double> { static constexpr int v = 64; };
+
+template <typename T>
+__device__ __forceinline__ void stage_terms(const int* __restrict__ terms,
+                                            const cplx<T>* __restrict__ coef, int nout, int nterm,
+                                            int* s_off, int* s_idx, cplx<T>* s_coef) {
+  for (int e = threadIdx.x; e <= nout; e += blockDim.x) s_off[e] = terms[e];
+  for (int e = threadIdx.x; e < nterm; e += blockDim.x) {
+    s_idx[e] = terms[nout + 1 + e];
+    s_coef[e] = coef[e];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RedTpb<T>::v) bubble_reduced_kernel(
+    const cplx<T>* __restrict__ GR, const cplx<T>* __restrict__ GL, const int* __restrict__ mR,
+    const int* __restrict__ terms, const cplx<T>* __restrict__ coef, int nterm,
+    cplx<T>* __restrict__ Pt, int no2, int nout, int nk) {
+  using V = cplx<T>;
+  constexpr int TPB = RedTpb<T>::v;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* s_coef = reinterpret_cast<V*>(smem_raw);
+  V* g = s_coef + nterm;                      // [no2][TPB]
+  V* gl = g + no2 * TPB;                      // [no2][TPB]
+  int* s_off = reinterpret_cast<int*>(gl + no2 * TPB);
+  int* s_idx = s_off + nout + 1;
+  const int tid = threadIdx.x;
+  const int t = blockIdx.y;
+  const int R = blockIdx.x * TPB + tid;
+  stage_terms<T>(terms, coef, nout, nterm, s_off, s_idx, s_coef);
+  if (R < nk) {
+    const int mr = mR[R];
+    const V* gt = GR + static_cast<size_t>(t) * no2 * nk;
+    const V* lt = GL + static_cast<size_t>(t) * no2 * nk;
+    for (int e = 0; e < no2; ++e) {
+      g[e * TPB + tid] = gt[static_cast<size_t>(e) * nk + R];
+      gl[e * TPB + tid] = lt[static_cast<size_t>(e) * nk + mr];
+    }
+  }
+  __syncthreads();
+  if (R >= nk) return;                        // no barriers below
+  V* out = Pt + static_cast<size_t>(t) * nout * nk + R;
+  int e0 = s_off[0];
+  for (int o = 0; o < nout; ++o) {
+    const int e1 = s_off[o + 1];
+    V acc0 = cmk<V>(0, 0), acc1 = cmk<V>(0, 0);
+    int e = e0;
+    for (; e + 1 < e1; e += 2) {
+      const int i0 = s_idx[e], i1 = s_idx[e + 1];
+      acc0 = cfma(s_coef[e], cmul(g[(i0 & 255) * TPB + tid], gl[(i0 >> 8) * TPB + tid]), acc0);
+      acc1 = cfma(s_coef[e + 1], cmul(g[(i1 & 255) * TPB + tid], gl[(i1 >> 8) * TPB + tid]), acc1);
+    }
+    if (e < e1) {
+      const int i0 = s_idx[e];
+      acc0 = cfma(s_coef[e], cmul(g[(i0 & 255) * TPB + tid], gl[(i0 >> 8) * TPB + tid]), acc0);
+    }
+    out[static_cast<size_t>(o) * nk] = cadd(acc0, acc1);
+    e0 = e1;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RedTpb<T>::v) sigma_reduced_kernel(
+    const cplx<T>* __restrict__ GR, const cplx<T>* __restrict__ Wt, const int* __restrict__ terms,
+    const cplx<T>* __restrict__ coef, int nterm, cplx<T>* __restrict__ Sig, int no2, int nout,
+    int nk) {
+  using V = cplx<T>;
+  constexpr int TPB = RedTpb<T>::v;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* s_coef = reinterpret_cast<V*>(smem_raw);
+  V* g = s_coef + nterm;                      // [no2][TPB]
+  V* sg = g + no2 * TPB;                      // [no2][TPB] accumulators
+  int* s_off = reinterpret_cast<int*>(sg + no2 * TPB);
+  int* s_idx = s_off + nout + 1;
+  const int tid = threadIdx.x;
+  const int t = blockIdx.y;
+  const int R = blockIdx.x * TPB + tid;
+  stage_terms<T>(terms, coef, nout, nterm, s_off, s_idx, s_coef);
+  if (R < nk) {
+    const V* gt = GR + static_cast<size_t>(t) * no2 * nk;
+    for (int e = 0; e < no2; ++e) {
+      g[e * TPB + tid] = gt[static_cast<size_t>(e) * nk + R];
+      sg[e * TPB + tid] = cmk<V>(0, 0);
+    }
+  }
+  __syncthreads();
+  if (R >= nk) return;                        // no barriers below
+  const V* w = Wt + static_cast<size_t>(t) * nout * nk + R;
+  V wn = w[0];
+  int e0 = s_off[0];
+  for (int o = 0; o < nout; ++o) {
+    const V wc = wn;
+    if (o + 1 < nout) wn = w[static_cast<size_t>(o + 1) * nk];   // prefetch the next entry
+    const int e1 = s_off[o + 1];
+    for (int e = e0; e < e1; ++e) {
+      const int id = s_idx[e];
+      V* sp = sg + (id >> 8) * TPB + tid;
+      *sp = cfma(cmul(s_coef[e], wc), g[(id & 255) * TPB + tid], *sp);
+    }
+    e0 = e1;
+  }
+  V* out = Sig + static_cast<size_t>(t) * no2 * nk + R;
+  for (int e = 0; e < no2; ++e) out[static_cast<size_t>(e) * nk] = sg[e * TPB + tid];
+}
+
+template <typename T>
+size_t reduced_smem(int no2, int nout, int nterm) {
+  return static_cast<size_t>(nterm) * sizeof(cplx<T>) +
+         static_cast<size_t>(2) * no2 * RedTpb<T>::v * sizeof(cplx<T>) +
+         static_cast<size_t>(nout + 1 + nterm) * sizeof(int);
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_bubble_reduced(const void* GR, const void* GreflR, const int* mR,
+                                  const int* terms, const void* coef, int nterm, void* Pt, int r,
+                                  int norb, int rho, int nk, cudaStream_t st) {
+  if (nterm < 0 || nterm > kMaxPairTerms || norb * norb > 256 || rho < 1) return cudaErrorInvalidValue;
+  const int no2 = norb * norb, nout = rho * rho;
+  const size_t smem = reduced_smem<T>(no2, nout, nterm);
+  cudaError_t e = set_smem(reinterpret_cast<const void*>(&bubble_reduced_kernel<T>), smem);
+  if (e != cudaSuccess) return e;
+  constexpr int TPB = RedTpb<T>::v;
+  dim3 grid((nk + TPB - 1) / TPB, r);
+  bubble_reduced_kernel<T><<<grid, TPB, smem, st>>>(
+      reinterpret_cast<const cplx<T>*>(GR), reinterpret_cast<const cplx<T>*>(GreflR), mR, terms,
+      reinterpret_cast<const cplx<T>*>(coef), nterm, reinterpret_cast<cplx<T>*>(Pt), no2, nout, nk);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_sigma_reduced(const void* GR, const void* Wt, const int* terms, const void* coef,
+                                 int nterm, void* Sig, int r, int norb, int rho, int nk,
+                                 cudaStream_t st) {
+  if (nterm < 0 || nterm > kMaxPairTerms || norb * norb > 256 || rho < 1) return cudaErrorInvalidValue;
+  const int no2 = norb * norb, nout = rho * rho;
+  const size_t smem = reduced_smem<T>(no2, nout, nterm);
+  cudaError_t e = set_smem(reinterpret_cast<const void*>(&sigma_reduced_kernel<T>), smem);
+  if (e != cudaSuccess) return e;
+  constexpr int TPB = RedTpb<T>::v;
+  dim3 grid((nk + TPB - 1) / TPB, r);
+  sigma_reduced_kernel<T><<<grid, TPB, smem, st>>>(
+      reinterpret_cast<const cplx<T>*>(GR), reinterpret_cast<const cplx<T>*>(Wt), terms,
+      reinterpret_cast<const cplx<T>*>(coef), nterm, reinterpret_cast<cplx<T>*>(Sig), no2, nout, nk);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_bubble_reduced<double>(const void*, const void*, const int*, const int*,
+                                                   const void*, int, void*, int, int, int, int,
+                                                   cudaStream_t);
+template cudaError_t launch_bubble_reduced<float>(const void*, const void*, const int*, const int*,
+                                                  const void*, int, void*, int, int, int, int,
+                                                  cudaStream_t);
+template cudaError_t launch_sigma_reduced<double>(const void*, const void*, const int*, const void*,
+                                                  int, void*, int, int, int, int, cudaStream_t);
+template cudaError_t launch_sigma_reduced<float>(const void*, const void*, const int*, const void*,
+                                                 int, void*, int, int, int, int, cudaStream_t);
+
+}  // namespace qa

@@ -18,12 +18,13 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libqa.so")
 
 QA_FP64, QA_MIXED = 0, 1
+QA_PAIRS_AUTO, QA_PAIRS_FULL, QA_PAIRS_REDUCED = 0, 1, 2
 QA_P_QNU, QA_WC_RTAU, QA_SIGC_KTAU, QA_SIGC_KIW, QA_SIGHF_K, QA_G0, QA_HK, QA_MU0 = range(1, 9)
 
 EXPORTED = ["qa_create", "qa_workspace_size", "qa_bind", "qa_get_grid", "qa_get_plan",
             "qa_get_sizes", "qa_gw_step", "qa_density", "qa_density_static", "qa_get",
-            "qa_set_timing", "qa_set_mu", "qa_set_params", "qa_gw_backward", "qa_destroy",
-            "qa_strerror"]
+            "qa_set_timing", "qa_set_mu", "qa_set_params", "qa_gw_backward", "qa_set_pair_basis",
+            "qa_get_pair_basis", "qa_destroy", "qa_strerror"]
 
 STAGES = ["hartree_fock", "g_to_R", "bubble", "fft_R_to_q", "dlr_tau_to_nu", "dyson_w",
           "dlr_nu_to_tau", "fft_q_to_R", "sigma", "sigma_to_k_iw", "mu_search", "dyson_g"]
@@ -81,6 +82,8 @@ def load(path: str = LIB_PATH):
     L.qa_set_mu.argtypes = [vp, i, d]
     L.qa_set_params.argtypes = [vp, C.POINTER(Hoppings), C.POINTER(Interaction), vp]
     L.qa_gw_backward.argtypes = [vp, vp, d, vp, vp, vp, vp, vp, vp, vp]
+    L.qa_set_pair_basis.argtypes = [vp, i]
+    L.qa_get_pair_basis.argtypes = [vp, C.POINTER(i), C.POINTER(i), vp]
     L.qa_destroy.argtypes = [vp]
     L.qa_destroy.restype = None
     L.qa_strerror.argtypes = [i]
@@ -112,10 +115,12 @@ class Problem:
     """Host-side problem handle (qa_create): validation, DLR grid and FFT plans.
 
     `model` provides n, norb, s_spin, hop_R, hop_t, eps, V_R, V, beta, Lambda,
-    eps_dlr and filling (see workloads.Model).  No GPU is touched.
+    eps_dlr and filling (see workloads.Model).  `pairs` selects the basis of
+    the big tensors: "auto" (reduced on the mixed path), "full" or "reduced"
+    (include/qa.h, qa_set_pair_basis).  No GPU is touched.
     """
 
-    def __init__(self, model, precision: str = "fp64"):
+    def __init__(self, model, precision: str = "fp64", pairs: str = "auto"):
         L = load()
         self.model = model
         self.precision = {"fp64": QA_FP64, "mixed": QA_MIXED}[precision]
@@ -127,10 +132,23 @@ class Problem:
                            float(model.Lambda), float(model.eps_dlr), float(model.filling),
                            self.precision, C.byref(ctx)), "qa_create")
         self.ctx = ctx
+        mode = {"auto": QA_PAIRS_AUTO, "full": QA_PAIRS_FULL, "reduced": QA_PAIRS_REDUCED}[pairs]
+        _check(L.qa_set_pair_basis(ctx, mode), "qa_set_pair_basis")
         nk, no, r = C.c_int(), C.c_int(), C.c_int()
         _check(L.qa_get_sizes(ctx, C.byref(nk), C.byref(no), C.byref(r)), "qa_get_sizes")
         self.nk, self.norb, self.r = nk.value, no.value, r.value
         self.npair = self.norb * self.norb
+        self.rho, self.reduced, self.basis = self.pair_basis()
+        self.nb = self.rho if self.reduced else self.npair
+
+    def pair_basis(self):
+        """(rho, reduced basis in use, B [npair, rho] complex128)."""
+        rho, act = C.c_int(), C.c_int()
+        _check(load().qa_get_pair_basis(self.ctx, C.byref(rho), C.byref(act), None), "qa_get_pair_basis")
+        B = np.zeros(2 * self.npair * max(rho.value, 1))
+        _check(load().qa_get_pair_basis(self.ctx, None, None, B.ctypes.data), "qa_get_pair_basis")
+        B = B.view(np.complex128)[:self.npair * rho.value].reshape(self.npair, rho.value)
+        return rho.value, bool(act.value), B
 
     def _structs(self, model):
         hR = _as(model.hop_R, np.int32)
@@ -187,11 +205,11 @@ class Problem:
 class Context(Problem):
     """A bound context: Problem + device workspace (torch) + G0 (qa_bind)."""
 
-    def __init__(self, model, precision: str = "fp64", device: str = "cuda"):
+    def __init__(self, model, precision: str = "fp64", device: str = "cuda", pairs: str = "auto"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("libqa needs a CUDA GPU; no CPU fallback exists")
-        super().__init__(model, precision)
+        super().__init__(model, precision, pairs)
         self.torch = torch
         self.device = torch.device(device)
         nbytes = self.workspace_size()
@@ -264,9 +282,10 @@ class Context(Problem):
         return n.view(np.complex128).reshape(self.norb, self.norb), N.value
 
     def get(self, which: int):
-        """Copy an intermediate into a new device tensor (shape per include/qa.h)."""
+        """Copy an intermediate into a new device tensor (shape per include/qa.h;
+        the big tensors are [r][nb][nb][N_k], nb = rho on the reduced basis)."""
         torch = self.torch
-        r, no, np_, nk = self.r, self.norb, self.npair, self.nk
+        r, no, np_, nk = self.r, self.norb, self.nb, self.nk
         big_dt = torch.complex128 if self.precision == QA_FP64 else torch.complex64
         shapes = {QA_P_QNU: ((r, np_, np_, nk), big_dt), QA_WC_RTAU: ((r, np_, np_, nk), big_dt),
                   QA_SIGC_KTAU: ((r, no, no, nk), big_dt), QA_SIGC_KIW: ((r, no, no, nk), big_dt),

@@ -17,16 +17,17 @@ def main(argv=None):
     ap.add_argument("--workload", default="five-orbital-16x16x8")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="mixed")
     ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--pairs", choices=["auto", "full", "reduced"], default="auto")
     args = ap.parse_args(argv)
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import workloads
     from . import build, qa
     build()
-    ctx = qa.Context(workloads.config(args.workload), args.precision)
+    ctx = qa.Context(workloads.config(args.workload), args.precision, pairs=args.pairs)
     G = None
     for i in range(args.steps):
         G, mu, n, st = ctx.step(G, None, timing=True)
-        print(json.dumps({"step": i, "mu": mu, "N": st["N"], "mu_evals": st["mu_evals"],
+        print(json.dumps({"step": i, "pairs": ctx.nb, "mu": mu, "N": st["N"], "mu_evals": st["mu_evals"],
                           "launches": st["launches"], "stage_ms": st["stage_ms"]}))
 
 

@@ -111,3 +111,55 @@ def test_invalid_inputs_rejected():
             qa.Problem(mm)
     p = qa.Problem(m)
     assert p.workspace_size() > 0
+
+
+def subspace_projector(Vs, tol=1e-12):
+    """Projector on the span of the columns of every V(R) and V(R)^H, from an
+    SVD of the stacked matrix (independent of the library's construction)."""
+    X = np.concatenate([np.concatenate([V, V.conj().T], axis=1) for V in Vs], axis=1)
+    U, s, _ = np.linalg.svd(X)
+    k = int(np.sum(s > tol * s[0])) if s.size and s[0] > 0 else 0
+    return U[:, :k] @ U[:, :k].conj().T, k
+
+
+@pytest.mark.parametrize("name,rho", [("five-orbital-6x5x1", 15), ("five-orbital-32x32x8", 15),
+                                      ("graphene-36x36", 2), ("peierls-3x3", 3),
+                                      ("square-8x8", 1)])
+def test_pair_basis(name, rho):
+    """The reduced pair basis: its rank, orthonormality, the subspace it spans
+    (against an SVD), V(R) = Pi V(R) Pi, and the rank of the Kanamori plus
+    density-density interaction, norb + norb(norb - 1)/2 (one density per orbital
+    and one symmetric exchange/pair-hopping combination per orbital pair)."""
+    m = wl.config(name)
+    p = qa.Problem(m, "mixed")
+    assert p.rho == rho
+    B = p.basis
+    assert B.shape == (m.norb ** 2, rho)
+    assert np.abs(B.conj().T @ B - np.eye(rho)).max() <= 1e-14
+    Pi_svd, k = subspace_projector(list(m.V))
+    assert k == rho
+    Pi = B @ B.conj().T
+    assert np.abs(Pi - Pi_svd).max() <= 1e-12
+    for V in m.V:
+        assert np.abs(Pi @ V @ Pi - V).max() <= 1e-14 * max(1.0, np.abs(V).max())
+    # default choice: reduced on the mixed path when it is smaller, full on FP64
+    assert p.reduced == (rho < m.norb ** 2)
+    assert not qa.Problem(m, "fp64").reduced
+    assert qa.Problem(m, "fp64", pairs="reduced").reduced == (rho < m.norb ** 2)
+    assert not qa.Problem(m, "mixed", pairs="full").reduced
+    # the reduced workspace is smaller
+    if rho < m.norb ** 2:
+        assert qa.Problem(m, "mixed").workspace_size() < qa.Problem(m, "mixed", pairs="full").workspace_size()
+
+
+def test_pair_basis_rank_deficient_block():
+    """A model whose only coupling is a rank-1 block on the pairs (01), (10)
+    gets the single vector (e_01 + e_10)/sqrt 2 (up to sign), not the unit vectors."""
+    m = wl.config("peierls-3x3")
+    V = np.zeros_like(m.V)
+    V[0][1, 1] = V[0][1, 2] = V[0][2, 1] = V[0][2, 2] = 0.7
+    m.V = V
+    p = qa.Problem(m, "mixed")
+    assert p.rho == 1 and p.reduced
+    b = p.basis[:, 0] * np.sign(p.basis[1, 0].real)
+    assert np.allclose(b, [0, 2 ** -0.5, 2 ** -0.5, 0], atol=1e-15)

@@ -4,6 +4,12 @@ Small workloads span several FFT tiles, ragged grids (5x3x2, 6x5x1, 4x3x2), the
 degenerate 1x1x1 grid, complex hoppings and 1, 2 and 5 orbitals; each is
 compared element by element on G0, P(q, i nu), W^C(R, tau), Sigma^C(k, tau),
 Sigma^C(k, i w), Sigma^H + Sigma^F, the new G(k, tau), mu and the density.
+On the reduced pair basis (include/qa.h, qa_set_pair_basis) the GPU holds
+Pt = B^H P B and Wt^C = B^H W^C B; they are compared with B^H P B of the
+oracle's P and, expanded as B Wt^C B^H, with the oracle's full W^C (exact,
+since W^C lives in the interaction subspace).  B itself is pinned on the CPU
+(tests/test_abi.py): orthonormal, and spanning the same subspace as an SVD of
+the stacked V(R), V(R)^H.
 
 Bounds (relative max-norm error, max|gpu - oracle| / max|oracle|):
   FP64 path : 1e-10 for every quantity (the target stated for the FP64 path).
@@ -73,12 +79,28 @@ def gpu_arrays(ctx, qa):
     return out
 
 
+def project_P(ctx, P):
+    """B^H P B of a [.., npair, npair, k] array on the reduced basis, else P."""
+    if not ctx.reduced:
+        return P
+    B = ctx.basis
+    return np.einsum("ai,...abk,bj->...ijk", B.conj(), P, B)
+
+
+def expand_W(ctx, W):
+    """B Wt B^H of a [.., rho, rho, k] array on the reduced basis, else W."""
+    if not ctx.reduced:
+        return W
+    B = ctx.basis
+    return np.einsum("ai,...ijk,bj->...abk", B, W, B.conj())
+
+
 def compare_step(ctx, qa, m, o, G_gpu, mu, n_loc, bound):
     arr = gpu_arrays(ctx, qa)
     no = m.norb
     errs = {
-        "P_qnu": rel(arr["P_qnu"], k_last(o["P_qnu"])),
-        "WC_Rtau": rel(arr["WC_Rtau"], k_last(o["WC_Rtau"])),
+        "P_qnu": rel(arr["P_qnu"], project_P(ctx, k_last(o["P_qnu"]))),
+        "WC_Rtau": rel(expand_W(ctx, arr["WC_Rtau"]), k_last(o["WC_Rtau"])),
         "sigc_ktau": rel(arr["sigc_ktau"], k_last(o["sigc_ktau"])),
         "sigc_kiw": rel(arr["sigc_kiw"], k_last(o["sigc_kiw"])),
         "sighf": rel(arr["sighf"], o["sig_hf_k"]),
@@ -120,15 +142,34 @@ def test_fp64_two_steps(name):
     assert np.abs(n_chk - n2).max() <= 1e-9
 
 
+@pytest.mark.parametrize("pairs", ["auto", "full"])
 @pytest.mark.parametrize("name", SMALL)
-def test_mixed_one_step(name):
+def test_mixed_one_step(name, pairs):
     from paper_2604_22223_gb300 import qa
     m, d, G0, mu0, outs = oracle_run(name)
-    ctx = qa.Context(m, "mixed")
+    ctx = qa.Context(m, "mixed", pairs=pairs)
+    assert ctx.reduced == (pairs == "auto" and 0 < ctx.rho < ctx.npair)
     g = ctx.get(qa.QA_G0).cpu().numpy()
     assert rel(g, k_last(G0)) <= FP64_BOUND        # G0 is built in FP64 in both modes
     G1, mu1, n1, st = ctx.step()
     compare_step(ctx, qa, m, outs[0], G1, mu1, n1, MIXED_BOUND)
+
+
+@pytest.mark.parametrize("name", ["peierls-3x3", "peierls-5x3x2", "five-orbital-6x5x1",
+                                  "five-orbital-4x3x2", "graphene-6x6"])
+def test_fp64_reduced_two_steps(name):
+    """The reduced pair basis on the FP64 path meets the FP64 bound."""
+    from paper_2604_22223_gb300 import qa
+    m, d, G0, mu0, outs = oracle_run(name)
+    ctx = qa.Context(m, "fp64", pairs="reduced")
+    assert ctx.reduced and ctx.rho < ctx.npair
+    G1, mu1, n1, st = ctx.step()
+    compare_step(ctx, qa, m, outs[0], G1, mu1, n1, FP64_BOUND)
+    G2, mu2, n2, st = ctx.step(G1)
+    compare_step(ctx, qa, m, outs[1], G2, mu2, n2, FP64_BOUND)
+    # the adjoint needs the full basis
+    with pytest.raises(qa.QAError):
+        ctx.backward(G1, mu2)
 
 
 def test_in_place_step_and_timing():
