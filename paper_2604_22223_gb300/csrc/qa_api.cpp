@@ -107,9 +107,12 @@ struct qa_ctx {
   int nH_user = 0;
   // tensor-core DLR operands (mixed contexts)
   bool use_tc = false;
-  std::vector<uint16_t> tc_Ttn, tc_Tnt;
+  std::vector<uint16_t> tc_Ttn, tc_Tnt, tc_Trefl, tc_Ttw, tc_Twt;
   void* d_tc_Ttn = nullptr;
   void* d_tc_Tnt = nullptr;
+  void* d_tc_Trefl = nullptr;
+  void* d_tc_Ttw = nullptr;
+  void* d_tc_Twt = nullptr;
   // pair basis of the big tensors: full (npair) or reduced (rho, qa_basis.cpp)
   int pair_mode = QA_PAIRS_AUTO;
   bool reduced = false;
@@ -123,6 +126,9 @@ struct qa_ctx {
   int* d_tsig = nullptr;
   void* d_csig = nullptr;
   double2* d_sV = nullptr;        // [nV][rho][rho] FP64
+  void* d_Bm = nullptr;           // mu-independent part of the G Dyson argument (sized for FP64)
+  double2* d_phV = nullptr;       // [nV + 1][N_k] e^{+i k.R_v} of the interaction's R list
+  double mu_ref = 0.0;            // reference chemical potential folded into d_Bm
 };
 
 namespace {
@@ -258,6 +264,8 @@ size_t layout(qa_ctx* c, char* base) {
   c->d_SigIw = take(r * no2 * nk * es);
   c->d_Giw = take(r * no2 * nk * 16);
   c->d_Gt = take(r * no2 * nk * 16);
+  c->d_Bm = take(r * no2 * nk * 16);
+  c->d_phV = static_cast<double2*>(take((c->nV + 1) * nk * 16));
   // big tensors last; P must also hold the FP64 V(q) staging of qa_bind
   c->d_P = take(std::max(r * nb2 * nk * es, nk * nb2 * 16));
   c->d_W = take(r * nb2 * nk * es);
@@ -270,6 +278,9 @@ size_t layout(qa_ctx* c, char* base) {
   if (c->precision == QA_MIXED && c->use_tc) {
     c->d_tc_Ttn = take(c->tc_Ttn.size() * 2);
     c->d_tc_Tnt = take(c->tc_Tnt.size() * 2);
+    c->d_tc_Trefl = take(c->tc_Trefl.size() * 2);
+    c->d_tc_Ttw = take(c->tc_Ttw.size() * 2);
+    c->d_tc_Twt = take(c->tc_Twt.size() * 2);
   }
   if (c->reduced) {
     c->d_sV = static_cast<double2*>(take(std::max(1, c->nV) * nb2 * 16));
@@ -351,12 +362,28 @@ int upload_interaction(qa_ctx* c, cudaStream_t st) {
   return QA_OK;
 }
 
-// Density and derivative at mu.  Result: N(mu), dN/dmu.
+// The mu-independent part of the G Dyson argument, relative to mu_ref, and
+// an upper bound of the norm of H + Sigma - mu_ref (all k, all DLR nodes).
 template <typename T>
-int eval_density(qa_ctx* c, const double2* SigHF, const void* SigIw, const DevTables& tab,
-                 double mu, double* N, double* dN, cudaStream_t st) {
-  QA_LAUNCH(c, 1, qa::launch_dyson_g<T>(c->d_Hk, SigHF, SigIw, tab.dw, c->d_iw, mu, c->r, c->norb, c->nk,
-                               nullptr, c->d_part, c->nblocks_g, 0, c->d_err, st));
+int prepare_g(qa_ctx* c, const double2* SigHF, const void* SigIw, double mu_ref, double* bound,
+              cudaStream_t st) {
+  c->mu_ref = mu_ref;
+  QA_LAUNCH(c, 1, qa::launch_dyson_g_prep<T>(c->d_Hk, SigHF, SigIw, mu_ref, c->r, c->norb, c->nk,
+                                             c->d_Bm, c->d_part, c->nblocks_g, st));
+  QA_LAUNCH(c, 1, qa::launch_reduce_pairs(c->d_part, c->nblocks_g, 1, c->d_red, st));
+  double h[2];
+  QA_TRY(cudaMemcpyAsync(h, c->d_red, 16, cudaMemcpyDeviceToHost, st));
+  QA_TRY(cudaStreamSynchronize(st));
+  *bound = h[0];
+  return QA_OK;
+}
+
+// Density and derivative at mu (after prepare_g).  Result: N(mu), dN/dmu.
+template <typename T>
+int eval_density(qa_ctx* c, const DevTables& tab, double mu, double* N, double* dN,
+                 cudaStream_t st) {
+  QA_LAUNCH(c, 1, qa::launch_dyson_g<T>(c->d_Bm, tab.dw, c->d_iw, mu - c->mu_ref, c->r, c->norb,
+                                        c->nk, nullptr, c->d_part, c->nblocks_g, 0, c->d_err, st));
   QA_LAUNCH(c, 1, qa::launch_reduce_pairs(c->d_part, c->nblocks_g, 0, c->d_red, st));
   double h[2];
   QA_TRY(cudaMemcpyAsync(h, c->d_red, 16, cudaMemcpyDeviceToHost, st));
@@ -367,9 +394,10 @@ int eval_density(qa_ctx* c, const double2* SigHF, const void* SigIw, const DevTa
 }
 
 // Chemical potential: the root of N(mu) = filling (N increases with mu).
-// A bracket is found by marching from the warm start (the previous mu) in
-// the direction of the root with growing steps, clamped to the window
-// |mu| <= max ||H + Sigma|| + 1 + 10/beta where N is empty or full; then
+// A bracket is found by marching from the warm start mu_s (the previous mu)
+// in the direction of the root with growing steps, clamped to the window
+// |mu - mu_s| <= max ||H + Sigma - mu_s|| + 1 + 10/beta outside which N is
+// empty or full; then
 // bisection with Newton steps taken when they stay inside the bracket and
 // at least halve the step before last (safeguarded Newton, "rtsafe").
 // Stop when |N - filling| <= tolN or the bracket (or, on the mixed path
@@ -377,14 +405,12 @@ int eval_density(qa_ctx* c, const double2* SigHF, const void* SigIw, const DevTa
 template <typename T>
 int mu_search(qa_ctx* c, const double2* SigHF, const void* SigIw, const DevTables& tab,
               double mu_start, double* mu_out, double* N_out, int* evals, cudaStream_t st) {
-  QA_LAUNCH(c, 1, qa::launch_norm_bound<T>(c->d_Hk, SigHF, SigIw, c->r, c->norb, c->nk, c->d_part,
-                                           c->nblocks_g, st));
-  QA_LAUNCH(c, 1, qa::launch_reduce_pairs(c->d_part, c->nblocks_g, 1, c->d_red, st));
-  double h[2];
-  QA_TRY(cudaMemcpyAsync(h, c->d_red, 16, cudaMemcpyDeviceToHost, st));
-  QA_TRY(cudaStreamSynchronize(st));
-  if (!std::isfinite(h[0])) return QA_ERANGE;
-  const double wid = h[0] + 1.0 + 10.0 / c->beta;
+  const double mu_s = std::isfinite(mu_start) ? mu_start : 0.0;
+  double bound = 0;
+  if (int rc = prepare_g<T>(c, SigHF, SigIw, mu_s, &bound, st)) return rc;
+  if (!std::isfinite(bound)) return QA_ERANGE;
+  const double wid = bound + 1.0 + 10.0 / c->beta;
+  const double wlo = mu_s - wid, whi = mu_s + wid;
   const double target = c->filling;
   const bool fp64 = sizeof(T) == 8;
   // FP32 densities carry ~1e-6 relative noise: stop at that level on the mixed path
@@ -393,7 +419,7 @@ int mu_search(qa_ctx* c, const double2* SigHF, const void* SigIw, const DevTable
   int count = 0;
   double N = 0, dN = 0;
   auto ev = [&](double m, double* f, double* d) -> int {
-    int rc = eval_density<T>(c, SigHF, SigIw, tab, m, &N, &dN, st);
+    int rc = eval_density<T>(c, tab, m, &N, &dN, st);
     ++count;
     if (rc != QA_OK) return rc;
     if (!std::isfinite(N)) return QA_ERANGE;
@@ -401,7 +427,7 @@ int mu_search(qa_ctx* c, const double2* SigHF, const void* SigIw, const DevTable
     *d = dN;
     return QA_OK;
   };
-  double mu = std::isfinite(mu_start) ? std::min(std::max(mu_start, -wid), wid) : 0.0;
+  double mu = mu_s;
   double f = 0, d = 0;
   int rc = ev(mu, &f, &d);
   if (rc != QA_OK) return rc;
@@ -409,17 +435,17 @@ int mu_search(qa_ctx* c, const double2* SigHF, const void* SigIw, const DevTable
   if (std::fabs(f) > tolN) {
     // march toward the root until the sign of N - filling changes
     double step = (d > 0 && std::isfinite(f / d)) ? 1.5 * std::fabs(f / d) : 1.0;
-    step = std::min(std::max(step, 1e-6), 2.0 * wid);
+    step = std::min(std::max(step, 1e-6), wid);
     const double dir = f < 0 ? 1.0 : -1.0;
     double fa = f, a = mu, b = mu, fb = f, db = d;
     for (int m = 0; m < 64; ++m) {
       b = a + dir * step;
-      if (b > wid) b = wid;
-      if (b < -wid) b = -wid;
+      if (b > whi) b = whi;
+      if (b < wlo) b = wlo;
       rc = ev(b, &fb, &db);
       if (rc != QA_OK) return rc;
       if ((fb < 0) != (fa < 0) || std::fabs(fb) <= tolN) break;
-      if (b == wid || b == -wid) return QA_ERANGE;   // filling not reachable in the window
+      if (b == whi || b == wlo) return QA_ERANGE;   // filling not reachable in the window
       a = b;
       fa = fb;
       step *= 4.0;
@@ -507,17 +533,20 @@ int reset_err(qa_ctx* c, cudaStream_t st) {
   return QA_OK;
 }
 
-// G(k,tau) = Twt G(k, i w) at mu, and the local density matrix.
+// G(k,tau) = Twt G(k, i w) at mu (after prepare_g), and the local density matrix.
 template <typename T>
-int finish_g(qa_ctx* c, const double2* SigHF, const void* SigIw, const DevTables& tab, double mu,
-             void* G_out_c128, double* n_out, cudaStream_t st) {
+int finish_g(qa_ctx* c, const DevTables& tab, double mu, void* G_out_c128, double* n_out,
+             cudaStream_t st) {
   const long long ncol = static_cast<long long>(c->norb) * c->norb * c->nk;
-  QA_LAUNCH(c, 1, qa::launch_dyson_g<T>(c->d_Hk, SigHF, SigIw, tab.dw, c->d_iw, mu, c->r, c->norb, c->nk,
-                               c->d_Giw, c->d_part, c->nblocks_g, 1, c->d_err, st));
+  QA_LAUNCH(c, 1, qa::launch_dyson_g<T>(c->d_Bm, tab.dw, c->d_iw, mu - c->mu_ref, c->r, c->norb,
+                                        c->nk, c->d_Giw, c->d_part, c->nblocks_g, 1, c->d_err, st));
   if (sizeof(T) == 8) {
     QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Twt, c->r, c->r, c->d_Giw, G_out_c128, ncol, st));
   } else {
-    QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Twt, c->r, c->r, c->d_Giw, c->d_Gt, ncol, st));
+    if (c->use_tc)
+      QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Twt, c->r, c->d_Giw, c->d_Gt, ncol, c->d_err, st));
+    else
+      QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Twt, c->r, c->r, c->d_Giw, c->d_Gt, ncol, st));
     QA_LAUNCH(c, 1, qa::launch_c64_to_c128(static_cast<const float2*>(c->d_Gt),
                                   static_cast<double2*>(G_out_c128), ncol * c->r, st));
   }
@@ -572,20 +601,23 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
   const int r = c->r, no2 = c->norb * c->norb, nk = c->nk, nb2 = c->nb * c->nb;
   const long long ncs = static_cast<long long>(no2) * nk;     // small-tensor columns
   const long long ncb = static_cast<long long>(nb2) * nk;     // big-tensor columns
-  // n(k) = -G(k, beta^-) of the input, Hartree and Fock (FP64)
-  QA_LAUNCH(c, 1, qa::launch_dlr_apply<double>(c->t64.dtau, 1, r, Gin, c->d_nk, ncs, st));
-  QA_LAUNCH(c, 1, qa::launch_density_R(c->d_nk, c->d_vR, c->nV + 1, no2, nullptr, nk, c->n[0], c->n[1],
-                              c->n[2], c->d_nR, st));
-  QA_LAUNCH(c, 2, qa::launch_hf(c->d_vV, c->d_nR, c->d_vR, c->nV, c->norb, c->nspin, nullptr, nk, c->n[0],
-                       c->n[1], c->n[2], c->d_sigFR, c->d_SigHF, st));
-  tm.mark();  // 0: HF
-  // G in compute precision, G(k, beta - tau), real-space G
+  // n(k) = -G(k, beta^-) of the input (FP64) with G in the compute precision,
+  // then Hartree and Fock (FP64)
   const void* Gk = Gin;
-  if (sizeof(T) == 4) {
-    QA_LAUNCH(c, 1, qa::launch_c128_to_c64(Gin, static_cast<float2*>(c->d_Gk), ncs * r, st));
-    Gk = c->d_Gk;
-  }
-  QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Trefl, r, r, Gk, c->d_Grefl, ncs, st));
+  if (sizeof(T) == 4) Gk = c->d_Gk;
+  QA_LAUNCH(c, 1, qa::launch_g_input(Gin, static_cast<const double2*>(c->t64.dtau), r, ncs,
+                                     sizeof(T) == 4 ? static_cast<float2*>(c->d_Gk) : nullptr,
+                                     c->d_nk, st));
+  QA_LAUNCH(c, 1, qa::launch_density_R(c->d_nk, c->d_vR, c->nV + 1, no2, nullptr, nk, c->n[0], c->n[1],
+                              c->n[2], c->d_nR, st, c->d_phV));
+  QA_LAUNCH(c, 2, qa::launch_hf(c->d_vV, c->d_nR, c->d_vR, c->nV, c->norb, c->nspin, nullptr, nk, c->n[0],
+                       c->n[1], c->n[2], c->d_sigFR, c->d_SigHF, st, c->d_phV));
+  tm.mark();  // 0: HF
+  // G(k, beta - tau), real-space G
+  if (sizeof(T) == 4 && c->use_tc)
+    QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Trefl, r, Gk, c->d_Grefl, ncs, c->d_err, st));
+  else
+    QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Trefl, r, r, Gk, c->d_Grefl, ncs, st));
   QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, +1, Gk, c->d_GR, ncs / nk * r, st));
   QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, +1, c->d_Grefl, c->d_Grefl, ncs / nk * r, st));
   tm.mark();  // 1: G -> R
@@ -620,7 +652,10 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
     QA_LAUNCH(c, 1, qa::launch_sigma<T>(c->d_GR, c->d_W, c->d_SigC, r, c->norb, nk, st));
   tm.mark();  // 8: Sigma contraction
   QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, -1, c->d_SigC, c->d_SigC, ncs / nk * r, st));
-  QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Ttw, r, r, c->d_SigC, c->d_SigIw, ncs, st));
+  if (sizeof(T) == 4 && c->use_tc)
+    QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Ttw, r, c->d_SigC, c->d_SigIw, ncs, c->d_err, st));
+  else
+    QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Ttw, r, r, c->d_SigC, c->d_SigIw, ncs, st));
   tm.mark();  // 9: Sigma -> (k, i w)
   return QA_OK;
 }
@@ -638,9 +673,10 @@ int gw_step_impl(qa_ctx* c, const void* G_in, void* G_out, double* mu_out, doubl
   int evals = 0;
   int rc = QA_OK;
   if (c->mu_fixed) {
-    double dN = 0;
+    double dN = 0, bound = 0;
     mu = c->mu_value;
-    rc = eval_density<T>(c, c->d_SigHF, c->d_SigIw, tab, mu, &N, &dN, st);
+    rc = prepare_g<T>(c, c->d_SigHF, c->d_SigIw, mu, &bound, st);
+    if (rc == QA_OK) rc = eval_density<T>(c, tab, mu, &N, &dN, st);
     evals = 1;
   } else {
     rc = mu_search<T>(c, c->d_SigHF, c->d_SigIw, tab, c->have_mu ? c->mu : c->mu0, &mu, &N,
@@ -648,7 +684,7 @@ int gw_step_impl(qa_ctx* c, const void* G_in, void* G_out, double* mu_out, doubl
   }
   if (rc != QA_OK) return rc;
   tm.mark();  // 10: mu search
-  rc = finish_g<T>(c, c->d_SigHF, c->d_SigIw, tab, mu, G_out, n_out, st);
+  rc = finish_g<T>(c, tab, mu, G_out, n_out, st);
   if (rc != QA_OK) return rc;
   tm.mark();  // 11: Dyson G + G(tau)
   tm.finish(stats);
@@ -876,6 +912,9 @@ int qa_create(const qa_lattice* lat, const qa_hoppings* hop, const qa_interactio
     if (c->use_tc) {
       qa::pack_dlr_tc(c->mats.Ttn.data(), c->r, &c->tc_Ttn);
       qa::pack_dlr_tc(c->mats.Tnt.data(), c->r, &c->tc_Tnt);
+      qa::pack_dlr_tc(c->mats.Trefl.data(), c->r, &c->tc_Trefl);
+      qa::pack_dlr_tc(c->mats.Ttw.data(), c->r, &c->tc_Ttw);
+      qa::pack_dlr_tc(c->mats.Twt.data(), c->r, &c->tc_Twt);
     }
   }
   // FFT plans and the -R map
@@ -944,6 +983,9 @@ int qa_bind(qa_ctx* c, void* workspace, size_t bytes, void* stream) {
   if (c->use_tc) {
     QA_TRY(cudaMemcpyAsync(c->d_tc_Ttn, c->tc_Ttn.data(), c->tc_Ttn.size() * 2, cudaMemcpyHostToDevice, st));
     QA_TRY(cudaMemcpyAsync(c->d_tc_Tnt, c->tc_Tnt.data(), c->tc_Tnt.size() * 2, cudaMemcpyHostToDevice, st));
+    QA_TRY(cudaMemcpyAsync(c->d_tc_Trefl, c->tc_Trefl.data(), c->tc_Trefl.size() * 2, cudaMemcpyHostToDevice, st));
+    QA_TRY(cudaMemcpyAsync(c->d_tc_Ttw, c->tc_Ttw.data(), c->tc_Ttw.size() * 2, cudaMemcpyHostToDevice, st));
+    QA_TRY(cudaMemcpyAsync(c->d_tc_Twt, c->tc_Twt.data(), c->tc_Twt.size() * 2, cudaMemcpyHostToDevice, st));
   }
   if (c->precision == QA_FP64) {
     auto ctrans = [r](const std::vector<cd>& T) {
@@ -990,6 +1032,7 @@ int qa_bind(qa_ctx* c, void* workspace, size_t bytes, void* stream) {
   QA_TRY(cudaMemcpyAsync(c->d_hR, c->hopR.data(), c->hopR.size() * 4, cudaMemcpyHostToDevice, st));
   QA_TRY(upload_c<double>(c->d_hH, c->hopH, st));
   QA_TRY(cudaMemcpyAsync(c->d_vR, c->vR.data(), c->vR.size() * 4, cudaMemcpyHostToDevice, st));
+  QA_LAUNCH(c, 1, qa::launch_phase_table(c->d_vR, c->nV + 1, c->nk, c->n[0], c->n[1], c->n[2], c->d_phV, st));
   if (c->nV > 0) QA_TRY(upload_c<double>(c->d_vV, c->vV, st));
   // H(k), V(q) (or S(q) on the reduced pair basis)
   const int no2 = c->norb * c->norb;
@@ -1002,7 +1045,7 @@ int qa_bind(qa_ctx* c, void* workspace, size_t bytes, void* stream) {
   int ev = 0;
   int rc = mu_search<double>(c, nullptr, nullptr, c->t64, 0.0, &mu0, &N0, &ev, st);
   if (rc != QA_OK) return rc;
-  rc = finish_g<double>(c, nullptr, nullptr, c->t64, mu0, c->d_G0, nullptr, st);
+  rc = finish_g<double>(c, c->t64, mu0, c->d_G0, nullptr, st);
   if (rc != QA_OK) return rc;
   QA_TRY(cudaStreamSynchronize(st));
   rc = check_err(c, nullptr, st);
@@ -1068,8 +1111,8 @@ int qa_density(qa_ctx* c, const void* G, double* n_out, double* N_total, void* s
   if (!c->bound) return QA_ESTATE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int no2 = c->norb * c->norb;
-  QA_LAUNCH(c, 1, qa::launch_dlr_apply<double>(c->t64.dtau, 1, c->r, G, c->d_nk,
-                                      static_cast<long long>(no2) * c->nk, st));
+  QA_LAUNCH(c, 1, qa::launch_g_input(static_cast<const double2*>(G), static_cast<const double2*>(c->t64.dtau),
+                                     c->r, static_cast<long long>(no2) * c->nk, nullptr, c->d_nk, st));
   QA_LAUNCH(c, 1, qa::launch_k_average<double>(c->d_nk, no2, c->nk, c->d_nloc, st));
   std::vector<double> h(2 * no2);
   QA_TRY(cudaMemcpyAsync(h.data(), c->d_nloc, no2 * 16, cudaMemcpyDeviceToHost, st));

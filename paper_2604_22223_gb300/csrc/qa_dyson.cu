@@ -12,8 +12,9 @@
 // Green's function (paper Eq. for the full Green's function):
 // G(k, i w_n) = (i w_n + mu - H(k) - Sigma^HF(k) - Sigma^C(k, i w_n))^-1 per
 // (n, k), one thread per system, Gauss-Jordan with partial pivoting in
-// registers.  The density N(mu) = (s/N_k) sum_{k,n} Re(dw_n Tr G) and its
-// derivative -(s/N_k) sum Re(dw_n Tr G^2) are accumulated in FP64.
+// registers, from a per-step table of the mu-independent part.  The density
+// N(mu) = (s/N_k) sum_{k,n} Re(dw_n Tr G) and its derivative
+// -(s/N_k) sum Re(dw_n Tr G^2) are accumulated in FP64.
 #include "qa_common.cuh"
 
 namespace qa {
@@ -232,10 +233,13 @@ __global__ void __launch_bounds__(kWarpsR * 32) dyson_w_reg_kernel(const float2*
       float2 apc = make_float2(__shfl_sync(0xffffffffu, a[c].x, p, W),
                                __shfl_sync(0xffffffffu, a[c].y, p, W));
       float2 f = used ? make_float2(0.f, 0.f) : cmul(a[c], cinv(apc));
-      // a fixed range with a predicate (not j = c + 1 ..) keeps a[] in registers
+      // Up to 16 rows, a fixed range with a predicate (not j = c + 1 ..) keeps
+      // a[] in registers.  The 25-row systems keep the shorter loop: their
+      // register-resident form needs 162 registers (one block per SM) and
+      // measured slower than the variant that holds a[] in local memory.
 #pragma unroll
-      for (int j = 1; j < MAXN; ++j) {
-        if (j > c && j < n) {
+      for (int j = (W < 32 ? 1 : c + 1); j < MAXN; ++j) {
+        if ((W == 32 || j > c) && j < n) {
           float2 apj = make_float2(__shfl_sync(0xffffffffu, a[j].x, p, W),
                                    __shfl_sync(0xffffffffu, a[j].y, p, W));
           a[j] = cfms(f, apj, a[j]);
@@ -350,17 +354,18 @@ __device__ __forceinline__ bool gj_inverse(V (&a)[NO][NO]) {
   return bad;
 }
 
-// T: arithmetic of the inverse; TS: storage type of Sigma^C(k, i w) (may be
-// narrower, e.g. the FP64 refinement of mu on the mixed path)
-template <typename T, int NO, typename TS = T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) dyson_g_kernel(const double2* __restrict__ Hk,
-                                                      const double2* __restrict__ SigHF,
-                                                      const cplx<TS>* __restrict__ SigIw,
-                                                      const cplx<T>* __restrict__ dw,
-                                                      const double* __restrict__ iw, double mu,
-                                                      int r, int nk, cplx<T>* Giw, double* part,
-                                                      int mode, int* err) {
-  using V = cplx<T>;
+// Direct form for the FP64 density check of the mixed path: FP64 inverse of
+// i w_n + mu - H - Sigma^HF - Sigma^C with Sigma^C(k, i w) stored as complex64;
+// accumulates the per-block density sums (mode 0 of dyson_g_kernel).
+template <int NO>
+__global__ void __launch_bounds__(256) dyson_g_direct_kernel(const double2* __restrict__ Hk,
+                                                             const double2* __restrict__ SigHF,
+                                                             const float2* __restrict__ SigIw,
+                                                             const double2* __restrict__ dw,
+                                                             const double* __restrict__ iw,
+                                                             double mu, int r, int nk,
+                                                             double* part, int* err) {
+  using V = double2;
   __shared__ double sh[64];
   const long long total = static_cast<long long>(r) * nk;
   double s1 = 0.0, s2 = 0.0;
@@ -375,33 +380,123 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) dyson_g_kernel(co
 #pragma unroll
       for (int j = 0; j < NO; ++j) {
         double2 h = Hk[static_cast<size_t>(k) * NO * NO + i * NO + j];
-        if (SigHF) {
-          double2 s = SigHF[static_cast<size_t>(k) * NO * NO + i * NO + j];
-          h.x += s.x; h.y += s.y;
-        }
-        V m = from_d2<V>(make_double2(-h.x, -h.y));
-        if (SigIw)
-          m = csub(m, from_d2<V>(to_c64d(SigIw[(static_cast<size_t>(n) * NO * NO + i * NO + j) * nk + k])));
-        if (i == j) { m.x += static_cast<T>(mu); m.y += static_cast<T>(iw[n]); }
+        double2 sh2 = SigHF[static_cast<size_t>(k) * NO * NO + i * NO + j];
+        float2 sc = SigIw[(static_cast<size_t>(n) * NO * NO + i * NO + j) * nk + k];
+        V m = make_double2(-h.x - sh2.x - sc.x, -h.y - sh2.y - sc.y);
+        if (i == j) { m.x += mu; m.y += iw[n]; }
+        a[i][j] = m;
+      }
+    bad |= gj_inverse<V, NO>(a);
+    double2 tr = make_double2(0, 0), tr2 = make_double2(0, 0);
+#pragma unroll
+    for (int i = 0; i < NO; ++i) {
+      tr.x += a[i][i].x; tr.y += a[i][i].y;
+#pragma unroll
+      for (int j = 0; j < NO; ++j) {
+        tr2.x += a[i][j].x * a[j][i].x - a[i][j].y * a[j][i].y;
+        tr2.y += a[i][j].x * a[j][i].y + a[i][j].y * a[j][i].x;
+      }
+    }
+    const double2 wn = dw[n];
+    s1 += wn.x * tr.x - wn.y * tr.y;
+    s2 += wn.x * tr2.x - wn.y * tr2.y;
+  }
+  if (bad) atomicCAS(err, 0, QA_ESINGULAR_CODE);
+  block_sum2(s1, s2, sh);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = s1;
+    part[2 * blockIdx.x + 1] = s2;
+  }
+}
+
+// Bm(k, i w_n) = (mu_ref - H(k) - Sigma^HF(k)) - Sigma^C(k, i w_n), the
+// mu-independent part of the inverse's argument, with a reference chemical
+// potential folded into the diagonal in FP64 (the search then adds the small
+// difference mu - mu_ref).  One thread per (k, matrix entry) walks the r
+// frequencies.  part[2 b] receives norb * max (|mu_ref - H - Sigma^HF|_entry +
+// |Sigma^C|_entry), an upper bound of the row-sum norm of H + Sigma^HF +
+// Sigma^C - mu_ref (the window of the chemical-potential search).
+template <typename T>
+__global__ void __launch_bounds__(256) dyson_g_prep_kernel(const double2* __restrict__ Hk,
+                                                           const double2* __restrict__ SigHF,
+                                                           const cplx<T>* __restrict__ SigIw,
+                                                           double mu_ref, int r, int no, int nk,
+                                                           cplx<T>* __restrict__ Bm, double* part) {
+  using V = cplx<T>;
+  __shared__ double sh[32];
+  const int no2 = no * no;
+  const long long total = static_cast<long long>(nk) * no2;
+  double best = 0.0;
+  for (long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
+       idx += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int e = static_cast<int>(idx / nk);
+    const int k = static_cast<int>(idx - static_cast<long long>(e) * nk);
+    double2 h = Hk[static_cast<size_t>(k) * no2 + e];
+    if (SigHF) {
+      const double2 s = SigHF[static_cast<size_t>(k) * no2 + e];
+      h.x += s.x; h.y += s.y;
+    }
+    h.x = -h.x; h.y = -h.y;
+    if (e / no == e % no) h.x += mu_ref;
+    const V hb = from_d2<V>(h);
+    T smax = 0;
+    for (int n = 0; n < r; ++n) {
+      const size_t o = (static_cast<size_t>(n) * no2 + e) * nk + k;
+      V b = hb;
+      if (SigIw) {
+        const V s = SigIw[o];
+        b = csub(hb, s);
+        smax = fmax(smax, sqrt(cabs2(s)));
+      }
+      Bm[o] = b;
+    }
+    best = fmax(best, sqrt(h.x * h.x + h.y * h.y) + static_cast<double>(smax));
+  }
+  best = block_max(best, sh);
+  if (threadIdx.x == 0) { part[2 * blockIdx.x] = best * no; part[2 * blockIdx.x + 1] = 0.0; }
+}
+
+// G(k, i w_n) = (i w_n + dmu + Bm(k, i w_n))^-1, dmu = mu - mu_ref.
+// mode 0: per-block partial sums of Re(dw_n Tr G) and Re(dw_n Tr G^2) (FP64
+// accumulation of the per-system traces); mode 1: also store G.
+template <typename T, int NO>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) dyson_g_kernel(const cplx<T>* __restrict__ Bm,
+                                                      const cplx<T>* __restrict__ dw,
+                                                      const double* __restrict__ iw, double dmu,
+                                                      int r, int nk, cplx<T>* Giw, double* part,
+                                                      int mode, int* err) {
+  using V = cplx<T>;
+  __shared__ double sh[64];
+  const long long total = static_cast<long long>(r) * nk;
+  double s1 = 0.0, s2 = 0.0;
+  bool bad = false;
+  const T dm = static_cast<T>(dmu);
+  for (long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
+       idx += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int n = static_cast<int>(idx / nk);
+    const int k = static_cast<int>(idx - static_cast<long long>(n) * nk);
+    const T wv = static_cast<T>(iw[n]);
+    V a[NO][NO];
+#pragma unroll
+    for (int i = 0; i < NO; ++i)
+#pragma unroll
+      for (int j = 0; j < NO; ++j) {
+        V m = Bm[(static_cast<size_t>(n) * NO * NO + i * NO + j) * nk + k];
+        if (i == j) { m.x += dm; m.y += wv; }
         a[i][j] = m;
       }
     bad |= gj_inverse<V, NO>(a);
     // a = G(k, i w_n)
-    double2 tr = make_double2(0, 0), tr2 = make_double2(0, 0);
+    V tr = cmk<V>(0, 0), tr2 = cmk<V>(0, 0);
 #pragma unroll
     for (int i = 0; i < NO; ++i) {
-      double2 d = to_c64d(a[i][i]);
-      tr.x += d.x; tr.y += d.y;
+      tr = cadd(tr, a[i][i]);
 #pragma unroll
-      for (int j = 0; j < NO; ++j) {
-        double2 x = to_c64d(a[i][j]), y = to_c64d(a[j][i]);
-        tr2.x += x.x * y.x - x.y * y.y;
-        tr2.y += x.x * y.y + x.y * y.x;
-      }
+      for (int j = 0; j < NO; ++j) tr2 = cfma(a[i][j], a[j][i], tr2);
     }
-    double2 wn = to_c64d(dw[n]);
-    s1 += wn.x * tr.x - wn.y * tr.y;
-    s2 += wn.x * tr2.x - wn.y * tr2.y;
+    const V wn = dw[n];
+    s1 += static_cast<double>(wn.x * tr.x - wn.y * tr.y);
+    s2 += static_cast<double>(wn.x * tr2.x - wn.y * tr2.y);
     if (mode == 1) {
 #pragma unroll
       for (int i = 0; i < NO; ++i)
@@ -415,41 +510,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) dyson_g_kernel(co
     part[2 * blockIdx.x] = s1;
     part[2 * blockIdx.x + 1] = s2;
   }
-}
-
-template <typename T, int NO>
-__global__ void __launch_bounds__(256) norm_bound_kernel(const double2* __restrict__ Hk,
-                                                         const double2* __restrict__ SigHF,
-                                                         const cplx<T>* __restrict__ SigIw, int r,
-                                                         int nk, double* part) {
-  __shared__ double sh[32];
-  const long long total = static_cast<long long>(r) * nk;
-  double best = 0.0;
-  for (long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
-       idx += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int n = static_cast<int>(idx / nk);
-    const int k = static_cast<int>(idx - static_cast<long long>(n) * nk);
-#pragma unroll
-    for (int i = 0; i < NO; ++i) {
-      double rs = 0.0;
-#pragma unroll
-      for (int j = 0; j < NO; ++j) {
-        double2 h = Hk[static_cast<size_t>(k) * NO * NO + i * NO + j];
-        if (SigHF) {
-          double2 s = SigHF[static_cast<size_t>(k) * NO * NO + i * NO + j];
-          h.x += s.x; h.y += s.y;
-        }
-        if (SigIw) {
-          double2 s = to_c64d(SigIw[(static_cast<size_t>(n) * NO * NO + i * NO + j) * nk + k]);
-          h.x += s.x; h.y += s.y;
-        }
-        rs += sqrt(h.x * h.x + h.y * h.y);
-      }
-      best = fmax(best, rs);
-    }
-  }
-  best = block_max(best, sh);
-  if (threadIdx.x == 0) { part[2 * blockIdx.x] = best; part[2 * blockIdx.x + 1] = 0.0; }
 }
 
 __global__ void reduce_pairs_kernel(const double* part, int n, int op_max, double* out) {
@@ -499,17 +559,26 @@ cudaError_t launch_dyson_w(const void* P, const void* Vq, void* WC, int r, int n
   return cudaGetLastError();
 }
 
-template <typename T, typename TS>
-cudaError_t launch_dyson_g_impl(const double2* Hk, const double2* SigHF, const void* SigIw,
-                                const void* dw, const double* iw, double mu, int r, int norb,
-                                int nk, void* Giw, double* part, int nblocks, int mode, int* err,
-                                cudaStream_t st) {
-  auto s = reinterpret_cast<const cplx<TS>*>(SigIw);
+template <typename T>
+cudaError_t launch_dyson_g_prep(const double2* Hk, const double2* SigHF, const void* SigIw,
+                                double mu_ref, int r, int norb, int nk, void* Bm, double* part,
+                                int nblocks, cudaStream_t st) {
+  dyson_g_prep_kernel<T><<<nblocks, 256, 0, st>>>(Hk, SigHF, reinterpret_cast<const cplx<T>*>(SigIw),
+                                                  mu_ref, r, norb, nk, reinterpret_cast<cplx<T>*>(Bm),
+                                                  part);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_dyson_g(const void* Bm, const void* dw, const double* iw, double dmu, int r,
+                           int norb, int nk, void* Giw, double* part, int nblocks, int mode,
+                           int* err, cudaStream_t st) {
+  auto b = reinterpret_cast<const cplx<T>*>(Bm);
   auto d = reinterpret_cast<const cplx<T>*>(dw);
   auto g = reinterpret_cast<cplx<T>*>(Giw);
   switch (norb) {
 #define QA_CASE(NO) \
-    case NO: dyson_g_kernel<T, NO, TS><<<nblocks, 256, 0, st>>>(Hk, SigHF, s, d, iw, mu, r, nk, g, part, mode, err); break;
+    case NO: dyson_g_kernel<T, NO><<<nblocks, 256, 0, st>>>(b, d, iw, dmu, r, nk, g, part, mode, err); break;
     QA_CASE(1) QA_CASE(2) QA_CASE(3) QA_CASE(4) QA_CASE(5)
 #undef QA_CASE
     default: return cudaErrorInvalidValue;
@@ -517,29 +586,14 @@ cudaError_t launch_dyson_g_impl(const double2* Hk, const double2* SigHF, const v
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_dyson_g(const double2* Hk, const double2* SigHF, const void* SigIw,
-                           const void* dw, const double* iw, double mu, int r, int norb, int nk,
-                           void* Giw, double* part, int nblocks, int mode, int* err,
-                           cudaStream_t st) {
-  return launch_dyson_g_impl<T, T>(Hk, SigHF, SigIw, dw, iw, mu, r, norb, nk, Giw, part, nblocks,
-                                   mode, err, st);
-}
-
 cudaError_t launch_dyson_g_f64_sig32(const double2* Hk, const double2* SigHF, const void* SigIw,
                                      const void* dw, const double* iw, double mu, int r, int norb,
                                      int nk, double* part, int nblocks, int* err, cudaStream_t st) {
-  return launch_dyson_g_impl<double, float>(Hk, SigHF, SigIw, dw, iw, mu, r, norb, nk, nullptr,
-                                            part, nblocks, 0, err, st);
-}
-
-template <typename T>
-cudaError_t launch_norm_bound(const double2* Hk, const double2* SigHF, const void* SigIw, int r,
-                              int norb, int nk, double* part, int nblocks, cudaStream_t st) {
-  auto s = reinterpret_cast<const cplx<T>*>(SigIw);
+  auto s = reinterpret_cast<const float2*>(SigIw);
+  auto d = reinterpret_cast<const double2*>(dw);
   switch (norb) {
 #define QA_CASE(NO) \
-    case NO: norm_bound_kernel<T, NO><<<nblocks, 256, 0, st>>>(Hk, SigHF, s, r, nk, part); break;
+    case NO: dyson_g_direct_kernel<NO><<<nblocks, 256, 0, st>>>(Hk, SigHF, s, d, iw, mu, r, nk, part, err); break;
     QA_CASE(1) QA_CASE(2) QA_CASE(3) QA_CASE(4) QA_CASE(5)
 #undef QA_CASE
     default: return cudaErrorInvalidValue;
@@ -557,15 +611,13 @@ template cudaError_t launch_dyson_w<double>(const void*, const void*, void*, int
                                             long long*, cudaStream_t);
 template cudaError_t launch_dyson_w<float>(const void*, const void*, void*, int, int, int, int*,
                                            long long*, cudaStream_t);
-template cudaError_t launch_dyson_g<double>(const double2*, const double2*, const void*,
-                                            const void*, const double*, double, int, int, int,
-                                            void*, double*, int, int, int*, cudaStream_t);
-template cudaError_t launch_dyson_g<float>(const double2*, const double2*, const void*, const void*,
-                                           const double*, double, int, int, int, void*, double*,
-                                           int, int, int*, cudaStream_t);
-template cudaError_t launch_norm_bound<double>(const double2*, const double2*, const void*, int,
-                                               int, int, double*, int, cudaStream_t);
-template cudaError_t launch_norm_bound<float>(const double2*, const double2*, const void*, int, int,
-                                              int, double*, int, cudaStream_t);
+template cudaError_t launch_dyson_g<double>(const void*, const void*, const double*, double, int,
+                                            int, int, void*, double*, int, int, int*, cudaStream_t);
+template cudaError_t launch_dyson_g<float>(const void*, const void*, const double*, double, int, int,
+                                           int, void*, double*, int, int, int*, cudaStream_t);
+template cudaError_t launch_dyson_g_prep<double>(const double2*, const double2*, const void*, double,
+                                                 int, int, int, void*, double*, int, cudaStream_t);
+template cudaError_t launch_dyson_g_prep<float>(const double2*, const double2*, const void*, double,
+                                                int, int, int, void*, double*, int, cudaStream_t);
 
 }  // namespace qa

@@ -138,25 +138,25 @@ cudaError_t launch_sigma_reduced(const void* GR, const void* Wt, const int* term
                                  int nterm, void* Sig, int r, int norb, int rho, int nk,
                                  cudaStream_t st);
 
-// Dyson for G at chemical potential mu.  mode 0: accumulate per-block
-// partial sums of Re(dw_n Tr G) and Re(dw_n Tr G^2) into part[2*blocks];
-// mode 1: also store G(k, i w_n) in Giw [r][norb][norb][N_k].
-// SigHF (FP64, [N_k][norb][norb]) and SigIw may be null.
+// Dyson for G.  prep: Bm[n][a][b][k] = (mu_ref - H(k) - SigHF(k))_ab - SigIw[n][a][b][k]
+// (SigHF FP64 [N_k][norb][norb] and SigIw may be null) and per-block bounds
+// part[2 b] of the row-sum norm of H + Sigma - mu_ref over all (k, n).
 template <typename T>
-cudaError_t launch_dyson_g(const double2* Hk, const double2* SigHF, const void* SigIw,
-                           const void* dw, const double* iw, double mu, int r, int norb, int nk,
-                           void* Giw, double* part, int nblocks, int mode, int* err,
-                           cudaStream_t st);
+cudaError_t launch_dyson_g_prep(const double2* Hk, const double2* SigHF, const void* SigIw,
+                                double mu_ref, int r, int norb, int nk, void* Bm, double* part,
+                                int nblocks, cudaStream_t st);
+// G = (i w_n + dmu + Bm)^-1 with dmu = mu - mu_ref.  mode 0: per-block partial
+// sums of Re(dw_n Tr G) and Re(dw_n Tr G^2) into part[2*blocks]; mode 1: also
+// store G(k, i w_n) in Giw [r][norb][norb][N_k].
+template <typename T>
+cudaError_t launch_dyson_g(const void* Bm, const void* dw, const double* iw, double dmu, int r,
+                           int norb, int nk, void* Giw, double* part, int nblocks, int mode,
+                           int* err, cudaStream_t st);
 int dyson_g_blocks(int r, int nk);
-// FP64 density sums (mode 0) with Sigma^C(k, i w) stored as complex64.
+// FP64 density sums (mode 0) at mu with Sigma^C(k, i w) stored as complex64.
 cudaError_t launch_dyson_g_f64_sig32(const double2* Hk, const double2* SigHF, const void* SigIw,
                                      const void* dw, const double* iw, double mu, int r, int norb,
                                      int nk, double* part, int nblocks, int* err, cudaStream_t st);
-
-// max over (k, n) of the row-sum norm of H(k) + SigHF(k) + SigIw(k, i w_n)
-template <typename T>
-cudaError_t launch_norm_bound(const double2* Hk, const double2* SigHF, const void* SigIw, int r,
-                              int norb, int nk, double* part, int nblocks, cudaStream_t st);
 
 // Deterministic final reduction of `n` partial pairs (sum or max).
 cudaError_t launch_reduce_pairs(const double* part, int n, int op_max, double* out,
@@ -166,15 +166,25 @@ cudaError_t launch_reduce_pairs(const double* part, int n, int op_max, double* o
 cudaError_t launch_ft_table(const int* R, const double2* XR, int nR, int msize, const int* kpts,
                             int nk, int n1, int n2, int n3, double2* out, cudaStream_t st);
 
-// n(R_v) = (1/N_k) sum_k e^{+i k.R_v} n(k) for the interaction's R list,
-// n(k) given as [norb^2][N_k] FP64.
-cudaError_t launch_density_R(const double2* nk_, const int* R, int nRv, int norb2, const int* kpts,
-                             int nk, int n1, int n2, int n3, double2* nR_out, cudaStream_t st);
+// ph[v][k] = e^{+i k.R_v} (FP64) for a list of R.
+cudaError_t launch_phase_table(const int* R, int nR, int nk, int n1, int n2, int n3, double2* ph,
+                               cudaStream_t st);
 
-// Sigma^H and Sigma^F(R_v) (one block), then Sigma^HF(k) per k.
+// n(R_v) = (1/N_k) sum_k e^{+i k.R_v} n(k) for the interaction's R list,
+// n(k) given as [norb^2][N_k] FP64; phases from ph ([nRv][N_k]) when given.
+cudaError_t launch_density_R(const double2* nk_, const int* R, int nRv, int norb2, const int* kpts,
+                             int nk, int n1, int n2, int n3, double2* nR_out, cudaStream_t st,
+                             const double2* ph = nullptr);
+
+// Sigma^H and Sigma^F(R_v) (one block), then Sigma^HF(k) per k (phases from ph when given).
 cudaError_t launch_hf(const double2* VR, const double2* nR_in, const int* R, int nRv, int norb,
                       double s, const int* kpts, int nk, int n1, int n2, int n3, double2* sigF_R,
-                      double2* SigHF, cudaStream_t st);
+                      double2* SigHF, cudaStream_t st, const double2* ph = nullptr);
+
+// n(k) = sum_j dtau_j G(k, tau_j) (FP64, [ncol]) of a complex128 G [r][ncol], and
+// its complex64 copy G32 when G32 != null (one pass; r <= 128).
+cudaError_t launch_g_input(const double2* G, const double2* dtau, int r, long long ncol,
+                           float2* G32, double2* nk_out, cudaStream_t st);
 
 // Local average over k: out[e] = (1/N_k) sum_k x[e][k], e < m (FP64 out).
 template <typename T>

@@ -25,14 +25,24 @@ __global__ void ft_table_kernel(const int* __restrict__ R, const double2* __rest
   out[idx] = acc;
 }
 
-// block per (v, e)
+// exp(+i k.R_v) for every listed R_v and k: [nR][N_k]
+__global__ void phase_table_kernel(const int* __restrict__ R, int nR, int nk, int n1, int n2, int n3,
+                                   double2* ph) {
+  const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= static_cast<long long>(nR) * nk) return;
+  const int v = static_cast<int>(idx / nk), k = static_cast<int>(idx - static_cast<long long>(v) * nk);
+  ph[idx] = lattice_phase(k, n1, n2, n3, R + 3 * v, +1);
+}
+
+// block per (v, e); phases from the table ph (exp(+i k.R_v)) when given
 __global__ void density_R_kernel(const double2* __restrict__ nk_, const int* __restrict__ R,
-                                 int norb2, int nk, int n1, int n2, int n3, double2* nR) {
+                                 const double2* __restrict__ ptab, int norb2, int nk, int n1,
+                                 int n2, int n3, double2* nR) {
   __shared__ double sh[64];
   const int v = blockIdx.x / norb2, e = blockIdx.x % norb2;
   double re = 0.0, im = 0.0;
   for (int k = threadIdx.x; k < nk; k += blockDim.x) {
-    double2 ph = lattice_phase(k, n1, n2, n3, R + 3 * v, +1);
+    double2 ph = ptab ? ptab[static_cast<size_t>(v) * nk + k] : lattice_phase(k, n1, n2, n3, R + 3 * v, +1);
     double2 x = nk_[static_cast<size_t>(e) * nk + k];
     re += x.x * ph.x - x.y * ph.y;
     im += x.x * ph.y + x.y * ph.x;
@@ -72,15 +82,16 @@ __global__ void hf_real_kernel(const double2* __restrict__ VR, const double2* __
   }
 }
 
-__global__ void hf_k_kernel(const double2* __restrict__ sigF_R, const int* __restrict__ R, int nRv,
-                            int no, int nk, int n1, int n2, int n3, double2* SigHF) {
+__global__ void hf_k_kernel(const double2* __restrict__ sigF_R, const int* __restrict__ R,
+                            const double2* __restrict__ ptab, int nRv, int no, int nk, int n1,
+                            int n2, int n3, double2* SigHF) {
   const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int np = no * no;
   if (idx >= static_cast<long long>(nk) * np) return;
   const int k = static_cast<int>(idx / np), e = static_cast<int>(idx % np);
   double2 acc = sigF_R[static_cast<size_t>(nRv) * np + e];   // Sigma^H
   for (int v = 0; v < nRv; ++v) {
-    double2 ph = lattice_phase(k, n1, n2, n3, R + 3 * v, -1);
+    double2 ph = ptab ? cconj(ptab[static_cast<size_t>(v) * nk + k]) : lattice_phase(k, n1, n2, n3, R + 3 * v, -1);
     acc = cfma(sigF_R[static_cast<size_t>(v) * np + e], ph, acc);
   }
   SigHF[idx] = acc;
@@ -98,6 +109,39 @@ __global__ void k_average_kernel(const cplx<T>* __restrict__ x, int nk, double2*
   }
   block_sum2(re, im, sh);
   if (threadIdx.x == 0) out[e] = make_double2(re / nk, im / nk);
+}
+
+// n(k) = sum_j dtau_j G(k, tau_j) for every column of a complex128 G (FP64),
+// and the complex64 copy of G when G32 is given: one pass over G, one thread
+// per column, coalesced along the columns.
+__global__ void __launch_bounds__(256) g_input_kernel(const double2* __restrict__ G,
+                                                      const double2* __restrict__ dtau, int r,
+                                                      long long ncol, float2* __restrict__ G32,
+                                                      double2* __restrict__ nk_out) {
+  __shared__ double2 d[128];
+  for (int l = threadIdx.x; l < r; l += blockDim.x) d[l] = dtau[l];
+  __syncthreads();
+  for (long long col = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; col < ncol;
+       col += static_cast<long long>(gridDim.x) * blockDim.x) {
+    double2 acc0 = make_double2(0, 0), acc1 = make_double2(0, 0);
+    int l = 0;
+    for (; l + 1 < r; l += 2) {
+      const double2 x0 = G[static_cast<long long>(l) * ncol + col];
+      const double2 x1 = G[static_cast<long long>(l + 1) * ncol + col];
+      if (G32) {
+        G32[static_cast<long long>(l) * ncol + col] = make_float2(static_cast<float>(x0.x), static_cast<float>(x0.y));
+        G32[static_cast<long long>(l + 1) * ncol + col] = make_float2(static_cast<float>(x1.x), static_cast<float>(x1.y));
+      }
+      acc0 = cfma(d[l], x0, acc0);
+      acc1 = cfma(d[l + 1], x1, acc1);
+    }
+    if (l < r) {
+      const double2 x0 = G[static_cast<long long>(l) * ncol + col];
+      if (G32) G32[static_cast<long long>(l) * ncol + col] = make_float2(static_cast<float>(x0.x), static_cast<float>(x0.y));
+      acc0 = cfma(d[l], x0, acc0);
+    }
+    nk_out[col] = cadd(acc0, acc1);
+  }
 }
 
 __global__ void c128_to_c64_kernel(const double2* in, float2* out, long long n) {
@@ -127,19 +171,35 @@ cudaError_t launch_ft_table(const int* R, const double2* XR, int nR, int msize, 
   return cudaGetLastError();
 }
 
+cudaError_t launch_phase_table(const int* R, int nR, int nk, int n1, int n2, int n3, double2* ph,
+                               cudaStream_t st) {
+  long long n = static_cast<long long>(nR) * nk;
+  if (n <= 0) return cudaSuccess;
+  phase_table_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, st>>>(R, nR, nk, n1, n2, n3, ph);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_density_R(const double2* nk_, const int* R, int nRv, int norb2, const int*,
-                             int nk, int n1, int n2, int n3, double2* nR_out, cudaStream_t st) {
-  density_R_kernel<<<nRv * norb2, 256, 0, st>>>(nk_, R, norb2, nk, n1, n2, n3, nR_out);
+                             int nk, int n1, int n2, int n3, double2* nR_out, cudaStream_t st,
+                             const double2* ph) {
+  density_R_kernel<<<nRv * norb2, 256, 0, st>>>(nk_, R, ph, norb2, nk, n1, n2, n3, nR_out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_hf(const double2* VR, const double2* nR_in, const int* R, int nRv, int norb,
                       double s, const int*, int nk, int n1, int n2, int n3, double2* sigF_R,
-                      double2* SigHF, cudaStream_t st) {
+                      double2* SigHF, cudaStream_t st, const double2* ph) {
   hf_real_kernel<<<1, 256, 0, st>>>(VR, nR_in, nRv, norb, s, sigF_R);
   long long n = static_cast<long long>(nk) * norb * norb;
-  hf_k_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, st>>>(sigF_R, R, nRv, norb, nk, n1,
-                                                                     n2, n3, SigHF);
+  hf_k_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, st>>>(sigF_R, R, ph, nRv, norb, nk,
+                                                                     n1, n2, n3, SigHF);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_g_input(const double2* G, const double2* dtau, int r, long long ncol,
+                           float2* G32, double2* nk_out, cudaStream_t st) {
+  if (r > 128) return cudaErrorInvalidValue;
+  g_input_kernel<<<grid_for(ncol, 256), 256, 0, st>>>(G, dtau, r, ncol, G32, nk_out);
   return cudaGetLastError();
 }
 
