@@ -127,16 +127,17 @@ __host__ __device__ constexpr int brev_bits(int i, int bits) {
 }
 __host__ __device__ constexpr int ilog2(int L) { return L <= 1 ? 0 : 1 + ilog2(L / 2); }
 
+// One length-L transform of the points base + j*S (j < L) of a padded line.
+// The padding (one element per 2^lp points, 2^lp = the innermost non-trivial
+// axis length) is linear along every axis: physical index = pb + j * ps.
+// Radix-2 in registers, natural order in and out.
 template <typename V, int L>
-__device__ __forceinline__ void line_fft(V* __restrict__ buf, int base, int S, int pad,
+__device__ __forceinline__ void line_fft(V* __restrict__ buf, int pb, int ps,
                                          const V* __restrict__ tw64, int sign) {
   constexpr int B = ilog2(L);
   V x[L];
 #pragma unroll
-  for (int j = 0; j < L; ++j) {
-    int e = base + brev_bits(j, B) * S;
-    x[j] = buf[e + e / pad];
-  }
+  for (int j = 0; j < L; ++j) x[brev_bits(j, B)] = buf[pb + j * ps];
 #pragma unroll
   for (int m = 2; m <= L; m <<= 1) {
 #pragma unroll
@@ -153,23 +154,25 @@ __device__ __forceinline__ void line_fft(V* __restrict__ buf, int base, int S, i
     }
   }
 #pragma unroll
-  for (int j = 0; j < L; ++j) {
-    int e = base + j * S;
-    buf[e + e / pad] = x[j];
-  }
+  for (int j = 0; j < L; ++j) buf[pb + j * ps] = x[j];
 }
 
+// Lines of N1 x N2 x N3 points with every N_d a power of two <= 32: a block
+// keeps lpb lines in shared memory (one padding element per 2^lp points
+// spreads the strided axis passes over the banks), each axis pass gives one
+// length-L transform per thread, and all index arithmetic is shifts and masks.
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) fft3d_reg_kernel(int n1, int n2, int n3, int sign,
-                                                        const cplx<T>* in, cplx<T>* out, int nk,
-                                                        int lpb, long long nlines, int pad,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) fft3d_reg_kernel(int l1, int l2, int l3, int sign,
+                                                        const cplx<T>* in, cplx<T>* out,
+                                                        int lpb, long long nlines, int lp,
                                                         T scale) {
   using V = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* tw = reinterpret_cast<V*>(smem_raw);               // exp(-2 pi i k / 64), k < 32
   V* buf = tw + 32;
   const int tid = threadIdx.x, bd = blockDim.x;
-  const int line_sz = nk + nk / pad;
+  const int lnk = l1 + l2 + l3, nk = 1 << lnk;
+  const int line_sz = nk + (nk >> lp);
   const long long line0 = static_cast<long long>(blockIdx.x) * lpb;
   const int nl = static_cast<int>(min(static_cast<long long>(lpb), nlines - line0));
   if (tid < 32) {
@@ -178,38 +181,39 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) fft3d_reg_kernel(
     tw[tid] = cmk<V>(cs, sn);
   }
   const V* src = in + line0 * nk;
-  for (int i = tid; i < nl * nk; i += bd) {
-    int line = i / nk, e = i - line * nk;
-    buf[line * line_sz + e + e / pad] = src[i];
+  const int tot = nl << lnk;
+  for (int i = tid; i < tot; i += bd) {
+    const int line = i >> lnk, e = i & (nk - 1);
+    buf[line * line_sz + e + (e >> lp)] = src[i];
   }
   __syncthreads();
-  const int n[3] = {n1, n2, n3};
-  const int stride[3] = {n2 * n3, n3, 1};
   for (int d = 2; d >= 0; --d) {
-    const int L = n[d];
-    if (L == 1) continue;
-    const int S = stride[d];
-    const int per_line = nk / L;
-    for (int task = tid; task < nl * per_line; task += bd) {
-      int line = task / per_line, rem = task - line * per_line;
-      int o_lo = rem % S, o_hi = rem / S;
+    const int lL = d == 2 ? l3 : (d == 1 ? l2 : l1);
+    if (lL == 0) continue;
+    const int lS = d == 2 ? 0 : (d == 1 ? l3 : l2 + l3);
+    const int lper = lnk - lL;                          // transforms per line = 2^lper
+    for (int task = tid; task < (nl << lper); task += bd) {
+      const int line = task >> lper, rem = task & ((1 << lper) - 1);
+      const int o_lo = rem & ((1 << lS) - 1), o_hi = rem >> lS;
       V* lb = buf + line * line_sz;
-      int base = o_hi * L * S + o_lo;
-      switch (L) {
-        case 2: line_fft<V, 2>(lb, base, S, pad, tw, sign); break;
-        case 4: line_fft<V, 4>(lb, base, S, pad, tw, sign); break;
-        case 8: line_fft<V, 8>(lb, base, S, pad, tw, sign); break;
-        case 16: line_fft<V, 16>(lb, base, S, pad, tw, sign); break;
-        case 32: line_fft<V, 32>(lb, base, S, pad, tw, sign); break;
+      const int base = (o_hi << (lL + lS)) + o_lo;
+      const int S = 1 << lS;
+      const int pb = base + (base >> lp), ps = S + (S >> lp);
+      switch (lL) {
+        case 1: line_fft<V, 2>(lb, pb, ps, tw, sign); break;
+        case 2: line_fft<V, 4>(lb, pb, ps, tw, sign); break;
+        case 3: line_fft<V, 8>(lb, pb, ps, tw, sign); break;
+        case 4: line_fft<V, 16>(lb, pb, ps, tw, sign); break;
+        case 5: line_fft<V, 32>(lb, pb, ps, tw, sign); break;
         default: break;
       }
     }
     __syncthreads();
   }
   V* dst = out + line0 * nk;
-  for (int i = tid; i < nl * nk; i += bd) {
-    int line = i / nk, e = i - line * nk;
-    V v = buf[line * line_sz + e + e / pad];
+  for (int i = tid; i < tot; i += bd) {
+    const int line = i >> lnk, e = i & (nk - 1);
+    V v = buf[line * line_sz + e + (e >> lp)];
     v.x *= scale;
     v.y *= scale;
     dst[i] = v;
@@ -232,7 +236,8 @@ cudaError_t launch_fft3d(const FftDev& plan, int sign, const void* in, void* out
   if (reg_axis_ok(plan.n[0], maxL) && reg_axis_ok(plan.n[1], maxL) && reg_axis_ok(plan.n[2], maxL) &&
       nk >= 2) {
     const int pad = plan.n[2] > 1 ? plan.n[2] : (plan.n[1] > 1 ? plan.n[1] : plan.n[0]);
-    const int line_sz = nk + nk / pad;
+    const int lp = ilog2(pad);
+    const int line_sz = nk + (nk >> lp);
     int lpb = 1;
     while (lpb * 2 * line_sz * static_cast<int>(sizeof(cplx<T>)) <= 32768 && lpb * 2 <= 64) lpb *= 2;
     size_t smem = (static_cast<size_t>(lpb) * line_sz + 32) * sizeof(cplx<T>);
@@ -240,8 +245,8 @@ cudaError_t launch_fft3d(const FftDev& plan, int sign, const void* in, void* out
     if (e != cudaSuccess) return e;
     long long nblk = (nlines + lpb - 1) / lpb;
     fft3d_reg_kernel<T><<<static_cast<unsigned>(nblk), 256, smem, st>>>(
-        plan.n[0], plan.n[1], plan.n[2], sign, reinterpret_cast<const cplx<T>*>(in),
-        reinterpret_cast<cplx<T>*>(out), nk, lpb, nlines, pad, sc);
+        ilog2(plan.n[0]), ilog2(plan.n[1]), ilog2(plan.n[2]), sign,
+        reinterpret_cast<const cplx<T>*>(in), reinterpret_cast<cplx<T>*>(out), lpb, nlines, lp, sc);
     return cudaGetLastError();
   }
   // lines per block: keep the tile near 16 KB for small grids

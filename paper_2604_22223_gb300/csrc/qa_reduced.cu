@@ -20,14 +20,22 @@ namespace {
 template <typename T> struct RedTpb { static constexpr int v = 128; };
 template <> struct RedTpb<double> { static constexpr int v = 64; };
 
+// one term as a single shared-memory record (one 16- or 32-byte load)
+template <typename T> struct __align__(2 * sizeof(T) < 16 ? 16 : 32) TermRec {
+  cplx<T> c;
+  int idx;
+};
+
 template <typename T>
 __device__ __forceinline__ void stage_terms(const int* __restrict__ terms,
                                             const cplx<T>* __restrict__ coef, int nout, int nterm,
-                                            int* s_off, int* s_idx, cplx<T>* s_coef) {
+                                            int* s_off, TermRec<T>* s_rec) {
   for (int e = threadIdx.x; e <= nout; e += blockDim.x) s_off[e] = terms[e];
   for (int e = threadIdx.x; e < nterm; e += blockDim.x) {
-    s_idx[e] = terms[nout + 1 + e];
-    s_coef[e] = coef[e];
+    TermRec<T> t;
+    t.c = coef[e];
+    t.idx = terms[nout + 1 + e];
+    s_rec[e] = t;
   }
 }
 
@@ -38,16 +46,15 @@ __global__ void __launch_bounds__(RedTpb<T>::v) bubble_reduced_kernel(
     cplx<T>* __restrict__ Pt, int no2, int nout, int nk) {
   using V = cplx<T>;
   constexpr int TPB = RedTpb<T>::v;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* s_coef = reinterpret_cast<V*>(smem_raw);
-  V* g = s_coef + nterm;                      // [no2][TPB]
-  V* gl = g + no2 * TPB;                      // [no2][TPB]
+  extern __shared__ __align__(32) unsigned char smem_raw[];
+  TermRec<T>* s_rec = reinterpret_cast<TermRec<T>*>(smem_raw);
+  V* g = reinterpret_cast<V*>(s_rec + nterm);   // [no2][TPB]
+  V* gl = g + no2 * TPB;                        // [no2][TPB]
   int* s_off = reinterpret_cast<int*>(gl + no2 * TPB);
-  int* s_idx = s_off + nout + 1;
   const int tid = threadIdx.x;
   const int t = blockIdx.y;
   const int R = blockIdx.x * TPB + tid;
-  stage_terms<T>(terms, coef, nout, nterm, s_off, s_idx, s_coef);
+  stage_terms<T>(terms, coef, nout, nterm, s_off, s_rec);
   if (R < nk) {
     const int mr = mR[R];
     const V* gt = GR + static_cast<size_t>(t) * no2 * nk;
@@ -66,18 +73,22 @@ __global__ void __launch_bounds__(RedTpb<T>::v) bubble_reduced_kernel(
     V acc0 = cmk<V>(0, 0), acc1 = cmk<V>(0, 0);
     int e = e0;
     for (; e + 1 < e1; e += 2) {
-      const int i0 = s_idx[e], i1 = s_idx[e + 1];
-      acc0 = cfma(s_coef[e], cmul(g[(i0 & 255) * TPB + tid], gl[(i0 >> 8) * TPB + tid]), acc0);
-      acc1 = cfma(s_coef[e + 1], cmul(g[(i1 & 255) * TPB + tid], gl[(i1 >> 8) * TPB + tid]), acc1);
+      const TermRec<T> r0 = s_rec[e], r1 = s_rec[e + 1];
+      acc0 = cfma(r0.c, cmul(g[(r0.idx & 255) * TPB + tid], gl[(r0.idx >> 8) * TPB + tid]), acc0);
+      acc1 = cfma(r1.c, cmul(g[(r1.idx & 255) * TPB + tid], gl[(r1.idx >> 8) * TPB + tid]), acc1);
     }
     if (e < e1) {
-      const int i0 = s_idx[e];
-      acc0 = cfma(s_coef[e], cmul(g[(i0 & 255) * TPB + tid], gl[(i0 >> 8) * TPB + tid]), acc0);
+      const TermRec<T> r0 = s_rec[e];
+      acc0 = cfma(r0.c, cmul(g[(r0.idx & 255) * TPB + tid], gl[(r0.idx >> 8) * TPB + tid]), acc0);
     }
     out[static_cast<size_t>(o) * nk] = cadd(acc0, acc1);
     e0 = e1;
   }
 }
+
+// W^C entries are read in batches of kWb (independent loads in flight per
+// thread) before their terms are applied.
+constexpr int kWb = 16;
 
 template <typename T>
 __global__ void __launch_bounds__(RedTpb<T>::v) sigma_reduced_kernel(
@@ -86,16 +97,15 @@ __global__ void __launch_bounds__(RedTpb<T>::v) sigma_reduced_kernel(
     int nk) {
   using V = cplx<T>;
   constexpr int TPB = RedTpb<T>::v;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* s_coef = reinterpret_cast<V*>(smem_raw);
-  V* g = s_coef + nterm;                      // [no2][TPB]
-  V* sg = g + no2 * TPB;                      // [no2][TPB] accumulators
+  extern __shared__ __align__(32) unsigned char smem_raw[];
+  TermRec<T>* s_rec = reinterpret_cast<TermRec<T>*>(smem_raw);
+  V* g = reinterpret_cast<V*>(s_rec + nterm);   // [no2][TPB]
+  V* sg = g + no2 * TPB;                        // [no2][TPB] accumulators
   int* s_off = reinterpret_cast<int*>(sg + no2 * TPB);
-  int* s_idx = s_off + nout + 1;
   const int tid = threadIdx.x;
   const int t = blockIdx.y;
   const int R = blockIdx.x * TPB + tid;
-  stage_terms<T>(terms, coef, nout, nterm, s_off, s_idx, s_coef);
+  stage_terms<T>(terms, coef, nout, nterm, s_off, s_rec);
   if (R < nk) {
     const V* gt = GR + static_cast<size_t>(t) * no2 * nk;
     for (int e = 0; e < no2; ++e) {
@@ -106,18 +116,22 @@ __global__ void __launch_bounds__(RedTpb<T>::v) sigma_reduced_kernel(
   __syncthreads();
   if (R >= nk) return;                        // no barriers below
   const V* w = Wt + static_cast<size_t>(t) * nout * nk + R;
-  V wn = w[0];
-  int e0 = s_off[0];
-  for (int o = 0; o < nout; ++o) {
-    const V wc = wn;
-    if (o + 1 < nout) wn = w[static_cast<size_t>(o + 1) * nk];   // prefetch the next entry
-    const int e1 = s_off[o + 1];
-    for (int e = e0; e < e1; ++e) {
-      const int id = s_idx[e];
-      V* sp = sg + (id >> 8) * TPB + tid;
-      *sp = cfma(cmul(s_coef[e], wc), g[(id & 255) * TPB + tid], *sp);
+  for (int o0 = 0; o0 < nout; o0 += kWb) {
+    V wb[kWb];
+#pragma unroll
+    for (int u = 0; u < kWb; ++u)
+      wb[u] = o0 + u < nout ? w[static_cast<size_t>(o0 + u) * nk] : cmk<V>(0, 0);
+#pragma unroll
+    for (int u = 0; u < kWb; ++u) {
+      if (o0 + u < nout) {
+        const int e1 = s_off[o0 + u + 1];
+        for (int e = s_off[o0 + u]; e < e1; ++e) {
+          const TermRec<T> r0 = s_rec[e];
+          V* sp = sg + (r0.idx >> 8) * TPB + tid;
+          *sp = cfma(cmul(r0.c, wb[u]), g[(r0.idx & 255) * TPB + tid], *sp);
+        }
+      }
     }
-    e0 = e1;
   }
   V* out = Sig + static_cast<size_t>(t) * no2 * nk + R;
   for (int e = 0; e < no2; ++e) out[static_cast<size_t>(e) * nk] = sg[e * TPB + tid];
@@ -125,9 +139,9 @@ __global__ void __launch_bounds__(RedTpb<T>::v) sigma_reduced_kernel(
 
 template <typename T>
 size_t reduced_smem(int no2, int nout, int nterm) {
-  return static_cast<size_t>(nterm) * sizeof(cplx<T>) +
+  return static_cast<size_t>(nterm) * sizeof(TermRec<T>) +
          static_cast<size_t>(2) * no2 * RedTpb<T>::v * sizeof(cplx<T>) +
-         static_cast<size_t>(nout + 1 + nterm) * sizeof(int);
+         static_cast<size_t>(nout + 1) * sizeof(int);
 }
 
 }  // namespace
