@@ -179,6 +179,12 @@ int setup_pairs(qa_ctx* c, bool bound) {
                     (c->pair_mode == QA_PAIRS_AUTO && c->precision == QA_MIXED);
   const bool red = want && ok;
   if (bound && (red != c->reduced || (red && rho != c->rho))) return QA_EINVAL;
+  if (!red) {
+    // the full product basis is the special case B = identity (one term per entry)
+    std::vector<cd> I(static_cast<size_t>(c->npair) * c->npair, cd(0, 0));
+    for (int A = 0; A < c->npair; ++A) I[static_cast<size_t>(A) * c->npair + A] = cd(1, 0);
+    qa::pair_basis_terms(I, c->norb, c->npair, static_cast<double>(c->nspin), &tb, &ts);
+  }
   c->rho = rho;
   c->basis = B;
   c->reduced = red;
@@ -210,11 +216,20 @@ int setup_pairs(qa_ctx* c, bool bound) {
   return QA_OK;
 }
 
-// Room for the reduced term lists: every list a later qa_set_params can make
-// (rho^2 outputs of at most npair^2 terms each), capped by the kernels' limit.
+// Room for the term lists: every list a later qa_set_params can make (rho^2
+// outputs of at most npair^2 terms each, capped by the kernels' limit), or
+// one term per entry on the full basis.
 size_t term_capacity(const qa_ctx* c) {
+  if (!c->reduced) return static_cast<size_t>(c->npair) * c->npair;
   const size_t bound = static_cast<size_t>(c->rho) * c->rho * c->npair * c->npair;
   return std::min(bound, static_cast<size_t>(qa::kMaxPairTerms));
+}
+
+// the largest term count of one output entry
+int max_terms_per_entry(const qa::PairTerms& t) {
+  int m = 0;
+  for (size_t o = 0; o + 1 < t.off.size(); ++o) m = std::max(m, t.off[o + 1] - t.off[o]);
+  return m;
 }
 
 // layout of the workspace; when `base` is null only sizes are accumulated
@@ -282,8 +297,8 @@ size_t layout(qa_ctx* c, char* base) {
     c->d_tc_Ttw = take(c->tc_Ttw.size() * 2);
     c->d_tc_Twt = take(c->tc_Twt.size() * 2);
   }
-  if (c->reduced) {
-    c->d_sV = static_cast<double2*>(take(std::max(1, c->nV) * nb2 * 16));
+  {
+    if (c->reduced) c->d_sV = static_cast<double2*>(take(std::max(1, c->nV) * nb2 * 16));
     const size_t cap = term_capacity(c);
     c->d_tbub = static_cast<int*>(take((nb2 + 1 + cap) * 4));
     c->d_cbub = take(cap * es);
@@ -333,7 +348,7 @@ cudaError_t upload_c(void* dst, const std::vector<cd>& src, cudaStream_t st) {
 int upload_interaction(qa_ctx* c, cudaStream_t st) {
   const int nb2 = c->nb * c->nb;
   const double2* src = c->d_vV;
-  if (c->reduced) {
+  {
     const qa::PairTerms* tl[2] = {&c->tbub, &c->tsig};
     int* di[2] = {c->d_tbub, c->d_tsig};
     void* dc[2] = {c->d_cbub, c->d_csig};
@@ -345,6 +360,8 @@ int upload_interaction(qa_ctx* c, cudaStream_t st) {
       if (c->precision == QA_FP64) QA_TRY(upload_c<double>(dc[k], tl[k]->coef, st));
       else QA_TRY(upload_c<float>(dc[k], tl[k]->coef, st));
     }
+  }
+  if (c->reduced) {
     if (c->nV > 0) QA_TRY(upload_c<double>(c->d_sV, c->sV, st));
     src = c->d_sV;
   }
@@ -621,14 +638,21 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
   QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, +1, Gk, c->d_GR, ncs / nk * r, st));
   QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, +1, c->d_Grefl, c->d_Grefl, ncs / nk * r, st));
   tm.mark();  // 1: G -> R
-  if (c->reduced)
-    QA_LAUNCH(c, 1, qa::launch_bubble_reduced<T>(c->d_GR, c->d_Grefl, c->d_mR, c->d_tbub, c->d_cbub,
-                                                 static_cast<int>(c->tbub.idx.size()), c->d_P, r,
-                                                 c->norb, c->rho, nk, st));
-  else
-    QA_LAUNCH(c, 1, qa::launch_bubble<T>(c->d_GR, c->d_Grefl, c->d_mR, c->d_P, r, c->norb, nk, c->nspin, st));
-  tm.mark();  // 2: bubble
-  QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, -1, c->d_P, c->d_P, ncb / nk * r, st));
+  if (qa::fft3d_bubble_supported(fft) && max_terms_per_entry(c->tbub) <= 640) {
+    // bubble and R -> q transform in one pass (the bubble stage reads as 0)
+    tm.mark();  // 2: bubble
+    QA_LAUNCH(c, 1, qa::launch_fft3d_bubble<T>(fft, c->d_GR, c->d_Grefl, c->d_mR, c->d_tbub, c->d_cbub,
+                                               max_terms_per_entry(c->tbub), nb2, c->norb, c->d_P, r, st));
+  } else {
+    if (c->reduced)
+      QA_LAUNCH(c, 1, qa::launch_bubble_reduced<T>(c->d_GR, c->d_Grefl, c->d_mR, c->d_tbub, c->d_cbub,
+                                                   static_cast<int>(c->tbub.idx.size()), c->d_P, r,
+                                                   c->norb, c->rho, nk, st));
+    else
+      QA_LAUNCH(c, 1, qa::launch_bubble<T>(c->d_GR, c->d_Grefl, c->d_mR, c->d_P, r, c->norb, nk, c->nspin, st));
+    tm.mark();  // 2: bubble
+    QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, -1, c->d_P, c->d_P, ncb / nk * r, st));
+  }
   tm.mark();  // 3: FFT R -> q
   if (sizeof(T) == 4 && c->use_tc)
     QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Ttn, r, c->d_P, c->d_P, ncb, c->d_err, st));

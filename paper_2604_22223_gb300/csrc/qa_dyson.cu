@@ -167,15 +167,37 @@ __global__ void __launch_bounds__(kWarpsR * 32) dyson_w_reg_kernel(const float2*
   const int q0 = blockIdx.x * NSYS;
   const int nu = blockIdx.y;
   const size_t slab = static_cast<size_t>(nu) * nn * nk;
-  for (int idx = tid; idx < NSYS * nn; idx += blockDim.x) {
-    int e = idx / NSYS, ss = idx - e * NSYS;
-    int q = q0 + ss;
-    Ps[ss * nn + e] = q < nk ? P[slab + static_cast<size_t>(e) * nk + q] : make_float2(0.f, 0.f);
+  // batches of 8 loads per thread in flight (the trip count depends on n)
+  for (int idx0 = tid; idx0 < NSYS * nn; idx0 += 8 * kWarpsR * 32) {
+    float2 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = idx0 + u * kWarpsR * 32;
+      const int e = idx / NSYS, ss = idx - e * NSYS;
+      const int q = q0 + ss;
+      v[u] = (idx < NSYS * nn && q < nk) ? P[slab + static_cast<size_t>(e) * nk + q] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = idx0 + u * kWarpsR * 32;
+      const int e = idx / NSYS, ss = idx - e * NSYS;
+      if (idx < NSYS * nn) Ps[ss * nn + e] = v[u];
+    }
   }
-  for (int idx = tid; idx < NSYS * nn; idx += blockDim.x) {
-    int ss = idx / nn, e = idx - ss * nn;
-    int q = q0 + ss;
-    Vs[idx] = q < nk ? Vq[static_cast<size_t>(q) * nn + e] : make_float2(0.f, 0.f);
+  for (int idx0 = tid; idx0 < NSYS * nn; idx0 += 8 * kWarpsR * 32) {
+    float2 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = idx0 + u * kWarpsR * 32;
+      const int ss = idx / nn;
+      const int q = q0 + ss;
+      v[u] = (idx < NSYS * nn && q < nk) ? Vq[static_cast<size_t>(q0) * nn + idx] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = idx0 + u * kWarpsR * 32;
+      if (idx < NSYS * nn) Vs[idx] = v[u];
+    }
   }
   __syncthreads();
   const int q = q0 + sys;
@@ -286,6 +308,228 @@ cudaError_t launch_dyson_w_reg(const void* P, const void* Vq, void* WC, int r, i
   constexpr int NSYS = kWarpsR * (32 / W);
   const size_t smem = static_cast<size_t>(2) * NSYS * n * n * sizeof(float2);
   auto fn = &dyson_w_reg_kernel<MAXN, W>;
+  cudaError_t e = set_smem(reinterpret_cast<const void*>(fn), smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((nk + NSYS - 1) / NSYS, r);
+  fn<<<grid, kWarpsR * 32, smem, st>>>(reinterpret_cast<const float2*>(P),
+                                       reinterpret_cast<const float2*>(Vq),
+                                       reinterpret_cast<float2*>(WC), n, nk, err, first_bad);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------- Dyson W, swizzled tiles
+// FP32 kernel for systems of n <= 16 (the reduced pair basis): MAXN lanes
+// own one system (lane i = row i of A = 1 - V P and of the right-hand side
+// V P V), 32/MAXN systems per warp, 8 warps per block over consecutive q.
+// P and V sit in shared memory as MAXN x MAXN tiles whose rows hold pairs of
+// complex values, the pair index XOR-swizzled by the row: a lane reading its
+// own row and all lanes reading one row (a broadcast) both move 16 bytes per
+// load without bank conflicts.  The pivot of each column is found with a
+// packed (|a|^2 | row) key, and the pivot row reaches the other lanes
+// through shared memory (one 16-byte store and load per two values instead
+// of two shuffles per value).  Back substitution is column-parallel.
+
+template <int MAXN>
+__device__ __forceinline__ int swz(int row, int col) {
+  return row * MAXN + 2 * ((col >> 1) ^ (row & (MAXN / 2 - 1))) + (col & 1);
+}
+
+template <int MAXN>
+__device__ __forceinline__ float4 lds_pair(const float2* tile, int row, int pair) {
+  return *reinterpret_cast<const float4*>(tile + row * MAXN + 2 * (pair ^ (row & (MAXN / 2 - 1))));
+}
+
+template <int MAXN>
+__global__ void __launch_bounds__(kWarpsR * 32) dyson_w_tile_kernel(const float2* __restrict__ P,
+                                                                   const float2* __restrict__ Vq,
+                                                                   float2* WC, int n, int nk,
+                                                                   int* err, long long* first_bad) {
+  static_assert(MAXN == 4 || MAXN == 8 || MAXN == 16, "tile width");
+  constexpr int W = MAXN;                      // lanes per system
+  constexpr int SPW = 32 / W;
+  constexpr int NSYS = kWarpsR * SPW;
+  constexpr int TT = MAXN * MAXN;              // tile entries
+  constexpr int NPAIR = MAXN / 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* Ps = reinterpret_cast<float2*>(smem_raw);        // [NSYS][TT]
+  float2* Vs = Ps + NSYS * TT;                              // [NSYS][TT]
+  float2* Rs = Vs + NSYS * TT;                              // [NSYS][2 * MAXN] pivot rows
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int l = lane & (W - 1);
+  const int sys = w * SPW + lane / W;
+  const int q0 = blockIdx.x * NSYS;
+  const int nu = blockIdx.y;
+  const int nn = n * n;
+  const size_t slab = static_cast<size_t>(nu) * nn * nk;
+  // tile loads: compile-time trip counts, so all of a thread's loads are in
+  // flight together (NSYS * TT is a multiple of the block size)
+  constexpr int kThr = kWarpsR * 32, kIt = NSYS * TT / kThr;
+  static_assert(NSYS * TT % kThr == 0, "tile / block size");
+  {
+    float2 v[kIt];
+#pragma unroll
+    for (int it = 0; it < kIt; ++it) {
+      const int idx = tid + it * kThr;
+      const int pos = idx / NSYS, ss = idx - pos * NSYS;
+      const int row = pos / MAXN, col = pos - row * MAXN;
+      const int q = q0 + ss;
+      v[it] = (row < n && col < n && q < nk) ? P[slab + static_cast<size_t>(row * n + col) * nk + q]
+                                             : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int it = 0; it < kIt; ++it) {
+      const int idx = tid + it * kThr;
+      const int pos = idx / NSYS, ss = idx - pos * NSYS;
+      Ps[ss * TT + swz<MAXN>(pos / MAXN, pos % MAXN)] = v[it];
+    }
+#pragma unroll
+    for (int it = 0; it < kIt; ++it) {
+      const int idx = tid + it * kThr;
+      const int ss = idx / TT, pos = idx - ss * TT;
+      const int row = pos / MAXN, col = pos - row * MAXN;
+      const int q = q0 + ss;
+      v[it] = (row < n && col < n && q < nk) ? Vq[static_cast<size_t>(q) * nn + row * n + col]
+                                             : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int it = 0; it < kIt; ++it) {
+      const int idx = tid + it * kThr;
+      const int ss = idx / TT, pos = idx - ss * TT;
+      Vs[ss * TT + swz<MAXN>(pos / MAXN, pos % MAXN)] = v[it];
+    }
+  }
+  __syncthreads();
+  const int q = q0 + sys;
+  float2* Pw = Ps + sys * TT;
+  float2* Vw = Vs + sys * TT;
+  float2* Ra = Rs + sys * 2 * MAXN;             // pivot row of A
+  float2* Rb = Ra + MAXN;                       // pivot row of the right-hand side
+  float2 a[MAXN], b[MAXN];
+  const bool row = l < n;
+  // a = row l of V P (padding rows and columns of the tiles are zero)
+#pragma unroll
+  for (int j = 0; j < MAXN; ++j) a[j] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int mp = 0; mp < NPAIR; ++mp) {
+    if (2 * mp < n) {
+      const float4 vv = lds_pair<MAXN>(Vw, l, mp);
+      const float2 v0 = make_float2(vv.x, vv.y), v1 = make_float2(vv.z, vv.w);
+#pragma unroll
+      for (int jp = 0; jp < NPAIR; ++jp) {
+        if (2 * jp < n) {
+          const float4 p0 = lds_pair<MAXN>(Pw, 2 * mp, jp);
+          const float4 p1 = lds_pair<MAXN>(Pw, 2 * mp + 1, jp);
+          a[2 * jp] = cfma(v0, make_float2(p0.x, p0.y), a[2 * jp]);
+          a[2 * jp] = cfma(v1, make_float2(p1.x, p1.y), a[2 * jp]);
+          a[2 * jp + 1] = cfma(v0, make_float2(p0.z, p0.w), a[2 * jp + 1]);
+          a[2 * jp + 1] = cfma(v1, make_float2(p1.z, p1.w), a[2 * jp + 1]);
+        }
+      }
+    }
+  }
+  // b = row l of (V P) V
+#pragma unroll
+  for (int j = 0; j < MAXN; ++j) b[j] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int m = 0; m < MAXN; ++m) {
+    if (m < n) {
+#pragma unroll
+      for (int jp = 0; jp < NPAIR; ++jp) {
+        if (2 * jp < n) {
+          const float4 vr = lds_pair<MAXN>(Vw, m, jp);
+          b[2 * jp] = cfma(a[m], make_float2(vr.x, vr.y), b[2 * jp]);
+          b[2 * jp + 1] = cfma(a[m], make_float2(vr.z, vr.w), b[2 * jp + 1]);
+        }
+      }
+    }
+  }
+  // a = 1 - V P
+#pragma unroll
+  for (int j = 0; j < MAXN; ++j) {
+    a[j].x = (row && j == l ? 1.f : 0.f) - a[j].x;
+    a[j].y = -a[j].y;
+  }
+  bool used = !row;
+  int mypos = -1;
+  bool singular = false;
+#pragma unroll
+  for (int c = 0; c < MAXN; ++c) {
+    if (c < n) {
+      // pivot: largest |a_ic|^2 over the unused rows, near-ties (low 4 mantissa
+      // bits) to the lowest row; used rows carry key 0
+      const float v2 = cabs2(a[c]);
+      unsigned key = used ? 0u : (max(__float_as_uint(v2) & ~0xFu, 0x10u) | (W - 1 - l));
+#pragma unroll
+      for (int o = W / 2; o > 0; o >>= 1) key = max(key, __shfl_xor_sync(0xffffffffu, key, o));
+      const int p = W - 1 - static_cast<int>(key & (W - 1));
+      if (!(__uint_as_float(key & ~0xFu) >= 1e-12f)) singular = true;
+      if (l == p) {
+        used = true;
+        mypos = c;
+#pragma unroll
+        for (int jp = c / 2; jp < NPAIR; ++jp)
+          *reinterpret_cast<float4*>(Ra + 2 * jp) = make_float4(a[2 * jp].x, a[2 * jp].y, a[2 * jp + 1].x, a[2 * jp + 1].y);
+#pragma unroll
+        for (int jp = 0; jp < NPAIR; ++jp)
+          *reinterpret_cast<float4*>(Rb + 2 * jp) = make_float4(b[2 * jp].x, b[2 * jp].y, b[2 * jp + 1].x, b[2 * jp + 1].y);
+      }
+      __syncwarp();
+      const float2 apc = Ra[c];
+      const float2 f = used ? make_float2(0.f, 0.f) : cmul(a[c], cinv(apc));
+#pragma unroll
+      for (int jp = (c + 1) / 2; jp < NPAIR; ++jp) {
+        if (2 * jp < n) {
+          const float4 pr = *reinterpret_cast<const float4*>(Ra + 2 * jp);
+          if (2 * jp > c) a[2 * jp] = cfms(f, make_float2(pr.x, pr.y), a[2 * jp]);
+          a[2 * jp + 1] = cfms(f, make_float2(pr.z, pr.w), a[2 * jp + 1]);
+        }
+      }
+#pragma unroll
+      for (int jp = 0; jp < NPAIR; ++jp) {
+        if (2 * jp < n) {
+          const float4 br = *reinterpret_cast<const float4*>(Rb + 2 * jp);
+          b[2 * jp] = cfms(f, make_float2(br.x, br.y), b[2 * jp]);
+          b[2 * jp + 1] = cfms(f, make_float2(br.z, br.w), b[2 * jp + 1]);
+        }
+      }
+      __syncwarp();
+    }
+  }
+  // rows of the triangular factor (P tile) and right-hand side (V tile), in pivot order
+  if (mypos >= 0) {
+#pragma unroll
+    for (int jp = 0; jp < NPAIR; ++jp) {
+      *reinterpret_cast<float4*>(Pw + mypos * MAXN + 2 * (jp ^ (mypos & (NPAIR - 1)))) =
+          make_float4(a[2 * jp].x, a[2 * jp].y, a[2 * jp + 1].x, a[2 * jp + 1].y);
+      *reinterpret_cast<float4*>(Vw + mypos * MAXN + 2 * (jp ^ (mypos & (NPAIR - 1)))) =
+          make_float4(b[2 * jp].x, b[2 * jp].y, b[2 * jp + 1].x, b[2 * jp + 1].y);
+    }
+  }
+  __syncwarp();
+  if (row) {
+    for (int c = n - 1; c >= 0; --c) {
+      float2 x = Vw[swz<MAXN>(c, l)];
+      for (int m = c + 1; m < n; ++m) x = cfms(Pw[swz<MAXN>(c, m)], Vw[swz<MAXN>(m, l)], x);
+      Vw[swz<MAXN>(c, l)] = cmul(x, cinv(Pw[swz<MAXN>(c, c)]));
+    }
+  }
+  if (singular && l == 0 && q < nk)
+    report(err, first_bad, QA_ESINGULAR_CODE, static_cast<long long>(nu) * nk + q);
+  __syncthreads();
+  for (int idx = tid; idx < NSYS * nn; idx += blockDim.x) {
+    const int e = idx / NSYS, ss = idx - e * NSYS;
+    const int rr = e / n, cc = e - rr * n;
+    const int qq = q0 + ss;
+    if (qq < nk) WC[slab + static_cast<size_t>(e) * nk + qq] = Vs[ss * TT + swz<MAXN>(rr, cc)];
+  }
+}
+
+template <int MAXN>
+cudaError_t launch_dyson_w_tile(const void* P, const void* Vq, void* WC, int r, int n, int nk,
+                                int* err, long long* first_bad, cudaStream_t st) {
+  constexpr int NSYS = kWarpsR * (32 / MAXN);
+  const size_t smem = (static_cast<size_t>(2) * NSYS * MAXN * MAXN + NSYS * 2 * MAXN) * sizeof(float2);
+  auto fn = &dyson_w_tile_kernel<MAXN>;
   cudaError_t e = set_smem(reinterpret_cast<const void*>(fn), smem);
   if (e != cudaSuccess) return e;
   dim3 grid((nk + NSYS - 1) / NSYS, r);
@@ -543,9 +787,9 @@ cudaError_t launch_dyson_w(const void* P, const void* Vq, void* WC, int r, int n
   if (npair > kMaxPair) return cudaErrorInvalidValue;
   if (sizeof(T) == 4) {
     // register-row kernel: W^C = (1 - V P)^-1 V P V directly
-    if (npair <= 4) return launch_dyson_w_reg<4, 4>(P, Vq, WC, r, npair, nk, err, first_bad, st);
-    if (npair <= 8) return launch_dyson_w_reg<8, 8>(P, Vq, WC, r, npair, nk, err, first_bad, st);
-    if (npair <= 16) return launch_dyson_w_reg<16, 16>(P, Vq, WC, r, npair, nk, err, first_bad, st);
+    if (npair <= 4) return launch_dyson_w_tile<4>(P, Vq, WC, r, npair, nk, err, first_bad, st);
+    if (npair <= 8) return launch_dyson_w_tile<8>(P, Vq, WC, r, npair, nk, err, first_bad, st);
+    if (npair <= 16) return launch_dyson_w_tile<16>(P, Vq, WC, r, npair, nk, err, first_bad, st);
     return launch_dyson_w_reg<25, 32>(P, Vq, WC, r, npair, nk, err, first_bad, st);
   }
   size_t smem = static_cast<size_t>(kWarpsW) * 2 * npair * (npair + 1) * sizeof(cplx<T>);

@@ -13,6 +13,19 @@ namespace qa {
 namespace {
 
 constexpr int kMaxRadix = 13;
+constexpr int kMaxLineTerms = 640;      // terms of one bubble output (<= npair^2 = 625)
+constexpr int kFftThreads = 256;        // block size of the register-FFT kernel
+
+// term lists of the bubble for the fused bubble + FFT lines (may be empty)
+struct BubbleSrc {
+  const void* GR;
+  const void* GL;
+  const int* mR;
+  const int* terms;       // off[nout + 1] then idx[]
+  const void* coef;
+  int nout;
+  int no2;
+};
 
 template <typename V>
 __device__ __forceinline__ V tw_get(const V* tw, int idx, int sign) {
@@ -161,15 +174,21 @@ __device__ __forceinline__ void line_fft(V* __restrict__ buf, int pb, int ps,
 // keeps lpb lines in shared memory (one padding element per 2^lp points
 // spreads the strided axis passes over the banks), each axis pass gives one
 // length-L transform per thread, and all index arithmetic is shifts and masks.
-template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) fft3d_reg_kernel(int l1, int l2, int l3, int sign,
+// With BUB the lines are not read but produced in shared memory by the bubble
+// term lists (launch_fft3d_bubble): line (tau, o) holds
+// sum_terms coef G[tau][g1](R) G^refl[tau][g2](-R), so P(R, tau) never goes
+// through HBM before its transform to q.
+template <typename T, bool BUB>
+__global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1) fft3d_reg_kernel(int l1, int l2, int l3, int sign,
                                                         const cplx<T>* in, cplx<T>* out,
                                                         int lpb, long long nlines, int lp,
-                                                        T scale) {
+                                                        T scale, BubbleSrc bs) {
   using V = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* tw = reinterpret_cast<V*>(smem_raw);               // exp(-2 pi i k / 64), k < 32
-  V* buf = tw + 32;
+  V* tc = tw + 32;                                      // [kMaxLineTerms] term coefficients
+  int* ti = reinterpret_cast<int*>(tc + (BUB ? kMaxLineTerms : 0));
+  V* buf = reinterpret_cast<V*>(ti + (BUB ? kMaxLineTerms : 0));
   const int tid = threadIdx.x, bd = blockDim.x;
   const int lnk = l1 + l2 + l3, nk = 1 << lnk;
   const int line_sz = nk + (nk >> lp);
@@ -180,11 +199,70 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) fft3d_reg_kernel(
     sincospi(-tid / 32.0, &sn, &cs);
     tw[tid] = cmk<V>(cs, sn);
   }
-  const V* src = in + line0 * nk;
   const int tot = nl << lnk;
-  for (int i = tid; i < tot; i += bd) {
-    const int line = i >> lnk, e = i & (nk - 1);
-    buf[line * line_sz + e + (e >> lp)] = src[i];
+  if (BUB) {
+    const V* GR = reinterpret_cast<const V*>(bs.GR);
+    const V* GL = reinterpret_cast<const V*>(bs.GL);
+    const V* cf = reinterpret_cast<const V*>(bs.coef);
+    for (int line = 0; line < nl; ++line) {
+      const long long gline = line0 + line;
+      const int tau = static_cast<int>(gline / bs.nout), o = static_cast<int>(gline - static_cast<long long>(tau) * bs.nout);
+      const int e0 = bs.terms[o], nt = bs.terms[o + 1] - e0;
+      __syncthreads();                                  // the previous line's terms are consumed
+      for (int e = tid; e < nt; e += bd) {
+        tc[e] = cf[e0 + e];
+        ti[e] = bs.terms[bs.nout + 1 + e0 + e];
+      }
+      __syncthreads();
+      const V* gt = GR + static_cast<size_t>(tau) * bs.no2 * nk;
+      const V* lt = GL + static_cast<size_t>(tau) * bs.no2 * nk;
+      // four points per thread at a time: eight loads in flight per term
+      for (int e0 = tid; e0 < nk; e0 += 4 * kFftThreads) {
+        int mr[4];
+        V acc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int e = e0 + u * kFftThreads;
+          mr[u] = e < nk ? bs.mR[e] : 0;
+          acc[u] = cmk<V>(0, 0);
+        }
+        for (int v = 0; v < nt; ++v) {
+          const int id = ti[v];
+          const V c = tc[v];
+          const V* g1 = gt + static_cast<size_t>(id & 255) * nk;
+          const V* g2 = lt + static_cast<size_t>(id >> 8) * nk;
+          V x[4], y[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int e = e0 + u * kFftThreads;
+            x[u] = e < nk ? g1[e] : cmk<V>(0, 0);
+            y[u] = e < nk ? g2[mr[u]] : cmk<V>(0, 0);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acc[u] = cfma(c, cmul(x[u], y[u]), acc[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int e = e0 + u * kFftThreads;
+          if (e < nk) buf[line * line_sz + e + (e >> lp)] = acc[u];
+        }
+      }
+    }
+  } else {
+    const V* src = in + line0 * nk;
+    for (int i0 = tid; i0 < tot; i0 += 8 * kFftThreads) {   // eight loads in flight per thread
+      V v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = i0 + u * kFftThreads;
+        v[u] = i < tot ? src[i] : cmk<V>(0, 0);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = i0 + u * kFftThreads;
+        if (i < tot) buf[(i >> lnk) * line_sz + (i & (nk - 1)) + ((i & (nk - 1)) >> lp)] = v[u];
+      }
+    }
   }
   __syncthreads();
   for (int d = 2; d >= 0; --d) {
@@ -224,7 +302,46 @@ bool reg_axis_ok(int L, int maxL) {
   return L >= 1 && L <= maxL && (L & (L - 1)) == 0;
 }
 
+bool reg_plan_ok(const FftDev& plan) {
+  const int nk = plan.n[0] * plan.n[1] * plan.n[2];
+  return reg_axis_ok(plan.n[0], 32) && reg_axis_ok(plan.n[1], 32) && reg_axis_ok(plan.n[2], 32) &&
+         nk >= 2;
+}
+
+template <typename T, bool BUB>
+cudaError_t launch_fft3d_reg(const FftDev& plan, int sign, const void* in, void* out,
+                             long long nlines, cudaStream_t st, T sc, const BubbleSrc& bs) {
+  const int nk = plan.n[0] * plan.n[1] * plan.n[2];
+  const int pad = plan.n[2] > 1 ? plan.n[2] : (plan.n[1] > 1 ? plan.n[1] : plan.n[0]);
+  const int lp = ilog2(pad);
+  const int line_sz = nk + (nk >> lp);
+  int lpb = 1;
+  while (lpb * 2 * line_sz * static_cast<int>(sizeof(cplx<T>)) <= 32768 && lpb * 2 <= 64) lpb *= 2;
+  const size_t extra = BUB ? static_cast<size_t>(kMaxLineTerms) * (sizeof(cplx<T>) + sizeof(int)) : 0;
+  size_t smem = (static_cast<size_t>(lpb) * line_sz + 32) * sizeof(cplx<T>) + extra;
+  auto fn = &fft3d_reg_kernel<T, BUB>;
+  cudaError_t e = set_smem(reinterpret_cast<const void*>(fn), smem, true);
+  if (e != cudaSuccess) return e;
+  long long nblk = (nlines + lpb - 1) / lpb;
+  fn<<<static_cast<unsigned>(nblk), kFftThreads, smem, st>>>(
+      ilog2(plan.n[0]), ilog2(plan.n[1]), ilog2(plan.n[2]), sign,
+      reinterpret_cast<const cplx<T>*>(in), reinterpret_cast<cplx<T>*>(out), lpb, nlines, lp, sc, bs);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+bool fft3d_bubble_supported(const FftDev& plan) { return reg_plan_ok(plan); }
+
+template <typename T>
+cudaError_t launch_fft3d_bubble(const FftDev& plan, const void* GR, const void* GreflR,
+                                const int* mR, const int* terms, const void* coef, int max_terms,
+                                int nout, int norb, void* out, int r, cudaStream_t st) {
+  if (!reg_plan_ok(plan) || max_terms > kMaxLineTerms || norb * norb > 256) return cudaErrorInvalidValue;
+  BubbleSrc bs{GR, GreflR, mR, terms, coef, nout, norb * norb};
+  return launch_fft3d_reg<T, true>(plan, -1, nullptr, out, static_cast<long long>(nout) * r, st,
+                                   static_cast<T>(1), bs);
+}
 
 template <typename T>
 cudaError_t launch_fft3d(const FftDev& plan, int sign, const void* in, void* out, long long nlines,
@@ -232,23 +349,7 @@ cudaError_t launch_fft3d(const FftDev& plan, int sign, const void* in, void* out
   if (nlines <= 0) return cudaSuccess;
   const int nk = plan.n[0] * plan.n[1] * plan.n[2];
   const T sc = static_cast<T>(scale > 0 ? scale : (sign > 0 ? 1.0 / nk : 1.0));
-  const int maxL = 32;
-  if (reg_axis_ok(plan.n[0], maxL) && reg_axis_ok(plan.n[1], maxL) && reg_axis_ok(plan.n[2], maxL) &&
-      nk >= 2) {
-    const int pad = plan.n[2] > 1 ? plan.n[2] : (plan.n[1] > 1 ? plan.n[1] : plan.n[0]);
-    const int lp = ilog2(pad);
-    const int line_sz = nk + (nk >> lp);
-    int lpb = 1;
-    while (lpb * 2 * line_sz * static_cast<int>(sizeof(cplx<T>)) <= 32768 && lpb * 2 <= 64) lpb *= 2;
-    size_t smem = (static_cast<size_t>(lpb) * line_sz + 32) * sizeof(cplx<T>);
-    cudaError_t e = set_smem(reinterpret_cast<const void*>(&fft3d_reg_kernel<T>), smem, true);
-    if (e != cudaSuccess) return e;
-    long long nblk = (nlines + lpb - 1) / lpb;
-    fft3d_reg_kernel<T><<<static_cast<unsigned>(nblk), 256, smem, st>>>(
-        ilog2(plan.n[0]), ilog2(plan.n[1]), ilog2(plan.n[2]), sign,
-        reinterpret_cast<const cplx<T>*>(in), reinterpret_cast<cplx<T>*>(out), lpb, nlines, lp, sc);
-    return cudaGetLastError();
-  }
+  if (reg_plan_ok(plan)) return launch_fft3d_reg<T, false>(plan, sign, in, out, nlines, st, sc, BubbleSrc{});
   // lines per block: keep the tile near 16 KB for small grids
   int lpb = 1;
   while (lpb * 2 * nk * static_cast<int>(sizeof(cplx<T>)) <= 16384 && lpb * 2 <= 64) lpb *= 2;
@@ -263,6 +364,12 @@ cudaError_t launch_fft3d(const FftDev& plan, int sign, const void* in, void* out
   return cudaGetLastError();
 }
 
+template cudaError_t launch_fft3d_bubble<double>(const FftDev&, const void*, const void*, const int*,
+                                                 const int*, const void*, int, int, int, void*, int,
+                                                 cudaStream_t);
+template cudaError_t launch_fft3d_bubble<float>(const FftDev&, const void*, const void*, const int*,
+                                                const int*, const void*, int, int, int, void*, int,
+                                                cudaStream_t);
 template cudaError_t launch_fft3d<double>(const FftDev&, int, const void*, void*, long long,
                                           cudaStream_t, double);
 template cudaError_t launch_fft3d<float>(const FftDev&, int, const void*, void*, long long,

@@ -109,6 +109,16 @@ template <typename T>
 cudaError_t launch_fft3d(const FftDev& plan, int sign, const void* in, void* out, long long nlines,
                          cudaStream_t st, double scale = 0.0);
 
+// Bubble and R -> q transform in one pass (power-of-two axes <= 32, see
+// fft3d_bubble_supported): line (t, o) of out = FFT over R of
+// sum_{terms of o} coef G[t][g1][R] Grefl[t][g2][mR[R]] (term lists as for
+// launch_bubble_reduced, at most max_terms terms per output, <= 640).
+bool fft3d_bubble_supported(const FftDev& plan);
+template <typename T>
+cudaError_t launch_fft3d_bubble(const FftDev& plan, const void* GR, const void* GreflR,
+                                const int* mR, const int* terms, const void* coef, int max_terms,
+                                int nout, int norb, void* out, int r, cudaStream_t st);
+
 // P[t][(ab)][(cd)][R] = -s G[t][b][c][R] Grefl[t][d][a][mR[R]]
 template <typename T>
 cudaError_t launch_bubble(const void* GR, const void* GreflR, const int* mR, void* P, int r,

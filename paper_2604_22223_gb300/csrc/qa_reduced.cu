@@ -59,9 +59,12 @@ __global__ void __launch_bounds__(RedTpb<T>::v) bubble_reduced_kernel(
     const int mr = mR[R];
     const V* gt = GR + static_cast<size_t>(t) * no2 * nk;
     const V* lt = GL + static_cast<size_t>(t) * no2 * nk;
-    for (int e = 0; e < no2; ++e) {
-      g[e * TPB + tid] = gt[static_cast<size_t>(e) * nk + R];
-      gl[e * TPB + tid] = lt[static_cast<size_t>(e) * nk + mr];
+#pragma unroll
+    for (int e = 0; e < 25; ++e) {        // no2 <= 25: all loads in flight together
+      if (e < no2) {
+        g[e * TPB + tid] = gt[static_cast<size_t>(e) * nk + R];
+        gl[e * TPB + tid] = lt[static_cast<size_t>(e) * nk + mr];
+      }
     }
   }
   __syncthreads();
@@ -108,9 +111,12 @@ __global__ void __launch_bounds__(RedTpb<T>::v) sigma_reduced_kernel(
   stage_terms<T>(terms, coef, nout, nterm, s_off, s_rec);
   if (R < nk) {
     const V* gt = GR + static_cast<size_t>(t) * no2 * nk;
-    for (int e = 0; e < no2; ++e) {
-      g[e * TPB + tid] = gt[static_cast<size_t>(e) * nk + R];
-      sg[e * TPB + tid] = cmk<V>(0, 0);
+#pragma unroll
+    for (int e = 0; e < 25; ++e) {        // no2 <= 25: all loads in flight together
+      if (e < no2) {
+        g[e * TPB + tid] = gt[static_cast<size_t>(e) * nk + R];
+        sg[e * TPB + tid] = cmk<V>(0, 0);
+      }
     }
   }
   __syncthreads();
@@ -150,7 +156,7 @@ template <typename T>
 cudaError_t launch_bubble_reduced(const void* GR, const void* GreflR, const int* mR,
                                   const int* terms, const void* coef, int nterm, void* Pt, int r,
                                   int norb, int rho, int nk, cudaStream_t st) {
-  if (nterm < 0 || nterm > kMaxPairTerms || norb * norb > 256 || rho < 1) return cudaErrorInvalidValue;
+  if (nterm < 0 || nterm > kMaxPairTerms || norb > 5 || rho < 1) return cudaErrorInvalidValue;
   const int no2 = norb * norb, nout = rho * rho;
   const size_t smem = reduced_smem<T>(no2, nout, nterm);
   cudaError_t e = set_smem(reinterpret_cast<const void*>(&bubble_reduced_kernel<T>), smem);
@@ -167,7 +173,7 @@ template <typename T>
 cudaError_t launch_sigma_reduced(const void* GR, const void* Wt, const int* terms, const void* coef,
                                  int nterm, void* Sig, int r, int norb, int rho, int nk,
                                  cudaStream_t st) {
-  if (nterm < 0 || nterm > kMaxPairTerms || norb * norb > 256 || rho < 1) return cudaErrorInvalidValue;
+  if (nterm < 0 || nterm > kMaxPairTerms || norb > 5 || rho < 1) return cudaErrorInvalidValue;
   const int no2 = norb * norb, nout = rho * rho;
   const size_t smem = reduced_smem<T>(no2, nout, nterm);
   cudaError_t e = set_smem(reinterpret_cast<const void*>(&sigma_reduced_kernel<T>), smem);

@@ -123,24 +123,21 @@ __global__ void __launch_bounds__(256) g_input_kernel(const double2* __restrict_
   __syncthreads();
   for (long long col = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; col < ncol;
        col += static_cast<long long>(gridDim.x) * blockDim.x) {
-    double2 acc0 = make_double2(0, 0), acc1 = make_double2(0, 0);
-    int l = 0;
-    for (; l + 1 < r; l += 2) {
-      const double2 x0 = G[static_cast<long long>(l) * ncol + col];
-      const double2 x1 = G[static_cast<long long>(l + 1) * ncol + col];
-      if (G32) {
-        G32[static_cast<long long>(l) * ncol + col] = make_float2(static_cast<float>(x0.x), static_cast<float>(x0.y));
-        G32[static_cast<long long>(l + 1) * ncol + col] = make_float2(static_cast<float>(x1.x), static_cast<float>(x1.y));
+    double2 acc[4] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
+    for (int l0 = 0; l0 < r; l0 += 8) {       // eight loads in flight per thread
+      double2 x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        x[u] = l0 + u < r ? G[static_cast<long long>(l0 + u) * ncol + col] : make_double2(0, 0);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (l0 + u < r) {
+          if (G32) G32[static_cast<long long>(l0 + u) * ncol + col] = make_float2(static_cast<float>(x[u].x), static_cast<float>(x[u].y));
+          acc[u & 3] = cfma(d[l0 + u], x[u], acc[u & 3]);
+        }
       }
-      acc0 = cfma(d[l], x0, acc0);
-      acc1 = cfma(d[l + 1], x1, acc1);
     }
-    if (l < r) {
-      const double2 x0 = G[static_cast<long long>(l) * ncol + col];
-      if (G32) G32[static_cast<long long>(l) * ncol + col] = make_float2(static_cast<float>(x0.x), static_cast<float>(x0.y));
-      acc0 = cfma(d[l], x0, acc0);
-    }
-    nk_out[col] = cadd(acc0, acc1);
+    nk_out[col] = cadd(cadd(acc[0], acc[1]), cadd(acc[2], acc[3]));
   }
 }
 
