@@ -128,6 +128,7 @@ struct qa_ctx {
   double2* d_sV = nullptr;        // [nV][rho][rho] FP64
   void* d_Bm = nullptr;           // mu-independent part of the G Dyson argument (sized for FP64)
   double2* d_phV = nullptr;       // [nV + 1][N_k] e^{+i k.R_v} of the interaction's R list
+  void* d_hs = nullptr;           // [N_k][norb^2] double-float mu - H - Sigma^HF (mixed density check)
   double mu_ref = 0.0;            // reference chemical potential folded into d_Bm
 };
 
@@ -281,6 +282,7 @@ size_t layout(qa_ctx* c, char* base) {
   c->d_Gt = take(r * no2 * nk * 16);
   c->d_Bm = take(r * no2 * nk * 16);
   c->d_phV = static_cast<double2*>(take((c->nV + 1) * nk * 16));
+  c->d_hs = take(nk * no2 * 16);
   // big tensors last; P must also hold the FP64 V(q) staging of qa_bind
   c->d_P = take(std::max(r * nb2 * nk * es, nk * nb2 * 16));
   c->d_W = take(r * nb2 * nk * es);
@@ -504,11 +506,12 @@ int mu_search(qa_ctx* c, const double2* SigHF, const void* SigIw, const DevTable
     }
   }
   if (!fp64) {
-    // one FP64 evaluation at the FP32 root (FP64 inverse of the stored Sigma)
-    // and a Newton correction: removes the FP32 density noise from mu
-    QA_LAUNCH(c, 1, qa::launch_dyson_g_f64_sig32(c->d_Hk, SigHF, SigIw, c->t64.dw, c->d_iw, mu, c->r,
-                                                 c->norb, c->nk, c->d_part, c->nblocks_g, c->d_err,
-                                                 st));
+    // one FP64-accurate evaluation at the FP32 root (FP32 inverse refined by a
+    // double-float residual step) and a Newton correction: removes the bias
+    // of FP32 densities (the DLR density weights amplify FP32 rounding) from mu
+    QA_LAUNCH(c, 2, qa::launch_dyson_g_refine(c->d_Hk, SigHF, SigIw, c->t64.dw, c->d_iw, mu, c->r,
+                                              c->norb, c->nk, c->d_hs, c->d_part, c->nblocks_g,
+                                              c->d_err, st));
     QA_LAUNCH(c, 1, qa::launch_reduce_pairs(c->d_part, c->nblocks_g, 0, c->d_red, st));
     double h2[2];
     QA_TRY(cudaMemcpyAsync(h2, c->d_red, 16, cudaMemcpyDeviceToHost, st));

@@ -349,11 +349,13 @@ __global__ void __launch_bounds__(kWarpsR * 32) dyson_w_tile_kernel(const float2
   constexpr int SPW = 32 / W;
   constexpr int NSYS = kWarpsR * SPW;
   constexpr int TT = MAXN * MAXN;              // tile entries
+  constexpr int TS = TT + 2;                   // tile stride: 16 bytes of padding per system
+                                               // spread the per-q loads and stores over the banks
   constexpr int NPAIR = MAXN / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* Ps = reinterpret_cast<float2*>(smem_raw);        // [NSYS][TT]
-  float2* Vs = Ps + NSYS * TT;                              // [NSYS][TT]
-  float2* Rs = Vs + NSYS * TT;                              // [NSYS][2 * MAXN] pivot rows
+  float2* Ps = reinterpret_cast<float2*>(smem_raw);        // [NSYS][TS]
+  float2* Vs = Ps + NSYS * TS;                              // [NSYS][TS]
+  float2* Rs = Vs + NSYS * TS;                              // [NSYS][2 * MAXN] pivot rows
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int l = lane & (W - 1);
   const int sys = w * SPW + lane / W;
@@ -380,7 +382,7 @@ __global__ void __launch_bounds__(kWarpsR * 32) dyson_w_tile_kernel(const float2
     for (int it = 0; it < kIt; ++it) {
       const int idx = tid + it * kThr;
       const int pos = idx / NSYS, ss = idx - pos * NSYS;
-      Ps[ss * TT + swz<MAXN>(pos / MAXN, pos % MAXN)] = v[it];
+      Ps[ss * TS + swz<MAXN>(pos / MAXN, pos % MAXN)] = v[it];
     }
 #pragma unroll
     for (int it = 0; it < kIt; ++it) {
@@ -395,13 +397,13 @@ __global__ void __launch_bounds__(kWarpsR * 32) dyson_w_tile_kernel(const float2
     for (int it = 0; it < kIt; ++it) {
       const int idx = tid + it * kThr;
       const int ss = idx / TT, pos = idx - ss * TT;
-      Vs[ss * TT + swz<MAXN>(pos / MAXN, pos % MAXN)] = v[it];
+      Vs[ss * TS + swz<MAXN>(pos / MAXN, pos % MAXN)] = v[it];
     }
   }
   __syncthreads();
   const int q = q0 + sys;
-  float2* Pw = Ps + sys * TT;
-  float2* Vw = Vs + sys * TT;
+  float2* Pw = Ps + sys * TS;
+  float2* Vw = Vs + sys * TS;
   float2* Ra = Rs + sys * 2 * MAXN;             // pivot row of A
   float2* Rb = Ra + MAXN;                       // pivot row of the right-hand side
   float2 a[MAXN], b[MAXN];
@@ -520,7 +522,7 @@ __global__ void __launch_bounds__(kWarpsR * 32) dyson_w_tile_kernel(const float2
     const int e = idx / NSYS, ss = idx - e * NSYS;
     const int rr = e / n, cc = e - rr * n;
     const int qq = q0 + ss;
-    if (qq < nk) WC[slab + static_cast<size_t>(e) * nk + qq] = Vs[ss * TT + swz<MAXN>(rr, cc)];
+    if (qq < nk) WC[slab + static_cast<size_t>(e) * nk + qq] = Vs[ss * TS + swz<MAXN>(rr, cc)];
   }
 }
 
@@ -528,7 +530,7 @@ template <int MAXN>
 cudaError_t launch_dyson_w_tile(const void* P, const void* Vq, void* WC, int r, int n, int nk,
                                 int* err, long long* first_bad, cudaStream_t st) {
   constexpr int NSYS = kWarpsR * (32 / MAXN);
-  const size_t smem = (static_cast<size_t>(2) * NSYS * MAXN * MAXN + NSYS * 2 * MAXN) * sizeof(float2);
+  const size_t smem = (static_cast<size_t>(2) * NSYS * (MAXN * MAXN + 2) + NSYS * 2 * MAXN) * sizeof(float2);
   auto fn = &dyson_w_tile_kernel<MAXN>;
   cudaError_t e = set_smem(reinterpret_cast<const void*>(fn), smem);
   if (e != cudaSuccess) return e;
@@ -644,6 +646,147 @@ __global__ void __launch_bounds__(256) dyson_g_direct_kernel(const double2* __re
     const double2 wn = dw[n];
     s1 += wn.x * tr.x - wn.y * tr.y;
     s2 += wn.x * tr2.x - wn.y * tr2.y;
+  }
+  if (bad) atomicCAS(err, 0, QA_ESINGULAR_CODE);
+  block_sum2(s1, s2, sh);
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = s1;
+    part[2 * blockIdx.x + 1] = s2;
+  }
+}
+
+// ---- FP64-accurate density from FP32 arithmetic (mixed path)
+// A = i w_n + mu - H(k) - Sigma^HF(k) - Sigma^C(k, i w_n) with Sigma^C given
+// in complex64.  G32 = FP32 inverse of A rounded to FP32; one refinement
+// step G = G32 + G32 R with the residual R = I - A G32 evaluated in
+// double-float arithmetic (each FP32 product split exactly by an FMA,
+// compensated sums, Dekker/Knuth), so that Tr G carries FP64-level accuracy
+// although no FP64 multiply runs per matrix entry.  The mu-dependent part
+// mu - H - Sigma^HF comes from a per-k double-float table (hi, lo).
+
+// x = hi + lo exactly as FP32 pair (hi = rn(x))
+__device__ __forceinline__ float2 df_split(double x) {
+  const float hi = static_cast<float>(x);
+  return make_float2(hi, static_cast<float>(x - static_cast<double>(hi)));
+}
+
+// TwoSum: s = rn(a + b), e = (a + b) - s exactly.  The _rn intrinsics keep
+// the compiler from contracting or reassociating these steps.
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+  const float s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+  return s;
+}
+
+// s + c += a * b exactly up to the final rounding of c (TwoProd + TwoSum)
+__device__ __forceinline__ void df_madd(float a, float b, float& s, float& c) {
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);
+  float es;
+  s = two_sum(s, p, es);
+  c = __fadd_rn(c, __fadd_rn(es, e));
+}
+
+__global__ void hs_table_kernel(const double2* __restrict__ Hk, const double2* __restrict__ SigHF,
+                                double mu, int no, int nk, float4* __restrict__ hs) {
+  const int no2 = no * no;
+  const long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= static_cast<long long>(nk) * no2) return;
+  const int e = static_cast<int>(idx % no2);
+  double2 h = Hk[idx];
+  if (SigHF) { h.x += SigHF[idx].x; h.y += SigHF[idx].y; }
+  double re = -h.x, im = -h.y;
+  if (e / no == e % no) re += mu;
+  const float2 a = df_split(re), b = df_split(im);
+  hs[idx] = make_float4(a.x, b.x, a.y, b.y);      // (hi.re, hi.im, lo.re, lo.im)
+}
+
+// A_ij = hs - SigIw (+ i w_n on the diagonal) as hi + lo pairs
+template <int NO>
+__device__ __forceinline__ void df_entry(const float4* __restrict__ hs_k, const float2* __restrict__ SigIw,
+                                         const float2 wdf, int n, int k, int nk, int i, int j,
+                                         float2& hi, float2& lo) {
+  const float4 t = hs_k[i * NO + j];
+  const float2 sc = SigIw[(static_cast<size_t>(n) * NO * NO + i * NO + j) * nk + k];
+  // re: t.x + t.z - sc.x ; im: t.y + t.w - sc.y (+ w on the diagonal)
+  float er, ei;
+  const float sr = two_sum(t.x, -sc.x, er);
+  float si = two_sum(t.y, -sc.y, ei);
+  const float lr = __fadd_rn(t.z, er);
+  float li = __fadd_rn(t.w, ei);
+  if (i == j) {
+    float ew;
+    si = two_sum(si, wdf.x, ew);
+    li = __fadd_rn(li, __fadd_rn(ew, wdf.y));
+  }
+  hi = make_float2(sr, si);
+  lo = make_float2(lr, li);
+}
+
+template <int NO>
+__global__ void __launch_bounds__(256) dyson_g_refine_kernel(const float4* __restrict__ hs,
+                                                             const float2* __restrict__ SigIw,
+                                                             const double2* __restrict__ dw,
+                                                             const double* __restrict__ iw, int r,
+                                                             int nk, double* part, int* err) {
+  __shared__ double sh[64];
+  const long long total = static_cast<long long>(r) * nk;
+  double s1 = 0.0, s2 = 0.0;
+  bool bad = false;
+  for (long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
+       idx += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int n = static_cast<int>(idx / nk);
+    const int k = static_cast<int>(idx - static_cast<long long>(n) * nk);
+    const float4* hk = hs + static_cast<size_t>(k) * NO * NO;
+    const float2 wdf = df_split(iw[n]);
+    float2 g[NO][NO];
+#pragma unroll
+    for (int i = 0; i < NO; ++i)
+#pragma unroll
+      for (int j = 0; j < NO; ++j) {
+        float2 hi, lo;
+        df_entry<NO>(hk, SigIw, wdf, n, k, nk, i, j, hi, lo);
+        g[i][j] = hi;
+      }
+    bad |= gj_inverse<float2, NO>(g);
+    // Tr G = Tr G32 + sum_ij G32_ij R_ji,  R = I - A G32 (double-float)
+    float2 corr = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < NO; ++i) {
+      float2 ahi[NO], alo[NO];
+#pragma unroll
+      for (int m = 0; m < NO; ++m) df_entry<NO>(hk, SigIw, wdf, n, k, nk, i, m, ahi[m], alo[m]);
+#pragma unroll
+      for (int j = 0; j < NO; ++j) {
+        float sr = (i == j) ? -1.f : 0.f, cr = 0.f, si = 0.f, ci = 0.f;   // (A G32 - I)_ij
+#pragma unroll
+        for (int m = 0; m < NO; ++m) {
+          df_madd(ahi[m].x, g[m][j].x, sr, cr);
+          df_madd(-ahi[m].y, g[m][j].y, sr, cr);
+          df_madd(ahi[m].x, g[m][j].y, si, ci);
+          df_madd(ahi[m].y, g[m][j].x, si, ci);
+          cr = fmaf(alo[m].x, g[m][j].x, cr);
+          cr = fmaf(-alo[m].y, g[m][j].y, cr);
+          ci = fmaf(alo[m].x, g[m][j].y, ci);
+          ci = fmaf(alo[m].y, g[m][j].x, ci);
+        }
+        const float2 Rij = make_float2(-(sr + cr), -(si + ci));
+        corr = cfma(g[j][i], Rij, corr);        // sum_ij G32_ji R_ij
+      }
+    }
+    double trr = corr.x, tri = corr.y;
+    float2 tr2 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < NO; ++i) {
+      trr += static_cast<double>(g[i][i].x);
+      tri += static_cast<double>(g[i][i].y);
+#pragma unroll
+      for (int j = 0; j < NO; ++j) tr2 = cfma(g[i][j], g[j][i], tr2);
+    }
+    const double2 wn = dw[n];
+    s1 += wn.x * trr - wn.y * tri;
+    s2 += wn.x * static_cast<double>(tr2.x) - wn.y * static_cast<double>(tr2.y);
   }
   if (bad) atomicCAS(err, 0, QA_ESINGULAR_CODE);
   block_sum2(s1, s2, sh);
@@ -823,6 +966,25 @@ cudaError_t launch_dyson_g(const void* Bm, const void* dw, const double* iw, dou
   switch (norb) {
 #define QA_CASE(NO) \
     case NO: dyson_g_kernel<T, NO><<<nblocks, 256, 0, st>>>(b, d, iw, dmu, r, nk, g, part, mode, err); break;
+    QA_CASE(1) QA_CASE(2) QA_CASE(3) QA_CASE(4) QA_CASE(5)
+#undef QA_CASE
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dyson_g_refine(const double2* Hk, const double2* SigHF, const void* SigIw,
+                                  const void* dw, const double* iw, double mu, int r, int norb,
+                                  int nk, void* hs, double* part, int nblocks, int* err,
+                                  cudaStream_t st) {
+  const long long ne = static_cast<long long>(nk) * norb * norb;
+  hs_table_kernel<<<static_cast<unsigned>((ne + 255) / 256), 256, 0, st>>>(
+      Hk, SigHF, mu, norb, nk, reinterpret_cast<float4*>(hs));
+  auto h = reinterpret_cast<const float4*>(hs);
+  auto s = reinterpret_cast<const float2*>(SigIw);
+  auto d = reinterpret_cast<const double2*>(dw);
+  switch (norb) {
+#define QA_CASE(NO)     case NO: dyson_g_refine_kernel<NO><<<nblocks, 256, 0, st>>>(h, s, d, iw, r, nk, part, err); break;
     QA_CASE(1) QA_CASE(2) QA_CASE(3) QA_CASE(4) QA_CASE(5)
 #undef QA_CASE
     default: return cudaErrorInvalidValue;

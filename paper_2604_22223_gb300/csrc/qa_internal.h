@@ -163,6 +163,13 @@ cudaError_t launch_dyson_g(const void* Bm, const void* dw, const double* iw, dou
                            int norb, int nk, void* Giw, double* part, int nblocks, int mode,
                            int* err, cudaStream_t st);
 int dyson_g_blocks(int r, int nk);
+// FP64-accurate density sums (mode 0) at mu with Sigma^C(k, i w) stored as
+// complex64, from FP32 arithmetic: FP32 inverse and one residual correction in
+// double-float (two launches; hs = scratch of N_k * norb^2 * 16 bytes).
+cudaError_t launch_dyson_g_refine(const double2* Hk, const double2* SigHF, const void* SigIw,
+                                  const void* dw, const double* iw, double mu, int r, int norb,
+                                  int nk, void* hs, double* part, int nblocks, int* err,
+                                  cudaStream_t st);
 // FP64 density sums (mode 0) at mu with Sigma^C(k, i w) stored as complex64.
 cudaError_t launch_dyson_g_f64_sig32(const double2* Hk, const double2* SigHF, const void* SigIw,
                                      const void* dw, const double* iw, double mu, int r, int norb,
