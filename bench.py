@@ -3,10 +3,14 @@
 
 One step = one full GW iteration through qa_gw_step (G -> P -> W -> Sigma ->
 Dyson -> mu -> G) on the mixed-precision path, inputs resident in HBM; the
-steps alternate between two fixed inputs, G0 and its first iteration.  The FP64 path is timed beside it.  The JSON
-line also carries the end-to-end number through the public API with host
-buffers, the per-stage times, the roofline of the dominant kernel, sampled
-clocks and the CPU oracle baseline.
+steps alternate between two fixed inputs, G0 and its first iteration.  The
+headline runs the library's default for the mixed path: the big tensors on the
+exact reduced pair basis (rho = 15 of the 25 pairs, W^C = B Wt^C B^H; see
+include/qa.h, qa_set_pair_basis).  The same line reports the mixed path on the
+full 25 x 25 product basis and the FP64 path on both bases.  It also carries
+the end-to-end number through the public API with host buffers, the
+per-stage times, the roofline of the dominant kernel, sampled clocks and the
+CPU oracle baseline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -90,18 +94,23 @@ class Clocks:
 
 
 def stage_costs(ctx, mixed: bool):
-    """Algorithmic bytes and flops per launch of each stage (see the design notes)."""
-    r, nk, no, npair = ctx.r, ctx.nk, ctx.norb, ctx.npair
+    """Algorithmic bytes and flops per launch of each big-tensor stage.
+
+    X = r * nb^2 * N_k big-tensor elements (nb = rho on the reduced basis, npair
+    on the full one), Y = r * norb^2 * N_k small-tensor elements.  On grids of
+    power-of-two axes the bubble is produced inside the R -> q FFT (one launch,
+    reported under fft_R_to_q; the bubble stage then reads ~0)."""
+    r, nk, no, nb = ctx.r, ctx.nk, ctx.norb, ctx.nb
     es = 8 if mixed else 16
-    X = r * npair * npair * nk          # big-tensor elements
-    Y = r * no * no * nk                # small-tensor elements
+    X = r * nb * nb * nk
+    Y = r * no * no * nk
     import math
     lg = math.log2(nk)
-    n = npair
+    n = nb
     fd = 8 * (n ** 3 + (n ** 3 if mixed else 0) + n ** 3 / 3 + n ** 3)   # VP, [VPV], LU, solve
     return {
         "bubble": (X * es + 2 * Y * es, 6 * X),
-        "fft_R_to_q": (2 * X * es, 5 * X * lg),
+        "fft_R_to_q": (X * es + 2 * Y * es, 5 * X * lg + 6 * X),
         "dlr_tau_to_nu": (2 * X * es, 8 * r * X),
         "dyson_w": (2 * X * es + nk * n * n * es, r * nk * fd),
         "dlr_nu_to_tau": (2 * X * es, 8 * r * X),
@@ -111,12 +120,13 @@ def stage_costs(ctx, mixed: bool):
 
 
 def iteration_bytes(ctx, mixed: bool):
-    """Minimum HBM bytes of one iteration: P and W^C written and read once each,
-    about six passes over the small G/Sigma tensors (complex128) and V(q)."""
-    r, nk, no, npair = ctx.r, ctx.nk, ctx.norb, ctx.npair
-    X = r * npair * npair * nk
+    """Minimum HBM bytes of one iteration: P and W^C written and read once each
+    (in the basis the path stores), about six passes over the small G/Sigma
+    tensors (complex128) and V(q)."""
+    r, nk, no, nb = ctx.r, ctx.nk, ctx.norb, ctx.nb
+    X = r * nb * nb * nk
     Y = r * no * no * nk
-    return 4 * X * (8 if mixed else 16) + 6 * Y * 16 + nk * npair * npair * 16
+    return 4 * X * (8 if mixed else 16) + 6 * Y * 16 + nk * nb * nb * 16
 
 
 def roofline(ctx, mixed, stage_ms, pk):
@@ -278,7 +288,7 @@ def run_ours(args):
         ms = e0.elapsed_time(e1)
         return ms, {k: v / K for k, v in stage.items()}, launches, evals, ck
 
-    # mixed path (headline)
+    # mixed path on the default (reduced) pair basis: the headline
     ctx = qa.Context(model, "mixed", device=str(dev))
     clocks = Clocks(local)
     ms_mixed, stage_mixed, launches, evals, ck = timed(ctx, args.steps, args.warmup, clocks)
@@ -309,17 +319,27 @@ def run_ours(args):
     barrier(pg)
     ms_e2e = max_over_ranks(pg, e0.elapsed_time(e1), dev)
     gbytes = Gh_in.numel() * Gh_in.element_size()
-    r, nk, no = ctx.r, ctx.nk, ctx.norb
+    r, nk, no, rho, nb = ctx.r, ctx.nk, ctx.norb, ctx.rho, ctx.nb
     del ctx, Gd_in, Gd_out
     torch.cuda.empty_cache()
-    # FP64 path
-    ctx64 = qa.Context(model, "fp64", device=str(dev))
-    ms64, stage64, _, _, _ = timed(ctx64, args.fp64_steps, 1)
-    ms64 = max_over_ranks(pg, ms64, dev)
-    rl64 = roofline(ctx64, False, stage64, pk)
-    it_bytes64 = iteration_bytes(ctx64, False)
-    del ctx64
-    torch.cuda.empty_cache()
+
+    def other(prec, pairs, K):
+        c = qa.Context(model, prec, device=str(dev), pairs=pairs)
+        ms, stg, _, _, _ = timed(c, K, 1)
+        ms = max_over_ranks(pg, ms, dev)
+        mixed = prec == "mixed"
+        out = {"value": world * K / (ms / 1e3), "ms_per_step": ms / K, "steps": K,
+               "pair_basis": "reduced rho=%d" % c.rho if c.reduced else "full npair=%d" % c.npair,
+               "stage_ms": stg, "roofline": roofline(c, mixed, stg, pk),
+               "iteration_hbm_frac": iteration_bytes(c, mixed) / (ms / K * 1e-3) / 1e9 / pk["hbm_gbs"]}
+        del c
+        torch.cuda.empty_cache()
+        return out
+
+    full_mixed = other("mixed", "full", args.other_steps)
+    fp64 = other("fp64", "full", args.fp64_steps)
+    fp64_red = other("fp64", "reduced", args.fp64_steps)
+    ms64 = fp64["ms_per_step"] * args.fp64_steps
     if rank != 0:
         return
     cpu = None
@@ -338,16 +358,18 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "c64/f32 (mixed path; FP64 mu and density)",
         "data": "synthetic: seeded five-orbital Hund-Hubbard model (SplitMix64), no dataset",
         "config": {"workload": WORKLOAD, "k_grid": [32, 32, 8], "norb": no, "npair": no * no,
-                   "dlr_rank": r, "beta": 100.0, "Lambda": 1e4, "eps": 1e-12,
-                   "precision": "mixed", "l2": "no flush: per-step working set (P, W^C: 2 x %.1f GB) "
-                   "is far larger than the 129 MB L2" % (r * 625 * nk * 8 / 1e9),
+                   "pair_basis": "reduced: rho=%d of %d pairs (exact; W^C = B Wt^C B^H)" % (rho, no * no)
+                   if nb < no * no else "full", "dlr_rank": r, "beta": 100.0, "Lambda": 1e4, "eps": 1e-12,
+                   "precision": "mixed", "l2": "no flush: per-step working set (P, W^C: 2 x %.2f GB) "
+                   "is far larger than the 129 MB L2" % (r * nb * nb * nk * 8 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "iteration": {"hbm_bytes": it_bytes, "hbm_frac": it_bytes / (ms_step * 1e-3) / 1e9 / pk["hbm_gbs"],
                       "mu_evals_per_step": statistics.mean(evals)},
         "stage_ms": stage_mixed,
-        "fp64": {"value": world * args.fp64_steps / (ms64 / 1e3), "ms_per_step": ms64 / args.fp64_steps,
-                 "steps": args.fp64_steps, "stage_ms": stage64, "roofline": rl64,
-                 "iteration_hbm_frac": it_bytes64 / (ms64 / args.fp64_steps * 1e-3) / 1e9 / pk["hbm_gbs"]},
+        "mixed_full_pair_basis": full_mixed,
+        "fp64": fp64,
+        "fp64_reduced_pair_basis": fp64_red,
+        "speedup_mixed_over_fp64": (ms64 / args.fp64_steps) / ms_step,
         "roofline": rl,
         "cpu_baseline": cpu,
         "e2e": {"value": world * K2 / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": gbytes,
@@ -417,6 +439,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--other-steps", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
