@@ -1,7 +1,7 @@
-// DLR node-to-node transforms (Kaye, Chen & Parcollet 2022, as used by the
-// paper's FLatDyn/BLatDyn "Fourier transforms between Matsubara frequency and
-// imaginary time"): out[j][c] = sum_l T[j][l] in[l][c] for every column c of
-// a node-major array (c runs over orbital pairs and lattice points).
+// DLR node-to-node transforms (Kaye, Chen & Parcollet 2022; the imaginary-time
+// <-> Matsubara maps of the paper's dynamic lattice classes, Sec. on the code
+// structure): out[j][c] = sum_l T[j][l] in[l][c] for every column c of a
+// node-major array (c runs over orbital pairs and lattice points).
 //
 // Each block stages TILE columns x r nodes in shared memory (one HBM read),
 // then every thread produces RB output rows of one column from registers.

@@ -1,5 +1,5 @@
 // Batched 3-D lattice FFT in shared memory (paper Eq. for the k <-> R
-// transform; "implemented using fast Fourier transform algorithms").
+// transform, which the paper evaluates with FFTs).
 //
 // One block owns `lpb` whole lines of N_k = N1*N2*N3 points (k fastest,
 // C order over (i1, i2, i3)).  The line is staged in shared memory once,
