@@ -105,20 +105,6 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 __device__ __forceinline__ void split3(float x, uint16_t& h0, uint16_t& h1, uint16_t& h2) {
   __nv_bfloat16 b0 = __float2bfloat16_rn(x);
   float r1 = x - __bfloat162float(b0);
@@ -139,16 +125,20 @@ struct TcArgs {
   int* err;
 };
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
-  uint32_t r[8];
+// acc[0..23] += the 24 TMEM columns at taddr (this thread's lane), rounded to
+// nearest: three x8 loads (column offsets multiples of 8), one wait and the
+// adds in one block (only 24 temporaries live beside the accumulators)
+__device__ __forceinline__ void tmem_acc24(uint32_t taddr, float* acc) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+      "{\n\t.reg .b32 t0, t1, t2, t3, t4, t5, t6, t7, t8, t9, t10, t11, t12, t13, t14, t15, t16, t17, t18, t19, t20, t21, t22, t23;\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {t0, t1, t2, t3, t4, t5, t6, t7}, [%24];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {t8, t9, t10, t11, t12, t13, t14, t15}, [%25];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {t16, t17, t18, t19, t20, t21, t22, t23}, [%26];\n\t"
+      "tcgen05.wait::ld.sync.aligned;\n\t"
+      "add.rn.f32 %0, %0, t0;\n\tadd.rn.f32 %1, %1, t1;\n\tadd.rn.f32 %2, %2, t2;\n\tadd.rn.f32 %3, %3, t3;\n\tadd.rn.f32 %4, %4, t4;\n\tadd.rn.f32 %5, %5, t5;\n\tadd.rn.f32 %6, %6, t6;\n\tadd.rn.f32 %7, %7, t7;\n\tadd.rn.f32 %8, %8, t8;\n\tadd.rn.f32 %9, %9, t9;\n\tadd.rn.f32 %10, %10, t10;\n\tadd.rn.f32 %11, %11, t11;\n\tadd.rn.f32 %12, %12, t12;\n\tadd.rn.f32 %13, %13, t13;\n\tadd.rn.f32 %14, %14, t14;\n\tadd.rn.f32 %15, %15, t15;\n\tadd.rn.f32 %16, %16, t16;\n\tadd.rn.f32 %17, %17, t17;\n\tadd.rn.f32 %18, %18, t18;\n\tadd.rn.f32 %19, %19, t19;\n\tadd.rn.f32 %20, %20, t20;\n\tadd.rn.f32 %21, %21, t21;\n\tadd.rn.f32 %22, %22, t22;\n\tadd.rn.f32 %23, %23, t23;\n\t}"
+      : "+f"(acc[0]), "+f"(acc[1]), "+f"(acc[2]), "+f"(acc[3]), "+f"(acc[4]), "+f"(acc[5]), "+f"(acc[6]), "+f"(acc[7]), "+f"(acc[8]), "+f"(acc[9]), "+f"(acc[10]), "+f"(acc[11]), "+f"(acc[12]), "+f"(acc[13]), "+f"(acc[14]), "+f"(acc[15]), "+f"(acc[16]), "+f"(acc[17]), "+f"(acc[18]), "+f"(acc[19]), "+f"(acc[20]), "+f"(acc[21]), "+f"(acc[22]), "+f"(acc[23])
+      : "r"(taddr), "r"(taddr + 8u), "r"(taddr + 16u)
+      : "memory");
 }
 
 constexpr int kHalfMax = 96;            // accumulator columns per thread (Np <= 192)
@@ -225,15 +215,11 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1) dlr_tc_kernel(TcArgs a) {
       bool w = mbar_wait(&bar[gd & 1], static_cast<uint32_t>((gd >> 1) & 1));
       tc_fence_after();
       const uint32_t dcol = static_cast<uint32_t>((gd & 1) * kTmemCols + half * nh);
+      // batches of 24 columns, one wait each (columns past nh lie inside the
+      // allocation; their sums are never stored)
 #pragma unroll
-      for (int c8 = 0; c8 < kHalfMax / 8; ++c8) {
-        if (c8 * 8 < nh) {
-          float v[8];
-          tmem_ld8(taddr + lane_base + dcol + static_cast<uint32_t>(c8 * 8), v);
-#pragma unroll
-          for (int i = 0; i < 8; ++i) acc[c8 * 8 + i] += v[i];
-        }
-      }
+      for (int c24 = 0; c24 < kHalfMax / 24; ++c24)
+        if (c24 * 24 < nh) tmem_acc24(taddr + lane_base + dcol + static_cast<uint32_t>(c24 * 24), acc + c24 * 24);
       tc_fence_before();
       return w;
     };
