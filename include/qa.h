@@ -218,6 +218,47 @@ int qa_gw_backward(qa_ctx* ctx, const void* G_in, double mu, const void* Gbar_ou
                    const void* Sigbar, const double* nbar, void* Gbar_in, double* grad_t,
                    double* grad_V, void* stream);
 
+/* qa_hf_solve: self-consistent Hartree-Fock (paper Sec. "Hartree-Fock
+ * self-consistency" and Fig. 3(a), the first stage of the QAssemble workflow).
+ * Starting from the Fermi-Dirac density of H0 at its own chemical potential,
+ * each iteration builds Sigma^HF(k) = Sigma^H + Sigma^F(k) from n(k) (the same
+ * Hartree and Fock equations as qa_gw_step), mixes it,
+ *   Sigma^HF <- Sigma^HF_old + mix (Sigma^HF_new - Sigma^HF_old),
+ * diagonalises H(k) + Sigma^HF(k) per k (FP64 Jacobi rotations), sets mu to
+ * the filling (s/N_k) sum_{k,i} f(beta (E_ki - mu)) = filling, and takes
+ * n(k) = U f(beta (E - mu)) U^H.  It stops when max |Sigma^HF_new -
+ * Sigma^HF_old| <= tol or after max_iter iterations.  Arguments: max_iter >= 1;
+ * tol >= 0; 0 < mix <= 1 (1 = plain iteration).  Outputs (each may be NULL):
+ *   G_out     device, G layout complex128: the HF Green's function
+ *             G(k, i w) = (i w + mu - H - Sigma^HF)^-1 on the tau nodes, the
+ *             usual starting point of qa_gw_step;
+ *   mu_out, iters_out, resid_out: host scalars (last change of Sigma^HF);
+ *   n_out     host [norb][norb] complex: local density matrix of the result.
+ * Sigma^HF stays in the workspace (qa_get QA_SIGHF_K), mu becomes the warm
+ * start of the next mu search, and qa_qp then uses Sigma^HF alone (Z = 1).
+ * Returns QA_ENOCONV (outputs filled) when tol was not reached.  Needs the
+ * workspace scratch of three N_k norb^2 complex arrays (r >= 3: QA_ENOMEM
+ * otherwise).  Synchronises `stream`. */
+int qa_hf_solve(qa_ctx* ctx, int max_iter, double tol, double mix, void* G_out, double* mu_out,
+                int* iters_out, double* resid_out, double* n_out, void* stream);
+
+/* qa_qp: quasiparticle quantities from the self-energy of the last qa_gw_step
+ * (Sigma^HF and Sigma^C(k, i w) of that step; after qa_hf_solve, Sigma^HF
+ * alone) and the current H(k) (paper Secs. on the renormalisation factor and
+ * the static self-energy, and the quasiparticle Hamiltonian of the graphene
+ * results):
+ *   Sigma(+-i w0), w0 = pi/beta, from the DLR expansion of Sigma^C(k, i w_n);
+ *   Sig0 = Sigma^HF + (Sigma(i w0) + Sigma(-i w0)) / 2          (Sigma at w = 0)
+ *   Z    = [1 - (Sigma(i w0) - Sigma(-i w0)) / (2 i w0)]^-1      (Hermitian part inverted)
+ *   Hqp  = sqrt(Z) (H0 + Sig0) sqrt(Z)  (Hermitian parts; sqrt(Z) the positive root)
+ *   eps  = eigenvalues of Hqp, ascending.
+ * The limit w -> 0 is taken on the Matsubara axis at the lowest fermionic
+ * frequencies (continuing the DLR pole form to w = 0 is ill-conditioned).
+ * Outputs: device, [N_k][norb][norb] complex128 (eps: [N_k][norb] double); each
+ * may be NULL.  QA_ESTATE before any step or HF solve; QA_ERANGE when some
+ * Z(k)^-1 is not positive definite.  Synchronises `stream`. */
+int qa_qp(qa_ctx* ctx, void* Z, void* Sig0, void* Hqp, double* eps, void* stream);
+
 /* Density of a G in G layout (device): n_out [norb][norb] complex local density
  * matrix -G(R=0, beta^-), *N_total = s * Tr n (electrons per cell). */
 int qa_density(qa_ctx* ctx, const void* G, double* n_out, double* N_total, void* stream);

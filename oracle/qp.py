@@ -37,7 +37,7 @@ import numpy as np
 
 from . import lattice
 from .dlr import DLR
-from .gw import hartree_fock
+from .gw import _node_axis_apply, _node_axis_solve, g_iw, hartree_fock
 
 MU_TOL_N = 1e-12
 
@@ -101,6 +101,14 @@ def hf_loop(model, tol: float = 1e-10, max_iter: int = 500, mix: float = 1.0) ->
         if resid <= tol:
             break
     return {"mu": mu, "sig_hf_k": sig, "n_k": nk, "iters": it, "resid": resid}
+
+
+def hf_green(model, dlr: DLR, mu: float, sig_hf_k: np.ndarray) -> np.ndarray:
+    """The Hartree-Fock Green's function on the tau nodes, [k, node, a, b]:
+    Dyson with the static Sigma^HF at mu, DLR fit at the Matsubara nodes,
+    evaluation at the tau nodes."""
+    Giw = g_iw(dlr, lattice.H_k(model), mu, sig_hf_k)
+    return _node_axis_apply(dlr.K_tau(), _node_axis_solve(dlr.K_iw(), Giw))
 
 
 def sigma_static(dlr: DLR, sig_iw: np.ndarray):

@@ -130,6 +130,10 @@ struct qa_ctx {
   double2* d_phV = nullptr;       // [nV + 1][N_k] e^{+i k.R_v} of the interaction's R list
   void* d_hs = nullptr;           // [N_k][norb^2] double-float mu - H - Sigma^HF (mixed density check)
   double mu_ref = 0.0;            // reference chemical potential folded into d_Bm
+  // Hartree-Fock loop and quasiparticle quantities
+  double2* d_wq = nullptr;        // [2][r] weights of Sigma(+i w0), Sigma(-i w0)
+  bool sighf_valid = false;       // d_SigHF holds the last step's (or the HF loop's) Sigma^HF
+  bool sigc_valid = false;        // d_SigIw holds the last step's Sigma^C(k, i w)
 };
 
 namespace {
@@ -292,6 +296,7 @@ size_t layout(qa_ctx* c, char* base) {
   c->d_err = static_cast<int*>(take(4));
   c->d_bad = static_cast<long long*>(take(8));
   c->d_nloc = static_cast<double2*>(take(no2 * 16));
+  c->d_wq = static_cast<double2*>(take(2 * r * 16));
   if (c->precision == QA_MIXED && c->use_tc) {
     c->d_tc_Ttn = take(c->tc_Ttn.size() * 2);
     c->d_tc_Tnt = take(c->tc_Tnt.size() * 2);
@@ -684,6 +689,7 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
   else
     QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Ttw, r, r, c->d_SigC, c->d_SigIw, ncs, st));
   tm.mark();  // 9: Sigma -> (k, i w)
+  c->sighf_valid = c->sigc_valid = true;
   return QA_OK;
 }
 
@@ -817,6 +823,168 @@ int gw_backward_impl(qa_ctx* c, const double2* Gin, double mu, const double2* Gb
   if (grad_V && c->nV > 0)
     QA_TRY(cudaMemcpyAsync(grad_V, c->d_Vbar, static_cast<size_t>(c->nV) * np2 * 16,
                            cudaMemcpyDeviceToHost, st));
+  QA_TRY(cudaStreamSynchronize(st));
+  return check_err(c, nullptr, st);
+}
+
+// ------------------------------------------------- Hartree-Fock loop, QP
+
+// Scratch of the Hartree-Fock loop inside d_Gt: U [N_k][norb^2], E [N_k][norb],
+// the previous Sigma^HF [N_k][norb^2].
+struct HfScratch {
+  double2* U;
+  double* E;
+  double2* old;
+};
+
+bool hf_scratch(qa_ctx* c, HfScratch* h) {
+  const size_t nk = c->nk, no = c->norb, no2 = no * no;
+  const size_t u = nk * no2 * 16, e = align_up(nk * no * 8), o = nk * no2 * 16;
+  if (u + e + o > static_cast<size_t>(c->r) * no2 * nk * 16) return false;
+  char* base = static_cast<char*>(c->d_Gt);
+  h->U = reinterpret_cast<double2*>(base);
+  h->E = reinterpret_cast<double*>(base + u);
+  h->old = reinterpret_cast<double2*>(base + u + e);
+  return true;
+}
+
+int fd_blocks(const qa_ctx* c) {
+  const long long n = static_cast<long long>(c->nk) * c->norb;
+  return static_cast<int>(std::min<long long>(std::max<long long>((n + 255) / 256, 1), c->nblocks_g));
+}
+
+// N(mu) = (s / N_k) sum_{k,i} f(beta (E_ki - mu)) and dN/dmu from the device eigenvalues.
+int fd_eval(qa_ctx* c, const double* E, double mu, double* N, double* dN, cudaStream_t st) {
+  const long long n = static_cast<long long>(c->nk) * c->norb;
+  const int nb = fd_blocks(c);
+  QA_LAUNCH(c, 1, qa::launch_fd_sum(E, n, c->beta, mu, c->d_part, nb, st));
+  QA_LAUNCH(c, 1, qa::launch_reduce_pairs(c->d_part, nb, 0, c->d_red, st));
+  double h[2];
+  QA_TRY(cudaMemcpyAsync(h, c->d_red, 16, cudaMemcpyDeviceToHost, st));
+  QA_TRY(cudaStreamSynchronize(st));
+  *N = c->nspin * h[0] / c->nk;
+  *dN = c->nspin * h[1] / c->nk;
+  return QA_OK;
+}
+
+// Chemical potential of the Fermi-Dirac filling of the eigenvalues E: the
+// bracket [E_min - 1 - 40/beta, E_max + 1 + 40/beta] (empty below, full above),
+// then bisection with Newton steps taken when they stay inside the bracket
+// and shrink faster than bisection; stop at |N - filling| <= 1e-12 max(1,
+// filling) or a bracket below 1e-14 max(1, |mu|).
+int fd_mu(qa_ctx* c, const double* E, double* mu_out, int* evals, cudaStream_t st) {
+  const long long n = static_cast<long long>(c->nk) * c->norb;
+  const int nb = fd_blocks(c);
+  QA_LAUNCH(c, 1, qa::launch_fd_range(E, n, c->d_part, nb, st));
+  QA_LAUNCH(c, 1, qa::launch_reduce_pairs(c->d_part, nb, 1, c->d_red, st));
+  double h[2];
+  QA_TRY(cudaMemcpyAsync(h, c->d_red, 16, cudaMemcpyDeviceToHost, st));
+  QA_TRY(cudaStreamSynchronize(st));
+  if (!std::isfinite(h[0]) || !std::isfinite(h[1])) return QA_ERANGE;
+  double lo = -h[1] - 1.0 - 40.0 / c->beta, hi = h[0] + 1.0 + 40.0 / c->beta;
+  const double target = c->filling, tolN = 1e-12 * std::max(1.0, target);
+  double mu = 0.5 * (lo + hi), N = 0, dN = 0, dxold = hi - lo;
+  int count = 0;
+  for (int it = 0; it < 300; ++it) {
+    if (int rc = fd_eval(c, E, mu, &N, &dN, st)) return rc;
+    ++count;
+    if (!std::isfinite(N)) return QA_ERANGE;
+    const double f = N - target;
+    if (std::fabs(f) <= tolN) break;
+    if (f < 0) lo = mu; else hi = mu;
+    if (hi - lo < 1e-14 * std::max(1.0, std::fabs(mu))) break;
+    const double cand = mu - f / dN;
+    if (dN > 0 && std::isfinite(cand) && cand > lo && cand < hi &&
+        std::fabs(2.0 * f) <= std::fabs(dxold * dN)) {
+      dxold = std::fabs(f / dN);
+      mu = cand;
+    } else {
+      dxold = 0.5 * (hi - lo);
+      mu = 0.5 * (lo + hi);
+    }
+    if (it == 299) return QA_ENOCONV;
+  }
+  *mu_out = mu;
+  *evals += count;
+  return QA_OK;
+}
+
+// eigenvalues of H + Sigma^HF (null: H alone), mu of the filling, n(k) into d_nk
+int hf_density(qa_ctx* c, const HfScratch& h, const double2* sig, double* mu, int* evals,
+               cudaStream_t st) {
+  QA_LAUNCH(c, 1, qa::launch_hf_eig(c->d_Hk, sig, c->norb, c->nk, h.E, h.U, st));
+  if (int rc = fd_mu(c, h.E, mu, evals, st)) return rc;
+  QA_LAUNCH(c, 1, qa::launch_fd_density(h.E, h.U, c->norb, c->nk, c->beta, *mu, c->d_nk, st));
+  return QA_OK;
+}
+
+// Self-consistent Hartree-Fock (paper Sec. "Hartree-Fock self-consistency",
+// Fig. 3(a)): start from the Fermi-Dirac density of H0, then repeat
+// Sigma^HF(n) -> mix -> eigenvalues of H0 + Sigma^HF -> mu -> n until the
+// largest change of Sigma^HF is <= tol.  G_out: the HF Green's function
+// (Dyson with Sigma^HF at the HF mu) on the DLR tau nodes.
+int hf_solve_impl(qa_ctx* c, int max_iter, double tol, double mix, void* G_out, double* mu_out,
+                  int* iters_out, double* resid_out, double* n_out, cudaStream_t st) {
+  HfScratch h;
+  if (!hf_scratch(c, &h)) return QA_ENOMEM;
+  c->launches = 0;
+  if (int rc = reset_err(c, st)) return rc;
+  const int no2 = c->norb * c->norb;
+  const long long nsig = static_cast<long long>(c->nk) * no2;
+  int evals = 0;
+  double mu = 0;
+  if (int rc = hf_density(c, h, nullptr, &mu, &evals, st)) return rc;
+  QA_TRY(cudaMemsetAsync(h.old, 0, nsig * 16, st));
+  double resid = INFINITY;
+  int it = 0;
+  const int nb = fd_blocks(c);
+  c->sigc_valid = false;
+  for (it = 1; it <= max_iter; ++it) {
+    QA_LAUNCH(c, 1, qa::launch_density_R(c->d_nk, c->d_vR, c->nV + 1, no2, nullptr, c->nk, c->n[0],
+                                         c->n[1], c->n[2], c->d_nR, st, c->d_phV));
+    QA_LAUNCH(c, 2, qa::launch_hf(c->d_vV, c->d_nR, c->d_vR, c->nV, c->norb, c->nspin, nullptr, c->nk,
+                                  c->n[0], c->n[1], c->n[2], c->d_sigFR, c->d_SigHF, st, c->d_phV));
+    QA_LAUNCH(c, 1, qa::launch_mix(c->d_SigHF, h.old, mix, nsig, c->d_part, nb, st));
+    QA_LAUNCH(c, 1, qa::launch_reduce_pairs(c->d_part, nb, 1, c->d_red, st));
+    double hr[2];
+    QA_TRY(cudaMemcpyAsync(hr, c->d_red, 16, cudaMemcpyDeviceToHost, st));
+    if (int rc = hf_density(c, h, c->d_SigHF, &mu, &evals, st)) return rc;   // synchronises
+    resid = hr[0];
+    if (!std::isfinite(resid)) return QA_ERANGE;
+    if (resid <= tol) break;
+  }
+  c->sighf_valid = true;
+  if (it > max_iter) it = max_iter;
+  if (G_out || n_out) {
+    double bound = 0;
+    if (int rc = prepare_g<double>(c, c->d_SigHF, nullptr, mu, &bound, st)) return rc;
+    if (G_out) {
+      if (int rc = finish_g<double>(c, c->t64, mu, G_out, n_out, st)) return rc;
+    } else {
+      // local density n(R = 0) of the HF solution: k-average of n(k)
+      QA_LAUNCH(c, 1, qa::launch_k_average<double>(c->d_nk, no2, c->nk, c->d_nloc, st));
+      QA_TRY(cudaMemcpyAsync(n_out, c->d_nloc, static_cast<size_t>(no2) * 16,
+                             cudaMemcpyDeviceToHost, st));
+    }
+  }
+  QA_TRY(cudaStreamSynchronize(st));
+  c->mu = mu;
+  c->have_mu = true;
+  if (mu_out) *mu_out = mu;
+  if (iters_out) *iters_out = it;
+  if (resid_out) *resid_out = resid;
+  if (int herr = check_err(c, nullptr, st)) return herr;
+  return resid <= tol ? QA_OK : QA_ENOCONV;
+}
+
+// Quasiparticle quantities from the self-energy in the workspace.
+template <typename T>
+int qp_impl(qa_ctx* c, double2* Z, double2* S0, double2* Hqp, double* eps, cudaStream_t st) {
+  if (int rc = reset_err(c, st)) return rc;
+  const int r = c->sigc_valid ? c->r : 0;
+  QA_LAUNCH(c, 1, qa::launch_qp<T>(c->d_Hk, c->d_SigHF, c->sigc_valid ? c->d_SigIw : nullptr, c->d_wq,
+                                   c->d_wq + c->r, r, c->norb, c->nk, M_PI / c->beta, Z, S0, Hqp,
+                                   eps, c->d_err, st));
   QA_TRY(cudaStreamSynchronize(st));
   return check_err(c, nullptr, st);
 }
@@ -1007,6 +1175,12 @@ int qa_bind(qa_ctx* c, void* workspace, size_t bytes, void* stream) {
   QA_TRY(upload_c<float>(c->t32.dtau, m.dtau, st));
   QA_TRY(upload_c<float>(c->t32.dw, m.dw, st));
   QA_TRY(cudaMemcpyAsync(c->d_iw, m.iw.data(), r * 8, cudaMemcpyHostToDevice, st));
+  {
+    std::vector<cd> wq(m.wq_p);
+    wq.insert(wq.end(), m.wq_m.begin(), m.wq_m.end());
+    QA_TRY(upload_c<double>(c->d_wq, wq, st));
+    QA_TRY(cudaStreamSynchronize(st));    // wq goes out of scope
+  }
   if (c->use_tc) {
     QA_TRY(cudaMemcpyAsync(c->d_tc_Ttn, c->tc_Ttn.data(), c->tc_Ttn.size() * 2, cudaMemcpyHostToDevice, st));
     QA_TRY(cudaMemcpyAsync(c->d_tc_Tnt, c->tc_Tnt.data(), c->tc_Tnt.size() * 2, cudaMemcpyHostToDevice, st));
@@ -1242,6 +1416,25 @@ int qa_gw_backward(qa_ctx* c, const void* G_in, double mu, const void* Gbar_out,
   return gw_backward_impl(c, Gin, mu, static_cast<const double2*>(Gbar_out),
                           static_cast<const double2*>(Sigbar), nbar, static_cast<double2*>(Gbar_in),
                           grad_t, grad_V, static_cast<cudaStream_t>(stream));
+}
+
+int qa_hf_solve(qa_ctx* c, int max_iter, double tol, double mix, void* G_out, double* mu_out,
+                int* iters_out, double* resid_out, double* n_out, void* stream) {
+  if (!c || max_iter < 1 || !(tol >= 0) || !(mix > 0 && mix <= 1)) return QA_EINVAL;
+  if (!c->bound) return QA_ESTATE;
+  return hf_solve_impl(c, max_iter, tol, mix, G_out, mu_out, iters_out, resid_out, n_out,
+                       static_cast<cudaStream_t>(stream));
+}
+
+int qa_qp(qa_ctx* c, void* Z, void* Sig0, void* Hqp, double* eps, void* stream) {
+  if (!c) return QA_EINVAL;
+  if (!c->bound || !c->sighf_valid) return QA_ESTATE;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double2* z = static_cast<double2*>(Z);
+  double2* s0 = static_cast<double2*>(Sig0);
+  double2* hq = static_cast<double2*>(Hqp);
+  if (c->precision == QA_FP64) return qp_impl<double>(c, z, s0, hq, eps, st);
+  return qp_impl<float>(c, z, s0, hq, eps, st);
 }
 
 void qa_destroy(qa_ctx* c) { delete c; }

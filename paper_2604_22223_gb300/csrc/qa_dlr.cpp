@@ -278,6 +278,16 @@ void build_dlr_matrices(const DlrGrid& g, double beta, DlrMatrices* m) {
   m->Twt = matmul(Kt, KFi, r, r);
   m->dtau = matmul(f, Kti, 1, r);
   m->dw = matmul(f, KFi, 1, r);
+  // Sigma(+-i pi/beta) = sum_n wq_{+-}[n] Sigma(i w_n): K_F at the lowest
+  // fermionic frequencies times K_F^-1 (the DLR fit at the Matsubara nodes)
+  std::vector<cld> kp(r), km(r);
+  for (int l = 0; l < r; ++l) {
+    const ld x = g.x[l];
+    kp[l] = b / cld(-x, pi);
+    km[l] = b / cld(-x, -pi);
+  }
+  m->wq_p = matmul(kp, KFi, 1, r);
+  m->wq_m = matmul(km, KFi, 1, r);
   m->iw.resize(r);
   for (int j = 0; j < r; ++j) m->iw[j] = (2.0 * g.nf[j] + 1.0) * M_PI / beta;
 }

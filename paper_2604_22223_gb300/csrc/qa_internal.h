@@ -39,6 +39,8 @@ struct DlrMatrices {
   std::vector<std::complex<double>> Twt;    // i w -> tau
   std::vector<std::complex<double>> dtau;   // n = sum_j dtau_j G(tau_j)
   std::vector<std::complex<double>> dw;     // n = sum_n dw_n G(i w_n)
+  std::vector<std::complex<double>> wq_p;   // X(+i pi/beta) = sum_n wq_p[n] X(i w_n)
+  std::vector<std::complex<double>> wq_m;   // X(-i pi/beta) = sum_n wq_m[n] X(i w_n)
   std::vector<double> iw;                   // w_n values (imaginary parts)
 };
 void build_dlr_matrices(const DlrGrid& g, double beta, DlrMatrices* m);
@@ -227,6 +229,32 @@ cudaError_t launch_add_dw_nbar(double2* Gbar_iw, const double2* dw, const double
                                int np, int nk, cudaStream_t st);
 cudaError_t launch_axpy(double2* y, const double2* x, double a, long long n, cudaStream_t st);
 cudaError_t launch_scale(double2* y, double a, long long n, cudaStream_t st);
+
+// ---- Hartree-Fock loop and quasiparticle quantities (FP64), qa_qp.cu
+// E[k][i] (ascending) and U[k][a][i] of the Hermitian part of H(k) + SigHF(k)
+// (SigHF may be null); both [N_k][norb][norb].
+cudaError_t launch_hf_eig(const double2* Hk, const double2* SigHF, int norb, int nk, double* E,
+                          double2* U, cudaStream_t st);
+// part[2b] >= max E, part[2b+1] >= max(-E) (bounds for a bracket), n = N_k norb
+cudaError_t launch_fd_range(const double* E, long long n, double* part, int nblocks,
+                            cudaStream_t st);
+// part[2b], part[2b+1]: block sums of f(beta (E - mu)) and beta f (1 - f)
+cudaError_t launch_fd_sum(const double* E, long long n, double beta, double mu, double* part,
+                          int nblocks, cudaStream_t st);
+// n(k) = U f(beta (E - mu)) U^H into nk_out [norb^2][N_k]
+cudaError_t launch_fd_density(const double* E, const double2* U, int norb, int nk, double beta,
+                              double mu, double2* nk_out, cudaStream_t st);
+// part[2b] = block max |cur - old|; then cur = old = old + mix (cur - old)
+cudaError_t launch_mix(double2* cur, double2* old, double mix, long long n, double* part,
+                       int nblocks, cudaStream_t st);
+// Z, Sigma(0), H_QP ([N_k][norb][norb]) and eps ([N_k][norb]) per k from
+// Sigma^C(k, i w) (storage TS, [r][norb][norb][N_k]; r = 0: none), SigHF and
+// the weights wp, wm of Sigma(+-i w0); any output may be null; err = 5 where
+// Z^-1 is not positive definite.
+template <typename TS>
+cudaError_t launch_qp(const double2* Hk, const double2* SigHF, const void* SigIw,
+                      const double2* wp, const double2* wm, int r, int norb, int nk, double w0,
+                      double2* Z, double2* S0, double2* Hqp, double* eps, int* err, cudaStream_t st);
 
 // Host copies a density call needs (valid for the context's lifetime).
 int density_tables(const ::qa_ctx* ctx, const std::complex<double>** dtau, int* r, int* norb,

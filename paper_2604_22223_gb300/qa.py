@@ -24,7 +24,7 @@ QA_P_QNU, QA_WC_RTAU, QA_SIGC_KTAU, QA_SIGC_KIW, QA_SIGHF_K, QA_G0, QA_HK, QA_MU
 EXPORTED = ["qa_create", "qa_workspace_size", "qa_bind", "qa_get_grid", "qa_get_plan",
             "qa_get_sizes", "qa_gw_step", "qa_density", "qa_density_static", "qa_get",
             "qa_set_timing", "qa_set_mu", "qa_set_params", "qa_gw_backward", "qa_set_pair_basis",
-            "qa_get_pair_basis", "qa_destroy", "qa_strerror"]
+            "qa_get_pair_basis", "qa_hf_solve", "qa_qp", "qa_destroy", "qa_strerror"]
 
 STAGES = ["hartree_fock", "g_to_R", "bubble", "fft_R_to_q", "dlr_tau_to_nu", "dyson_w",
           "dlr_nu_to_tau", "fft_q_to_R", "sigma", "sigma_to_k_iw", "mu_search", "dyson_g"]
@@ -84,6 +84,8 @@ def load(path: str = LIB_PATH):
     L.qa_gw_backward.argtypes = [vp, vp, d, vp, vp, vp, vp, vp, vp, vp]
     L.qa_set_pair_basis.argtypes = [vp, i]
     L.qa_get_pair_basis.argtypes = [vp, C.POINTER(i), C.POINTER(i), vp]
+    L.qa_hf_solve.argtypes = [vp, i, d, d, vp, C.POINTER(d), C.POINTER(i), C.POINTER(d), vp, vp]
+    L.qa_qp.argtypes = [vp, vp, vp, vp, vp, vp]
     L.qa_destroy.argtypes = [vp]
     L.qa_destroy.restype = None
     L.qa_strerror.argtypes = [i]
@@ -273,6 +275,34 @@ class Context(Problem):
                                      gV.ctypes.data, self._stream()), "qa_gw_backward")
         return (Gb, gt.view(np.complex128).reshape(nH, no, no),
                 gV.view(np.complex128)[:nV * npair * npair].reshape(nV, npair, npair))
+
+    def hf_solve(self, max_iter: int = 500, tol: float = 1e-10, mix: float = 1.0, G_out=None,
+                 check: bool = True):
+        """Self-consistent Hartree-Fock; returns (G_HF, mu, n_local, iters, resid, status).
+        check=False returns QA_ENOCONV as the status instead of raising."""
+        if G_out is None:
+            G_out = self.new_g()
+        mu, it, res = C.c_double(), C.c_int(), C.c_double()
+        n = np.zeros(2 * self.norb * self.norb)
+        status = load().qa_hf_solve(self.ctx, int(max_iter), float(tol), float(mix), G_out.data_ptr(),
+                                    C.byref(mu), C.byref(it), C.byref(res), n.ctypes.data,
+                                    self._stream())
+        if check or status != 4:
+            _check(status, "qa_hf_solve")
+        return (G_out, mu.value, n.view(np.complex128).reshape(self.norb, self.norb), it.value,
+                res.value, status)
+
+    def qp(self):
+        """Quasiparticle quantities of the current self-energy: dict of device
+        tensors Z, sig0, Hqp ([N_k, norb, norb] complex128) and eps ([N_k, norb])."""
+        torch = self.torch
+        nk, no = self.nk, self.norb
+        out = {k: torch.empty((nk, no, no), dtype=torch.complex128, device=self.device)
+               for k in ("Z", "sig0", "Hqp")}
+        out["eps"] = torch.empty((nk, no), dtype=torch.float64, device=self.device)
+        _check(load().qa_qp(self.ctx, out["Z"].data_ptr(), out["sig0"].data_ptr(),
+                            out["Hqp"].data_ptr(), out["eps"].data_ptr(), self._stream()), "qa_qp")
+        return out
 
     def density(self, G):
         n = np.zeros(2 * self.norb * self.norb)
