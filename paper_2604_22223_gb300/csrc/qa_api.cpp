@@ -980,11 +980,12 @@ int hf_solve_impl(qa_ctx* c, int max_iter, double tol, double mix, void* G_out, 
 // Quasiparticle quantities from the self-energy in the workspace.
 template <typename T>
 int qp_impl(qa_ctx* c, double2* Z, double2* S0, double2* Hqp, double* eps, cudaStream_t st) {
+  if (c->r < 2) return QA_ENOMEM;           // node sums use 2 N_k norb^2 of d_Gt
   if (int rc = reset_err(c, st)) return rc;
   const int r = c->sigc_valid ? c->r : 0;
-  QA_LAUNCH(c, 1, qa::launch_qp<T>(c->d_Hk, c->d_SigHF, c->sigc_valid ? c->d_SigIw : nullptr, c->d_wq,
-                                   c->d_wq + c->r, r, c->norb, c->nk, M_PI / c->beta, Z, S0, Hqp,
-                                   eps, c->d_err, st));
+  QA_LAUNCH(c, r > 0 ? 2 : 1, qa::launch_qp<T>(c->d_Hk, c->d_SigHF, c->sigc_valid ? c->d_SigIw : nullptr, c->d_wq,
+                                   c->d_wq + c->r, r, c->norb, c->nk, M_PI / c->beta,
+                                   static_cast<double2*>(c->d_Gt), Z, S0, Hqp, eps, c->d_err, st));
   QA_TRY(cudaStreamSynchronize(st));
   return check_err(c, nullptr, st);
 }

@@ -249,12 +249,13 @@ cudaError_t launch_mix(double2* cur, double2* old, double mix, long long n, doub
                        int nblocks, cudaStream_t st);
 // Z, Sigma(0), H_QP ([N_k][norb][norb]) and eps ([N_k][norb]) per k from
 // Sigma^C(k, i w) (storage TS, [r][norb][norb][N_k]; r = 0: none), SigHF and
-// the weights wp, wm of Sigma(+-i w0); any output may be null; err = 5 where
-// Z^-1 is not positive definite.
+// the weights wp, wm of Sigma(+-i w0); S = scratch of 2 N_k norb^2 complex128;
+// any output may be null; err = 5 where Z^-1 is not positive definite.
 template <typename TS>
 cudaError_t launch_qp(const double2* Hk, const double2* SigHF, const void* SigIw,
                       const double2* wp, const double2* wm, int r, int norb, int nk, double w0,
-                      double2* Z, double2* S0, double2* Hqp, double* eps, int* err, cudaStream_t st);
+                      double2* S, double2* Z, double2* S0, double2* Hqp, double* eps, int* err,
+                      cudaStream_t st);
 
 // Host copies a density call needs (valid for the context's lifetime).
 int density_tables(const ::qa_ctx* ctx, const std::complex<double>** dtau, int* r, int* norb,

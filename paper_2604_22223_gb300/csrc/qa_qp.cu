@@ -206,31 +206,53 @@ __global__ void fd_range_kernel(const double* __restrict__ E, long long n, doubl
   if (threadIdx.x == 0) { part[2 * blockIdx.x] = hi; part[2 * blockIdx.x + 1] = lo; }
 }
 
-// quasiparticle quantities per k; TS = storage type of Sigma^C(k, i w)
-template <int NO, typename TS>
+// Sigma(+-i w0) = sum_n w+-[n] Sigma^C(i w_n) for every (element, k): one
+// thread per column, FP64 accumulation; S[0][c] = Sigma(+i w0), S[1][c] = Sigma(-i w0)
+template <typename TS>
+__global__ void qp_sums_kernel(const cplx<TS>* __restrict__ SigIw, const double2* __restrict__ wp,
+                               const double2* __restrict__ wm, int r, long long m,
+                               double2* __restrict__ S) {
+  const long long c = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (c >= m) return;
+  double2 sp = make_double2(0, 0), sm = make_double2(0, 0);
+  int n = 0;
+  for (; n + 4 <= r; n += 4) {               // four independent loads in flight
+    double2 x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) x[u] = to_c64d(SigIw[static_cast<size_t>(n + u) * m + c]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      sp = cfma(wp[n + u], x[u], sp);
+      sm = cfma(wm[n + u], x[u], sm);
+    }
+  }
+  for (; n < r; ++n) {
+    const double2 x = to_c64d(SigIw[static_cast<size_t>(n) * m + c]);
+    sp = cfma(wp[n], x, sp);
+    sm = cfma(wm[n], x, sm);
+  }
+  S[c] = sp;
+  S[m + c] = sm;
+}
+
+// quasiparticle quantities per k from S (qp_sums_kernel; null: no Sigma^C)
+template <int NO>
 __global__ void qp_kernel(const double2* __restrict__ Hk, const double2* __restrict__ SigHF,
-                          const cplx<TS>* __restrict__ SigIw, const double2* __restrict__ wp,
-                          const double2* __restrict__ wm, int r, int nk, double w0,
+                          const double2* __restrict__ S, int nk, double w0,
                           double2* __restrict__ Zo, double2* __restrict__ S0o,
                           double2* __restrict__ Hqo, double* __restrict__ epso, int* err) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nk) return;
   double2 sp[NO][NO], sm[NO][NO];
+  const size_t m = static_cast<size_t>(NO) * NO * nk;
 #pragma unroll
   for (int i = 0; i < NO; ++i)
 #pragma unroll
-    for (int j = 0; j < NO; ++j) { sp[i][j] = make_double2(0, 0); sm[i][j] = make_double2(0, 0); }
-  for (int n = 0; n < r; ++n) {
-    const double2 p = wp[n], q = wm[n];
-#pragma unroll
-    for (int i = 0; i < NO; ++i)
-#pragma unroll
-      for (int j = 0; j < NO; ++j) {
-        const double2 x = to_c64d(SigIw[(static_cast<size_t>(n) * NO * NO + i * NO + j) * nk + k]);
-        sp[i][j] = cfma(p, x, sp[i][j]);
-        sm[i][j] = cfma(q, x, sm[i][j]);
-      }
-  }
+    for (int j = 0; j < NO; ++j) {
+      const size_t c = static_cast<size_t>(i * NO + j) * nk + k;
+      sp[i][j] = S ? S[c] : make_double2(0, 0);
+      sm[i][j] = S ? S[m + c] : make_double2(0, 0);
+    }
   // Zi = 1 - (sp - sm) / (2 i w0); S0 = (sp + sm) / 2 + SigHF (raw, then Hermitian parts)
   double2 zi[NO][NO], s0[NO][NO];
   const double h = 0.5 / w0;
@@ -376,24 +398,33 @@ cudaError_t launch_mix(double2* cur, double2* old, double mix, long long n, doub
 template <typename TS>
 cudaError_t launch_qp(const double2* Hk, const double2* SigHF, const void* SigIw,
                       const double2* wp, const double2* wm, int r, int norb, int nk, double w0,
-                      double2* Z, double2* S0, double2* Hqp, double* eps, int* err, cudaStream_t st) {
+                      double2* S, double2* Z, double2* S0, double2* Hqp, double* eps, int* err,
+                      cudaStream_t st) {
+  if (norb < 1 || norb > 5) return cudaErrorInvalidValue;
+  const double2* Sp = nullptr;
+  if (r > 0) {
+    const long long m = static_cast<long long>(norb) * norb * nk;
+    qp_sums_kernel<TS><<<static_cast<unsigned>((m + 255) / 256), 256, 0, st>>>(
+        reinterpret_cast<const cplx<TS>*>(SigIw), wp, wm, r, m, S);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    Sp = S;
+  }
   const unsigned g = static_cast<unsigned>((nk + 63) / 64);
-  auto s = reinterpret_cast<const cplx<TS>*>(SigIw);
   switch (norb) {
 #define QA_CASE(NO) \
-    case NO: qp_kernel<NO, TS><<<g, 64, 0, st>>>(Hk, SigHF, s, wp, wm, r, nk, w0, Z, S0, Hqp, eps, err); break;
+    case NO: qp_kernel<NO><<<g, 64, 0, st>>>(Hk, SigHF, Sp, nk, w0, Z, S0, Hqp, eps, err); break;
     QA_CASE(1) QA_CASE(2) QA_CASE(3) QA_CASE(4) QA_CASE(5)
 #undef QA_CASE
-    default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
 template cudaError_t launch_qp<double>(const double2*, const double2*, const void*, const double2*,
                                        const double2*, int, int, int, double, double2*, double2*,
-                                       double2*, double*, int*, cudaStream_t);
+                                       double2*, double2*, double*, int*, cudaStream_t);
 template cudaError_t launch_qp<float>(const double2*, const double2*, const void*, const double2*,
                                       const double2*, int, int, int, double, double2*, double2*,
-                                      double2*, double*, int*, cudaStream_t);
+                                      double2*, double2*, double*, int*, cudaStream_t);
 
 }  // namespace qa

@@ -146,3 +146,46 @@ def test_qp_mixed(name):
     ctx = qa.Context(m, "mixed")
     ctx.step()
     _compare_qp(ctx.qp(), ref, 1e-4)
+
+
+def test_paper_graphene_workflow():
+    """The paper's graphene validation model (t = 1, U = 2, V = 0.2 eV, 2000 K,
+    25x25x1): HF -> GW step from the HF G -> quasiparticles, each against the
+    oracle, with the particle-hole value mu = U/2 + 3V (tests/test_golden_paper.py)."""
+    from paper_2604_22223_gb300 import qa
+    m, d, res, G_ref = oracle_hf("graphene-paper-25x25", 1.0)
+    mu_ph = 2.0 / 2 + 3 * 0.2
+    ctx = qa.Context(m, "fp64")
+    G, mu, n_loc, iters, resid, status = ctx.hf_solve(200, HF_TOL, 1.0)
+    assert abs(mu - mu_ph) <= 1e-10
+    assert rel(ctx.get(qa.QA_SIGHF_K).cpu().numpy(), res["sig_hf_k"]) <= 1e-9
+    assert rel(G.cpu().numpy(), np.moveaxis(G_ref, 0, -1)) <= 1e-9
+    o = gw.gw_step(m, d, G_ref)
+    G1, mu1, n1, st = ctx.step(G)
+    assert abs(mu1 - mu_ph) <= 1e-8
+    assert rel(G1.cpu().numpy(), np.moveaxis(o["G_ktau"], 0, -1)) <= 1e-9
+    ref = qp.quasiparticle(m, d, o["sig_hf_k"], o["sigc_kiw"])
+    _compare_qp(ctx.qp(), ref, 1e-8)
+
+
+@pytest.mark.parametrize("precision,bound", [("fp64", 1e-8), ("mixed", 1e-4)])
+def test_paper_five_orbital_step_and_qp(precision, bound):
+    """The paper's degenerate five-orbital benchmark model on a 3x3x2 grid."""
+    from paper_2604_22223_gb300 import qa
+    m, d, o, ref = oracle_qp("five-orbital-paper-3x3x2")
+    ctx = qa.Context(m, precision)
+    G1, mu1, n1, st = ctx.step()
+    assert abs(mu1 - o["mu"]) <= (1e-10 if precision == "fp64" else 2e-5) * max(1.0, abs(o["mu"]))
+    _compare_qp(ctx.qp(), ref, bound)
+
+
+def test_paper_five_orbital_hf_half_filling():
+    """qa_hf_solve on the paper's five-orbital model (8x8x8) reaches the
+    particle-hole value mu = 9.5 (tests/test_golden_paper.py)."""
+    from paper_2604_22223_gb300 import qa
+    m = wl.config("five-orbital-paper-8x8x8")
+    ctx = qa.Context(m, "mixed")
+    G, mu, n_loc, iters, resid, status = ctx.hf_solve(200, 1e-12, 1.0)
+    assert abs(mu - 9.5) <= 1e-10
+    # n_loc is the DLR density -G(beta^-) of the HF G (eps = 1e-10 grid at beta Lambda = 2500)
+    assert np.abs(np.diag(n_loc) - 0.5).max() <= 1e-8

@@ -146,11 +146,12 @@ def square_single_band(n=(8, 8, 1), t=1.0, U=2.0, beta=10.0, Lambda=100.0, eps_d
 
 
 def honeycomb(n=(36, 36, 1), t=2.7, U=9.3, V1=5.5, beta=40.0, Lambda=1000.0, eps_dlr=1e-10,
-              filling=2.0, name="graphene") -> Model:
+              filling=2.0, name="graphene", v_range=2.0) -> Model:
     """Graphene p_z model: two sublattices, nearest-neighbour hopping t.
 
-    Interaction: on-site U and a 1/r density-density tail V(r) = V1 * d / r up
-    to third neighbours (d = carbon-carbon distance = 1).
+    Interaction: on-site U and a 1/r density-density tail V(r) = V1 * d / r for
+    r <= v_range (d = carbon-carbon distance = 1; 2.0 reaches the third
+    neighbours, 1.0 keeps the nearest neighbours only).
     """
     s3 = math.sqrt(3.0)
     a1 = np.array([s3, 0.0, 0.0])
@@ -170,7 +171,7 @@ def honeycomb(n=(36, 36, 1), t=2.7, U=9.3, V1=5.5, beta=40.0, Lambda=1000.0, eps
                         T[a, b] = t
                     if d < 1e-9:
                         Vd[a, b] = U
-                    elif d < 2.0 + 1e-9:
+                    elif d < v_range + 1e-9:
                         Vd[a, b] = V1 * 1.0 / d
             if np.any(T != 0):
                 hops[R] = T
@@ -218,6 +219,26 @@ def five_orbital(n=(16, 16, 1), seed=DEFAULT_SEED, U=3.0, J=0.6, Vnn=0.5, beta=4
     hop_R, hop_t, V_R, V = _finish(hops, Vs, norb)
     return Model(name, tuple(n), norb, hop_R, hop_t, cf, V_R, V, beta, Lambda, eps_dlr, filling,
                  orb_pos=np.zeros((norb, 3)))
+
+
+def degenerate_cubic(n=(8, 8, 8), norb=5, t=1.0, U=1.0, J=0.1, Vnn=0.2, beta=100.0,
+                     Lambda=2500.0, eps_dlr=1e-10, filling=5.0,
+                     name="five-orbital-degenerate") -> Model:
+    """Degenerate multi-orbital extended Hund-Hubbard model on a simple cubic
+    lattice: orbital-diagonal nearest-neighbour hopping t (six neighbours),
+    Kanamori (U, J, U' = U - 2J) on site, density-density Vnn between all
+    orbitals of nearest-neighbour cells.  No random draws."""
+    nn = [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]
+    hops = {R: t * np.eye(norb, dtype=np.complex128) for R in nn}
+    Vs = {(0, 0, 0): kanamori_local(norb, U, J)}
+    for R in nn:
+        Vs[R] = density_density(norb, np.full((norb, norb), Vnn))
+    hop_R, hop_t, V_R, V = _finish(hops, Vs, norb)
+    return Model(name, tuple(n), norb, hop_R, hop_t, np.zeros(norb), V_R, V, beta, Lambda, eps_dlr,
+                 filling, orb_pos=np.zeros((norb, 3)))
+
+
+KB_EV_PER_K = 8.617333262e-5          # Boltzmann constant (CODATA 2018), eV/K
 
 
 def peierls_two_orbital(n=(3, 3, 1), seed=DEFAULT_SEED + 7, U=2.0, J=0.4, Vnn=0.3, beta=8.0,
@@ -276,6 +297,23 @@ def config(name: str) -> Model:
     if name == "five-orbital-16x16x8":      # same beta/Lambda/eps at 1/4 of the k-points
         return five_orbital(n=(16, 16, 8), beta=100.0, Lambda=1.0e4, eps_dlr=1e-12,
                             name="five-orbital-16x16x8")
+    # the paper's own models (Sec. "Validation: Electronic structure of graphene"
+    # and the five-orbital benchmark of Table 1); parameters in eV, beta = 1/(k_B T),
+    # dimensionless Lambda = beta * (cutoff energy)
+    if name == "graphene-paper-25x25":
+        beta = 1.0 / (KB_EV_PER_K * 2000.0)
+        return honeycomb(n=(25, 25, 1), t=1.0, U=2.0, V1=0.2, v_range=1.0, beta=beta,
+                         Lambda=100.0 * beta, name="graphene-paper-25x25")
+    if name == "five-orbital-paper-8x8x8":
+        return degenerate_cubic(n=(8, 8, 8), t=1.0, U=1.0, J=0.1, Vnn=0.2, beta=100.0,
+                                Lambda=25.0 * 100.0, name="five-orbital-paper-8x8x8")
+    if name == "graphene-paper-6x6":          # the paper's graphene parameters on a small grid
+        beta = 1.0 / (KB_EV_PER_K * 2000.0)
+        return honeycomb(n=(6, 6, 1), t=1.0, U=2.0, V1=0.2, v_range=1.0, beta=beta,
+                         Lambda=100.0 * beta, name="graphene-paper-6x6")
+    if name == "five-orbital-paper-3x3x2":    # the paper's five-orbital parameters, small grid
+        return degenerate_cubic(n=(3, 3, 2), t=1.0, U=1.0, J=0.1, Vnn=0.2, beta=100.0,
+                                Lambda=25.0 * 100.0, name="five-orbital-paper-3x3x2")
     # small parity cases
     if name == "five-orbital-6x5x1":
         return five_orbital(n=(6, 5, 1), beta=10.0, Lambda=200.0, name="five-orbital-6x5x1")
