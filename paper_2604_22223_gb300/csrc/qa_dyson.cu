@@ -327,7 +327,8 @@ cudaError_t launch_dyson_w_reg(const void* P, const void* Vq, void* WC, int r, i
 // load without bank conflicts.  The pivot of each column is found with a
 // packed (|a|^2 | row) key, and the pivot row reaches the other lanes
 // through shared memory (one 16-byte store and load per two values instead
-// of two shuffles per value).  Back substitution is column-parallel.
+// of two shuffles per value).  Gauss-Jordan elimination leaves each lane with
+// one row of the solution (no back-substitution phase).
 
 template <int MAXN>
 __device__ __forceinline__ int swz(int row, int col) {
@@ -355,7 +356,7 @@ __global__ void __launch_bounds__(kWarpsR * 32) dyson_w_tile_kernel(const float2
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* Ps = reinterpret_cast<float2*>(smem_raw);        // [NSYS][TS]
   float2* Vs = Ps + NSYS * TS;                              // [NSYS][TS]
-  float2* Rs = Vs + NSYS * TS;                              // [NSYS][2 * MAXN] pivot rows
+  float2* Rs = Vs + NSYS * TS;                              // [NSYS][2][2 * MAXN] pivot rows
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int l = lane & (W - 1);
   const int sys = w * SPW + lane / W;
@@ -404,8 +405,7 @@ __global__ void __launch_bounds__(kWarpsR * 32) dyson_w_tile_kernel(const float2
   const int q = q0 + sys;
   float2* Pw = Ps + sys * TS;
   float2* Vw = Vs + sys * TS;
-  float2* Ra = Rs + sys * 2 * MAXN;             // pivot row of A
-  float2* Rb = Ra + MAXN;                       // pivot row of the right-hand side
+  float2* Ra = Rs + sys * 4 * MAXN;             // two buffers: pivot row of A, then of B
   float2 a[MAXN], b[MAXN];
   const bool row = l < n;
   // a = row l of V P (padding rows and columns of the tiles are zero)
@@ -451,12 +451,21 @@ __global__ void __launch_bounds__(kWarpsR * 32) dyson_w_tile_kernel(const float2
     a[j].x = (row && j == l ? 1.f : 0.f) - a[j].x;
     a[j].y = -a[j].y;
   }
+  // Gauss-Jordan elimination of [A | B] with partial pivoting: at column c the
+  // pivot row (largest |a_ic| among the rows not yet used) reaches the other
+  // lanes through shared memory and every other row, used or not, eliminates
+  // column c.  A ends diagonal in pivot order, so the lane that pivoted column
+  // c holds row c of the solution as b / a_c: no back substitution.  The pivot
+  // rows alternate between two buffers, one warp barrier per column.
   bool used = !row;
   int mypos = -1;
+  float2 dval = make_float2(1.f, 0.f);
   bool singular = false;
 #pragma unroll
   for (int c = 0; c < MAXN; ++c) {
     if (c < n) {
+      float2* Ra_c = Ra + (c & 1) * 2 * MAXN;
+      float2* Rb_c = Ra_c + MAXN;
       // pivot: largest |a_ic|^2 over the unused rows, near-ties (low 4 mantissa
       // bits) to the lowest row; used rows carry key 0
       const float v2 = cabs2(a[c]);
@@ -465,23 +474,25 @@ __global__ void __launch_bounds__(kWarpsR * 32) dyson_w_tile_kernel(const float2
       for (int o = W / 2; o > 0; o >>= 1) key = max(key, __shfl_xor_sync(0xffffffffu, key, o));
       const int p = W - 1 - static_cast<int>(key & (W - 1));
       if (!(__uint_as_float(key & ~0xFu) >= 1e-12f)) singular = true;
-      if (l == p) {
+      const bool me = (l == p);
+      if (me) {
         used = true;
         mypos = c;
+        dval = a[c];
 #pragma unroll
         for (int jp = c / 2; jp < NPAIR; ++jp)
-          *reinterpret_cast<float4*>(Ra + 2 * jp) = make_float4(a[2 * jp].x, a[2 * jp].y, a[2 * jp + 1].x, a[2 * jp + 1].y);
+          *reinterpret_cast<float4*>(Ra_c + 2 * jp) = make_float4(a[2 * jp].x, a[2 * jp].y, a[2 * jp + 1].x, a[2 * jp + 1].y);
 #pragma unroll
         for (int jp = 0; jp < NPAIR; ++jp)
-          *reinterpret_cast<float4*>(Rb + 2 * jp) = make_float4(b[2 * jp].x, b[2 * jp].y, b[2 * jp + 1].x, b[2 * jp + 1].y);
+          *reinterpret_cast<float4*>(Rb_c + 2 * jp) = make_float4(b[2 * jp].x, b[2 * jp].y, b[2 * jp + 1].x, b[2 * jp + 1].y);
       }
       __syncwarp();
-      const float2 apc = Ra[c];
-      const float2 f = used ? make_float2(0.f, 0.f) : cmul(a[c], cinv(apc));
+      const float2 apc = Ra_c[c];
+      const float2 f = me ? make_float2(0.f, 0.f) : cmul(a[c], cinv(apc));
 #pragma unroll
       for (int jp = (c + 1) / 2; jp < NPAIR; ++jp) {
         if (2 * jp < n) {
-          const float4 pr = *reinterpret_cast<const float4*>(Ra + 2 * jp);
+          const float4 pr = *reinterpret_cast<const float4*>(Ra_c + 2 * jp);
           if (2 * jp > c) a[2 * jp] = cfms(f, make_float2(pr.x, pr.y), a[2 * jp]);
           a[2 * jp + 1] = cfms(f, make_float2(pr.z, pr.w), a[2 * jp + 1]);
         }
@@ -489,30 +500,21 @@ __global__ void __launch_bounds__(kWarpsR * 32) dyson_w_tile_kernel(const float2
 #pragma unroll
       for (int jp = 0; jp < NPAIR; ++jp) {
         if (2 * jp < n) {
-          const float4 br = *reinterpret_cast<const float4*>(Rb + 2 * jp);
+          const float4 br = *reinterpret_cast<const float4*>(Rb_c + 2 * jp);
           b[2 * jp] = cfms(f, make_float2(br.x, br.y), b[2 * jp]);
           b[2 * jp + 1] = cfms(f, make_float2(br.z, br.w), b[2 * jp + 1]);
         }
       }
-      __syncwarp();
     }
   }
-  // rows of the triangular factor (P tile) and right-hand side (V tile), in pivot order
+  // row `mypos` of the solution into the V tile (rows of other systems untouched)
   if (mypos >= 0) {
+    const float2 inv = cinv(dval);
 #pragma unroll
     for (int jp = 0; jp < NPAIR; ++jp) {
-      *reinterpret_cast<float4*>(Pw + mypos * MAXN + 2 * (jp ^ (mypos & (NPAIR - 1)))) =
-          make_float4(a[2 * jp].x, a[2 * jp].y, a[2 * jp + 1].x, a[2 * jp + 1].y);
+      const float2 x0 = cmul(b[2 * jp], inv), x1 = cmul(b[2 * jp + 1], inv);
       *reinterpret_cast<float4*>(Vw + mypos * MAXN + 2 * (jp ^ (mypos & (NPAIR - 1)))) =
-          make_float4(b[2 * jp].x, b[2 * jp].y, b[2 * jp + 1].x, b[2 * jp + 1].y);
-    }
-  }
-  __syncwarp();
-  if (row) {
-    for (int c = n - 1; c >= 0; --c) {
-      float2 x = Vw[swz<MAXN>(c, l)];
-      for (int m = c + 1; m < n; ++m) x = cfms(Pw[swz<MAXN>(c, m)], Vw[swz<MAXN>(m, l)], x);
-      Vw[swz<MAXN>(c, l)] = cmul(x, cinv(Pw[swz<MAXN>(c, c)]));
+          make_float4(x0.x, x0.y, x1.x, x1.y);
     }
   }
   if (singular && l == 0 && q < nk)
@@ -530,7 +532,7 @@ template <int MAXN>
 cudaError_t launch_dyson_w_tile(const void* P, const void* Vq, void* WC, int r, int n, int nk,
                                 int* err, long long* first_bad, cudaStream_t st) {
   constexpr int NSYS = kWarpsR * (32 / MAXN);
-  const size_t smem = (static_cast<size_t>(2) * NSYS * (MAXN * MAXN + 2) + NSYS * 2 * MAXN) * sizeof(float2);
+  const size_t smem = (static_cast<size_t>(2) * NSYS * (MAXN * MAXN + 2) + NSYS * 4 * MAXN) * sizeof(float2);
   auto fn = &dyson_w_tile_kernel<MAXN>;
   cudaError_t e = set_smem(reinterpret_cast<const void*>(fn), smem);
   if (e != cudaSuccess) return e;
