@@ -9,16 +9,18 @@
 // leading cross products x_i t_j (i + j <= 2) accumulate in FP32 in tensor
 // memory, which keeps the FP32-level accuracy of the SIMT kernel.
 //
-// One persistent CTA per SM (128 threads): the three Tt pieces stay resident
+// One persistent CTA per SM (512 threads): the three Tt pieces stay resident
 // in shared memory (K-major canonical layout, no swizzle); each 128-column
 // tile of X streams through double-buffered K-chunks of 16 (8 nodes x re/im)
 // that all threads convert to bf16 pieces while the previous chunk's six
 // MMAs run; one thread issues tcgen05.mma (M = 128, N = 2r padded to 16,
 // K = 16) into a 128 x N FP32 accumulator in TMEM; the epilogue reads it
-// back with tcgen05.ld (warp w <-> TMEM lanes 32w..32w+31, thread <-> column)
-// and stores Y in place of X.  Every mbarrier wait is bounded; on time-out
-// the kernel records QA_ETIMEOUT, waits (bounded) for its own MMAs, frees
-// TMEM and returns.
+// back with tcgen05.ld (warps w, w+4, w+8, w+12 <-> TMEM lanes 32w..32w+31,
+// thread <-> column, each warp a quarter of the accumulator columns) and
+// stores Y in place of X.  The input is read through a register ring several
+// chunks deep (the kernel is otherwise bound by the latency of its loads).
+// Every mbarrier wait is bounded; on time-out the kernel records
+// QA_ETIMEOUT, waits (bounded) for its own MMAs, frees TMEM and returns.
 #include <cuda_bf16.h>
 
 #include <cstring>
@@ -141,18 +143,23 @@ __device__ __forceinline__ void tmem_acc24(uint32_t taddr, float* acc) {
       : "memory");
 }
 
-constexpr int kHalfMax = 96;            // accumulator columns per thread (Np <= 192)
+constexpr int kQMax = 48;               // accumulator columns per thread (Np <= 192)
+constexpr int kDrainGroup = 1;          // K-chunks summed in TMEM between two drains
+constexpr int kDepth = 4;               // K-chunks of input in flight per thread (registers)
 
-// 256 threads: thread (w, lane) owns TMEM lane / tile row m = 32 (w % 4) + lane
-// and half h = w / 4 of the accumulator columns and of each chunk's 8 nodes.
-// Each K-chunk's six MMAs go to a fresh accumulator (two alternate in TMEM),
-// which is drained into FP32 registers with round-to-nearest adds while the
-// next chunk's MMAs run, so the tensor core never sums more than 96 products.
-__global__ void __launch_bounds__(2 * kTcThreads, 1) dlr_tc_kernel(TcArgs a) {
+// 512 threads: thread (w, lane) owns TMEM lane / tile row m = 32 (w % 4) + lane
+// and quarter qt = w / 4 of the work of that row: accumulator columns
+// [48 qt, 48 qt + 48) and nodes 2 qt, 2 qt + 1 of each chunk's 8.  Each
+// K-chunk's six MMAs go to a fresh accumulator (two alternate in TMEM), which
+// is drained into FP32 registers with round-to-nearest adds while the next
+// chunk's MMAs run, so the tensor core never sums more than 96 products.  The
+// input streams through a register ring kDepth chunks deep that runs on across
+// this CTA's tiles, so 512 x kDepth x 16 bytes per SM are in flight.
+__global__ void __launch_bounds__(4 * kTcThreads, 1) dlr_tc_kernel(TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m = 32 * (warp & 3) + lane;
-  const int half = warp >> 2;
+  const int qt = warp >> 2;
   const uint32_t bpiece = static_cast<uint32_t>(a.Np) * a.Kp * 2;    // bytes of one Tt piece
   uint8_t* Bs = smem;
   uint8_t* As = smem + 3 * bpiece;                                    // [2 buffers][3 pieces][4096 B]
@@ -184,98 +191,112 @@ __global__ void __launch_bounds__(2 * kTcThreads, 1) dlr_tc_kernel(TcArgs a) {
   const int nchunk = a.Kp / kChunkK;
   const uint32_t bsbo = static_cast<uint32_t>(a.Kp / 8) * 128;
   const long long ntiles = (a.ncol + kTileM - 1) / kTileM;
+  const long long my_tiles = blockIdx.x < ntiles ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const long long nstream = my_tiles * nchunk;       // this CTA's chunks, tile after tile
   const int nodes = a.r;
-  const int nh = a.Np / 2;                           // accumulator columns of this thread
+  const int cb = kQMax * qt;                         // first accumulator column of this thread
+  const int nq = a.Np - cb < kQMax ? a.Np - cb : kQMax;   // its column count (may be <= 0)
   const uint32_t lane_base = static_cast<uint32_t>(32 * (warp & 3)) << 16;
   const uint32_t roff = static_cast<uint32_t>(m >> 3) * 256 + static_cast<uint32_t>(m & 7) * 16 +
-                        static_cast<uint32_t>(half) * 128;
-  long long g = 0;                                   // global chunk counter
+                        static_cast<uint32_t>(qt >> 1) * 128 + static_cast<uint32_t>(qt & 1) * 8;
+  long long g = 0;                                   // global chunk counter (mbarrier phases)
+  long long gbase = 0;                               // drain groups of the earlier tiles
   bool ok = true;
   const int pa[6] = {0, 0, 1, 0, 1, 2};
   const int pb[6] = {0, 1, 0, 2, 1, 0};
 
+  // this thread's two input values of stream chunk s (zero past the end)
+  auto load_chunk = [&](long long s, float2* dst) {
+    const long long tile = blockIdx.x + (s / nchunk) * gridDim.x;
+    const int ch = static_cast<int>(s % nchunk);
+    const long long col = tile * kTileM + m;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int l = ch * 8 + qt * 2 + e;
+      dst[e] = (s < nstream && col < a.ncol && l < nodes) ? a.in[static_cast<long long>(l) * a.ncol + col]
+                                                          : make_float2(0.f, 0.f);
+    }
+  };
+  float2 ring[kDepth][2];
+#pragma unroll
+  for (int d = 0; d < kDepth; ++d) load_chunk(d, ring[d]);
+  long long s = 0;
+
   for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
     const long long col = tile * kTileM + m;
     const bool colok = col < a.ncol;
-    float acc[kHalfMax];
+    float acc[kQMax];
 #pragma unroll
-    for (int i = 0; i < kHalfMax; ++i) acc[i] = 0.f;
-    // register prefetch two chunks ahead: this thread's 4 nodes of a chunk
-    float2 xn[4], xnn[4];
-    auto load_chunk = [&](int ch, float2* dst) {
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int l = ch * 8 + half * 4 + e;
-        dst[e] = (colok && ch < nchunk && l < nodes) ? a.in[static_cast<long long>(l) * a.ncol + col]
-                                                     : make_float2(0.f, 0.f);
-      }
-    };
-    auto drain = [&](long long gd) {
-      // wait for chunk gd's MMAs and add its accumulator into registers
-      bool w = mbar_wait(&bar[gd & 1], static_cast<uint32_t>((gd >> 1) & 1));
-      tc_fence_after();
-      const uint32_t dcol = static_cast<uint32_t>((gd & 1) * kTmemCols + half * nh);
-      // batches of 24 columns, one wait each (columns past nh lie inside the
+    for (int i = 0; i < kQMax; ++i) acc[i] = 0.f;
+    // add the accumulator of drain group grp (kDrainGroup chunks) into registers
+    auto drain = [&](long long grp) {
+      const uint32_t dcol = static_cast<uint32_t>((grp & 1) * kTmemCols + cb);
+      // batches of 24 columns, one wait each (columns past nq lie inside the
       // allocation; their sums are never stored)
 #pragma unroll
-      for (int c24 = 0; c24 < kHalfMax / 24; ++c24)
-        if (c24 * 24 < nh) tmem_acc24(taddr + lane_base + dcol + static_cast<uint32_t>(c24 * 24), acc + c24 * 24);
+      for (int c24 = 0; c24 < kQMax / 24; ++c24)
+        if (c24 * 24 < nq) tmem_acc24(taddr + lane_base + dcol + static_cast<uint32_t>(c24 * 24), acc + c24 * 24);
       tc_fence_before();
+    };
+    // wait for chunk gd's MMAs (and every earlier one of this thread's issue order)
+    auto wait_chunk = [&](long long gd) {
+      bool w = mbar_wait(&bar[gd & 1], static_cast<uint32_t>((gd >> 1) & 1));
+      tc_fence_after();
       return w;
     };
-    load_chunk(0, xn);
-    load_chunk(1, xnn);
-    for (int ch = 0; ch < nchunk; ++ch, ++g) {
+    for (int ch = 0; ch < nchunk; ++ch, ++g, ++s) {
       const int b = static_cast<int>(g & 1);
-      // (chunk g-2's MMAs were drained in the previous iteration, so buffer b is free)
-      float2 cur[4];
+      // (chunk g-2's MMAs completed before the previous iteration's barrier, so buffer b is free)
+      const float2 c0 = ring[0][0], c1 = ring[0][1];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) { cur[e] = xn[e]; xn[e] = xnn[e]; }
-      load_chunk(ch + 2, xnn);
-      uint16_t h[3][8];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        split3(cur[e].x, h[0][2 * e], h[1][2 * e], h[2][2 * e]);
-        split3(cur[e].y, h[0][2 * e + 1], h[1][2 * e + 1], h[2][2 * e + 1]);
-      }
+      for (int d = 0; d + 1 < kDepth; ++d) { ring[d][0] = ring[d + 1][0]; ring[d][1] = ring[d + 1][1]; }
+      load_chunk(s + kDepth, ring[kDepth - 1]);
+      uint16_t h[3][4];
+      split3(c0.x, h[0][0], h[1][0], h[2][0]);
+      split3(c0.y, h[0][1], h[1][1], h[2][1]);
+      split3(c1.x, h[0][2], h[1][2], h[2][2]);
+      split3(c1.y, h[0][3], h[1][3], h[2][3]);
 #pragma unroll
       for (int p = 0; p < 3; ++p) {
-        uint4 v;
+        uint2 v;
         v.x = h[p][0] | (static_cast<uint32_t>(h[p][1]) << 16);
         v.y = h[p][2] | (static_cast<uint32_t>(h[p][3]) << 16);
-        v.z = h[p][4] | (static_cast<uint32_t>(h[p][5]) << 16);
-        v.w = h[p][6] | (static_cast<uint32_t>(h[p][7]) << 16);
-        *reinterpret_cast<uint4*>(As + (b * 3 + p) * (kTileM * kChunkK * 2) + roff) = v;
+        *reinterpret_cast<uint2*>(As + (b * 3 + p) * (kTileM * kChunkK * 2) + roff) = v;
       }
       fence_async_smem();
       __syncthreads();
       if (tid == 0) {
         tc_fence_after();
-        const uint32_t dcol = static_cast<uint32_t>(b) * kTmemCols;
+        const long long grp = gbase + ch / kDrainGroup;
+        const uint32_t dcol = static_cast<uint32_t>(grp & 1) * kTmemCols;
+        const bool first = (ch % kDrainGroup) == 0;
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
           const uint32_t aaddr = smem_u32(As + (b * 3 + pa[q]) * (kTileM * kChunkK * 2));
           const uint32_t baddr = smem_u32(Bs + pb[q] * bpiece) + static_cast<uint32_t>(ch) * 256;
           mma_bf16(taddr + dcol, smem_desc(aaddr, 128, 256), smem_desc(baddr, 128, bsbo), idesc,
-                   q > 0 ? 1u : 0u);
+                   (q > 0 || !first) ? 1u : 0u);
         }
         mma_commit(&bar[b]);
       }
       if (ch > 0) {
-        bool w = drain(g - 1);
+        bool w = wait_chunk(g - 1);
+        if ((ch - 1) % kDrainGroup == kDrainGroup - 1 && nq > 0) drain(gbase + (ch - 1) / kDrainGroup);
         if (__syncthreads_or(!w)) { ok = false; break; }
       }
     }
     if (!ok) break;
     {
-      bool w = drain(g - 1);                         // the tile's last chunk
+      bool w = wait_chunk(g - 1);                    // the tile's last group
+      if (nq > 0) drain(gbase + (nchunk - 1) / kDrainGroup);
       if (__syncthreads_or(!w)) { ok = false; break; }
     }
+    gbase += (nchunk + kDrainGroup - 1) / kDrainGroup;
     if (colok) {
 #pragma unroll
-      for (int i = 0; i < kHalfMax; i += 2) {
-        const int j = (half * nh + i) >> 1;
-        if (i < nh && j < nodes)
+      for (int i = 0; i < kQMax; i += 2) {
+        const int j = (cb + i) >> 1;
+        if (i < nq && j < nodes)
           a.out[static_cast<long long>(j) * a.ncol + col] = make_float2(acc[i], acc[i + 1]);
       }
     }
@@ -368,7 +389,7 @@ cudaError_t launch_dlr_tc(const void* Bsplit, int r, const void* in, void* out, 
   a.out = reinterpret_cast<float2*>(out);
   a.ncol = ncol;
   a.err = err;
-  dlr_tc_kernel<<<grid, 2 * kTcThreads, smem, st>>>(a);
+  dlr_tc_kernel<<<grid, 4 * kTcThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 
