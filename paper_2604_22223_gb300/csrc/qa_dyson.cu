@@ -341,7 +341,7 @@ __device__ __forceinline__ float4 lds_pair(const float2* tile, int row, int pair
 }
 
 template <int MAXN>
-__global__ void __launch_bounds__(kWarpsR * 32) dyson_w_tile_kernel(const float2* __restrict__ P,
+__global__ void __launch_bounds__(kWarpsR * 32, 3) dyson_w_tile_kernel(const float2* __restrict__ P,
                                                                    const float2* __restrict__ Vq,
                                                                    float2* WC, int n, int nk,
                                                                    int* err, long long* first_bad) {

@@ -25,6 +25,7 @@ struct BubbleSrc {
   const void* coef;
   int nout;
   int no2;
+  int mt;                 // term capacity of the shared-memory lists (multiple of 4)
 };
 
 template <typename V>
@@ -186,9 +187,9 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1) fft3d_reg
   using V = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* tw = reinterpret_cast<V*>(smem_raw);               // exp(-2 pi i k / 64), k < 32
-  V* tc = tw + 32;                                      // [kMaxLineTerms] term coefficients
-  int* ti = reinterpret_cast<int*>(tc + (BUB ? kMaxLineTerms : 0));
-  V* buf = reinterpret_cast<V*>(ti + (BUB ? kMaxLineTerms : 0));
+  V* tc = tw + 32;                                      // [bs.mt] term coefficients
+  int* ti = reinterpret_cast<int*>(tc + (BUB ? bs.mt : 0));
+  V* buf = reinterpret_cast<V*>(ti + (BUB ? bs.mt : 0));
   const int tid = threadIdx.x, bd = blockDim.x;
   const int lnk = l1 + l2 + l3, nk = 1 << lnk;
   const int line_sz = nk + (nk >> lp);
@@ -216,12 +217,12 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1) fft3d_reg
       __syncthreads();
       const V* gt = GR + static_cast<size_t>(tau) * bs.no2 * nk;
       const V* lt = GL + static_cast<size_t>(tau) * bs.no2 * nk;
-      // four points per thread at a time: eight loads in flight per term
-      for (int e0 = tid; e0 < nk; e0 += 4 * kFftThreads) {
-        int mr[4];
-        V acc[4];
+      // eight points per thread at a time: sixteen loads in flight per term
+      for (int e0 = tid; e0 < nk; e0 += 8 * kFftThreads) {
+        int mr[8];
+        V acc[8];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 8; ++u) {
           const int e = e0 + u * kFftThreads;
           mr[u] = e < nk ? bs.mR[e] : 0;
           acc[u] = cmk<V>(0, 0);
@@ -231,18 +232,18 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1) fft3d_reg
           const V c = tc[v];
           const V* g1 = gt + static_cast<size_t>(id & 255) * nk;
           const V* g2 = lt + static_cast<size_t>(id >> 8) * nk;
-          V x[4], y[4];
+          V x[8], y[8];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
+          for (int u = 0; u < 8; ++u) {
             const int e = e0 + u * kFftThreads;
             x[u] = e < nk ? g1[e] : cmk<V>(0, 0);
             y[u] = e < nk ? g2[mr[u]] : cmk<V>(0, 0);
           }
 #pragma unroll
-          for (int u = 0; u < 4; ++u) acc[u] = cfma(c, cmul(x[u], y[u]), acc[u]);
+          for (int u = 0; u < 8; ++u) acc[u] = cfma(c, cmul(x[u], y[u]), acc[u]);
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 8; ++u) {
           const int e = e0 + u * kFftThreads;
           if (e < nk) buf[line * line_sz + e + (e >> lp)] = acc[u];
         }
@@ -250,15 +251,15 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1) fft3d_reg
     }
   } else {
     const V* src = in + line0 * nk;
-    for (int i0 = tid; i0 < tot; i0 += 8 * kFftThreads) {   // eight loads in flight per thread
-      V v[8];
+    for (int i0 = tid; i0 < tot; i0 += 16 * kFftThreads) {   // sixteen loads in flight per thread
+      V v[16];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < 16; ++u) {
         const int i = i0 + u * kFftThreads;
         v[u] = i < tot ? src[i] : cmk<V>(0, 0);
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < 16; ++u) {
         const int i = i0 + u * kFftThreads;
         if (i < tot) buf[(i >> lnk) * line_sz + (i & (nk - 1)) + ((i & (nk - 1)) >> lp)] = v[u];
       }
@@ -317,7 +318,7 @@ cudaError_t launch_fft3d_reg(const FftDev& plan, int sign, const void* in, void*
   const int line_sz = nk + (nk >> lp);
   int lpb = 1;
   while (lpb * 2 * line_sz * static_cast<int>(sizeof(cplx<T>)) <= 32768 && lpb * 2 <= 64) lpb *= 2;
-  const size_t extra = BUB ? static_cast<size_t>(kMaxLineTerms) * (sizeof(cplx<T>) + sizeof(int)) : 0;
+  const size_t extra = BUB ? static_cast<size_t>(bs.mt) * (sizeof(cplx<T>) + sizeof(int)) : 0;
   size_t smem = (static_cast<size_t>(lpb) * line_sz + 32) * sizeof(cplx<T>) + extra;
   auto fn = &fft3d_reg_kernel<T, BUB>;
   cudaError_t e = set_smem(reinterpret_cast<const void*>(fn), smem, true);
@@ -338,7 +339,8 @@ cudaError_t launch_fft3d_bubble(const FftDev& plan, const void* GR, const void* 
                                 const int* mR, const int* terms, const void* coef, int max_terms,
                                 int nout, int norb, void* out, int r, cudaStream_t st) {
   if (!reg_plan_ok(plan) || max_terms > kMaxLineTerms || norb * norb > 256) return cudaErrorInvalidValue;
-  BubbleSrc bs{GR, GreflR, mR, terms, coef, nout, norb * norb};
+  const int mt = (max_terms + 3) / 4 * 4;            // keeps the line buffer aligned
+  BubbleSrc bs{GR, GreflR, mR, terms, coef, nout, norb * norb, mt < 4 ? 4 : mt};
   return launch_fft3d_reg<T, true>(plan, -1, nullptr, out, static_cast<long long>(nout) * r, st,
                                    static_cast<T>(1), bs);
 }
