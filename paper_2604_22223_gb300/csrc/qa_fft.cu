@@ -141,53 +141,85 @@ __host__ __device__ constexpr int brev_bits(int i, int bits) {
 }
 __host__ __device__ constexpr int ilog2(int L) { return L <= 1 ? 0 : 1 + ilog2(L / 2); }
 
-// One length-L transform of the points base + j*S (j < L) of a padded line.
-// The padding (one element per 2^lp points, 2^lp = the innermost non-trivial
-// axis length) is linear along every axis: physical index = pb + j * ps.
-// Radix-2 in registers, natural order in and out.
-template <typename V, int L>
-__device__ __forceinline__ void line_fft(V* __restrict__ buf, int pb, int ps,
-                                         const V* __restrict__ tw64, int sign) {
-  constexpr int B = ilog2(L);
-  V x[L];
-#pragma unroll
-  for (int j = 0; j < L; ++j) x[brev_bits(j, B)] = buf[pb + j * ps];
+// cos(2 pi j / 64): the first-octant values (j = 0..16, rounded to double) and
+// the symmetries of the cosine; after unrolling every call has a constant
+// argument and folds to a literal.
+__host__ __device__ constexpr double cos64(int j) {
+  constexpr double c[17] = {1.0,
+                            0.99518472667219693, 0.98078528040323043, 0.95694033573220882,
+                            0.92387953251128674, 0.88192126434835505, 0.83146961230254524,
+                            0.77301045336273699, 0.70710678118654757, 0.63439328416364549,
+                            0.55557023301960229, 0.47139673682599781, 0.38268343236508984,
+                            0.29028467725446233, 0.19509032201612833, 0.09801714032956077,
+                            0.0};
+  j &= 63;
+  if (j > 32) j = 64 - j;
+  return j > 16 ? -c[32 - j] : c[j];
+}
+__host__ __device__ constexpr double sin64(int j) { return cos64((j + 48) & 63); }
+
+// v * exp(SIGN 2 pi i j / 64); j = 0 and j = 16 (a quarter turn) without multiplications
+template <typename V, int SIGN>
+__device__ __forceinline__ V tw_mul(int j, V v) {
+  if (j == 0) return v;
+  if (j == 16) return SIGN < 0 ? cmk<V>(v.y, -v.x) : cmk<V>(-v.y, v.x);
+  return cmul(cmk<V>(cos64(j), SIGN * sin64(j)), v);
+}
+
+// In-register radix-2 transform of length L (input in bit-reversed order,
+// output in natural order): X_f = sum_j x_j exp(SIGN 2 pi i f j / L).
+template <typename V, int L, int SIGN>
+__device__ __forceinline__ void fft_regs(V (&x)[L]) {
 #pragma unroll
   for (int m = 2; m <= L; m <<= 1) {
 #pragma unroll
     for (int k = 0; k < m / 2; ++k) {
-      V w = tw64[k * (64 / m)];
-      if (sign > 0) w.y = -w.y;
 #pragma unroll
       for (int s0 = 0; s0 < L; s0 += m) {
-        V u = x[s0 + k];
-        V t = k == 0 ? x[s0 + k + m / 2] : cmul(w, x[s0 + k + m / 2]);
+        const V u = x[s0 + k];
+        const V t = tw_mul<V, SIGN>(k * (64 / m), x[s0 + k + m / 2]);
         x[s0 + k] = cadd(u, t);
         x[s0 + k + m / 2] = csub(u, t);
       }
     }
   }
-#pragma unroll
-  for (int j = 0; j < L; ++j) buf[pb + j * ps] = x[j];
 }
 
-// Lines of N1 x N2 x N3 points with every N_d a power of two <= 32: a block
-// keeps lpb lines in shared memory (one padding element per 2^lp points
-// spreads the strided axis passes over the banks), each axis pass gives one
-// length-L transform per thread, and all index arithmetic is shifts and masks.
-// With BUB the lines are not read but produced in shared memory by the bubble
-// term lists (launch_fft3d_bubble): line (tau, o) holds
+// L contiguous values at p into x in bit-reversed order (16-byte loads when vec)
+template <typename V, int L>
+__device__ __forceinline__ void ld_seg_brev(const V* __restrict__ p, V (&x)[L], bool vec) {
+  constexpr int B = ilog2(L);
+  if (sizeof(V) == 8 && vec) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int i = 0; i < L / 2; ++i) {
+      const float4 v = q[i];
+      x[brev_bits(2 * i, B)] = cmk<V>(v.x, v.y);
+      x[brev_bits(2 * i + 1, B)] = cmk<V>(v.z, v.w);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < L; ++j) x[brev_bits(j, B)] = p[j];
+  }
+}
+
+// Lines of N1 x N2 x N3 points with every N_d a power of two <= 32.  The axes
+// are transformed innermost first, one length-L transform per thread and task,
+// in registers.  The first pass reads its contiguous segments straight from
+// global memory (16-byte loads); with BUB the lines are instead formed in
+// shared memory from the bubble term lists: line (tau, o) holds
 // sum_terms coef G[tau][g1](R) G^refl[tau][g2](-R), so P(R, tau) never goes
-// through HBM before its transform to q.
-template <typename T, bool BUB>
-__global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1) fft3d_reg_kernel(int l1, int l2, int l3, int sign,
-                                                        const cplx<T>* in, cplx<T>* out,
-                                                        int lpb, long long nlines, int lp,
-                                                        T scale, BubbleSrc bs) {
+// through HBM before its transform to q.  Middle passes work in shared memory
+// (one padding element per 2^lp points spreads the strided passes over the
+// banks); the last pass writes global memory directly (consecutive threads own
+// consecutive columns, so each of its stores is coalesced).
+template <typename T, bool BUB, int SIGN>
+__global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1)
+    fft3d_reg_kernel(int l1, int l2, int l3, const cplx<T>* in, cplx<T>* out, int lpb,
+                     long long nlines, int lp, T scale, int vec, BubbleSrc bs) {
   using V = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* tw = reinterpret_cast<V*>(smem_raw);               // exp(-2 pi i k / 64), k < 32
-  V* tc = tw + 32;                                      // [bs.mt] term coefficients
+  V* tc = reinterpret_cast<V*>(smem_raw);                 // [bs.mt] term coefficients (BUB)
   int* ti = reinterpret_cast<int*>(tc + (BUB ? bs.mt : 0));
   V* buf = reinterpret_cast<V*>(ti + (BUB ? bs.mt : 0));
   const int tid = threadIdx.x, bd = blockDim.x;
@@ -195,12 +227,6 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1) fft3d_reg
   const int line_sz = nk + (nk >> lp);
   const long long line0 = static_cast<long long>(blockIdx.x) * lpb;
   const int nl = static_cast<int>(min(static_cast<long long>(lpb), nlines - line0));
-  if (tid < 32) {
-    double sn, cs;
-    sincospi(-tid / 32.0, &sn, &cs);
-    tw[tid] = cmk<V>(cs, sn);
-  }
-  const int tot = nl << lnk;
   if (BUB) {
     const V* GR = reinterpret_cast<const V*>(bs.GR);
     const V* GL = reinterpret_cast<const V*>(bs.GL);
@@ -249,53 +275,56 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1) fft3d_reg
         }
       }
     }
-  } else {
-    const V* src = in + line0 * nk;
-    for (int i0 = tid; i0 < tot; i0 += 16 * kFftThreads) {   // sixteen loads in flight per thread
-      V v[16];
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int i = i0 + u * kFftThreads;
-        v[u] = i < tot ? src[i] : cmk<V>(0, 0);
-      }
-#pragma unroll
-      for (int u = 0; u < 16; ++u) {
-        const int i = i0 + u * kFftThreads;
-        if (i < tot) buf[(i >> lnk) * line_sz + (i & (nk - 1)) + ((i & (nk - 1)) >> lp)] = v[u];
-      }
-    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int d = 2; d >= 0; --d) {
-    const int lL = d == 2 ? l3 : (d == 1 ? l2 : l1);
-    if (lL == 0) continue;
-    const int lS = d == 2 ? 0 : (d == 1 ? l3 : l2 + l3);
+  const int na = (l1 > 0) + (l2 > 0) + (l3 > 0);       // non-trivial axes, innermost first
+  for (int pass = 0; pass < na; ++pass) {
+    const bool first = pass == 0, last = pass == na - 1;
+    int lL = 0, lS = 0;                                 // log2 length and log2 stride of the axis
+    {
+      int k = pass;
+      if (l3) { if (k == 0) { lL = l3; lS = 0; } --k; }
+      if (l2) { if (k == 0) { lL = l2; lS = l3; } --k; }
+      if (l1) { if (k == 0) { lL = l1; lS = l2 + l3; } }
+    }
     const int lper = lnk - lL;                          // transforms per line = 2^lper
     for (int task = tid; task < (nl << lper); task += bd) {
       const int line = task >> lper, rem = task & ((1 << lper) - 1);
       const int o_lo = rem & ((1 << lS) - 1), o_hi = rem >> lS;
-      V* lb = buf + line * line_sz;
       const int base = (o_hi << (lL + lS)) + o_lo;
       const int S = 1 << lS;
+      const long long gl = line0 + line;
+      V* lb = buf + static_cast<size_t>(line) * line_sz;
       const int pb = base + (base >> lp), ps = S + (S >> lp);
       switch (lL) {
-        case 1: line_fft<V, 2>(lb, pb, ps, tw, sign); break;
-        case 2: line_fft<V, 4>(lb, pb, ps, tw, sign); break;
-        case 3: line_fft<V, 8>(lb, pb, ps, tw, sign); break;
-        case 4: line_fft<V, 16>(lb, pb, ps, tw, sign); break;
-        case 5: line_fft<V, 32>(lb, pb, ps, tw, sign); break;
+#define QA_FFT_PASS(LL)                                                                          \
+  case LL: {                                                                                     \
+    constexpr int L = 1 << LL;                                                                   \
+    V x[L];                                                                                      \
+    if (first && !BUB) {                                                                         \
+      ld_seg_brev<V, L>(in + gl * nk + base, x, vec != 0);                                       \
+    } else {                                                                                     \
+      _Pragma("unroll") for (int j = 0; j < L; ++j) x[brev_bits(j, LL)] = lb[pb + j * ps];       \
+    }                                                                                            \
+    fft_regs<V, L, SIGN>(x);                                                                     \
+    if (last) {                                                                                  \
+      V* dst = out + gl * nk + base;                                                             \
+      _Pragma("unroll") for (int j = 0; j < L; ++j) dst[static_cast<size_t>(j) * S] =            \
+          cmk<V>(x[j].x * scale, x[j].y * scale);                                                \
+    } else {                                                                                     \
+      _Pragma("unroll") for (int j = 0; j < L; ++j) lb[pb + j * ps] = x[j];                      \
+    }                                                                                            \
+  } break;
+        QA_FFT_PASS(1)
+        QA_FFT_PASS(2)
+        QA_FFT_PASS(3)
+        QA_FFT_PASS(4)
+        QA_FFT_PASS(5)
+#undef QA_FFT_PASS
         default: break;
       }
     }
-    __syncthreads();
-  }
-  V* dst = out + line0 * nk;
-  for (int i = tid; i < tot; i += bd) {
-    const int line = i >> lnk, e = i & (nk - 1);
-    V v = buf[line * line_sz + e + (e >> lp)];
-    v.x *= scale;
-    v.y *= scale;
-    dst[i] = v;
+    if (!last) __syncthreads();
   }
 }
 
@@ -309,6 +338,8 @@ bool reg_plan_ok(const FftDev& plan) {
          nk >= 2;
 }
 
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
 template <typename T, bool BUB>
 cudaError_t launch_fft3d_reg(const FftDev& plan, int sign, const void* in, void* out,
                              long long nlines, cudaStream_t st, T sc, const BubbleSrc& bs) {
@@ -319,14 +350,15 @@ cudaError_t launch_fft3d_reg(const FftDev& plan, int sign, const void* in, void*
   int lpb = 1;
   while (lpb * 2 * line_sz * static_cast<int>(sizeof(cplx<T>)) <= 32768 && lpb * 2 <= 64) lpb *= 2;
   const size_t extra = BUB ? static_cast<size_t>(bs.mt) * (sizeof(cplx<T>) + sizeof(int)) : 0;
-  size_t smem = (static_cast<size_t>(lpb) * line_sz + 32) * sizeof(cplx<T>) + extra;
-  auto fn = &fft3d_reg_kernel<T, BUB>;
+  const size_t smem = static_cast<size_t>(lpb) * line_sz * sizeof(cplx<T>) + extra;
+  const int vec = BUB ? 0 : aligned16(in);
+  auto fn = sign > 0 ? &fft3d_reg_kernel<T, BUB, 1> : &fft3d_reg_kernel<T, BUB, -1>;
   cudaError_t e = set_smem(reinterpret_cast<const void*>(fn), smem, true);
   if (e != cudaSuccess) return e;
   long long nblk = (nlines + lpb - 1) / lpb;
   fn<<<static_cast<unsigned>(nblk), kFftThreads, smem, st>>>(
-      ilog2(plan.n[0]), ilog2(plan.n[1]), ilog2(plan.n[2]), sign,
-      reinterpret_cast<const cplx<T>*>(in), reinterpret_cast<cplx<T>*>(out), lpb, nlines, lp, sc, bs);
+      ilog2(plan.n[0]), ilog2(plan.n[1]), ilog2(plan.n[2]), reinterpret_cast<const cplx<T>*>(in),
+      reinterpret_cast<cplx<T>*>(out), lpb, nlines, lp, sc, vec, bs);
   return cudaGetLastError();
 }
 

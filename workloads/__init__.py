@@ -325,6 +325,12 @@ def config(name: str) -> Model:
         return peierls_two_orbital()
     if name == "peierls-5x3x2":
         return peierls_two_orbital(n=(5, 3, 2), name="peierls-5x3x2")
+    if name == "peierls-4x4x2":               # power-of-two 3-D grids (register FFT passes)
+        return peierls_two_orbital(n=(4, 4, 2), name="peierls-4x4x2")
+    if name == "five-orbital-2x4x4":
+        return five_orbital(n=(2, 4, 4), beta=10.0, Lambda=200.0, name="five-orbital-2x4x4")
+    if name == "square-16x1x1":               # one non-trivial axis
+        return square_single_band(n=(16, 1, 1), name="square-16x1x1")
     if name == "square-1x1":
         return square_single_band(n=(1, 1, 1), name="square-1x1")
     raise KeyError(name)
