@@ -9,18 +9,18 @@
 // leading cross products x_i t_j (i + j <= 2) accumulate in FP32 in tensor
 // memory, which keeps the FP32-level accuracy of the SIMT kernel.
 //
-// One persistent CTA per SM (512 threads): the three Tt pieces stay resident
-// in shared memory (K-major canonical layout, no swizzle); each 128-column
-// tile of X streams through double-buffered K-chunks of 16 (8 nodes x re/im)
-// that all threads convert to bf16 pieces while the previous chunk's six
-// MMAs run; one thread issues tcgen05.mma (M = 128, N = 2r padded to 16,
-// K = 16) into a 128 x N FP32 accumulator in TMEM; the epilogue reads it
-// back with tcgen05.ld (warps w, w+4, w+8, w+12 <-> TMEM lanes 32w..32w+31,
-// thread <-> column, each warp a quarter of the accumulator columns) and
-// stores Y in place of X.  The input is read through a register ring several
-// chunks deep (the kernel is otherwise bound by the latency of its loads).
-// Every mbarrier wait is bounded; on time-out the kernel records
-// QA_ETIMEOUT, waits (bounded) for its own MMAs, frees TMEM and returns.
+// One persistent CTA per SM, warp-specialised (16 worker warps and one MMA
+// issuer warp, synchronised only through mbarriers): the three Tt pieces stay
+// resident in shared memory (K-major canonical layout, no swizzle); each
+// 128-column tile of X streams through double-buffered K-chunks of 16 (8 nodes
+// x re/im) that the workers convert to bf16 pieces while the previous chunk's
+// six MMAs run; one thread issues tcgen05.mma (M = 128, N = 2r padded to 16,
+// K = 16) into a 128 x N FP32 accumulator in TMEM; the workers read it back
+// with tcgen05.ld (warps w, w+4, w+8, w+12 <-> TMEM lanes 32w..32w+31, thread
+// <-> column, each warp a quarter of the accumulator columns) and store Y in
+// place of X.  The input is read through a register ring several chunks deep.
+// Every mbarrier wait is bounded; on time-out the kernel records QA_ETIMEOUT,
+// waits (bounded) for its own MMAs, frees TMEM and returns.
 #include <cuda_bf16.h>
 
 #include <cstring>
@@ -143,37 +143,56 @@ __device__ __forceinline__ void tmem_acc24(uint32_t taddr, float* acc) {
       : "memory");
 }
 
-constexpr int kQMax = 48;               // accumulator columns per thread (Np <= 192)
-constexpr int kDrainGroup = 1;          // K-chunks summed in TMEM between two drains
-constexpr int kDepth = 4;               // K-chunks of input in flight per thread (registers)
+constexpr int kQMax = 48;               // accumulator columns per worker thread (Np <= 192)
+constexpr int kDepth = 4;               // K-chunks of input in flight per worker (registers)
+constexpr int kWorkers = 4 * kTcThreads;   // 16 worker warps; warp 16 issues the MMAs
 
-// 512 threads: thread (w, lane) owns TMEM lane / tile row m = 32 (w % 4) + lane
-// and quarter qt = w / 4 of the work of that row: accumulator columns
-// [48 qt, 48 qt + 48) and nodes 2 qt, 2 qt + 1 of each chunk's 8.  Each
-// K-chunk's six MMAs go to a fresh accumulator (two alternate in TMEM), which
-// is drained into FP32 registers with round-to-nearest adds while the next
-// chunk's MMAs run, so the tensor core never sums more than 96 products.  The
-// input streams through a register ring kDepth chunks deep that runs on across
-// this CTA's tiles, so 512 x kDepth x 16 bytes per SM are in flight.
-__global__ void __launch_bounds__(4 * kTcThreads, 1) dlr_tc_kernel(TcArgs a) {
+// bounded wait that also gives up once another thread has flagged an abort
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity,
+                                                   volatile int* abort_flag) {
+  for (long long i = 0; i < kWaitLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 1023) == 1023 && *abort_flag) return false;
+  }
+  return false;
+}
+
+// Warp-specialised: worker thread (w < 16, lane) owns TMEM lane / tile row
+// m = 32 (w % 4) + lane and quarter qt = w / 4 of the work of that row:
+// accumulator columns [48 qt, 48 qt + 48) and nodes 2 qt, 2 qt + 1 of each
+// chunk's 8.  For chunk g (this CTA's chunks numbered across its tiles) the
+// workers stage the bf16 pieces of X into buffer g % 2 and arrive on full[g % 2];
+// the issuer (one thread of warp 16) waits for it, issues the six MMAs into the
+// fresh accumulator g % 2 and commits to done[g % 2]; the workers wait on
+// done[(g-1) % 2] and drain chunk g-1 into FP32 registers with round-to-nearest
+// adds while chunk g runs, so the tensor core never sums more than 96 products.
+// No block-wide barrier inside the stream: the issuer never waits on the
+// drains of other chunks, and the workers never wait on the MMA issue.
+// Buffer and accumulator reuse: chunk g is staged only after each worker has
+// waited for chunk g-2's MMAs and drained it, and full[g % 2] completes only
+// when every worker warp has arrived for chunk g.
+__global__ void __launch_bounds__(kWorkers + 32, 1) dlr_tc_kernel(TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m = 32 * (warp & 3) + lane;
-  const int qt = warp >> 2;
   const uint32_t bpiece = static_cast<uint32_t>(a.Np) * a.Kp * 2;    // bytes of one Tt piece
   uint8_t* Bs = smem;
   uint8_t* As = smem + 3 * bpiece;                                    // [2 buffers][3 pieces][4096 B]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(As + 2 * 3 * kTileM * kChunkK * 2);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  uint64_t* done = reinterpret_cast<uint64_t*>(As + 2 * 3 * kTileM * kChunkK * 2);
+  uint64_t* full = done + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(full + 2);
   __shared__ int s_abort;
+  __shared__ long long s_issued;
 
   for (uint32_t i = tid; i < 3 * bpiece / 16; i += blockDim.x)
     reinterpret_cast<uint4*>(Bs)[i] = a.Bsplit[i];
   if (tid == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    mbar_init(&done[0], 1);
+    mbar_init(&done[1], 1);
+    mbar_init(&full[0], kWorkers / 32);
+    mbar_init(&full[1], kWorkers / 32);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
+    s_issued = 0;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -186,132 +205,143 @@ __global__ void __launch_bounds__(4 * kTcThreads, 1) dlr_tc_kernel(TcArgs a) {
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  volatile int* abort_flag = &s_abort;
   const uint32_t taddr = *tslot;
-  const uint32_t idesc = instr_desc(kTileM, a.Np);
   const int nchunk = a.Kp / kChunkK;
-  const uint32_t bsbo = static_cast<uint32_t>(a.Kp / 8) * 128;
   const long long ntiles = (a.ncol + kTileM - 1) / kTileM;
   const long long my_tiles = blockIdx.x < ntiles ? (ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
   const long long nstream = my_tiles * nchunk;       // this CTA's chunks, tile after tile
-  const int nodes = a.r;
-  const int cb = kQMax * qt;                         // first accumulator column of this thread
-  const int nq = a.Np - cb < kQMax ? a.Np - cb : kQMax;   // its column count (may be <= 0)
-  const uint32_t lane_base = static_cast<uint32_t>(32 * (warp & 3)) << 16;
-  const uint32_t roff = static_cast<uint32_t>(m >> 3) * 256 + static_cast<uint32_t>(m & 7) * 16 +
-                        static_cast<uint32_t>(qt >> 1) * 128 + static_cast<uint32_t>(qt & 1) * 8;
-  long long g = 0;                                   // global chunk counter (mbarrier phases)
-  long long gbase = 0;                               // drain groups of the earlier tiles
-  bool ok = true;
-  const int pa[6] = {0, 0, 1, 0, 1, 2};
-  const int pb[6] = {0, 1, 0, 2, 1, 0};
 
-  // this thread's two input values of stream chunk s (zero past the end)
-  auto load_chunk = [&](long long s, float2* dst) {
-    const long long tile = blockIdx.x + (s / nchunk) * gridDim.x;
-    const int ch = static_cast<int>(s % nchunk);
-    const long long col = tile * kTileM + m;
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const int l = ch * 8 + qt * 2 + e;
-      dst[e] = (s < nstream && col < a.ncol && l < nodes) ? a.in[static_cast<long long>(l) * a.ncol + col]
-                                                          : make_float2(0.f, 0.f);
-    }
-  };
-  float2 ring[kDepth][2];
-#pragma unroll
-  for (int d = 0; d < kDepth; ++d) load_chunk(d, ring[d]);
-  long long s = 0;
-
-  for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-    const long long col = tile * kTileM + m;
-    const bool colok = col < a.ncol;
-    float acc[kQMax];
-#pragma unroll
-    for (int i = 0; i < kQMax; ++i) acc[i] = 0.f;
-    // add the accumulator of drain group grp (kDrainGroup chunks) into registers
-    auto drain = [&](long long grp) {
-      const uint32_t dcol = static_cast<uint32_t>((grp & 1) * kTmemCols + cb);
-      // batches of 24 columns, one wait each (columns past nq lie inside the
-      // allocation; their sums are never stored)
-#pragma unroll
-      for (int c24 = 0; c24 < kQMax / 24; ++c24)
-        if (c24 * 24 < nq) tmem_acc24(taddr + lane_base + dcol + static_cast<uint32_t>(c24 * 24), acc + c24 * 24);
-      tc_fence_before();
-    };
-    // wait for chunk gd's MMAs (and every earlier one of this thread's issue order)
-    auto wait_chunk = [&](long long gd) {
-      bool w = mbar_wait(&bar[gd & 1], static_cast<uint32_t>((gd >> 1) & 1));
-      tc_fence_after();
-      return w;
-    };
-    for (int ch = 0; ch < nchunk; ++ch, ++g, ++s) {
-      const int b = static_cast<int>(g & 1);
-      // (chunk g-2's MMAs completed before the previous iteration's barrier, so buffer b is free)
-      const float2 c0 = ring[0][0], c1 = ring[0][1];
-#pragma unroll
-      for (int d = 0; d + 1 < kDepth; ++d) { ring[d][0] = ring[d + 1][0]; ring[d][1] = ring[d + 1][1]; }
-      load_chunk(s + kDepth, ring[kDepth - 1]);
-      uint16_t h[3][4];
-      split3(c0.x, h[0][0], h[1][0], h[2][0]);
-      split3(c0.y, h[0][1], h[1][1], h[2][1]);
-      split3(c1.x, h[0][2], h[1][2], h[2][2]);
-      split3(c1.y, h[0][3], h[1][3], h[2][3]);
-#pragma unroll
-      for (int p = 0; p < 3; ++p) {
-        uint2 v;
-        v.x = h[p][0] | (static_cast<uint32_t>(h[p][1]) << 16);
-        v.y = h[p][2] | (static_cast<uint32_t>(h[p][3]) << 16);
-        *reinterpret_cast<uint2*>(As + (b * 3 + p) * (kTileM * kChunkK * 2) + roff) = v;
-      }
-      fence_async_smem();
-      __syncthreads();
-      if (tid == 0) {
+  if (warp == kWorkers / 32) {
+    // ---- MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = instr_desc(kTileM, a.Np);
+      const uint32_t bsbo = static_cast<uint32_t>(a.Kp / 8) * 128;
+      const int pa[6] = {0, 0, 1, 0, 1, 2};
+      const int pb[6] = {0, 1, 0, 2, 1, 0};
+      int ch = 0;
+      long long g = 0;
+      for (; g < nstream; ++g) {
+        const int b = static_cast<int>(g & 1);
+        if (!mbar_wait_or_abort(&full[b], static_cast<uint32_t>((g >> 1) & 1), abort_flag)) {
+          *abort_flag = 1;
+          break;
+        }
         tc_fence_after();
-        const long long grp = gbase + ch / kDrainGroup;
-        const uint32_t dcol = static_cast<uint32_t>(grp & 1) * kTmemCols;
-        const bool first = (ch % kDrainGroup) == 0;
+        const uint32_t dcol = static_cast<uint32_t>(b) * kTmemCols;
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
           const uint32_t aaddr = smem_u32(As + (b * 3 + pa[q]) * (kTileM * kChunkK * 2));
           const uint32_t baddr = smem_u32(Bs + pb[q] * bpiece) + static_cast<uint32_t>(ch) * 256;
           mma_bf16(taddr + dcol, smem_desc(aaddr, 128, 256), smem_desc(baddr, 128, bsbo), idesc,
-                   (q > 0 || !first) ? 1u : 0u);
+                   q > 0 ? 1u : 0u);
         }
-        mma_commit(&bar[b]);
+        mma_commit(&done[b]);
+        if (++ch == nchunk) ch = 0;
       }
-      if (ch > 0) {
-        bool w = wait_chunk(g - 1);
-        if ((ch - 1) % kDrainGroup == kDrainGroup - 1 && nq > 0) drain(gbase + (ch - 1) / kDrainGroup);
-        if (__syncthreads_or(!w)) { ok = false; break; }
-      }
+      s_issued = g;
     }
-    if (!ok) break;
-    {
-      bool w = wait_chunk(g - 1);                    // the tile's last group
-      if (nq > 0) drain(gbase + (nchunk - 1) / kDrainGroup);
-      if (__syncthreads_or(!w)) { ok = false; break; }
-    }
-    gbase += (nchunk + kDrainGroup - 1) / kDrainGroup;
-    if (colok) {
+    __syncwarp();
+  } else {
+    // ---- workers
+    const int m = 32 * (warp & 3) + lane;
+    const int qt = warp >> 2;
+    const int nodes = a.r;
+    const int cb = kQMax * qt;                       // first accumulator column of this thread
+    const int nq = a.Np - cb < kQMax ? a.Np - cb : kQMax;   // its column count (may be <= 0)
+    const uint32_t lane_base = static_cast<uint32_t>(32 * (warp & 3)) << 16;
+    const uint32_t roff = static_cast<uint32_t>(m >> 3) * 256 + static_cast<uint32_t>(m & 7) * 16 +
+                          static_cast<uint32_t>(qt >> 1) * 128 + static_cast<uint32_t>(qt & 1) * 8;
+    // prefetch stream position (tile, chunk), advanced once per load
+    long long pf_tile = blockIdx.x, pf_s = 0;
+    int pf_ch = 0;
+    auto load_next = [&](float2* dst) {
+      const long long col = pf_tile * kTileM + m;
 #pragma unroll
-      for (int i = 0; i < kQMax; i += 2) {
-        const int j = (cb + i) >> 1;
-        if (i < nq && j < nodes)
-          a.out[static_cast<long long>(j) * a.ncol + col] = make_float2(acc[i], acc[i + 1]);
+      for (int e = 0; e < 2; ++e) {
+        const int l = pf_ch * 8 + qt * 2 + e;
+        dst[e] = (pf_s < nstream && col < a.ncol && l < nodes)
+                     ? a.in[static_cast<long long>(l) * a.ncol + col] : make_float2(0.f, 0.f);
+      }
+      ++pf_s;
+      if (++pf_ch == nchunk) { pf_ch = 0; pf_tile += gridDim.x; }
+    };
+    float2 ring[kDepth][2];
+#pragma unroll
+    for (int d = 0; d < kDepth; ++d) load_next(ring[d]);
+    auto drain = [&](long long gd, float* acc) {
+      const uint32_t dcol = static_cast<uint32_t>((gd & 1) * kTmemCols + cb);
+#pragma unroll
+      for (int c24 = 0; c24 < kQMax / 24; ++c24)
+        if (c24 * 24 < nq) tmem_acc24(taddr + lane_base + dcol + static_cast<uint32_t>(c24 * 24), acc + c24 * 24);
+      tc_fence_before();
+    };
+    long long g = 0;
+    bool ok = true;
+    for (long long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+      const long long col = tile * kTileM + m;
+      const bool colok = col < a.ncol;
+      float acc[kQMax];
+#pragma unroll
+      for (int i = 0; i < kQMax; ++i) acc[i] = 0.f;
+      for (int ch = 0; ch < nchunk; ++ch, ++g) {
+        const int b = static_cast<int>(g & 1);
+        const float2 c0 = ring[0][0], c1 = ring[0][1];
+#pragma unroll
+        for (int d = 0; d + 1 < kDepth; ++d) { ring[d][0] = ring[d + 1][0]; ring[d][1] = ring[d + 1][1]; }
+        load_next(ring[kDepth - 1]);
+        uint16_t h[3][4];
+        split3(c0.x, h[0][0], h[1][0], h[2][0]);
+        split3(c0.y, h[0][1], h[1][1], h[2][1]);
+        split3(c1.x, h[0][2], h[1][2], h[2][2]);
+        split3(c1.y, h[0][3], h[1][3], h[2][3]);
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+          uint2 v;
+          v.x = h[p][0] | (static_cast<uint32_t>(h[p][1]) << 16);
+          v.y = h[p][2] | (static_cast<uint32_t>(h[p][3]) << 16);
+          *reinterpret_cast<uint2*>(As + (b * 3 + p) * (kTileM * kChunkK * 2) + roff) = v;
+        }
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[b])) : "memory");
+        if (ch > 0) {
+          const bool w = mbar_wait_or_abort(&done[(g - 1) & 1], static_cast<uint32_t>(((g - 1) >> 1) & 1), abort_flag);
+          if (__any_sync(0xffffffffu, !w)) {          // warp-uniform exit
+            *abort_flag = 1;
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          if (nq > 0) drain(g - 1, acc);
+        }
+      }
+      if (!ok) break;
+      const bool w = mbar_wait_or_abort(&done[(g - 1) & 1], static_cast<uint32_t>(((g - 1) >> 1) & 1), abort_flag);
+      if (__any_sync(0xffffffffu, !w)) {
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      if (nq > 0) drain(g - 1, acc);                   // the tile's last chunk
+      if (colok) {
+#pragma unroll
+        for (int i = 0; i < kQMax; i += 2) {
+          const int j = (cb + i) >> 1;
+          if (i < nq && j < nodes)
+            a.out[static_cast<long long>(j) * a.ncol + col] = make_float2(acc[i], acc[i + 1]);
+        }
       }
     }
-  }
-  if (!ok && tid == 0) {
-    atomicCAS(a.err, 0, QA_ETIMEOUT_CODE);
-    s_abort = 1;
   }
   __syncthreads();
-  if (s_abort && g > 0) {
+  if (tid == 0 && *abort_flag) {
+    atomicCAS(a.err, 0, QA_ETIMEOUT_CODE);
     // let this CTA's own MMAs finish (bounded) before TMEM is released
-    const long long gl = g - 1;
-    mbar_wait(&bar[gl & 1], static_cast<uint32_t>((gl >> 1) & 1));
-    __syncthreads();
+    const long long gl = s_issued - 1;
+    if (gl >= 0) mbar_wait(&done[gl & 1], static_cast<uint32_t>((gl >> 1) & 1));
   }
+  __syncthreads();
   tc_fence_after();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr),
@@ -337,7 +367,7 @@ double bf16_val(uint16_t h) {
 
 bool dlr_tc_supported(int r, size_t* smem_bytes) {
   const int Kp = ((2 * r + 15) / 16) * 16;
-  const size_t bytes = 3ull * Kp * Kp * 2 + 2ull * 3 * kTileM * kChunkK * 2 + 2 * 8 + 16;
+  const size_t bytes = 3ull * Kp * Kp * 2 + 2ull * 3 * kTileM * kChunkK * 2 + 4 * 8 + 16;
   if (smem_bytes) *smem_bytes = bytes;
   return Kp <= 192 && bytes <= 227 * 1024;
 }
@@ -389,7 +419,7 @@ cudaError_t launch_dlr_tc(const void* Bsplit, int r, const void* in, void* out, 
   a.out = reinterpret_cast<float2*>(out);
   a.ncol = ncol;
   a.err = err;
-  dlr_tc_kernel<<<grid, 4 * kTcThreads, smem, st>>>(a);
+  dlr_tc_kernel<<<grid, kWorkers + 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 
