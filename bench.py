@@ -155,19 +155,24 @@ def roofline(ctx, mixed, stage_ms, pk):
 
 
 def traffic_for(stage):
-    """DRAM bytes per launch from a committed ncu summary, if its source matches."""
+    """DRAM bytes per launch of a stage's kernel at the bench workload, from a
+    committed ncu summary; None when the kernel's sources changed since (the
+    summary records a SHA-256 of their contents)."""
+    import hashlib
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
     try:
-        d = json.load(open(p))
-        ent = d.get(stage)
+        ent = json.load(open(p)).get(stage)
         if not ent:
             return None
-        from paper_2604_22223_gb300.builder import _stamp
-        if ent.get("stamp") != _stamp():
+        h = hashlib.sha256()
+        for rel in ent["sources"]:
+            with open(os.path.join(ROOT, rel), "rb") as fh:
+                h.update(fh.read())
+        if h.hexdigest() != ent["source_sha256"]:
             return None
-        return ent.get("dram_bytes_per_launch")
+        return ent["dram_bytes_per_launch"]
     except Exception:  # noqa: BLE001
         return None
 
