@@ -144,7 +144,8 @@ __device__ __forceinline__ void tmem_acc24(uint32_t taddr, float* acc) {
 }
 
 constexpr int kQMax = 48;               // accumulator columns per worker thread (Np <= 192)
-constexpr int kDepth = 4;               // K-chunks of input in flight per worker (registers)
+constexpr int kDepth = 2;               // K-chunks of input in flight per worker (registers)
+constexpr int kPrefetch = 16;            // further K-chunks requested into L2 ahead of the ring
 constexpr int kWorkers = 4 * kTcThreads;   // 16 worker warps; warp 16 issues the MMAs
 
 // bounded wait that also gives up once another thread has flagged an abort
@@ -266,6 +267,24 @@ __global__ void __launch_bounds__(kWorkers + 32, 1) dlr_tc_kernel(TcArgs a) {
       ++pf_s;
       if (++pf_ch == nchunk) { pf_ch = 0; pf_tile += gridDim.x; }
     };
+    // L2 prefetch cursor kPrefetch chunks ahead of the register ring (no
+    // registers held): deepens the loads in flight from HBM
+    long long pp_tile = blockIdx.x, pp_s = 0;
+    int pp_ch = 0;
+    auto prefetch_next = [&]() {
+      const long long col = pp_tile * kTileM + m;
+      if (pp_s < nstream && col < a.ncol) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int l = pp_ch * 8 + qt * 2 + e;
+          if (l < nodes)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(a.in + static_cast<long long>(l) * a.ncol + col));
+        }
+      }
+      ++pp_s;
+      if (++pp_ch == nchunk) { pp_ch = 0; pp_tile += gridDim.x; }
+    };
+    for (int d = 0; d < kDepth + kPrefetch; ++d) prefetch_next();
     float2 ring[kDepth][2];
 #pragma unroll
     for (int d = 0; d < kDepth; ++d) load_next(ring[d]);
@@ -290,6 +309,7 @@ __global__ void __launch_bounds__(kWorkers + 32, 1) dlr_tc_kernel(TcArgs a) {
 #pragma unroll
         for (int d = 0; d + 1 < kDepth; ++d) { ring[d][0] = ring[d + 1][0]; ring[d][1] = ring[d + 1][1]; }
         load_next(ring[kDepth - 1]);
+        prefetch_next();
         uint16_t h[3][4];
         split3(c0.x, h[0][0], h[1][0], h[2][0]);
         split3(c0.y, h[0][1], h[1][1], h[2][1]);
