@@ -340,11 +340,14 @@ __device__ __forceinline__ float4 lds_pair(const float2* tile, int row, int pair
   return *reinterpret_cast<const float4*>(tile + row * MAXN + 2 * (pair ^ (row & (MAXN / 2 - 1))));
 }
 
-template <int MAXN>
-__global__ void __launch_bounds__(kWarpsR * 32, 3) dyson_w_tile_kernel(const float2* __restrict__ P,
+// NFIX > 0: the system size is the compile-time constant NFIX (n is ignored), so
+// every size test below folds away; NFIX = 0: runtime n <= MAXN.
+template <int MAXN, int NFIX>
+__global__ void __launch_bounds__(kWarpsR * 32, NFIX > 0 ? 2 : 3) dyson_w_tile_kernel(const float2* __restrict__ P,
                                                                    const float2* __restrict__ Vq,
-                                                                   float2* WC, int n, int nk,
+                                                                   float2* WC, int n_arg, int nk,
                                                                    int* err, long long* first_bad) {
+  const int n = NFIX > 0 ? NFIX : n_arg;
   static_assert(MAXN == 4 || MAXN == 8 || MAXN == 16, "tile width");
   constexpr int W = MAXN;                      // lanes per system
   constexpr int SPW = 32 / W;
@@ -528,12 +531,12 @@ __global__ void __launch_bounds__(kWarpsR * 32, 3) dyson_w_tile_kernel(const flo
   }
 }
 
-template <int MAXN>
+template <int MAXN, int NFIX = 0>
 cudaError_t launch_dyson_w_tile(const void* P, const void* Vq, void* WC, int r, int n, int nk,
                                 int* err, long long* first_bad, cudaStream_t st) {
   constexpr int NSYS = kWarpsR * (32 / MAXN);
   const size_t smem = (static_cast<size_t>(2) * NSYS * (MAXN * MAXN + 2) + NSYS * 4 * MAXN) * sizeof(float2);
-  auto fn = &dyson_w_tile_kernel<MAXN>;
+  auto fn = &dyson_w_tile_kernel<MAXN, NFIX>;
   cudaError_t e = set_smem(reinterpret_cast<const void*>(fn), smem);
   if (e != cudaSuccess) return e;
   dim3 grid((nk + NSYS - 1) / NSYS, r);
@@ -934,6 +937,8 @@ cudaError_t launch_dyson_w(const void* P, const void* Vq, void* WC, int r, int n
     // register-row kernel: W^C = (1 - V P)^-1 V P V directly
     if (npair <= 4) return launch_dyson_w_tile<4>(P, Vq, WC, r, npair, nk, err, first_bad, st);
     if (npair <= 8) return launch_dyson_w_tile<8>(P, Vq, WC, r, npair, nk, err, first_bad, st);
+    if (npair == 15) return launch_dyson_w_tile<16, 15>(P, Vq, WC, r, npair, nk, err, first_bad, st);
+    if (npair == 16) return launch_dyson_w_tile<16, 16>(P, Vq, WC, r, npair, nk, err, first_bad, st);
     if (npair <= 16) return launch_dyson_w_tile<16>(P, Vq, WC, r, npair, nk, err, first_bad, st);
     return launch_dyson_w_reg<25, 32>(P, Vq, WC, r, npair, nk, err, first_bad, st);
   }
