@@ -679,7 +679,7 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
   if (c->reduced)
     QA_LAUNCH(c, 1, qa::launch_sigma_reduced<T>(c->d_GR, c->d_W, c->d_tsig, c->d_csig,
                                                 static_cast<int>(c->tsig.idx.size()), c->d_SigC, r,
-                                                c->norb, c->rho, nk, st));
+                                                c->norb, c->rho, nk, st, c->tsig.distinct_targets));
   else
     QA_LAUNCH(c, 1, qa::launch_sigma<T>(c->d_GR, c->d_W, c->d_SigC, r, c->norb, nk, st));
   tm.mark();  // 8: Sigma contraction

@@ -196,6 +196,13 @@ void pair_basis_terms(const std::vector<std::complex<double>>& B, int norb, int 
       bubble->off.push_back(static_cast<int>(bubble->idx.size()));
       sigma->off.push_back(static_cast<int>(sigma->idx.size()));
     }
+  for (PairTerms* t : {bubble, sigma}) {
+    t->distinct_targets = true;
+    for (size_t o = 0; o + 1 < t->off.size() && t->distinct_targets; ++o)
+      for (int e = t->off[o]; e < t->off[o + 1] && t->distinct_targets; ++e)
+        for (int f = e + 1; f < t->off[o + 1]; ++f)
+          if ((t->idx[e] >> 8) == (t->idx[f] >> 8)) { t->distinct_targets = false; break; }
+  }
 }
 
 }  // namespace qa

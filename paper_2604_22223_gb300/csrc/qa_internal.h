@@ -59,6 +59,7 @@ struct PairTerms {
   std::vector<int> off;
   std::vector<int> idx;
   std::vector<std::complex<double>> coef;
+  bool distinct_targets = false;   // no output list holds two terms with the same idx >> 8
 };
 void pair_basis_terms(const std::vector<std::complex<double>>& B, int norb, int rho, double s,
                       PairTerms* bubble, PairTerms* sigma);
@@ -145,10 +146,12 @@ template <typename T>
 cudaError_t launch_bubble_reduced(const void* GR, const void* GreflR, const int* mR,
                                   const int* terms, const void* coef, int nterm, void* Pt, int r,
                                   int norb, int rho, int nk, cudaStream_t st);
+// distinct != 0 (PairTerms::distinct_targets): the terms of one output entry
+// update distinct Sigma entries and run in parallel.
 template <typename T>
 cudaError_t launch_sigma_reduced(const void* GR, const void* Wt, const int* terms, const void* coef,
                                  int nterm, void* Sig, int r, int norb, int rho, int nk,
-                                 cudaStream_t st);
+                                 cudaStream_t st, int distinct = 0);
 
 // Dyson for G.  prep: Bm[n][a][b][k] = (mu_ref - H(k) - SigHF(k))_ab - SigIw[n][a][b][k]
 // (SigHF FP64 [N_k][norb][norb] and SigIw may be null) and per-block bounds

@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(RedTpb<T>::v) bubble_reduced_kernel(
 // thread) before their terms are applied.
 constexpr int kWb = 16;
 
-template <typename T>
+template <typename T, bool DISTINCT>
 __global__ void __launch_bounds__(RedTpb<T>::v) sigma_reduced_kernel(
     const cplx<T>* __restrict__ GR, const cplx<T>* __restrict__ Wt, const int* __restrict__ terms,
     const cplx<T>* __restrict__ coef, int nterm, cplx<T>* __restrict__ Sig, int no2, int nout,
@@ -131,7 +131,26 @@ __global__ void __launch_bounds__(RedTpb<T>::v) sigma_reduced_kernel(
     for (int u = 0; u < kWb; ++u) {
       if (o0 + u < nout) {
         const int e1 = s_off[o0 + u + 1];
-        for (int e = s_off[o0 + u]; e < e1; ++e) {
+        int e = s_off[o0 + u];
+        if (DISTINCT) {
+          // the terms of one output entry update distinct accumulators: four at a
+          // time, all loads before the stores
+          for (; e + 4 <= e1; e += 4) {
+            TermRec<T> rr[4];
+            V* sp[4];
+            V acc[4], gv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              rr[q] = s_rec[e + q];
+              sp[q] = sg + (rr[q].idx >> 8) * TPB + tid;
+              acc[q] = *sp[q];
+              gv[q] = g[(rr[q].idx & 255) * TPB + tid];
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) *sp[q] = cfma(cmul(rr[q].c, wb[u]), gv[q], acc[q]);
+          }
+        }
+        for (; e < e1; ++e) {
           const TermRec<T> r0 = s_rec[e];
           V* sp = sg + (r0.idx >> 8) * TPB + tid;
           *sp = cfma(cmul(r0.c, wb[u]), g[(r0.idx & 255) * TPB + tid], *sp);
@@ -172,15 +191,16 @@ cudaError_t launch_bubble_reduced(const void* GR, const void* GreflR, const int*
 template <typename T>
 cudaError_t launch_sigma_reduced(const void* GR, const void* Wt, const int* terms, const void* coef,
                                  int nterm, void* Sig, int r, int norb, int rho, int nk,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, int distinct) {
   if (nterm < 0 || nterm > kMaxPairTerms || norb > 5 || rho < 1) return cudaErrorInvalidValue;
   const int no2 = norb * norb, nout = rho * rho;
   const size_t smem = reduced_smem<T>(no2, nout, nterm);
-  cudaError_t e = set_smem(reinterpret_cast<const void*>(&sigma_reduced_kernel<T>), smem);
+  auto fn = distinct ? &sigma_reduced_kernel<T, true> : &sigma_reduced_kernel<T, false>;
+  cudaError_t e = set_smem(reinterpret_cast<const void*>(fn), smem);
   if (e != cudaSuccess) return e;
   constexpr int TPB = RedTpb<T>::v;
   dim3 grid((nk + TPB - 1) / TPB, r);
-  sigma_reduced_kernel<T><<<grid, TPB, smem, st>>>(
+  fn<<<grid, TPB, smem, st>>>(
       reinterpret_cast<const cplx<T>*>(GR), reinterpret_cast<const cplx<T>*>(Wt), terms,
       reinterpret_cast<const cplx<T>*>(coef), nterm, reinterpret_cast<cplx<T>*>(Sig), no2, nout, nk);
   return cudaGetLastError();
@@ -193,8 +213,8 @@ template cudaError_t launch_bubble_reduced<float>(const void*, const void*, cons
                                                   const void*, int, void*, int, int, int, int,
                                                   cudaStream_t);
 template cudaError_t launch_sigma_reduced<double>(const void*, const void*, const int*, const void*,
-                                                  int, void*, int, int, int, int, cudaStream_t);
+                                                  int, void*, int, int, int, int, cudaStream_t, int);
 template cudaError_t launch_sigma_reduced<float>(const void*, const void*, const int*, const void*,
-                                                 int, void*, int, int, int, int, cudaStream_t);
+                                                 int, void*, int, int, int, int, cudaStream_t, int);
 
 }  // namespace qa
