@@ -17,7 +17,7 @@
 namespace qa {
 namespace {
 
-template <typename T> struct RedTpb { static constexpr int v = 128; };
+template <typename T> struct RedTpb { static constexpr int v = 256; };
 template <> struct RedTpb<double> { static constexpr int v = 64; };
 
 // one term as a single shared-memory record (one 16- or 32-byte load)
