@@ -213,10 +213,14 @@ __device__ __forceinline__ void ld_seg_brev(const V* __restrict__ p, V (&x)[L], 
 // (one padding element per 2^lp points spreads the strided passes over the
 // banks); the last pass writes global memory directly (consecutive threads own
 // consecutive columns, so each of its stores is coalesced).
-template <typename T, bool BUB, int SIGN>
-__global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1)
-    fft3d_reg_kernel(int l1, int l2, int l3, const cplx<T>* in, cplx<T>* out, int lpb,
+// L1C, L2C, L3C >= 0: the log2 axis lengths as compile-time constants (every
+// pass compiles to its one transform length, which lowers the register need
+// enough for three blocks per SM in FP32); -1: runtime lengths.
+template <typename T, bool BUB, int SIGN, int L1C, int L2C, int L3C>
+__global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? (L1C >= 0 ? 3 : 2) : 1)
+    fft3d_reg_kernel(int l1_arg, int l2_arg, int l3_arg, const cplx<T>* in, cplx<T>* out, int lpb,
                      long long nlines, int lp, T scale, int vec, BubbleSrc bs) {
+  const int l1 = L1C >= 0 ? L1C : l1_arg, l2 = L2C >= 0 ? L2C : l2_arg, l3 = L3C >= 0 ? L3C : l3_arg;
   using V = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   V* tc = reinterpret_cast<V*>(smem_raw);                 // [bs.mt] term coefficients (BUB)
@@ -278,7 +282,9 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1)
     __syncthreads();
   }
   const int na = (l1 > 0) + (l2 > 0) + (l3 > 0);       // non-trivial axes, innermost first
-  for (int pass = 0; pass < na; ++pass) {
+#pragma unroll
+  for (int pass = 0; pass < 3; ++pass) {
+    if (pass >= na) break;
     const bool first = pass == 0, last = pass == na - 1;
     int lL = 0, lS = 0;                                 // log2 length and log2 stride of the axis
     {
@@ -352,12 +358,17 @@ cudaError_t launch_fft3d_reg(const FftDev& plan, int sign, const void* in, void*
   const size_t extra = BUB ? static_cast<size_t>(bs.mt) * (sizeof(cplx<T>) + sizeof(int)) : 0;
   const size_t smem = static_cast<size_t>(lpb) * line_sz * sizeof(cplx<T>) + extra;
   const int vec = BUB ? 0 : aligned16(in);
-  auto fn = sign > 0 ? &fft3d_reg_kernel<T, BUB, 1> : &fft3d_reg_kernel<T, BUB, -1>;
+  const int l1 = ilog2(plan.n[0]), l2 = ilog2(plan.n[1]), l3 = ilog2(plan.n[2]);
+  auto fn = sign > 0 ? &fft3d_reg_kernel<T, BUB, 1, -1, -1, -1> : &fft3d_reg_kernel<T, BUB, -1, -1, -1, -1>;
+  if (l1 == 5 && l2 == 5 && l3 == 3)          // 32 x 32 x 8
+    fn = sign > 0 ? &fft3d_reg_kernel<T, BUB, 1, 5, 5, 3> : &fft3d_reg_kernel<T, BUB, -1, 5, 5, 3>;
+  else if (l1 == 4 && l2 == 4 && l3 == 3)     // 16 x 16 x 8
+    fn = sign > 0 ? &fft3d_reg_kernel<T, BUB, 1, 4, 4, 3> : &fft3d_reg_kernel<T, BUB, -1, 4, 4, 3>;
   cudaError_t e = set_smem(reinterpret_cast<const void*>(fn), smem, true);
   if (e != cudaSuccess) return e;
   long long nblk = (nlines + lpb - 1) / lpb;
   fn<<<static_cast<unsigned>(nblk), kFftThreads, smem, st>>>(
-      ilog2(plan.n[0]), ilog2(plan.n[1]), ilog2(plan.n[2]), reinterpret_cast<const cplx<T>*>(in),
+      l1, l2, l3, reinterpret_cast<const cplx<T>*>(in),
       reinterpret_cast<cplx<T>*>(out), lpb, nlines, lp, sc, vec, bs);
   return cudaGetLastError();
 }

@@ -329,6 +329,10 @@ def config(name: str) -> Model:
         return peierls_two_orbital(n=(4, 4, 2), name="peierls-4x4x2")
     if name == "five-orbital-2x4x4":
         return five_orbital(n=(2, 4, 4), beta=10.0, Lambda=200.0, name="five-orbital-2x4x4")
+    if name == "peierls-32x32x8":             # the bench grid shape (specialised FFT kernels)
+        return peierls_two_orbital(n=(32, 32, 8), name="peierls-32x32x8")
+    if name == "peierls-16x16x8":
+        return peierls_two_orbital(n=(16, 16, 8), name="peierls-16x16x8")
     if name == "square-16x1x1":               # one non-trivial axis
         return square_single_band(n=(16, 1, 1), name="square-16x1x1")
     if name == "square-1x1":
