@@ -134,6 +134,7 @@ struct qa_ctx {
   double2* d_wq = nullptr;        // [2][r] weights of Sigma(+i w0), Sigma(-i w0)
   bool sighf_valid = false;       // d_SigHF holds the last step's (or the HF loop's) Sigma^HF
   bool sigc_valid = false;        // d_SigIw holds the last step's Sigma^C(k, i w)
+  qa::DysonBlocks dblk;           // diagonal blocks of S(q) on the reduced basis (nblk = 0: none)
 };
 
 namespace {
@@ -217,6 +218,32 @@ int setup_pairs(qa_ctx* c, bool bound) {
           for (int j = 0; j < rho; ++j) S[static_cast<size_t>(i) * rho + j] += bi * XB[static_cast<size_t>(A) * rho + j];
         }
     }
+  }
+  // diagonal blocks of S: indices coupled by some S(R) entry, as contiguous ranges
+  c->dblk = qa::DysonBlocks{};
+  if (red && rho <= 16) {
+    std::vector<int> comp(rho);
+    for (int i = 0; i < rho; ++i) comp[i] = i;
+    auto root = [&](int x) { while (comp[x] != x) x = comp[x] = comp[comp[x]]; return x; };
+    for (int v = 0; v < c->nV; ++v)
+      for (int i = 0; i < rho; ++i)
+        for (int k = 0; k < rho; ++k)
+          if (c->sV[(static_cast<size_t>(v) * rho + i) * rho + k] != cd(0, 0)) comp[root(i)] = root(k);
+    bool contiguous = true;
+    int nblk = 0;
+    for (int i = 0; i < rho && contiguous;) {
+      int k = i;
+      while (k < rho && root(k) == root(i)) ++k;
+      for (int t = k; t < rho; ++t)
+        if (root(t) == root(i)) contiguous = false;
+      for (int t = i; t < k; ++t) {
+        c->dblk.lo[t] = static_cast<unsigned char>(i);
+        c->dblk.hi[t] = static_cast<unsigned char>(k);
+      }
+      ++nblk;
+      i = k;
+    }
+    c->dblk.nblk = contiguous ? nblk : 0;
   }
   return QA_OK;
 }
@@ -667,7 +694,8 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
   else
     QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Ttn, r, r, c->d_P, c->d_P, ncb, st));
   tm.mark();  // 4: DLR tau -> nu
-  QA_LAUNCH(c, 1, qa::launch_dyson_w<T>(c->d_P, c->d_Vq, c->d_W, r, c->nb, nk, c->d_err, c->d_bad, st));
+  QA_LAUNCH(c, 1, qa::launch_dyson_w<T>(c->d_P, c->d_Vq, c->d_W, r, c->nb, nk, c->d_err, c->d_bad, st,
+                                        &c->dblk));
   tm.mark();  // 5: Dyson W
   if (sizeof(T) == 4 && c->use_tc)
     QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Tnt, r, c->d_W, c->d_W, ncb, c->d_err, st));

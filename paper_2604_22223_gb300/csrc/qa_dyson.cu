@@ -342,11 +342,14 @@ __device__ __forceinline__ float4 lds_pair(const float2* tile, int row, int pair
 
 // NFIX > 0: the system size is the compile-time constant NFIX (n is ignored), so
 // every size test below folds away; NFIX = 0: runtime n <= MAXN.
-template <int MAXN, int NFIX>
+// BLK: V(q) is block diagonal (blk.lo / blk.hi per index); the products V P and
+// V P V skip its zero blocks (the skipped terms are exact zeros).
+template <int MAXN, int NFIX, bool BLK>
 __global__ void __launch_bounds__(kWarpsR * 32, NFIX > 0 ? 2 : 3) dyson_w_tile_kernel(const float2* __restrict__ P,
                                                                    const float2* __restrict__ Vq,
                                                                    float2* WC, int n_arg, int nk,
-                                                                   int* err, long long* first_bad) {
+                                                                   int* err, long long* first_bad,
+                                                                   DysonBlocks blk) {
   const int n = NFIX > 0 ? NFIX : n_arg;
   static_assert(MAXN == 4 || MAXN == 8 || MAXN == 16, "tile width");
   constexpr int W = MAXN;                      // lanes per system
@@ -414,20 +417,36 @@ __global__ void __launch_bounds__(kWarpsR * 32, NFIX > 0 ? 2 : 3) dyson_w_tile_k
   // a = row l of V P (padding rows and columns of the tiles are zero)
 #pragma unroll
   for (int j = 0; j < MAXN; ++j) a[j] = make_float2(0.f, 0.f);
-#pragma unroll
-  for (int mp = 0; mp < NPAIR; ++mp) {
-    if (2 * mp < n) {
-      const float4 vv = lds_pair<MAXN>(Vw, l, mp);
-      const float2 v0 = make_float2(vv.x, vv.y), v1 = make_float2(vv.z, vv.w);
+  if (BLK) {
+    // row l of V is non-zero only on its block [lo, hi)
+    const int lo = row ? blk.lo[l] : 0, hi = row ? blk.hi[l] : 0;
+    for (int m = lo; m < hi; ++m) {
+      const float2 vlm = Vw[swz<MAXN>(l, m)];
 #pragma unroll
       for (int jp = 0; jp < NPAIR; ++jp) {
         if (2 * jp < n) {
-          const float4 p0 = lds_pair<MAXN>(Pw, 2 * mp, jp);
-          const float4 p1 = lds_pair<MAXN>(Pw, 2 * mp + 1, jp);
-          a[2 * jp] = cfma(v0, make_float2(p0.x, p0.y), a[2 * jp]);
-          a[2 * jp] = cfma(v1, make_float2(p1.x, p1.y), a[2 * jp]);
-          a[2 * jp + 1] = cfma(v0, make_float2(p0.z, p0.w), a[2 * jp + 1]);
-          a[2 * jp + 1] = cfma(v1, make_float2(p1.z, p1.w), a[2 * jp + 1]);
+          const float4 p0 = lds_pair<MAXN>(Pw, m, jp);
+          a[2 * jp] = cfma(vlm, make_float2(p0.x, p0.y), a[2 * jp]);
+          a[2 * jp + 1] = cfma(vlm, make_float2(p0.z, p0.w), a[2 * jp + 1]);
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int mp = 0; mp < NPAIR; ++mp) {
+      if (2 * mp < n) {
+        const float4 vv = lds_pair<MAXN>(Vw, l, mp);
+        const float2 v0 = make_float2(vv.x, vv.y), v1 = make_float2(vv.z, vv.w);
+#pragma unroll
+        for (int jp = 0; jp < NPAIR; ++jp) {
+          if (2 * jp < n) {
+            const float4 p0 = lds_pair<MAXN>(Pw, 2 * mp, jp);
+            const float4 p1 = lds_pair<MAXN>(Pw, 2 * mp + 1, jp);
+            a[2 * jp] = cfma(v0, make_float2(p0.x, p0.y), a[2 * jp]);
+            a[2 * jp] = cfma(v1, make_float2(p1.x, p1.y), a[2 * jp]);
+            a[2 * jp + 1] = cfma(v0, make_float2(p0.z, p0.w), a[2 * jp + 1]);
+            a[2 * jp + 1] = cfma(v1, make_float2(p1.z, p1.w), a[2 * jp + 1]);
+          }
         }
       }
     }
@@ -438,9 +457,11 @@ __global__ void __launch_bounds__(kWarpsR * 32, NFIX > 0 ? 2 : 3) dyson_w_tile_k
 #pragma unroll
   for (int m = 0; m < MAXN; ++m) {
     if (m < n) {
+      const int mlo = BLK ? blk.lo[m] : 0, mhi = BLK ? blk.hi[m] : MAXN;
 #pragma unroll
       for (int jp = 0; jp < NPAIR; ++jp) {
-        if (2 * jp < n) {
+        // (uniform test: the columns 2 jp, 2 jp + 1 meet row m's block)
+        if (2 * jp < n && 2 * jp + 1 >= mlo && 2 * jp < mhi) {
           const float4 vr = lds_pair<MAXN>(Vw, m, jp);
           b[2 * jp] = cfma(a[m], make_float2(vr.x, vr.y), b[2 * jp]);
           b[2 * jp + 1] = cfma(a[m], make_float2(vr.z, vr.w), b[2 * jp + 1]);
@@ -533,16 +554,19 @@ __global__ void __launch_bounds__(kWarpsR * 32, NFIX > 0 ? 2 : 3) dyson_w_tile_k
 
 template <int MAXN, int NFIX = 0>
 cudaError_t launch_dyson_w_tile(const void* P, const void* Vq, void* WC, int r, int n, int nk,
-                                int* err, long long* first_bad, cudaStream_t st) {
+                                int* err, long long* first_bad, cudaStream_t st,
+                                const DysonBlocks* blk) {
   constexpr int NSYS = kWarpsR * (32 / MAXN);
   const size_t smem = (static_cast<size_t>(2) * NSYS * (MAXN * MAXN + 2) + NSYS * 4 * MAXN) * sizeof(float2);
-  auto fn = &dyson_w_tile_kernel<MAXN, NFIX>;
+  const bool use_blk = blk && blk->nblk > 1;
+  auto fn = use_blk ? &dyson_w_tile_kernel<MAXN, NFIX, true> : &dyson_w_tile_kernel<MAXN, NFIX, false>;
   cudaError_t e = set_smem(reinterpret_cast<const void*>(fn), smem);
   if (e != cudaSuccess) return e;
   dim3 grid((nk + NSYS - 1) / NSYS, r);
   fn<<<grid, kWarpsR * 32, smem, st>>>(reinterpret_cast<const float2*>(P),
                                        reinterpret_cast<const float2*>(Vq),
-                                       reinterpret_cast<float2*>(WC), n, nk, err, first_bad);
+                                       reinterpret_cast<float2*>(WC), n, nk, err, first_bad,
+                                       use_blk ? *blk : DysonBlocks{});
   return cudaGetLastError();
 }
 
@@ -931,15 +955,16 @@ int dyson_g_blocks(int r, int nk) {
 
 template <typename T>
 cudaError_t launch_dyson_w(const void* P, const void* Vq, void* WC, int r, int npair, int nk,
-                           int* err, long long* first_bad, cudaStream_t st) {
+                           int* err, long long* first_bad, cudaStream_t st,
+                           const DysonBlocks* blk) {
   if (npair > kMaxPair) return cudaErrorInvalidValue;
   if (sizeof(T) == 4) {
     // register-row kernel: W^C = (1 - V P)^-1 V P V directly
-    if (npair <= 4) return launch_dyson_w_tile<4>(P, Vq, WC, r, npair, nk, err, first_bad, st);
-    if (npair <= 8) return launch_dyson_w_tile<8>(P, Vq, WC, r, npair, nk, err, first_bad, st);
-    if (npair == 15) return launch_dyson_w_tile<16, 15>(P, Vq, WC, r, npair, nk, err, first_bad, st);
-    if (npair == 16) return launch_dyson_w_tile<16, 16>(P, Vq, WC, r, npair, nk, err, first_bad, st);
-    if (npair <= 16) return launch_dyson_w_tile<16>(P, Vq, WC, r, npair, nk, err, first_bad, st);
+    if (npair <= 4) return launch_dyson_w_tile<4>(P, Vq, WC, r, npair, nk, err, first_bad, st, blk);
+    if (npair <= 8) return launch_dyson_w_tile<8>(P, Vq, WC, r, npair, nk, err, first_bad, st, blk);
+    if (npair == 15) return launch_dyson_w_tile<16, 15>(P, Vq, WC, r, npair, nk, err, first_bad, st, blk);
+    if (npair == 16) return launch_dyson_w_tile<16, 16>(P, Vq, WC, r, npair, nk, err, first_bad, st, blk);
+    if (npair <= 16) return launch_dyson_w_tile<16>(P, Vq, WC, r, npair, nk, err, first_bad, st, blk);
     return launch_dyson_w_reg<25, 32>(P, Vq, WC, r, npair, nk, err, first_bad, st);
   }
   size_t smem = static_cast<size_t>(kWarpsW) * 2 * npair * (npair + 1) * sizeof(cplx<T>);
@@ -1021,9 +1046,9 @@ cudaError_t launch_reduce_pairs(const double* part, int n, int op_max, double* o
 }
 
 template cudaError_t launch_dyson_w<double>(const void*, const void*, void*, int, int, int, int*,
-                                            long long*, cudaStream_t);
+                                            long long*, cudaStream_t, const DysonBlocks*);
 template cudaError_t launch_dyson_w<float>(const void*, const void*, void*, int, int, int, int*,
-                                           long long*, cudaStream_t);
+                                           long long*, cudaStream_t, const DysonBlocks*);
 template cudaError_t launch_dyson_g<double>(const void*, const void*, const double*, double, int,
                                             int, int, void*, double*, int, int, int*, cudaStream_t);
 template cudaError_t launch_dyson_g<float>(const void*, const void*, const double*, double, int, int,

@@ -127,10 +127,20 @@ template <typename T>
 cudaError_t launch_bubble(const void* GR, const void* GreflR, const int* mR, void* P, int r,
                           int norb, int nk, double s, cudaStream_t st);
 
-// W^C(q, i nu) from P(q, i nu) and V(q): per (nu, q) system of size npair.
+// Diagonal blocks of V(q) (or S(q)): index i couples only to [lo[i], hi[i]);
+// nblk = 0: no block structure known.
+struct DysonBlocks {
+  int nblk = 0;
+  unsigned char lo[16] = {0}, hi[16] = {0};
+};
+
+// W^C(q, i nu) from P(q, i nu) and V(q): per (nu, q) system of size npair.  blk
+// (optional, FP32 systems of size <= 16): V(q)'s block structure, used to skip
+// its zero blocks in V P and V P V.
 template <typename T>
 cudaError_t launch_dyson_w(const void* P, const void* Vq, void* WC, int r, int npair, int nk,
-                           int* err, long long* first_bad, cudaStream_t st);
+                           int* err, long long* first_bad, cudaStream_t st,
+                           const DysonBlocks* blk = nullptr);
 
 // Sigma^C[t][a][d][R] = -sum_bc G[t][b][c][R] W^C[t][(ab)][(cd)][R]
 template <typename T>
