@@ -93,6 +93,27 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def s_block_sizes(ctx):
+    """Size of the diagonal block of S = B^H V(R) B (all listed R) containing each
+    reduced index: indices coupled by a non-zero entry, connected components."""
+    import numpy as np
+    B = ctx.basis
+    rho = B.shape[1]
+    parent = list(range(rho))
+
+    def root(x):
+        while parent[x] != x:
+            parent[x] = parent[parent[x]]
+            x = parent[x]
+        return x
+    for V in np.asarray(ctx.model.V):
+        S = B.conj().T @ V @ B
+        for i, k in zip(*np.nonzero(np.abs(S) > 0)):
+            parent[root(int(i))] = root(int(k))
+    roots = [root(i) for i in range(rho)]
+    return [roots.count(roots[i]) for i in range(rho)]
+
+
 def stage_costs(ctx, mixed: bool):
     """Algorithmic bytes and flops per launch of each big-tensor stage.
 
@@ -108,6 +129,12 @@ def stage_costs(ctx, mixed: bool):
     lg = math.log2(nk)
     n = nb
     fd = 8 * (n ** 3 + (n ** 3 if mixed else 0) + n ** 3 / 3 + n ** 3)   # VP, [VPV], LU, solve
+    if mixed and ctx.reduced and n <= 16:
+        # the FP32 tile kernel: S P and S P S over the diagonal blocks of S only, then
+        # Gauss-Jordan on [A | B] (n - 1 rows x (2n - 1 - c) entries per column c) and
+        # the final row scaling
+        blk = s_block_sizes(ctx)
+        fd = 8 * (2 * n * sum(blk[i] for i in range(n)) + (n - 1) * n * (3 * n - 1) / 2 + n * n)
     return {
         "bubble": (X * es + 2 * Y * es, 6 * X),
         "fft_R_to_q": (X * es + 2 * Y * es, 5 * X * lg + 6 * X),
