@@ -441,6 +441,15 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier(pg)
     ms_e2e = max_over_ranks(pg, e0.elapsed_time(e1), dev)
+    # host <-> device copy rates of this machine (one pinned copy each way, alone)
+    rates = {}
+    for name, dst, src in (("h2d_gbs", Gd_in[0], Gh_in), ("d2h_gbs", Gh_out[0], Gd_out[0])):
+        torch.cuda.synchronize()
+        e0.record()
+        dst.copy_(src, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        rates[name] = Gh_in.numel() * Gh_in.element_size() / (e0.elapsed_time(e1) * 1e-3) / 1e9
     gbytes = Gh_in.numel() * Gh_in.element_size()
     r, nk, no, rho, nb = ctx.r, ctx.nk, ctx.norb, ctx.rho, ctx.nb
     hfqp = hf_qp_timing(ctx, pk)
@@ -503,7 +512,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": gbytes + 8 + no * no * 16,
                 "copies": "pinned host G in and out every step on a second stream, overlapped with "
                           "the neighbouring steps (double-buffered)",
-                "serial_value": world * K2 / (ms_e2e_serial / 1e3)},
+                "serial_value": world * K2 / (ms_e2e_serial / 1e3), **rates},
         "gpu_launches": launches,
         "clocks": ck,
     }

@@ -34,6 +34,18 @@ struct DevTables {          // DLR matrices in one precision (complex)
 
 }  // namespace
 
+// Scalar results the host reads after every density evaluation and at the end
+// of a call: pinned host memory that the kernels write through its device
+// alias, so reading them needs a stream synchronisation but no copy (copies of
+// large buffers on other streams, which share the copy engines, never delay them).
+struct QaMailbox {
+  double red[2];            // reduction results
+  long long bad;            // first failing (nu, q) or (n, k) index
+  int err;                  // device error word
+  int pad;
+  double2 nloc[25];         // local density matrix
+};
+
 struct qa_ctx {
   // problem
   int n[3] = {1, 1, 1};
@@ -135,6 +147,12 @@ struct qa_ctx {
   bool sighf_valid = false;       // d_SigHF holds the last step's (or the HF loop's) Sigma^HF
   bool sigc_valid = false;        // d_SigIw holds the last step's Sigma^C(k, i w)
   qa::DysonBlocks dblk;           // diagonal blocks of S(q) on the reduced basis (nblk = 0: none)
+  QaMailbox* mb = nullptr;        // pinned host mailbox (qa_bind) and its device alias
+  QaMailbox* mb_dev = nullptr;
+  size_t ws_need = 0;             // workspace bytes of the bound layout
+  ~qa_ctx() {
+    if (mb) cudaFreeHost(mb);
+  }
 };
 
 namespace {
@@ -423,8 +441,9 @@ int prepare_g(qa_ctx* c, const double2* SigHF, const void* SigIw, double mu_ref,
                                              c->d_Bm, c->d_part, c->nblocks_g, st));
   QA_LAUNCH(c, 1, qa::launch_reduce_pairs(c->d_part, c->nblocks_g, 1, c->d_red, st));
   double h[2];
-  QA_TRY(cudaMemcpyAsync(h, c->d_red, 16, cudaMemcpyDeviceToHost, st));
   QA_TRY(cudaStreamSynchronize(st));
+  h[0] = c->mb->red[0];
+  h[1] = c->mb->red[1];
   *bound = h[0];
   return QA_OK;
 }
@@ -437,8 +456,9 @@ int eval_density(qa_ctx* c, const DevTables& tab, double mu, double* N, double* 
                                         c->nk, nullptr, c->d_part, c->nblocks_g, 0, c->d_err, st));
   QA_LAUNCH(c, 1, qa::launch_reduce_pairs(c->d_part, c->nblocks_g, 0, c->d_red, st));
   double h[2];
-  QA_TRY(cudaMemcpyAsync(h, c->d_red, 16, cudaMemcpyDeviceToHost, st));
   QA_TRY(cudaStreamSynchronize(st));
+  h[0] = c->mb->red[0];
+  h[1] = c->mb->red[1];
   *N = c->nspin * h[0] / c->nk;
   *dN = -c->nspin * h[1] / c->nk;
   return QA_OK;
@@ -546,8 +566,9 @@ int mu_search(qa_ctx* c, const double2* SigHF, const void* SigIw, const DevTable
                                               c->d_err, st));
     QA_LAUNCH(c, 1, qa::launch_reduce_pairs(c->d_part, c->nblocks_g, 0, c->d_red, st));
     double h2[2];
-    QA_TRY(cudaMemcpyAsync(h2, c->d_red, 16, cudaMemcpyDeviceToHost, st));
     QA_TRY(cudaStreamSynchronize(st));
+    h2[0] = c->mb->red[0];
+    h2[1] = c->mb->red[1];
     ++count;
     const double N64 = c->nspin * h2[0] / c->nk;
     const double d64 = -c->nspin * h2[1] / c->nk;
@@ -567,11 +588,9 @@ int mu_search(qa_ctx* c, const double2* SigHF, const void* SigIw, const DevTable
 }
 
 int check_err(qa_ctx* c, qa_step_stats* stats, cudaStream_t st) {
-  int herr = 0;
-  long long hbad = -1;
-  QA_TRY(cudaMemcpyAsync(&herr, c->d_err, 4, cudaMemcpyDeviceToHost, st));
-  QA_TRY(cudaMemcpyAsync(&hbad, c->d_bad, 8, cudaMemcpyDeviceToHost, st));
   QA_TRY(cudaStreamSynchronize(st));
+  const int herr = c->mb->err;
+  const long long hbad = c->mb->bad;
   if (stats) {
     stats->status = herr;
     stats->first_bad = herr ? hbad : -1;
@@ -580,8 +599,10 @@ int check_err(qa_ctx* c, qa_step_stats* stats, cudaStream_t st) {
 }
 
 int reset_err(qa_ctx* c, cudaStream_t st) {
-  QA_TRY(cudaMemsetAsync(c->d_err, 0, 4, st));
-  QA_TRY(cudaMemsetAsync(c->d_bad, 0x7f, 8, st));
+  // host writes, ordered after the stream's earlier work
+  QA_TRY(cudaStreamSynchronize(st));
+  c->mb->err = 0;
+  c->mb->bad = 0x7f7f7f7f7f7f7f7fLL;
   return QA_OK;
 }
 
@@ -606,9 +627,8 @@ int finish_g(qa_ctx* c, const DevTables& tab, double mu, void* G_out_c128, doubl
     // n(k) = sum_n dw_n G(k, i w_n), then its k-average (n(R = 0))
     QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.dw, 1, c->r, c->d_Giw, c->d_Gt, ncol, st));
     QA_LAUNCH(c, 1, qa::launch_k_average<T>(c->d_Gt, c->norb * c->norb, c->nk, c->d_nloc, st));
-    QA_TRY(cudaMemcpyAsync(n_out, c->d_nloc, static_cast<size_t>(c->norb) * c->norb * 16,
-                           cudaMemcpyDeviceToHost, st));
     QA_TRY(cudaStreamSynchronize(st));
+    std::memcpy(n_out, c->mb->nloc, static_cast<size_t>(c->norb) * c->norb * 16);
   }
   return QA_OK;
 }
@@ -888,8 +908,9 @@ int fd_eval(qa_ctx* c, const double* E, double mu, double* N, double* dN, cudaSt
   QA_LAUNCH(c, 1, qa::launch_fd_sum(E, n, c->beta, mu, c->d_part, nb, st));
   QA_LAUNCH(c, 1, qa::launch_reduce_pairs(c->d_part, nb, 0, c->d_red, st));
   double h[2];
-  QA_TRY(cudaMemcpyAsync(h, c->d_red, 16, cudaMemcpyDeviceToHost, st));
   QA_TRY(cudaStreamSynchronize(st));
+  h[0] = c->mb->red[0];
+  h[1] = c->mb->red[1];
   *N = c->nspin * h[0] / c->nk;
   *dN = c->nspin * h[1] / c->nk;
   return QA_OK;
@@ -906,8 +927,9 @@ int fd_mu(qa_ctx* c, const double* E, double* mu_out, int* evals, cudaStream_t s
   QA_LAUNCH(c, 1, qa::launch_fd_range(E, n, c->d_part, nb, st));
   QA_LAUNCH(c, 1, qa::launch_reduce_pairs(c->d_part, nb, 1, c->d_red, st));
   double h[2];
-  QA_TRY(cudaMemcpyAsync(h, c->d_red, 16, cudaMemcpyDeviceToHost, st));
   QA_TRY(cudaStreamSynchronize(st));
+  h[0] = c->mb->red[0];
+  h[1] = c->mb->red[1];
   if (!std::isfinite(h[0]) || !std::isfinite(h[1])) return QA_ERANGE;
   double lo = -h[1] - 1.0 - 40.0 / c->beta, hi = h[0] + 1.0 + 40.0 / c->beta;
   const double target = c->filling, tolN = 1e-12 * std::max(1.0, target);
@@ -974,10 +996,9 @@ int hf_solve_impl(qa_ctx* c, int max_iter, double tol, double mix, void* G_out, 
                                   c->n[0], c->n[1], c->n[2], c->d_sigFR, c->d_SigHF, st, c->d_phV));
     QA_LAUNCH(c, 1, qa::launch_mix(c->d_SigHF, h.old, mix, nsig, c->d_part, nb, st));
     QA_LAUNCH(c, 1, qa::launch_reduce_pairs(c->d_part, nb, 1, c->d_red, st));
-    double hr[2];
-    QA_TRY(cudaMemcpyAsync(hr, c->d_red, 16, cudaMemcpyDeviceToHost, st));
-    if (int rc = hf_density(c, h, c->d_SigHF, &mu, &evals, st)) return rc;   // synchronises
-    resid = hr[0];
+    QA_TRY(cudaStreamSynchronize(st));
+    resid = c->mb->red[0];                 // read before the mu search reuses the mailbox
+    if (int rc = hf_density(c, h, c->d_SigHF, &mu, &evals, st)) return rc;
     if (!std::isfinite(resid)) return QA_ERANGE;
     if (resid <= tol) break;
   }
@@ -991,8 +1012,8 @@ int hf_solve_impl(qa_ctx* c, int max_iter, double tol, double mix, void* G_out, 
     } else {
       // local density n(R = 0) of the HF solution: k-average of n(k)
       QA_LAUNCH(c, 1, qa::launch_k_average<double>(c->d_nk, no2, c->nk, c->d_nloc, st));
-      QA_TRY(cudaMemcpyAsync(n_out, c->d_nloc, static_cast<size_t>(no2) * 16,
-                             cudaMemcpyDeviceToHost, st));
+      QA_TRY(cudaStreamSynchronize(st));
+      std::memcpy(n_out, c->mb->nloc, static_cast<size_t>(no2) * 16);
     }
   }
   QA_TRY(cudaStreamSynchronize(st));
@@ -1171,6 +1192,10 @@ int qa_get_pair_basis(const qa_ctx* c, int* rho, int* active, double* B) {
 
 int qa_workspace_size(const qa_ctx* c, size_t* bytes) {
   if (!c || !bytes) return QA_EINVAL;
+  if (c->bound) {                   // the bound layout stays as it is
+    *bytes = c->ws_need + kAlign;
+    return QA_OK;
+  }
   *bytes = layout(const_cast<qa_ctx*>(c), nullptr) + kAlign;
   return QA_OK;
 }
@@ -1185,6 +1210,16 @@ int qa_bind(qa_ctx* c, void* workspace, size_t bytes, void* stream) {
   c->ws = base + shift;
   c->ws_bytes = bytes - shift;
   layout(c, c->ws);
+  c->ws_need = need;
+  // the scalar results live in a pinned host mailbox written through its device alias
+  if (!c->mb) {
+    QA_TRY(cudaHostAlloc(reinterpret_cast<void**>(&c->mb), sizeof(QaMailbox), cudaHostAllocMapped));
+    QA_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->mb_dev), c->mb, 0));
+  }
+  c->d_red = c->mb_dev->red;
+  c->d_err = &c->mb_dev->err;
+  c->d_bad = &c->mb_dev->bad;
+  c->d_nloc = c->mb_dev->nloc;
   const int r = c->r;
   // DLR tables
   const qa::DlrMatrices& m = c->mats;
@@ -1345,8 +1380,8 @@ int qa_density(qa_ctx* c, const void* G, double* n_out, double* N_total, void* s
                                      c->r, static_cast<long long>(no2) * c->nk, nullptr, c->d_nk, st));
   QA_LAUNCH(c, 1, qa::launch_k_average<double>(c->d_nk, no2, c->nk, c->d_nloc, st));
   std::vector<double> h(2 * no2);
-  QA_TRY(cudaMemcpyAsync(h.data(), c->d_nloc, no2 * 16, cudaMemcpyDeviceToHost, st));
   QA_TRY(cudaStreamSynchronize(st));
+  std::memcpy(h.data(), c->mb->nloc, static_cast<size_t>(no2) * 16);
   double tr = 0;
   for (int a = 0; a < c->norb; ++a) tr += h[2 * (a * c->norb + a)];
   if (n_out) std::memcpy(n_out, h.data(), h.size() * 8);
