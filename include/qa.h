@@ -32,7 +32,10 @@
  *     memory.  The caller then obtains qa_workspace_size bytes of device
  *     memory (e.g. from PyTorch's allocator) and hands it over with qa_bind,
  *     which uploads the tables and builds G0.  The context owns nothing on the
- *     device; the workspace must outlive the context's use.
+ *     device; the workspace must outlive the context's use.  qa_bind also
+ *     allocates one small pinned host buffer (cudaHostAlloc, mapped, < 1 KB)
+ *     through which the kernels hand over scalar results (reductions, the
+ *     error word, the local density); qa_destroy frees it.
  *   * Device pointers passed to calls are borrowed for the duration of the call.
  *   * All GPU work is enqueued on the caller's stream (cudaStream_t passed as
  *     void*; NULL = legacy default stream).  Calls that return host scalars
