@@ -465,7 +465,8 @@ int eval_density(qa_ctx* c, const DevTables& tab, double mu, double* N, double* 
 }
 
 // Chemical potential: the root of N(mu) = filling (N increases with mu).
-// A bracket is found by marching from the warm start mu_s (the previous mu)
+// One Newton step from the warm start mu_s (the previous mu) is tried first;
+// otherwise a bracket is found by marching from the better of the two points
 // in the direction of the root with growing steps, clamped to the window
 // |mu - mu_s| <= max ||H + Sigma - mu_s|| + 1 + 10/beta outside which N is
 // empty or full; then
@@ -502,6 +503,15 @@ int mu_search(qa_ctx* c, const double2* SigHF, const void* SigIw, const DevTable
   double f = 0, d = 0;
   int rc = ev(mu, &f, &d);
   if (rc != QA_OK) return rc;
+  // from a warm start one Newton step usually lands within tolerance
+  if (std::fabs(f) > tolN && d > 0 && std::isfinite(f / d) && std::fabs(f / d) < 0.25 * wid) {
+    const double m1 = mu - f / d;
+    double f1 = 0, d1 = 0;
+    rc = ev(m1, &f1, &d1);
+    if (rc != QA_OK) return rc;
+    if (std::fabs(f1) <= tolN) { mu = m1; f = f1; d = d1; }
+    else if (std::fabs(f1) < std::fabs(f)) { mu = m1; f = f1; d = d1; }   // continue from the better point
+  }
   double lo = mu, hi = mu;
   if (std::fabs(f) > tolN) {
     // march toward the root until the sign of N - filling changes
@@ -616,12 +626,15 @@ int finish_g(qa_ctx* c, const DevTables& tab, double mu, void* G_out_c128, doubl
   if (sizeof(T) == 8) {
     QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Twt, c->r, c->r, c->d_Giw, G_out_c128, ncol, st));
   } else {
-    if (c->use_tc)
-      QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Twt, c->r, c->d_Giw, c->d_Gt, ncol, c->d_err, st));
-    else
+    if (c->use_tc) {
+      // the transform stores complex128 directly
+      QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Twt, c->r, c->d_Giw, G_out_c128, ncol, c->d_err, st,
+                                        true));
+    } else {
       QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Twt, c->r, c->r, c->d_Giw, c->d_Gt, ncol, st));
-    QA_LAUNCH(c, 1, qa::launch_c64_to_c128(static_cast<const float2*>(c->d_Gt),
-                                  static_cast<double2*>(G_out_c128), ncol * c->r, st));
+      QA_LAUNCH(c, 1, qa::launch_c64_to_c128(static_cast<const float2*>(c->d_Gt),
+                                             static_cast<double2*>(G_out_c128), ncol * c->r, st));
+    }
   }
   if (n_out) {
     // n(k) = sum_n dw_n G(k, i w_n), then its k-average (n(R = 0))

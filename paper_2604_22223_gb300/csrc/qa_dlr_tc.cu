@@ -123,6 +123,7 @@ struct TcArgs {
   int Np, Kp, r;
   const float2* in;
   float2* out;
+  double2* out64;          // when set, the result is stored here as complex128 instead
   long long ncol;
   int* err;
 };
@@ -172,6 +173,7 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parit
 // Buffer and accumulator reuse: chunk g is staged only after each worker has
 // waited for chunk g-2's MMAs and drained it, and full[g % 2] completes only
 // when every worker warp has arrived for chunk g.
+template <bool OUT64>
 __global__ void __launch_bounds__(kWorkers + 32, 1) dlr_tc_kernel(TcArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -349,7 +351,11 @@ __global__ void __launch_bounds__(kWorkers + 32, 1) dlr_tc_kernel(TcArgs a) {
         for (int i = 0; i < kQMax; i += 2) {
           const int j = (cb + i) >> 1;
           if (i < nq && j < nodes)
-            a.out[static_cast<long long>(j) * a.ncol + col] = make_float2(acc[i], acc[i + 1]);
+          {
+            const long long o = static_cast<long long>(j) * a.ncol + col;
+            if (OUT64) a.out64[o] = make_double2(acc[i], acc[i + 1]);
+            else a.out[o] = make_float2(acc[i], acc[i + 1]);
+          }
         }
       }
     }
@@ -417,11 +423,12 @@ void pack_dlr_tc(const std::complex<double>* T, int r, std::vector<uint16_t>* ds
 }
 
 cudaError_t launch_dlr_tc(const void* Bsplit, int r, const void* in, void* out, long long ncol,
-                          int* err, cudaStream_t st) {
+                          int* err, cudaStream_t st, bool out_c128) {
   size_t smem = 0;
   if (!dlr_tc_supported(r, &smem)) return cudaErrorInvalidValue;
   if (ncol <= 0) return cudaSuccess;
-  cudaError_t e = set_smem(reinterpret_cast<const void*>(&dlr_tc_kernel), smem, true);
+  auto fn = out_c128 ? &dlr_tc_kernel<true> : &dlr_tc_kernel<false>;
+  cudaError_t e = set_smem(reinterpret_cast<const void*>(fn), smem, true);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0;
   e = cudaGetDevice(&dev);
@@ -436,10 +443,11 @@ cudaError_t launch_dlr_tc(const void* Bsplit, int r, const void* in, void* out, 
   a.Np = a.Kp;
   a.r = r;
   a.in = reinterpret_cast<const float2*>(in);
-  a.out = reinterpret_cast<float2*>(out);
+  a.out = out_c128 ? nullptr : reinterpret_cast<float2*>(out);
+  a.out64 = out_c128 ? reinterpret_cast<double2*>(out) : nullptr;
   a.ncol = ncol;
   a.err = err;
-  dlr_tc_kernel<<<grid, kWorkers + 32, smem, st>>>(a);
+  fn<<<grid, kWorkers + 32, smem, st>>>(a);
   return cudaGetLastError();
 }
 

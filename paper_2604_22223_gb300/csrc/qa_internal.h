@@ -102,8 +102,9 @@ cudaError_t launch_dlr_apply(const void* Tm, int rows_out, int r, const void* in
 // Bsplit: the packed operand of pack_dlr_tc.  Supported when 2r <= 186.
 bool dlr_tc_supported(int r, size_t* smem_bytes);
 void pack_dlr_tc(const std::complex<double>* T, int r, std::vector<uint16_t>* dst);
+// out_c128: store the result as complex128 (out must not alias in then).
 cudaError_t launch_dlr_tc(const void* Bsplit, int r, const void* in, void* out, long long ncol,
-                          int* err, cudaStream_t st);
+                          int* err, cudaStream_t st, bool out_c128 = false);
 
 // Batched 3-D FFT of contiguous lines of N_k points (in place allowed).
 // sign = -1: X(k) = sum_R e^{-ikR} X(R); sign = +1: (1/N_k) sum_k e^{+ikR} X(k).
