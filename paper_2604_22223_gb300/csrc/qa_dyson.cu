@@ -629,60 +629,6 @@ __device__ __forceinline__ bool gj_inverse(V (&a)[NO][NO]) {
   return bad;
 }
 
-// Direct form for the FP64 density check of the mixed path: FP64 inverse of
-// i w_n + mu - H - Sigma^HF - Sigma^C with Sigma^C(k, i w) stored as complex64;
-// accumulates the per-block density sums (mode 0 of dyson_g_kernel).
-template <int NO>
-__global__ void __launch_bounds__(256) dyson_g_direct_kernel(const double2* __restrict__ Hk,
-                                                             const double2* __restrict__ SigHF,
-                                                             const float2* __restrict__ SigIw,
-                                                             const double2* __restrict__ dw,
-                                                             const double* __restrict__ iw,
-                                                             double mu, int r, int nk,
-                                                             double* part, int* err) {
-  using V = double2;
-  __shared__ double sh[64];
-  const long long total = static_cast<long long>(r) * nk;
-  double s1 = 0.0, s2 = 0.0;
-  bool bad = false;
-  for (long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
-       idx += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int n = static_cast<int>(idx / nk);
-    const int k = static_cast<int>(idx - static_cast<long long>(n) * nk);
-    V a[NO][NO];
-#pragma unroll
-    for (int i = 0; i < NO; ++i)
-#pragma unroll
-      for (int j = 0; j < NO; ++j) {
-        double2 h = Hk[static_cast<size_t>(k) * NO * NO + i * NO + j];
-        double2 sh2 = SigHF[static_cast<size_t>(k) * NO * NO + i * NO + j];
-        float2 sc = SigIw[(static_cast<size_t>(n) * NO * NO + i * NO + j) * nk + k];
-        V m = make_double2(-h.x - sh2.x - sc.x, -h.y - sh2.y - sc.y);
-        if (i == j) { m.x += mu; m.y += iw[n]; }
-        a[i][j] = m;
-      }
-    bad |= gj_inverse<V, NO>(a);
-    double2 tr = make_double2(0, 0), tr2 = make_double2(0, 0);
-#pragma unroll
-    for (int i = 0; i < NO; ++i) {
-      tr.x += a[i][i].x; tr.y += a[i][i].y;
-#pragma unroll
-      for (int j = 0; j < NO; ++j) {
-        tr2.x += a[i][j].x * a[j][i].x - a[i][j].y * a[j][i].y;
-        tr2.y += a[i][j].x * a[j][i].y + a[i][j].y * a[j][i].x;
-      }
-    }
-    const double2 wn = dw[n];
-    s1 += wn.x * tr.x - wn.y * tr.y;
-    s2 += wn.x * tr2.x - wn.y * tr2.y;
-  }
-  if (bad) atomicCAS(err, 0, QA_ESINGULAR_CODE);
-  block_sum2(s1, s2, sh);
-  if (threadIdx.x == 0) {
-    part[2 * blockIdx.x] = s1;
-    part[2 * blockIdx.x + 1] = s2;
-  }
-}
 
 // ---- FP64-accurate density from FP32 arithmetic (mixed path)
 // A = i w_n + mu - H(k) - Sigma^HF(k) - Sigma^C(k, i w_n) with Sigma^C given
@@ -1017,21 +963,6 @@ cudaError_t launch_dyson_g_refine(const double2* Hk, const double2* SigHF, const
   auto d = reinterpret_cast<const double2*>(dw);
   switch (norb) {
 #define QA_CASE(NO)     case NO: dyson_g_refine_kernel<NO><<<nblocks, 256, 0, st>>>(h, s, d, iw, r, nk, part, err); break;
-    QA_CASE(1) QA_CASE(2) QA_CASE(3) QA_CASE(4) QA_CASE(5)
-#undef QA_CASE
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_dyson_g_f64_sig32(const double2* Hk, const double2* SigHF, const void* SigIw,
-                                     const void* dw, const double* iw, double mu, int r, int norb,
-                                     int nk, double* part, int nblocks, int* err, cudaStream_t st) {
-  auto s = reinterpret_cast<const float2*>(SigIw);
-  auto d = reinterpret_cast<const double2*>(dw);
-  switch (norb) {
-#define QA_CASE(NO) \
-    case NO: dyson_g_direct_kernel<NO><<<nblocks, 256, 0, st>>>(Hk, SigHF, s, d, iw, mu, r, nk, part, err); break;
     QA_CASE(1) QA_CASE(2) QA_CASE(3) QA_CASE(4) QA_CASE(5)
 #undef QA_CASE
     default: return cudaErrorInvalidValue;

@@ -186,10 +186,6 @@ cudaError_t launch_dyson_g_refine(const double2* Hk, const double2* SigHF, const
                                   const void* dw, const double* iw, double mu, int r, int norb,
                                   int nk, void* hs, double* part, int nblocks, int* err,
                                   cudaStream_t st);
-// FP64 density sums (mode 0) at mu with Sigma^C(k, i w) stored as complex64.
-cudaError_t launch_dyson_g_f64_sig32(const double2* Hk, const double2* SigHF, const void* SigIw,
-                                     const void* dw, const double* iw, double mu, int r, int norb,
-                                     int nk, double* part, int nblocks, int* err, cudaStream_t st);
 
 // Deterministic final reduction of `n` partial pairs (sum or max).
 cudaError_t launch_reduce_pairs(const double* part, int n, int op_max, double* out,
