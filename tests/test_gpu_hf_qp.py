@@ -189,3 +189,26 @@ def test_paper_five_orbital_hf_half_filling():
     assert abs(mu - 9.5) <= 1e-10
     # n_loc is the DLR density -G(beta^-) of the HF G (eps = 1e-10 grid at beta Lambda = 2500)
     assert np.abs(np.diag(n_loc) - 0.5).max() <= 1e-8
+
+
+def test_bench_size_hf_and_qp_properties():
+    """The benchmark configuration (five-orbital 32x32x8, mixed context as bench.py runs
+    it): qa_hf_solve against the oracle's loop element by element, and after one GW
+    step the quasiparticle quantities satisfy what holds at any size: Z Hermitian with
+    eigenvalues in (0, 1], H_QP Hermitian, eps ascending and equal to its eigenvalues."""
+    from paper_2604_22223_gb300 import qa
+    m = wl.config("five-orbital-32x32x8")
+    res = qp.hf_loop(m, tol=HF_TOL, max_iter=200, mix=1.0)
+    ctx = qa.Context(m, "mixed")
+    G, mu, n_loc, iters, resid, status = ctx.hf_solve(200, HF_TOL, 1.0)
+    assert status == 0 and abs(iters - res["iters"]) <= 1
+    assert rel(ctx.get(qa.QA_SIGHF_K).cpu().numpy(), res["sig_hf_k"]) <= 1e-8
+    assert abs(mu - res["mu"]) <= 1e-8 * max(1.0, abs(res["mu"]))
+    ctx.step(G)
+    q = {k: v.cpu().numpy() for k, v in ctx.qp().items()}
+    herm = lambda X: np.abs(X - np.conj(np.swapaxes(X, 1, 2))).max() / np.abs(X).max()
+    assert herm(q["Z"]) <= 1e-12 and herm(q["Hqp"]) <= 1e-12
+    lam = np.linalg.eigvalsh(q["Z"])
+    assert lam.min() > 0 and lam.max() <= 1 + 1e-6     # complex64 Sigma^C: ~1e-7 noise
+    assert np.all(np.diff(q["eps"], axis=1) >= 0)
+    assert np.abs(np.linalg.eigvalsh(q["Hqp"]) - q["eps"]).max() <= 1e-9 * np.abs(q["eps"]).max()
