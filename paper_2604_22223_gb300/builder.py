@@ -23,7 +23,7 @@ LIB = os.path.join(PKG, "libqa.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-O3",
                   "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]
-CXXFLAGS = ["-O2", "-std=c++17", "-fPIC", "-I" + os.path.join(ROOT, "include")]
+CXXFLAGS = ["-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-I" + os.path.join(ROOT, "include")]
 
 
 def _nvcc() -> str:
