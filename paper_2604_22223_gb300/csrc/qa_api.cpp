@@ -129,6 +129,7 @@ struct qa_ctx {
   int pair_mode = QA_PAIRS_AUTO;
   bool reduced = false;
   int rho = 0;                    // rank of the interaction subspace
+  int sig_canon = 0;              // norb when the Sigma terms follow the canonical pattern
   int nb = 1;                     // size of the big-tensor matrices (npair or rho)
   std::vector<cd> basis;          // [npair][rho]
   std::vector<cd> sV;             // [nV][rho][rho] = B^H V(R) B
@@ -215,6 +216,10 @@ int setup_pairs(qa_ctx* c, bool bound) {
   c->nb = red ? rho : c->npair;
   c->tbub = tb;
   c->tsig = ts;
+  c->sig_canon = red ? qa::sigma_canonical_norb(ts.off.data(), ts.idx.data(),
+                                                static_cast<int>(ts.off.size()) - 1,
+                                                static_cast<int>(ts.idx.size()), c->norb)
+                     : 0;
   c->sV.clear();
   if (red) {
     const int np = c->npair;
@@ -737,7 +742,10 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
   tm.mark();  // 6: DLR nu -> tau
   QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, +1, c->d_W, c->d_W, ncb / nk * r, st));
   tm.mark();  // 7: FFT q -> R
-  if (c->reduced)
+  if (c->reduced && sizeof(T) == 4 && c->sig_canon)
+    QA_LAUNCH(c, 1, qa::launch_sigma_canonical(c->d_GR, c->d_W, c->tsig.coef.data(), c->sig_canon,
+                                               c->d_SigC, r, nk, st));
+  else if (c->reduced)
     QA_LAUNCH(c, 1, qa::launch_sigma_reduced<T>(c->d_GR, c->d_W, c->d_tsig, c->d_csig,
                                                 static_cast<int>(c->tsig.idx.size()), c->d_SigC, r,
                                                 c->norb, c->rho, nk, st, c->tsig.distinct_targets));

@@ -163,6 +163,16 @@ template <typename T>
 cudaError_t launch_sigma_reduced(const void* GR, const void* Wt, const int* terms, const void* coef,
                                  int nterm, void* Sig, int r, int norb, int rho, int nk,
                                  cudaStream_t st, int distinct = 0);
+// The Sigma term list of the canonical reduced basis (the norb diagonal pairs as
+// unit vectors, then one vector on {(a,b), (b,a)} per a < b in lexicographic
+// order; Kanamori-type interactions) has a fixed index pattern.  Returns norb
+// when off/idx (PairTerms of pair_basis_terms) follow it and a compile-time
+// kernel exists for norb (2, 5), else 0.
+int sigma_canonical_norb(const int* off, const int* idx, int nout, int nterm, int norb);
+// FP32 Sigma on such a basis: same inputs, outputs and bits as
+// launch_sigma_reduced<float>; coef: the list's norb^4 coefficients (host).
+cudaError_t launch_sigma_canonical(const void* GR, const void* Wt, const std::complex<double>* coef,
+                                   int norb, void* Sig, int r, int nk, cudaStream_t st);
 
 // Dyson for G.  prep: Bm[n][a][b][k] = (mu_ref - H(k) - SigHF(k))_ab - SigIw[n][a][b][k]
 // (SigHF FP64 [N_k][norb][norb] and SigIw may be null) and per-block bounds

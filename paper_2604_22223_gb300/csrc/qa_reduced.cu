@@ -12,6 +12,8 @@
 // shared memory [element][thread], and reads the term lists from shared
 // memory as broadcasts.  Global traffic: the rho^2 reduced entries plus
 // the small tensors, all coalesced along R.
+#include <utility>
+
 #include "qa_common.cuh"
 
 namespace qa {
@@ -169,7 +171,143 @@ size_t reduced_smem(int no2, int nout, int nterm) {
          static_cast<size_t>(nout + 1) * sizeof(int);
 }
 
+// ------------------------------------------- Sigma on the canonical basis
+// Kanamori-type interactions give the reduced basis a fixed shape: the N
+// diagonal pairs (a,a) as unit vectors, then one vector on {(a,b), (b,a)} for
+// each a < b in lexicographic order (the components of the pair graph, taken
+// in the order of their first pair).  Then the term list of the Sigma
+// contraction is a fixed pattern, N^4 terms with the entry of Wt, the source
+// G_bc and the target Sigma_ad of each known at compile time; only the
+// coefficients -B_(ab)i conj(B_(cd)j) depend on the interaction.  The kernel
+// keeps G and the N^2 accumulators in registers, reads each Wt entry once
+// (coalesced along R) and takes the coefficients from its parameter space, so
+// it moves the tensors' bytes and nothing else.  Its terms run in the order
+// of the generic list, so both kernels give the same bits.
+template <int N> struct CanonBasis {
+  static constexpr int RHO = N + N * (N - 1) / 2;
+  static constexpr int NO2 = N * N;
+  static constexpr int NT = NO2 * NO2;
+  // number of pairs of basis vector i, and of vectors 0 .. i-1
+  __host__ __device__ static constexpr int npairs(int i) { return i < N ? 1 : 2; }
+  __host__ __device__ static constexpr int before(int i) { return i < N ? i : N + 2 * (i - N); }
+  // first term of the output entry (i, j)
+  __host__ __device__ static constexpr int first_term(int i, int j) {
+    return before(i) * NO2 + npairs(i) * before(j);
+  }
+  // pair index a * N + b of the k-th pair of basis vector i
+  __host__ __device__ static constexpr int pair(int i, int k) {
+    if (i < N) return i * N + i;
+    int m = i - N, a = 0;
+    while (m >= N - 1 - a) { m -= N - 1 - a; ++a; }
+    const int b = a + 1 + m;
+    return k == 0 ? a * N + b : b * N + a;
+  }
+};
+
+template <int N> struct CanonCoefs { float2 c[CanonBasis<N>::NT]; };
+
+// one term: pair KA of vector i and pair KB of vector j of the entry O = i * rho + j
+template <int N, int O, int KA, int KB>
+__device__ __forceinline__ void canon_term(float2 w, const float2 (&g)[N * N], float2 (&acc)[N * N],
+                                           const CanonCoefs<N>& cf) {
+  using C = CanonBasis<N>;
+  constexpr int i = O / C::RHO, j = O % C::RHO;
+  if constexpr (KA < C::npairs(i) && KB < C::npairs(j)) {
+    constexpr int A = C::pair(i, KA), B = C::pair(j, KB);
+    constexpr int tgt = (A / N) * N + B % N;     // Sigma_ad with (ab) = A, (cd) = B
+    constexpr int src = (A % N) * N + B / N;     // G_bc
+    constexpr int e = C::first_term(i, j) + KA * C::npairs(j) + KB;
+    acc[tgt] = cfma(cmul(cf.c[e], w), g[src], acc[tgt]);
+  }
+}
+
+template <int N, int O>
+__device__ __forceinline__ void canon_entry(const float2* __restrict__ w, int nk, const float2 (&g)[N * N],
+                                            float2 (&acc)[N * N], const CanonCoefs<N>& cf) {
+  const float2 wv = __ldg(w + static_cast<size_t>(O) * nk);
+  canon_term<N, O, 0, 0>(wv, g, acc, cf);
+  canon_term<N, O, 0, 1>(wv, g, acc, cf);
+  canon_term<N, O, 1, 0>(wv, g, acc, cf);
+  canon_term<N, O, 1, 1>(wv, g, acc, cf);
+}
+
+template <int N, int... Os>
+__device__ __forceinline__ void canon_entries(const float2* __restrict__ w, int nk, const float2 (&g)[N * N],
+                                              float2 (&acc)[N * N], const CanonCoefs<N>& cf,
+                                              std::integer_sequence<int, Os...>) {
+  (canon_entry<N, Os>(w, nk, g, acc, cf), ...);
+}
+
+// 64 threads per block, one R each; 168 registers (N = 5) leave 12 warps per SM
+constexpr int kCanonTpb = 64;
+
+template <int N>
+__global__ void __launch_bounds__(kCanonTpb, 6) sigma_canonical_kernel(
+    const float2* __restrict__ GR, const float2* __restrict__ Wt, const __grid_constant__ CanonCoefs<N> cf,
+    float2* __restrict__ Sig, int nk) {
+  using C = CanonBasis<N>;
+  const int t = blockIdx.y, R = blockIdx.x * kCanonTpb + threadIdx.x;
+  if (R >= nk) return;
+  float2 g[C::NO2], acc[C::NO2];
+  const float2* gt = GR + static_cast<size_t>(t) * C::NO2 * nk + R;
+#pragma unroll
+  for (int e = 0; e < C::NO2; ++e) {
+    g[e] = __ldg(gt + static_cast<size_t>(e) * nk);
+    acc[e] = make_float2(0.f, 0.f);
+  }
+  const float2* w = Wt + static_cast<size_t>(t) * C::RHO * C::RHO * nk + R;
+  canon_entries<N>(w, nk, g, acc, cf, std::make_integer_sequence<int, C::RHO * C::RHO>{});
+  float2* out = Sig + static_cast<size_t>(t) * C::NO2 * nk + R;
+#pragma unroll
+  for (int e = 0; e < C::NO2; ++e) out[static_cast<size_t>(e) * nk] = acc[e];
+}
+
+template <int N>
+bool canon_matches(const int* off, const int* idx, int nout, int nterm) {
+  using C = CanonBasis<N>;
+  if (nout != C::RHO * C::RHO || nterm != C::NT || off[0] != 0) return false;
+  for (int i = 0; i < C::RHO; ++i)
+    for (int j = 0; j < C::RHO; ++j) {
+      const int o = i * C::RHO + j, e0 = C::first_term(i, j);
+      if (off[o] != e0 || off[o + 1] != e0 + C::npairs(i) * C::npairs(j)) return false;
+      for (int ka = 0; ka < C::npairs(i); ++ka)
+        for (int kb = 0; kb < C::npairs(j); ++kb) {
+          const int A = C::pair(i, ka), B = C::pair(j, kb);
+          const int want = ((A % N) * N + B / N) | (((A / N) * N + B % N) << 8);
+          if (idx[e0 + ka * C::npairs(j) + kb] != want) return false;
+        }
+    }
+  return true;
+}
+
+template <int N>
+cudaError_t launch_canon(const void* GR, const void* Wt, const std::complex<double>* coef, void* Sig,
+                         int r, int nk, cudaStream_t st) {
+  CanonCoefs<N> cf;
+  for (int e = 0; e < CanonBasis<N>::NT; ++e)
+    cf.c[e] = make_float2(static_cast<float>(coef[e].real()), static_cast<float>(coef[e].imag()));
+  dim3 grid((nk + kCanonTpb - 1) / kCanonTpb, r);
+  sigma_canonical_kernel<N><<<grid, kCanonTpb, 0, st>>>(reinterpret_cast<const float2*>(GR),
+                                                        reinterpret_cast<const float2*>(Wt), cf,
+                                                        reinterpret_cast<float2*>(Sig), nk);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+int sigma_canonical_norb(const int* off, const int* idx, int nout, int nterm, int norb) {
+  if (norb == 2 && canon_matches<2>(off, idx, nout, nterm)) return 2;
+  if (norb == 5 && canon_matches<5>(off, idx, nout, nterm)) return 5;
+  return 0;
+}
+
+cudaError_t launch_sigma_canonical(const void* GR, const void* Wt, const std::complex<double>* coef,
+                                   int norb, void* Sig, int r, int nk, cudaStream_t st) {
+  if (r < 1 || nk < 1 || r > 65535) return cudaErrorInvalidValue;
+  if (norb == 2) return launch_canon<2>(GR, Wt, coef, Sig, r, nk, st);
+  if (norb == 5) return launch_canon<5>(GR, Wt, coef, Sig, r, nk, st);
+  return cudaErrorInvalidValue;
+}
 
 template <typename T>
 cudaError_t launch_bubble_reduced(const void* GR, const void* GreflR, const int* mR,

@@ -152,6 +152,31 @@ def test_pair_basis(name, rho):
         assert qa.Problem(m, "mixed").workspace_size() < qa.Problem(m, "mixed", pairs="full").workspace_size()
 
 
+def _canonical_pattern(norb):
+    """Supports of the canonical reduced basis: the diagonal pairs as unit vectors,
+    then {(a,b), (b,a)} for each a < b in lexicographic order."""
+    supp = [[a * norb + a] for a in range(norb)]
+    supp += [[a * norb + b, b * norb + a] for a in range(norb) for b in range(a + 1, norb)]
+    return supp
+
+
+@pytest.mark.parametrize("name,canonical", [("five-orbital-6x5x1", True), ("five-orbital-32x32x8", True),
+                                            ("peierls-3x3", True), ("graphene-36x36", False)])
+def test_pair_basis_canonical_shape(name, canonical):
+    """Kanamori-type interactions give the canonical basis shape for which the
+    mixed path's Sigma contraction runs with compile-time indices (norb 2 and 5);
+    the GPU parity tests of these workloads therefore exercise that kernel, and
+    graphene's density-density basis exercises the generic term-list kernel."""
+    m = wl.config(name)
+    B = qa.Problem(m, "mixed").basis
+    supp = [sorted(np.flatnonzero(np.abs(B[:, j]) > 0).tolist()) for j in range(B.shape[1])]
+    match = supp == _canonical_pattern(m.norb)
+    assert match == canonical
+    if match:
+        for j, s in enumerate(supp):
+            assert np.allclose(np.abs(B[s, j]), len(s) ** -0.5, rtol=0, atol=1e-15)
+
+
 def test_pair_basis_rank_deficient_block():
     """A model whose only coupling is a rank-1 block on the pairs (01), (10)
     gets the single vector (e_01 + e_10)/sqrt 2 (up to sign), not the unit vectors."""
