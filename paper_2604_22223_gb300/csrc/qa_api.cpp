@@ -130,6 +130,7 @@ struct qa_ctx {
   bool reduced = false;
   int rho = 0;                    // rank of the interaction subspace
   int sig_canon = 0;              // norb when the Sigma terms follow the canonical pattern
+  bool dtau_real = false;         // the density weights dtau are real (they are by construction)
   int nb = 1;                     // size of the big-tensor matrices (npair or rho)
   std::vector<cd> basis;          // [npair][rho]
   std::vector<cd> sV;             // [nV][rho][rho] = B^H V(R) B
@@ -697,7 +698,7 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
   if (sizeof(T) == 4) Gk = c->d_Gk;
   QA_LAUNCH(c, 1, qa::launch_g_input(Gin, static_cast<const double2*>(c->t64.dtau), r, ncs,
                                      sizeof(T) == 4 ? static_cast<float2*>(c->d_Gk) : nullptr,
-                                     c->d_nk, st));
+                                     c->d_nk, st, c->dtau_real));
   QA_LAUNCH(c, 1, qa::launch_density_R(c->d_nk, c->d_vR, c->nV + 1, no2, nullptr, nk, c->n[0], c->n[1],
                               c->n[2], c->d_nR, st, c->d_phV));
   QA_LAUNCH(c, 2, qa::launch_hf(c->d_vV, c->d_nR, c->d_vR, c->nV, c->norb, c->nspin, nullptr, nk, c->n[0],
@@ -1251,6 +1252,8 @@ int qa_bind(qa_ctx* c, void* workspace, size_t bytes, void* stream) {
   QA_TRY(upload_c<double>(c->t64.Ttw, m.Ttw, st));
   QA_TRY(upload_c<double>(c->t64.Twt, m.Twt, st));
   QA_TRY(upload_c<double>(c->t64.dtau, m.dtau, st));
+  c->dtau_real = true;
+  for (const cd& v : m.dtau) c->dtau_real = c->dtau_real && v.imag() == 0.0;
   QA_TRY(upload_c<double>(c->t64.dw, m.dw, st));
   QA_TRY(upload_c<float>(c->t32.Trefl, m.Trefl, st));
   QA_TRY(upload_c<float>(c->t32.Ttn, m.Ttn, st));
@@ -1398,7 +1401,8 @@ int qa_density(qa_ctx* c, const void* G, double* n_out, double* N_total, void* s
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int no2 = c->norb * c->norb;
   QA_LAUNCH(c, 1, qa::launch_g_input(static_cast<const double2*>(G), static_cast<const double2*>(c->t64.dtau),
-                                     c->r, static_cast<long long>(no2) * c->nk, nullptr, c->d_nk, st));
+                                     c->r, static_cast<long long>(no2) * c->nk, nullptr, c->d_nk, st,
+                                     c->dtau_real));
   QA_LAUNCH(c, 1, qa::launch_k_average<double>(c->d_nk, no2, c->nk, c->d_nloc, st));
   std::vector<double> h(2 * no2);
   QA_TRY(cudaStreamSynchronize(st));

@@ -221,9 +221,11 @@ cudaError_t launch_hf(const double2* VR, const double2* nR_in, const int* R, int
                       double2* SigHF, cudaStream_t st, const double2* ph = nullptr);
 
 // n(k) = sum_j dtau_j G(k, tau_j) (FP64, [ncol]) of a complex128 G [r][ncol], and
-// its complex64 copy G32 when G32 != null (one pass; r <= 128).
+// its complex64 copy G32 when G32 != null (one pass; r <= 128).  real_w: every
+// dtau_j is real (the DLR weights f K_tau^-1 are), so each term takes two FP64
+// FMAs instead of four (same values).
 cudaError_t launch_g_input(const double2* G, const double2* dtau, int r, long long ncol,
-                           float2* G32, double2* nk_out, cudaStream_t st);
+                           float2* G32, double2* nk_out, cudaStream_t st, bool real_w = false);
 
 // Local average over k: out[e] = (1/N_k) sum_k x[e][k], e < m (FP64 out).
 template <typename T>

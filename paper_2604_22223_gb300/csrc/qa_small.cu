@@ -113,7 +113,10 @@ __global__ void k_average_kernel(const cplx<T>* __restrict__ x, int nk, double2*
 
 // n(k) = sum_j dtau_j G(k, tau_j) for every column of a complex128 G (FP64),
 // and the complex64 copy of G when G32 is given: one pass over G, one thread
-// per column, coalesced along the columns.
+// per column, coalesced along the columns.  The FP64 multiply-adds bound it
+// (GB300 runs FP64 at a small fraction of its FP32 rate), so REALW (real
+// weights) takes the two FMAs a real weight needs instead of the complex four.
+template <bool REALW>
 __global__ void __launch_bounds__(256) g_input_kernel(const double2* __restrict__ G,
                                                       const double2* __restrict__ dtau, int r,
                                                       long long ncol, float2* __restrict__ G32,
@@ -133,7 +136,12 @@ __global__ void __launch_bounds__(256) g_input_kernel(const double2* __restrict_
       for (int u = 0; u < 8; ++u) {
         if (l0 + u < r) {
           if (G32) G32[static_cast<long long>(l0 + u) * ncol + col] = make_float2(static_cast<float>(x[u].x), static_cast<float>(x[u].y));
-          acc[u & 3] = cfma(d[l0 + u], x[u], acc[u & 3]);
+          if (REALW) {
+            acc[u & 3].x = fma(d[l0 + u].x, x[u].x, acc[u & 3].x);
+            acc[u & 3].y = fma(d[l0 + u].x, x[u].y, acc[u & 3].y);
+          } else {
+            acc[u & 3] = cfma(d[l0 + u], x[u], acc[u & 3]);
+          }
         }
       }
     }
@@ -194,9 +202,12 @@ cudaError_t launch_hf(const double2* VR, const double2* nR_in, const int* R, int
 }
 
 cudaError_t launch_g_input(const double2* G, const double2* dtau, int r, long long ncol,
-                           float2* G32, double2* nk_out, cudaStream_t st) {
+                           float2* G32, double2* nk_out, cudaStream_t st, bool real_w) {
   if (r > 128) return cudaErrorInvalidValue;
-  g_input_kernel<<<grid_for(ncol, 256), 256, 0, st>>>(G, dtau, r, ncol, G32, nk_out);
+  if (real_w)
+    g_input_kernel<true><<<grid_for(ncol, 256), 256, 0, st>>>(G, dtau, r, ncol, G32, nk_out);
+  else
+    g_input_kernel<false><<<grid_for(ncol, 256), 256, 0, st>>>(G, dtau, r, ncol, G32, nk_out);
   return cudaGetLastError();
 }
 
