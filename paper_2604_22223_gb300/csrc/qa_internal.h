@@ -167,7 +167,7 @@ cudaError_t launch_sigma_reduced(const void* GR, const void* Wt, const int* term
 // unit vectors, then one vector on {(a,b), (b,a)} per a < b in lexicographic
 // order; Kanamori-type interactions) has a fixed index pattern.  Returns norb
 // when off/idx (PairTerms of pair_basis_terms) follow it and a compile-time
-// kernel exists for norb (2, 5), else 0.
+// kernel exists for norb (2 to 5), else 0.
 int sigma_canonical_norb(const int* off, const int* idx, int nout, int nterm, int norb);
 // FP32 Sigma on such a basis: same inputs, outputs and bits as
 // launch_sigma_reduced<float>; coef: the list's norb^4 coefficients (host).

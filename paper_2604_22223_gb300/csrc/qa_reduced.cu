@@ -296,17 +296,25 @@ cudaError_t launch_canon(const void* GR, const void* Wt, const std::complex<doub
 }  // namespace
 
 int sigma_canonical_norb(const int* off, const int* idx, int nout, int nterm, int norb) {
-  if (norb == 2 && canon_matches<2>(off, idx, nout, nterm)) return 2;
-  if (norb == 5 && canon_matches<5>(off, idx, nout, nterm)) return 5;
-  return 0;
+  switch (norb) {
+    case 2: return canon_matches<2>(off, idx, nout, nterm) ? 2 : 0;
+    case 3: return canon_matches<3>(off, idx, nout, nterm) ? 3 : 0;
+    case 4: return canon_matches<4>(off, idx, nout, nterm) ? 4 : 0;
+    case 5: return canon_matches<5>(off, idx, nout, nterm) ? 5 : 0;
+    default: return 0;
+  }
 }
 
 cudaError_t launch_sigma_canonical(const void* GR, const void* Wt, const std::complex<double>* coef,
                                    int norb, void* Sig, int r, int nk, cudaStream_t st) {
   if (r < 1 || nk < 1 || r > 65535) return cudaErrorInvalidValue;
-  if (norb == 2) return launch_canon<2>(GR, Wt, coef, Sig, r, nk, st);
-  if (norb == 5) return launch_canon<5>(GR, Wt, coef, Sig, r, nk, st);
-  return cudaErrorInvalidValue;
+  switch (norb) {
+    case 2: return launch_canon<2>(GR, Wt, coef, Sig, r, nk, st);
+    case 3: return launch_canon<3>(GR, Wt, coef, Sig, r, nk, st);
+    case 4: return launch_canon<4>(GR, Wt, coef, Sig, r, nk, st);
+    case 5: return launch_canon<5>(GR, Wt, coef, Sig, r, nk, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <typename T>

@@ -161,10 +161,11 @@ def _canonical_pattern(norb):
 
 
 @pytest.mark.parametrize("name,canonical", [("five-orbital-6x5x1", True), ("five-orbital-32x32x8", True),
-                                            ("peierls-3x3", True), ("graphene-36x36", False)])
+                                            ("peierls-3x3", True), ("three-orbital-4x3x2", True),
+                                            ("four-orbital-3x2x2", True), ("graphene-36x36", False)])
 def test_pair_basis_canonical_shape(name, canonical):
     """Kanamori-type interactions give the canonical basis shape for which the
-    mixed path's Sigma contraction runs with compile-time indices (norb 2 and 5);
+    mixed path's Sigma contraction runs with compile-time indices (norb 2 to 5);
     the GPU parity tests of these workloads therefore exercise that kernel, and
     graphene's density-density basis exercises the generic term-list kernel."""
     m = wl.config(name)

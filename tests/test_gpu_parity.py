@@ -3,7 +3,7 @@
 Small workloads span several FFT tiles, ragged grids (5x3x2, 6x5x1, 4x3x2), the
 degenerate 1x1x1 grid, power-of-two grids with three and with one non-trivial axis
 (4x4x2, 2x4x4, 16x1x1: the register FFT and the fused bubble; 16x16x8: its
-kernels specialised to that grid), complex hoppings and 1, 2 and 5 orbitals; each is
+kernels specialised to that grid), complex hoppings and 1 to 5 orbitals; each is
 compared element by element on G0, P(q, i nu), W^C(R, tau), Sigma^C(k, tau),
 Sigma^C(k, i w), Sigma^H + Sigma^F, the new G(k, tau), mu and the density.
 On the reduced pair basis (include/qa.h, qa_set_pair_basis) the GPU holds
@@ -34,7 +34,7 @@ pytestmark = pytest.mark.gpu
 
 SMALL = ["square-8x8", "peierls-3x3", "peierls-5x3x2", "five-orbital-6x5x1", "five-orbital-4x3x2",
          "graphene-6x6", "square-1x1", "peierls-4x4x2", "five-orbital-2x4x4", "square-16x1x1",
-         "peierls-16x16x8"]
+         "peierls-16x16x8", "three-orbital-4x3x2", "four-orbital-3x2x2"]
 FP64_BOUND = 1e-10
 MIXED_BOUND = {"P_qnu": 2e-6, "WC_Rtau": 1e-4, "sigc_ktau": 1e-4, "sigc_kiw": 1e-5,
                "sighf": 1e-9, "G": 1e-4, "mu": 2e-5, "n": 2e-5}

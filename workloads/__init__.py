@@ -221,6 +221,33 @@ def five_orbital(n=(16, 16, 1), seed=DEFAULT_SEED, U=3.0, J=0.6, Vnn=0.5, beta=4
                  orb_pos=np.zeros((norb, 3)))
 
 
+def hund_hubbard(norb, n=(4, 3, 2), seed=DEFAULT_SEED + 11, U=3.0, J=0.6, Vnn=0.5, beta=10.0,
+                 Lambda=200.0, eps_dlr=1e-10, filling=None, sig_nn=0.5, name=None) -> Model:
+    """norb-orbital extended Hund-Hubbard model with seeded random real hoppings on a
+    simple-tetragonal lattice (the five-orbital model's construction for any norb).
+
+    Draw order (SplitMix64 + Box-Muller): t(x) norb^2 normals (sigma sig_nn), t(y)
+    norb^2, t(z) norb^2, crystal field norb uniforms in [-0.3, 0.3).  t(-R) = t(R)^T.
+    Kanamori (U, J, U' = U - 2J) on site, density-density Vnn between nearest-neighbour
+    cells along x and y.  Default filling 1.2 electrons per orbital.
+    """
+    rng = SplitMix64(seed)
+    tx = rng.normals(norb * norb, sig_nn).reshape(norb, norb)
+    ty = rng.normals(norb * norb, sig_nn).reshape(norb, norb)
+    tz = rng.normals(norb * norb, sig_nn).reshape(norb, norb)
+    cf = np.array([-0.3 + 0.6 * rng.uniform() for _ in range(norb)])
+    hops = {(1, 0, 0): tx, (-1, 0, 0): tx.T, (0, 1, 0): ty, (0, -1, 0): ty.T,
+            (0, 0, 1): tz, (0, 0, -1): tz.T}
+    hops = {k: np.asarray(v, dtype=np.complex128) for k, v in hops.items()}
+    Vs = {(0, 0, 0): kanamori_local(norb, U, J)}
+    for R in [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0)]:
+        Vs[R] = density_density(norb, np.full((norb, norb), Vnn))
+    hop_R, hop_t, V_R, V = _finish(hops, Vs, norb)
+    return Model(name or "hund-hubbard-%d" % norb, tuple(n), norb, hop_R, hop_t, cf, V_R, V, beta,
+                 Lambda, eps_dlr, 1.2 * norb if filling is None else filling,
+                 orb_pos=np.zeros((norb, 3)))
+
+
 def degenerate_cubic(n=(8, 8, 8), norb=5, t=1.0, U=1.0, J=0.1, Vnn=0.2, beta=100.0,
                      Lambda=2500.0, eps_dlr=1e-10, filling=5.0,
                      name="five-orbital-degenerate") -> Model:
@@ -333,6 +360,10 @@ def config(name: str) -> Model:
         return peierls_two_orbital(n=(32, 32, 8), name="peierls-32x32x8")
     if name == "peierls-16x16x8":
         return peierls_two_orbital(n=(16, 16, 8), name="peierls-16x16x8")
+    if name == "three-orbital-4x3x2":         # 3- and 4-orbital Kanamori (ragged 3-D grids)
+        return hund_hubbard(3, n=(4, 3, 2), name="three-orbital-4x3x2")
+    if name == "four-orbital-3x2x2":
+        return hund_hubbard(4, n=(3, 2, 2), name="four-orbital-3x2x2")
     if name == "square-16x1x1":               # one non-trivial axis
         return square_single_band(n=(16, 1, 1), name="square-16x1x1")
     if name == "square-1x1":
