@@ -49,10 +49,41 @@ def peaks():
     return {"hbm_gbs": 6800.0, "src": "fallback"}
 
 
-class Clocks:
-    """nvidia-smi sampling during the timed region."""
+CLOCK_REASONS = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+
+def summarise_clock_rows(rows, t0, t1):
+    """Median SM clock, max clock and active throttle reasons of the nvidia-smi
+    rows (timestamp, index, clocks.sm, clocks.max.sm, power, active, the four
+    reasons) sampled inside the host window [t0, t1]; when no sample falls
+    inside, the one closest to the window's middle stands in for it."""
+    import datetime
+    parsed = []
+    for r in rows:
+        if len(r) < 10:
+            continue
+        try:
+            ts = datetime.datetime.strptime(r[0].strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            sm, mx = float(r[2]), float(r[3])
+        except ValueError:
+            continue
+        parsed.append((ts, sm, mx, [v.strip().lower() == "active" for v in r[6:10]]))
+    inside = [p for p in parsed if t0 <= p[0] <= t1]
+    if not inside and parsed:
+        mid = 0.5 * (t0 + t1)
+        inside = [min(parsed, key=lambda p: abs(p[0] - mid))]
+    reasons = sorted({nm for p in inside for nm, on in zip(CLOCK_REASONS, p[3]) if on})
+    return {"sm_mhz": statistics.median(p[1] for p in inside) if inside else None,
+            "sm_max_mhz": max(p[2] for p in inside) if inside else None, "reasons": reasons,
+            "samples": len(inside), "window_s": round(t1 - t0, 3)}
+
+
+class Clocks:
+    """nvidia-smi sampling (every 100 ms) around the timed region: started before
+    the warm-up, its samples are kept when their timestamps fall inside the
+    host-clock window that brackets the timed steps."""
+
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -60,37 +91,41 @@ class Clocks:
         self.index = index
         self.proc = None
         self.f = None
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
             self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:  # noqa: BLE001 - clocks are best effort
             self.proc = None
+            return
+        # wait (at most 5 s) until the sampler writes its first row
+        for _ in range(100):
+            if self.proc.poll() is not None or os.path.getsize(self.f.name) > 0:
+                break
+            time.sleep(0.05)
+
+    def begin(self):
+        self.t0 = time.time()
+
+    def end(self):
+        self.t1 = time.time()
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)                     # one more sample after the window
         self.proc.terminate()
         self.proc.wait(timeout=10)
         self.f.flush()
         rows = [l.split(",") for l in open(self.f.name).read().strip().splitlines() if l.strip()]
         os.unlink(self.f.name)
-        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
-        reasons = set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
-            if len(r) < 9:
-                continue
-            for nm, v in zip(names, r[5:9]):
-                if v.strip().lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        t0 = self.t0 if self.t0 is not None else 0.0
+        t1 = self.t1 if self.t1 is not None else time.time()
+        return summarise_clock_rows(rows, t0, t1)
 
 
 def s_block_sizes(ctx):
@@ -353,6 +388,8 @@ def run_ours(args):
         Ga = ctx.get(qa.QA_G0).clone()
         Gb = ctx.new_g()
         Gout = ctx.new_g()
+        if clocks:
+            clocks.start()                   # sampling before the warm-up
         ctx.step(Ga, Gb)
         for i in range(max(W - 1, 0)):
             ctx.step(Ga if i % 2 else Gb, Gout)
@@ -362,7 +399,7 @@ def run_ours(args):
         barrier(pg)
         torch.cuda.synchronize()
         if clocks:
-            clocks.start()
+            clocks.begin()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -374,6 +411,8 @@ def run_ours(args):
             evals.append(st["mu_evals"])
         e1.record()
         torch.cuda.synchronize()
+        if clocks:
+            clocks.end()
         ck = clocks.stop() if clocks else None
         barrier(pg)
         ms = e0.elapsed_time(e1)
@@ -575,7 +614,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--other-steps", type=int, default=5)
