@@ -124,6 +124,7 @@ def subspace_projector(Vs, tol=1e-12):
 
 @pytest.mark.parametrize("name,rho", [("five-orbital-6x5x1", 15), ("five-orbital-32x32x8", 15),
                                       ("graphene-36x36", 2), ("peierls-3x3", 3),
+                                      ("three-orbital-4x3x2", 6), ("four-orbital-3x2x2", 10),
                                       ("square-8x8", 1)])
 def test_pair_basis(name, rho):
     """The reduced pair basis: its rank, orthonormality, the subspace it spans
