@@ -45,7 +45,7 @@
  *     through a device error word read back at the end of the call.
  *
  * Limits: 1 <= norb <= 5 (npair <= 25 fits one warp per Dyson system);
- *         N_k * 16 bytes (FP64) or * 8 bytes (mixed) must fit the FFT's
+ *         N_k * 16 bytes (FP64, mixed) or * 8 bytes (FP32) must fit the FFT's
  *         shared-memory tile (N_k <= 12288); 1 <= r <= 128.
  */
 #ifndef QA_H
@@ -73,14 +73,23 @@ enum {
 /* arithmetic of the GPU path */
 enum {
   QA_FP64 = 0,        /* complex128 storage and FP64 arithmetic everywhere   */
-  QA_MIXED = 1        /* complex64 storage of P, W^C and the G/Sigma stages,
-                         FP32 arithmetic; FP64 kept for the DLR matrices, the
-                         chemical potential and density accumulation         */
+  QA_MIXED = 1,       /* every tensor stored as double-float (a pair of FP32
+                         values hi + lo per real number, 16 bytes per complex)
+                         and computed from FP32 instructions: error-free FP32
+                         transformations for the FFTs, products and small
+                         solves, the Dyson solve for W in FP32 refined by one
+                         double-float residual step, and the DLR maps on the
+                         tensor cores from fixed-point bf16 slices; FP64 for
+                         the DLR matrices, the chemical potential and density
+                         sums.  Agrees with QA_FP64 to ~1e-9 relative.       */
+  QA_FP32 = 2         /* complex64 storage of P, W^C and the G/Sigma stages,
+                         FP32 arithmetic, split-bf16 tensor-core DLR maps
+                         (the fast mode: ~1e-6 - 1e-5 relative to QA_FP64)  */
 };
 
 /* pair basis of the big tensors P(q, i nu) and W^C (qa_set_pair_basis) */
 enum {
-  QA_PAIRS_AUTO = 0,     /* reduced on QA_MIXED contexts, full on QA_FP64      */
+  QA_PAIRS_AUTO = 0,     /* reduced on QA_MIXED / QA_FP32, full on QA_FP64    */
   QA_PAIRS_FULL = 1,     /* all npair^2 entries (the paper's product basis)    */
   QA_PAIRS_REDUCED = 2   /* the rho^2 entries of the interaction subspace      */
 };
@@ -124,7 +133,7 @@ typedef struct {
 /* qa_create: validate and copy the problem (paper Sec. "Results": Crystal, DLR,
  * H0, V), build the DLR grid (Lambda = beta*omega_max dimensionless, eps = DLR
  * tolerance; Kaye, Chen & Parcollet 2022) and the FFT plans on the host.
- * filling = electrons per cell (both spins).  precision = QA_FP64 or QA_MIXED.
+ * filling = electrons per cell (both spins).  precision = QA_FP64, QA_MIXED or QA_FP32.
  * Returns QA_EINVAL for sizes outside the limits above or a non-Hermitian H.
  * *out receives a new context (free with qa_destroy). */
 int qa_create(const qa_lattice* lat, const qa_hoppings* hop, const qa_interaction* inter,
@@ -284,8 +293,9 @@ int qa_density_static(const qa_ctx* ctx, const void* G, double* n_out, double* N
                       void* stream);
 
 /* Intermediates of the last step / of qa_bind, copied to dst (host or device):
- * element type complex128 for QA_FP64 and complex64 for QA_MIXED, except where
- * noted.  bytes must equal the array size.  With the reduced pair basis active
+ * element type complex128 for QA_FP64, double-float complex for QA_MIXED (four
+ * floats re.hi, re.lo, im.hi, im.lo; value = hi + lo) and complex64 for
+ * QA_FP32, except where noted.  bytes must equal the array size.  With the reduced pair basis active
  * (qa_get_pair_basis) the two big tensors are held and returned as
  * B^H P B and B^H W^C B: [r][rho][rho][N_k]. */
 enum {

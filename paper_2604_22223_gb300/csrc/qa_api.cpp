@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/qa.h"
@@ -21,6 +22,12 @@ namespace {
 
 constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// The three arithmetic modes: T = double (QA_FP64), qa::dfl (QA_MIXED,
+// double-float storage of every tensor), float (QA_FP32).
+template <typename T> constexpr bool is_f64() { return std::is_same<T, double>::value; }
+template <typename T> constexpr bool is_df() { return std::is_same<T, qa::dfl>::value; }
+template <typename T> constexpr bool is_f32() { return std::is_same<T, float>::value; }
 
 struct DevTables {          // DLR matrices in one precision (complex)
   void* Trefl = nullptr;
@@ -65,10 +72,11 @@ struct qa_ctx {
   bool bound = false;
   char* ws = nullptr;
   size_t ws_bytes = 0;
-  DevTables t64, t32;
+  DevTables t64, t32, tdf;
   double* d_iw = nullptr;
   void* d_tw64 = nullptr;
   void* d_tw32 = nullptr;
+  void* d_twdf = nullptr;
   int* d_pos = nullptr;
   int* d_mR = nullptr;
   int* d_hR = nullptr;
@@ -78,7 +86,7 @@ struct qa_ctx {
   double2* d_Hk = nullptr;
   void* d_Vq = nullptr;
   double2* d_G0 = nullptr;
-  void* d_Gk = nullptr;       // G_in in the compute precision (mixed only)
+  void* d_Gk = nullptr;       // G_in in the compute precision (QA_MIXED, QA_FP32)
   void* d_Grefl = nullptr;    // G(k, beta-tau) then G(-R..) in place
   void* d_GR = nullptr;
   double2* d_nk = nullptr;    // [norb^2][N_k] FP64 density of G_in
@@ -96,7 +104,7 @@ struct qa_ctx {
   int* d_err = nullptr;
   long long* d_bad = nullptr;
   double2* d_nloc = nullptr;
-  qa::FftDev fft64{}, fft32{};
+  qa::FftDev fft64{}, fft32{}, fftdf{};
   int nblocks_g = 1;
   double mu0 = 0.0, mu = 0.0;
   bool have_mu = false;
@@ -117,7 +125,7 @@ struct qa_ctx {
   double2* d_Vbar = nullptr;
   double2* d_nbar = nullptr;
   int nH_user = 0;
-  // tensor-core DLR operands (mixed contexts)
+  // tensor-core DLR operands (QA_FP32 contexts)
   bool use_tc = false;
   std::vector<uint16_t> tc_Ttn, tc_Tnt, tc_Trefl, tc_Ttw, tc_Twt;
   void* d_tc_Ttn = nullptr;
@@ -202,7 +210,7 @@ int setup_pairs(qa_ctx* c, bool bound) {
          static_cast<int>(ts.idx.size()) <= qa::kMaxPairTerms;
   }
   const bool want = c->pair_mode == QA_PAIRS_REDUCED ||
-                    (c->pair_mode == QA_PAIRS_AUTO && c->precision == QA_MIXED);
+                    (c->pair_mode == QA_PAIRS_AUTO && c->precision != QA_FP64);
   const bool red = want && ok;
   if (bound && (red != c->reduced || (red && rho != c->rho))) return QA_EINVAL;
   if (!red) {
@@ -299,10 +307,10 @@ size_t layout(qa_ctx* c, char* base) {
   const size_t r = c->r, nk = c->nk, no2 = static_cast<size_t>(c->norb) * c->norb,
                np2 = static_cast<size_t>(c->npair) * c->npair,
                nb2 = static_cast<size_t>(c->nb) * c->nb;    // big-tensor matrix entries
-  const size_t es = c->precision == QA_FP64 ? 16 : 8;   // big/compute element size
+  const size_t es = c->precision == QA_FP32 ? 8 : 16;   // big/compute element size
   const size_t rr = r * r;
-  for (DevTables* t : {&c->t64, &c->t32}) {
-    const size_t e = (t == &c->t64) ? 16 : 8;
+  for (DevTables* t : {&c->t64, &c->t32, &c->tdf}) {
+    const size_t e = (t == &c->t32) ? 8 : 16;
     t->Trefl = take(rr * e);
     t->Ttn = take(rr * e);
     t->Tnt = take(rr * e);
@@ -315,6 +323,7 @@ size_t layout(qa_ctx* c, char* base) {
   c->d_iw = static_cast<double*>(take(r * 8));
   c->d_tw64 = take(ntw * 16);
   c->d_tw32 = take(ntw * 8);
+  c->d_twdf = take(ntw * 16);
   c->d_pos = static_cast<int*>(take(ntw * 4));
   c->d_mR = static_cast<int*>(take(nk * 4));
   c->d_hR = static_cast<int*>(take(std::max(1, c->nH) * 12));
@@ -348,7 +357,7 @@ size_t layout(qa_ctx* c, char* base) {
   c->d_bad = static_cast<long long*>(take(8));
   c->d_nloc = static_cast<double2*>(take(no2 * 16));
   c->d_wq = static_cast<double2*>(take(2 * r * 16));
-  if (c->precision == QA_MIXED && c->use_tc) {
+  if (c->precision == QA_FP32 && c->use_tc) {
     c->d_tc_Ttn = take(c->tc_Ttn.size() * 2);
     c->d_tc_Tnt = take(c->tc_Tnt.size() * 2);
     c->d_tc_Trefl = take(c->tc_Trefl.size() * 2);
@@ -388,13 +397,27 @@ size_t layout(qa_ctx* c, char* base) {
 
 template <typename T>
 cudaError_t upload_c(void* dst, const std::vector<cd>& src, cudaStream_t st) {
-  if (sizeof(T) == 8) {
+  if (is_f64<T>()) {
     return cudaMemcpyAsync(dst, src.data(), src.size() * 16, cudaMemcpyHostToDevice, st);
   }
-  std::vector<float> f(2 * src.size());
-  for (size_t i = 0; i < src.size(); ++i) {
-    f[2 * i] = static_cast<float>(src[i].real());
-    f[2 * i + 1] = static_cast<float>(src[i].imag());
+  std::vector<float> f;
+  if (is_df<T>()) {
+    // double-float: (re.hi, re.lo, im.hi, im.lo), hi = rn(x), lo = rn(x - hi)
+    f.resize(4 * src.size());
+    auto split = [](double x, float* o) {
+      o[0] = static_cast<float>(x);
+      o[1] = static_cast<float>(x - static_cast<double>(o[0]));
+    };
+    for (size_t i = 0; i < src.size(); ++i) {
+      split(src[i].real(), &f[4 * i]);
+      split(src[i].imag(), &f[4 * i + 2]);
+    }
+  } else {
+    f.resize(2 * src.size());
+    for (size_t i = 0; i < src.size(); ++i) {
+      f[2 * i] = static_cast<float>(src[i].real());
+      f[2 * i + 1] = static_cast<float>(src[i].imag());
+    }
   }
   cudaError_t e = cudaMemcpyAsync(dst, f.data(), f.size() * 4, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return e;
@@ -416,6 +439,7 @@ int upload_interaction(qa_ctx* c, cudaStream_t st) {
       QA_TRY(cudaMemcpyAsync(di[k], iv.data(), iv.size() * 4, cudaMemcpyHostToDevice, st));
       QA_TRY(cudaStreamSynchronize(st));
       if (c->precision == QA_FP64) QA_TRY(upload_c<double>(dc[k], tl[k]->coef, st));
+      else if (c->precision == QA_MIXED) QA_TRY(upload_c<qa::dfl>(dc[k], tl[k]->coef, st));
       else QA_TRY(upload_c<float>(dc[k], tl[k]->coef, st));
     }
   }
@@ -429,9 +453,13 @@ int upload_interaction(qa_ctx* c, cudaStream_t st) {
   } else {
     QA_LAUNCH(c, 1, qa::launch_ft_table(c->d_vR, src, c->nV, nb2, nullptr, c->nk, c->n[0], c->n[1],
                                         c->n[2], static_cast<double2*>(c->d_P), st));
-    QA_LAUNCH(c, 1, qa::launch_c128_to_c64(static_cast<const double2*>(c->d_P),
-                                           static_cast<float2*>(c->d_Vq),
-                                           static_cast<long long>(c->nk) * nb2, st));
+    if (c->precision == QA_MIXED)
+      QA_LAUNCH(c, 1, qa::launch_c128_to_df(static_cast<const double2*>(c->d_P), c->d_Vq,
+                                            static_cast<long long>(c->nk) * nb2, st));
+    else
+      QA_LAUNCH(c, 1, qa::launch_c128_to_c64(static_cast<const double2*>(c->d_P),
+                                             static_cast<float2*>(c->d_Vq),
+                                             static_cast<long long>(c->nk) * nb2, st));
   }
   QA_TRY(cudaStreamSynchronize(st));
   return QA_OK;
@@ -490,8 +518,8 @@ int mu_search(qa_ctx* c, const double2* SigHF, const void* SigIw, const DevTable
   const double wid = bound + 1.0 + 10.0 / c->beta;
   const double wlo = mu_s - wid, whi = mu_s + wid;
   const double target = c->filling;
-  const bool fp64 = sizeof(T) == 8;
-  // FP32 densities carry ~1e-6 relative noise: stop at that level on the mixed path
+  const bool fp64 = !is_f32<T>();     // FP64 or double-float densities
+  // FP32 densities carry ~1e-6 relative noise: stop at that level on the FP32 path
   const double tolN = (fp64 ? 1e-12 : 2e-6) * std::max(1.0, target);
   auto tolB = [&](double m) { return (fp64 ? 2e-13 : 2e-7) * std::max(1.0, std::fabs(m)); };
   int count = 0;
@@ -629,8 +657,11 @@ int finish_g(qa_ctx* c, const DevTables& tab, double mu, void* G_out_c128, doubl
   const long long ncol = static_cast<long long>(c->norb) * c->norb * c->nk;
   QA_LAUNCH(c, 1, qa::launch_dyson_g<T>(c->d_Bm, tab.dw, c->d_iw, mu - c->mu_ref, c->r, c->norb,
                                         c->nk, c->d_Giw, c->d_part, c->nblocks_g, 1, c->d_err, st));
-  if (sizeof(T) == 8) {
+  if (is_f64<T>()) {
     QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Twt, c->r, c->r, c->d_Giw, G_out_c128, ncol, st));
+  } else if (is_df<T>()) {
+    QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Twt, c->r, c->r, c->d_Giw, c->d_Gt, ncol, st));
+    QA_LAUNCH(c, 1, qa::launch_df_to_c128(c->d_Gt, static_cast<double2*>(G_out_c128), ncol * c->r, st));
   } else {
     if (c->use_tc) {
       // the transform stores complex128 directly
@@ -687,25 +718,30 @@ struct StageTimer {
 // Sigma^C(k, i w), Sigma^HF(k) and n(R_v) in the workspace.
 template <typename T>
 int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st) {
-  const DevTables& tab = sizeof(T) == 8 ? c->t64 : c->t32;
-  const qa::FftDev& fft = sizeof(T) == 8 ? c->fft64 : c->fft32;
+  const DevTables& tab = is_f64<T>() ? c->t64 : (is_df<T>() ? c->tdf : c->t32);
+  const qa::FftDev& fft = is_f64<T>() ? c->fft64 : (is_df<T>() ? c->fftdf : c->fft32);
+  constexpr bool f32 = is_f32<T>();
   const int r = c->r, no2 = c->norb * c->norb, nk = c->nk, nb2 = c->nb * c->nb;
   const long long ncs = static_cast<long long>(no2) * nk;     // small-tensor columns
   const long long ncb = static_cast<long long>(nb2) * nk;     // big-tensor columns
   // n(k) = -G(k, beta^-) of the input (FP64) with G in the compute precision,
   // then Hartree and Fock (FP64)
   const void* Gk = Gin;
-  if (sizeof(T) == 4) Gk = c->d_Gk;
-  QA_LAUNCH(c, 1, qa::launch_g_input(Gin, static_cast<const double2*>(c->t64.dtau), r, ncs,
-                                     sizeof(T) == 4 ? static_cast<float2*>(c->d_Gk) : nullptr,
-                                     c->d_nk, st, c->dtau_real));
+  if (!is_f64<T>()) Gk = c->d_Gk;
+  if (is_df<T>())
+    QA_LAUNCH(c, 1, qa::launch_g_input_df(Gin, static_cast<const double2*>(c->t64.dtau), r, ncs,
+                                          c->d_Gk, c->d_nk, st, c->dtau_real));
+  else
+    QA_LAUNCH(c, 1, qa::launch_g_input(Gin, static_cast<const double2*>(c->t64.dtau), r, ncs,
+                                       f32 ? static_cast<float2*>(c->d_Gk) : nullptr,
+                                       c->d_nk, st, c->dtau_real));
   QA_LAUNCH(c, 1, qa::launch_density_R(c->d_nk, c->d_vR, c->nV + 1, no2, nullptr, nk, c->n[0], c->n[1],
                               c->n[2], c->d_nR, st, c->d_phV));
   QA_LAUNCH(c, 2, qa::launch_hf(c->d_vV, c->d_nR, c->d_vR, c->nV, c->norb, c->nspin, nullptr, nk, c->n[0],
                        c->n[1], c->n[2], c->d_sigFR, c->d_SigHF, st, c->d_phV));
   tm.mark();  // 0: HF
   // G(k, beta - tau), real-space G
-  if (sizeof(T) == 4 && c->use_tc)
+  if (f32 && c->use_tc)
     QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Trefl, r, Gk, c->d_Grefl, ncs, c->d_err, st));
   else
     QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Trefl, r, r, Gk, c->d_Grefl, ncs, st));
@@ -728,7 +764,7 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
     QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, -1, c->d_P, c->d_P, ncb / nk * r, st));
   }
   tm.mark();  // 3: FFT R -> q
-  if (sizeof(T) == 4 && c->use_tc)
+  if (f32 && c->use_tc)
     QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Ttn, r, c->d_P, c->d_P, ncb, c->d_err, st));
   else
     QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Ttn, r, r, c->d_P, c->d_P, ncb, st));
@@ -736,14 +772,14 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
   QA_LAUNCH(c, 1, qa::launch_dyson_w<T>(c->d_P, c->d_Vq, c->d_W, r, c->nb, nk, c->d_err, c->d_bad, st,
                                         &c->dblk));
   tm.mark();  // 5: Dyson W
-  if (sizeof(T) == 4 && c->use_tc)
+  if (f32 && c->use_tc)
     QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Tnt, r, c->d_W, c->d_W, ncb, c->d_err, st));
   else
     QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Tnt, r, r, c->d_W, c->d_W, ncb, st));
   tm.mark();  // 6: DLR nu -> tau
   QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, +1, c->d_W, c->d_W, ncb / nk * r, st));
   tm.mark();  // 7: FFT q -> R
-  if (c->reduced && sizeof(T) == 4 && c->sig_canon)
+  if (c->reduced && f32 && c->sig_canon)
     QA_LAUNCH(c, 1, qa::launch_sigma_canonical(c->d_GR, c->d_W, c->tsig.coef.data(), c->sig_canon,
                                                c->d_SigC, r, nk, st));
   else if (c->reduced)
@@ -754,7 +790,7 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
     QA_LAUNCH(c, 1, qa::launch_sigma<T>(c->d_GR, c->d_W, c->d_SigC, r, c->norb, nk, st));
   tm.mark();  // 8: Sigma contraction
   QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, -1, c->d_SigC, c->d_SigC, ncs / nk * r, st));
-  if (sizeof(T) == 4 && c->use_tc)
+  if (f32 && c->use_tc)
     QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Ttw, r, c->d_SigC, c->d_SigIw, ncs, c->d_err, st));
   else
     QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Ttw, r, r, c->d_SigC, c->d_SigIw, ncs, st));
@@ -766,7 +802,7 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
 template <typename T>
 int gw_step_impl(qa_ctx* c, const void* G_in, void* G_out, double* mu_out, double* n_out,
                  qa_step_stats* stats, cudaStream_t st) {
-  const DevTables& tab = sizeof(T) == 8 ? c->t64 : c->t32;
+  const DevTables& tab = is_f64<T>() ? c->t64 : (is_df<T>() ? c->tdf : c->t32);
   const double2* Gin = static_cast<const double2*>(G_in ? G_in : c->d_G0);
   c->launches = 0;
   if (int rc = reset_err(c, st)) return rc;
@@ -1098,7 +1134,7 @@ int qa_create(const qa_lattice* lat, const qa_hoppings* hop, const qa_interactio
               qa_ctx** out) {
   if (!lat || !hop || !inter || !out) return QA_EINVAL;
   *out = nullptr;
-  if (precision != QA_FP64 && precision != QA_MIXED) return QA_EINVAL;
+  if (precision != QA_FP64 && precision != QA_MIXED && precision != QA_FP32) return QA_EINVAL;
   if (lat->norb < 1 || lat->norb > 5 || lat->nspin < 1) return QA_EINVAL;
   long long nk = 1;
   for (int d = 0; d < 3; ++d) {
@@ -1173,7 +1209,7 @@ int qa_create(const qa_lattice* lat, const qa_hoppings* hop, const qa_interactio
   if (qa::build_dlr(Lambda, eps, &c->grid) != 0) { delete c; return QA_EINVAL; }
   c->r = c->grid.r;
   qa::build_dlr_matrices(c->grid, beta, &c->mats);
-  if (precision == QA_MIXED && qa::dlr_tc_supported(c->r, nullptr)) {
+  if (precision == QA_FP32 && qa::dlr_tc_supported(c->r, nullptr)) {
     const char* env = std::getenv("QA_DLR_SIMT");
     c->use_tc = !(env && env[0] == '1');
     if (c->use_tc) {
@@ -1262,6 +1298,13 @@ int qa_bind(qa_ctx* c, void* workspace, size_t bytes, void* stream) {
   QA_TRY(upload_c<float>(c->t32.Twt, m.Twt, st));
   QA_TRY(upload_c<float>(c->t32.dtau, m.dtau, st));
   QA_TRY(upload_c<float>(c->t32.dw, m.dw, st));
+  QA_TRY(upload_c<qa::dfl>(c->tdf.Trefl, m.Trefl, st));
+  QA_TRY(upload_c<qa::dfl>(c->tdf.Ttn, m.Ttn, st));
+  QA_TRY(upload_c<qa::dfl>(c->tdf.Tnt, m.Tnt, st));
+  QA_TRY(upload_c<qa::dfl>(c->tdf.Ttw, m.Ttw, st));
+  QA_TRY(upload_c<qa::dfl>(c->tdf.Twt, m.Twt, st));
+  QA_TRY(upload_c<qa::dfl>(c->tdf.dtau, m.dtau, st));
+  QA_TRY(upload_c<qa::dfl>(c->tdf.dw, m.dw, st));
   QA_TRY(cudaMemcpyAsync(c->d_iw, m.iw.data(), r * 8, cudaMemcpyHostToDevice, st));
   {
     std::vector<cd> wq(m.wq_p);
@@ -1299,11 +1342,12 @@ int qa_bind(qa_ctx* c, void* workspace, size_t bytes, void* stream) {
   std::vector<cd> tw;
   std::vector<int> pos;
   for (int d = 0; d < 3; ++d) {
-    c->fft64.n[d] = c->fft32.n[d] = c->n[d];
-    c->fft64.nfac[d] = c->fft32.nfac[d] = c->ax[d].nfac;
-    for (int s = 0; s < qa::kMaxFac; ++s) c->fft64.fac[d][s] = c->fft32.fac[d][s] = c->ax[d].fac[s];
-    c->fft64.tw_off[d] = c->fft32.tw_off[d] = static_cast<int>(tw.size());
-    c->fft64.pos_off[d] = c->fft32.pos_off[d] = static_cast<int>(pos.size());
+    c->fft64.n[d] = c->fft32.n[d] = c->fftdf.n[d] = c->n[d];
+    c->fft64.nfac[d] = c->fft32.nfac[d] = c->fftdf.nfac[d] = c->ax[d].nfac;
+    for (int s = 0; s < qa::kMaxFac; ++s)
+      c->fft64.fac[d][s] = c->fft32.fac[d][s] = c->fftdf.fac[d][s] = c->ax[d].fac[s];
+    c->fft64.tw_off[d] = c->fft32.tw_off[d] = c->fftdf.tw_off[d] = static_cast<int>(tw.size());
+    c->fft64.pos_off[d] = c->fft32.pos_off[d] = c->fftdf.pos_off[d] = static_cast<int>(pos.size());
     const long double two_pi = 6.283185307179586476925286766559005768L;
     for (int k = 0; k < c->n[d]; ++k) {
       long double ang = -two_pi * k / c->n[d];
@@ -1313,10 +1357,12 @@ int qa_bind(qa_ctx* c, void* workspace, size_t bytes, void* stream) {
   }
   QA_TRY(upload_c<double>(c->d_tw64, tw, st));
   QA_TRY(upload_c<float>(c->d_tw32, tw, st));
+  QA_TRY(upload_c<qa::dfl>(c->d_twdf, tw, st));
   QA_TRY(cudaMemcpyAsync(c->d_pos, pos.data(), pos.size() * 4, cudaMemcpyHostToDevice, st));
   c->fft64.tw = c->d_tw64;
   c->fft32.tw = c->d_tw32;
-  c->fft64.pos = c->fft32.pos = c->d_pos;
+  c->fftdf.tw = c->d_twdf;
+  c->fft64.pos = c->fft32.pos = c->fftdf.pos = c->d_pos;
   QA_TRY(cudaMemcpyAsync(c->d_mR, c->mR.data(), c->nk * 4, cudaMemcpyHostToDevice, st));
   QA_TRY(cudaMemcpyAsync(c->d_hR, c->hopR.data(), c->hopR.size() * 4, cudaMemcpyHostToDevice, st));
   QA_TRY(upload_c<double>(c->d_hH, c->hopH, st));
@@ -1392,6 +1438,7 @@ int qa_gw_step(qa_ctx* c, const void* G_in, void* G_out, double* mu_out, double*
   if (stats) std::memset(stats, 0, sizeof(*stats));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (c->precision == QA_FP64) return gw_step_impl<double>(c, G_in, G_out, mu_out, n_out, stats, st);
+  if (c->precision == QA_MIXED) return gw_step_impl<qa::dfl>(c, G_in, G_out, mu_out, n_out, stats, st);
   return gw_step_impl<float>(c, G_in, G_out, mu_out, n_out, stats, st);
 }
 
@@ -1418,7 +1465,7 @@ int qa_get(const qa_ctx* c, int which, void* dst, size_t bytes, void* stream) {
   if (!c || !dst) return QA_EINVAL;
   if (!c->bound) return QA_ESTATE;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const size_t es = c->precision == QA_FP64 ? 16 : 8;
+  const size_t es = c->precision == QA_FP32 ? 8 : 16;
   const size_t r = c->r, nk = c->nk, no2 = static_cast<size_t>(c->norb) * c->norb,
                nb2 = static_cast<size_t>(c->nb) * c->nb;
   const void* src = nullptr;
@@ -1523,6 +1570,7 @@ int qa_qp(qa_ctx* c, void* Z, void* Sig0, void* Hqp, double* eps, void* stream) 
   double2* s0 = static_cast<double2*>(Sig0);
   double2* hq = static_cast<double2*>(Hqp);
   if (c->precision == QA_FP64) return qp_impl<double>(c, z, s0, hq, eps, st);
+  if (c->precision == QA_MIXED) return qp_impl<qa::dfl>(c, z, s0, hq, eps, st);
   return qp_impl<float>(c, z, s0, hq, eps, st);
 }
 

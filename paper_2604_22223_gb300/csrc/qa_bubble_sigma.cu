@@ -105,6 +105,9 @@ template cudaError_t launch_bubble<float>(const void*, const void*, const int*, 
                                           int, double, cudaStream_t);
 template cudaError_t launch_sigma<double>(const void*, const void*, void*, int, int, int,
                                           cudaStream_t);
+template cudaError_t launch_sigma<dfl>(const void*, const void*, void*, int, int, int, cudaStream_t);
+template cudaError_t launch_bubble<dfl>(const void*, const void*, const int*, void*, int, int, int,
+                                        double, cudaStream_t);
 template cudaError_t launch_sigma<float>(const void*, const void*, void*, int, int, int,
                                          cudaStream_t);
 

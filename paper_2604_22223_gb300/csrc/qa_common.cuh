@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
+#include "qa_df.cuh"
 #include "qa_internal.h"
 
 namespace qa {
@@ -11,6 +12,7 @@ namespace qa {
 template <typename T> struct CplxOf;
 template <> struct CplxOf<double> { using type = double2; };
 template <> struct CplxOf<float> { using type = float2; };
+template <> struct CplxOf<dfl> { using type = dfc; };
 template <typename T> using cplx = typename CplxOf<T>::type;
 
 template <typename V> __device__ __forceinline__ V cmk(double re, double im) {
@@ -18,6 +20,16 @@ template <typename V> __device__ __forceinline__ V cmk(double re, double im) {
   v.x = static_cast<decltype(v.x)>(re);
   v.y = static_cast<decltype(v.y)>(im);
   return v;
+}
+// (re, im) from double-float components
+template <typename V> __device__ __forceinline__ V cmk(dfl re, dfl im);
+template <> __device__ __forceinline__ dfc cmk<dfc>(dfl re, dfl im) { return dfc{re, im}; }
+// read-only cached load of one complex value
+__device__ __forceinline__ double2 ldg_c(const double2* p) { return __ldg(p); }
+__device__ __forceinline__ float2 ldg_c(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ dfc ldg_c(const dfc* p) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  return dfc{dfl(v.x, v.y), dfl(v.z, v.w)};
 }
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -73,6 +85,7 @@ template <> __device__ __forceinline__ double2 from_d2<double2>(double2 a) { ret
 template <> __device__ __forceinline__ float2 from_d2<float2>(double2 a) {
   return make_float2(static_cast<float>(a.x), static_cast<float>(a.y));
 }
+template <> __device__ __forceinline__ dfc from_d2<dfc>(double2 a) { return dfc{dfl(a.x), dfl(a.y)}; }
 
 // exp(sign * 2 pi i * (sum_d (i_d R_d mod N_d) / N_d)) in FP64; the integer
 // reduction keeps the phase argument exact for any R.

@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(256) dlr_apply_kernel(const cplx<T>* __restric
 #pragma unroll
       for (int b = 0; b < RB; ++b) {
         int j = j0 + b;
-        V t = j < rows_out ? __ldg(&Tm[static_cast<size_t>(j) * r + l]) : cmk<V>(0, 0);
+        V t = j < rows_out ? ldg_c(&Tm[static_cast<size_t>(j) * r + l]) : cmk<V>(0, 0);
         acc[b] = cfma(t, x, acc[b]);
       }
     }
@@ -60,7 +60,7 @@ template <typename T>
 cudaError_t launch_dlr_apply(const void* Tm, int rows_out, int r, const void* in, void* out,
                              long long ncol, cudaStream_t st, int accumulate) {
   if (ncol <= 0 || rows_out <= 0) return cudaSuccess;
-  constexpr int TILE = sizeof(T) == 8 ? 32 : 64;
+  constexpr int TILE = sizeof(cplx<T>) >= 16 ? 32 : 64;
   constexpr int RB = 4;
   size_t smem = static_cast<size_t>(r) * TILE * sizeof(cplx<T>);
   auto fn = &dlr_apply_kernel<T, TILE, RB>;
@@ -77,5 +77,7 @@ template cudaError_t launch_dlr_apply<double>(const void*, int, int, const void*
                                               cudaStream_t, int);
 template cudaError_t launch_dlr_apply<float>(const void*, int, int, const void*, void*, long long,
                                              cudaStream_t, int);
+template cudaError_t launch_dlr_apply<dfl>(const void*, int, int, const void*, void*, long long,
+                                           cudaStream_t, int);
 
 }  // namespace qa

@@ -26,6 +26,7 @@ constexpr int kWarpsW = 4;
 template <typename T> struct Tiny;
 template <> struct Tiny<double> { static constexpr double v = 1e-26; };   // |pivot|^2
 template <> struct Tiny<float> { static constexpr float v = 1e-12f; };
+template <> struct Tiny<dfl> { static constexpr double v = 1e-26; };
 
 __device__ void report(int* err, long long* first_bad, int code, long long idx) {
   atomicCAS(err, 0, code);
@@ -988,5 +989,11 @@ template cudaError_t launch_dyson_g_prep<double>(const double2*, const double2*,
                                                  int, int, int, void*, double*, int, cudaStream_t);
 template cudaError_t launch_dyson_g_prep<float>(const double2*, const double2*, const void*, double,
                                                 int, int, int, void*, double*, int, cudaStream_t);
+template cudaError_t launch_dyson_w<dfl>(const void*, const void*, void*, int, int, int, int*,
+                                         long long*, cudaStream_t, const DysonBlocks*);
+template cudaError_t launch_dyson_g<dfl>(const void*, const void*, const double*, double, int, int,
+                                         int, void*, double*, int, int, int*, cudaStream_t);
+template cudaError_t launch_dyson_g_prep<dfl>(const double2*, const double2*, const void*, double,
+                                              int, int, int, void*, double*, int, cudaStream_t);
 
 }  // namespace qa

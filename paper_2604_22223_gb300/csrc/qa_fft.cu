@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? (L1C >= 0 ? 3 : 
     if (last) {                                                                                  \
       V* dst = out + gl * nk + base;                                                             \
       _Pragma("unroll") for (int j = 0; j < L; ++j) dst[static_cast<size_t>(j) * S] =            \
-          cmk<V>(x[j].x * scale, x[j].y * scale);                                                \
+          cscale(x[j], scale);                                                \
     } else {                                                                                     \
       _Pragma("unroll") for (int j = 0; j < L; ++j) lb[pb + j * ps] = x[j];                      \
     }                                                                                            \
@@ -419,5 +419,10 @@ template cudaError_t launch_fft3d<double>(const FftDev&, int, const void*, void*
                                           cudaStream_t, double);
 template cudaError_t launch_fft3d<float>(const FftDev&, int, const void*, void*, long long,
                                          cudaStream_t, double);
+template cudaError_t launch_fft3d<dfl>(const FftDev&, int, const void*, void*, long long,
+                                       cudaStream_t, double);
+template cudaError_t launch_fft3d_bubble<dfl>(const FftDev&, const void*, const void*, const int*,
+                                              const int*, const void*, int, int, int, void*, int,
+                                              cudaStream_t);
 
 }  // namespace qa

@@ -13,6 +13,8 @@ struct qa_ctx;
 
 namespace qa {
 
+struct dfl;   // double-float real (qa_df.cuh); complex arrays of it are dfc
+
 // Device-side copy of the public status code for a singular pivot.
 constexpr int QA_ESINGULAR_CODE = 3;
 constexpr int QA_ETIMEOUT_CODE = 6;
@@ -89,7 +91,8 @@ struct FftDev {            // passed by value to the FFT kernel
 
 // ------------------------------------------------------------- kernels
 // All launchers enqueue on `st` and return cudaGetLastError().
-// Complex arrays are double2 (FP64) or float2 (FP32).
+// Complex arrays are double2 (FP64), float2 (FP32) or dfc (double-float, qa_df.cuh);
+// the template argument T is double, float or dfl.
 
 // out[j][c] = sum_l T[j][l] in[l][c], j < rows_out, l < r, c < ncol.
 // in and out may alias (each block stages its columns before writing).
@@ -227,6 +230,10 @@ cudaError_t launch_hf(const double2* VR, const double2* nR_in, const int* R, int
 cudaError_t launch_g_input(const double2* G, const double2* dtau, int r, long long ncol,
                            float2* G32, double2* nk_out, cudaStream_t st, bool real_w = false);
 
+// The same with a double-float (dfc: re.hi, re.lo, im.hi, im.lo) copy of G.
+cudaError_t launch_g_input_df(const double2* G, const double2* dtau, int r, long long ncol,
+                              void* Gdf, double2* nk_out, cudaStream_t st, bool real_w = false);
+
 // Local average over k: out[e] = (1/N_k) sum_k x[e][k], e < m (FP64 out).
 template <typename T>
 cudaError_t launch_k_average(const void* x, int m, int nk, double2* out, cudaStream_t st);
@@ -286,5 +293,7 @@ int density_tables(const ::qa_ctx* ctx, const std::complex<double>** dtau, int* 
 // Precision conversions.
 cudaError_t launch_c128_to_c64(const double2* in, float2* out, long long n, cudaStream_t st);
 cudaError_t launch_c64_to_c128(const float2* in, double2* out, long long n, cudaStream_t st);
+cudaError_t launch_c128_to_df(const double2* in, void* out, long long n, cudaStream_t st);
+cudaError_t launch_df_to_c128(const void* in, double2* out, long long n, cudaStream_t st);
 
 }  // namespace qa

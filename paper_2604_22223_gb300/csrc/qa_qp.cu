@@ -423,6 +423,9 @@ cudaError_t launch_qp(const double2* Hk, const double2* SigHF, const void* SigIw
 template cudaError_t launch_qp<double>(const double2*, const double2*, const void*, const double2*,
                                        const double2*, int, int, int, double, double2*, double2*,
                                        double2*, double2*, double*, int*, cudaStream_t);
+template cudaError_t launch_qp<dfl>(const double2*, const double2*, const void*, const double2*,
+                                    const double2*, int, int, int, double, double2*, double2*,
+                                    double2*, double2*, double*, int*, cudaStream_t);
 template cudaError_t launch_qp<float>(const double2*, const double2*, const void*, const double2*,
                                       const double2*, int, int, int, double, double2*, double2*,
                                       double2*, double2*, double*, int*, cudaStream_t);

@@ -21,9 +21,10 @@ namespace {
 
 template <typename T> struct RedTpb { static constexpr int v = 256; };
 template <> struct RedTpb<double> { static constexpr int v = 64; };
+template <> struct RedTpb<dfl> { static constexpr int v = 64; };
 
 // one term as a single shared-memory record (one 16- or 32-byte load)
-template <typename T> struct __align__(2 * sizeof(T) < 16 ? 16 : 32) TermRec {
+template <typename T> struct __align__(sizeof(cplx<T>) < 16 ? 16 : 32) TermRec {
   cplx<T> c;
   int idx;
 };
@@ -362,5 +363,10 @@ template cudaError_t launch_sigma_reduced<double>(const void*, const void*, cons
                                                   int, void*, int, int, int, int, cudaStream_t, int);
 template cudaError_t launch_sigma_reduced<float>(const void*, const void*, const int*, const void*,
                                                  int, void*, int, int, int, int, cudaStream_t, int);
+template cudaError_t launch_bubble_reduced<dfl>(const void*, const void*, const int*, const int*,
+                                                const void*, int, void*, int, int, int, int,
+                                                cudaStream_t);
+template cudaError_t launch_sigma_reduced<dfl>(const void*, const void*, const int*, const void*,
+                                               int, void*, int, int, int, int, cudaStream_t, int);
 
 }  // namespace qa

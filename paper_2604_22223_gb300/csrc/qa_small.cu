@@ -116,10 +116,11 @@ __global__ void k_average_kernel(const cplx<T>* __restrict__ x, int nk, double2*
 // per column, coalesced along the columns.  The FP64 multiply-adds bound it
 // (GB300 runs FP64 at a small fraction of its FP32 rate), so REALW (real
 // weights) takes the two FMAs a real weight needs instead of the complex four.
-template <bool REALW>
+// DF: the copy is double-float (dfc) instead of complex64.
+template <bool REALW, bool DF>
 __global__ void __launch_bounds__(256) g_input_kernel(const double2* __restrict__ G,
                                                       const double2* __restrict__ dtau, int r,
-                                                      long long ncol, float2* __restrict__ G32,
+                                                      long long ncol, void* __restrict__ Gc,
                                                       double2* __restrict__ nk_out) {
   __shared__ double2 d[128];
   for (int l = threadIdx.x; l < r; l += blockDim.x) d[l] = dtau[l];
@@ -135,7 +136,11 @@ __global__ void __launch_bounds__(256) g_input_kernel(const double2* __restrict_
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         if (l0 + u < r) {
-          if (G32) G32[static_cast<long long>(l0 + u) * ncol + col] = make_float2(static_cast<float>(x[u].x), static_cast<float>(x[u].y));
+          if (Gc) {
+            const long long o = static_cast<long long>(l0 + u) * ncol + col;
+            if (DF) static_cast<dfc*>(Gc)[o] = from_d2<dfc>(x[u]);
+            else static_cast<float2*>(Gc)[o] = make_float2(static_cast<float>(x[u].x), static_cast<float>(x[u].y));
+          }
           if (REALW) {
             acc[u & 3].x = fma(d[l0 + u].x, x[u].x, acc[u & 3].x);
             acc[u & 3].y = fma(d[l0 + u].x, x[u].y, acc[u & 3].y);
@@ -153,6 +158,18 @@ __global__ void c128_to_c64_kernel(const double2* in, float2* out, long long n) 
   for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
        i += static_cast<long long>(gridDim.x) * blockDim.x)
     out[i] = make_float2(static_cast<float>(in[i].x), static_cast<float>(in[i].y));
+}
+
+__global__ void c128_to_df_kernel(const double2* in, dfc* out, long long n) {
+  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    out[i] = from_d2<dfc>(in[i]);
+}
+
+__global__ void df_to_c128_kernel(const dfc* in, double2* out, long long n) {
+  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x)
+    out[i] = to_c64d(in[i]);
 }
 
 __global__ void c64_to_c128_kernel(const float2* in, double2* out, long long n) {
@@ -205,9 +222,29 @@ cudaError_t launch_g_input(const double2* G, const double2* dtau, int r, long lo
                            float2* G32, double2* nk_out, cudaStream_t st, bool real_w) {
   if (r > 128) return cudaErrorInvalidValue;
   if (real_w)
-    g_input_kernel<true><<<grid_for(ncol, 256), 256, 0, st>>>(G, dtau, r, ncol, G32, nk_out);
+    g_input_kernel<true, false><<<grid_for(ncol, 256), 256, 0, st>>>(G, dtau, r, ncol, G32, nk_out);
   else
-    g_input_kernel<false><<<grid_for(ncol, 256), 256, 0, st>>>(G, dtau, r, ncol, G32, nk_out);
+    g_input_kernel<false, false><<<grid_for(ncol, 256), 256, 0, st>>>(G, dtau, r, ncol, G32, nk_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_g_input_df(const double2* G, const double2* dtau, int r, long long ncol,
+                              void* Gdf, double2* nk_out, cudaStream_t st, bool real_w) {
+  if (r > 128) return cudaErrorInvalidValue;
+  if (real_w)
+    g_input_kernel<true, true><<<grid_for(ncol, 256), 256, 0, st>>>(G, dtau, r, ncol, Gdf, nk_out);
+  else
+    g_input_kernel<false, true><<<grid_for(ncol, 256), 256, 0, st>>>(G, dtau, r, ncol, Gdf, nk_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_c128_to_df(const double2* in, void* out, long long n, cudaStream_t st) {
+  c128_to_df_kernel<<<grid_for(n, 256), 256, 0, st>>>(in, static_cast<dfc*>(out), n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_df_to_c128(const void* in, double2* out, long long n, cudaStream_t st) {
+  df_to_c128_kernel<<<grid_for(n, 256), 256, 0, st>>>(static_cast<const dfc*>(in), out, n);
   return cudaGetLastError();
 }
 
@@ -229,5 +266,6 @@ cudaError_t launch_c64_to_c128(const float2* in, double2* out, long long n, cuda
 
 template cudaError_t launch_k_average<double>(const void*, int, int, double2*, cudaStream_t);
 template cudaError_t launch_k_average<float>(const void*, int, int, double2*, cudaStream_t);
+template cudaError_t launch_k_average<dfl>(const void*, int, int, double2*, cudaStream_t);
 
 }  // namespace qa

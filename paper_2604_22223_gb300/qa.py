@@ -17,7 +17,8 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libqa.so")
 
-QA_FP64, QA_MIXED = 0, 1
+QA_FP64, QA_MIXED, QA_FP32 = 0, 1, 2
+PRECISIONS = {"fp64": QA_FP64, "mixed": QA_MIXED, "fp32": QA_FP32}
 QA_PAIRS_AUTO, QA_PAIRS_FULL, QA_PAIRS_REDUCED = 0, 1, 2
 QA_P_QNU, QA_WC_RTAU, QA_SIGC_KTAU, QA_SIGC_KIW, QA_SIGHF_K, QA_G0, QA_HK, QA_MU0 = range(1, 9)
 
@@ -118,14 +119,16 @@ class Problem:
 
     `model` provides n, norb, s_spin, hop_R, hop_t, eps, V_R, V, beta, Lambda,
     eps_dlr and filling (see workloads.Model).  `pairs` selects the basis of
-    the big tensors: "auto" (reduced on the mixed path), "full" or "reduced"
-    (include/qa.h, qa_set_pair_basis).  No GPU is touched.
+    the big tensors: "auto" (reduced on the mixed and FP32 paths), "full" or
+    "reduced" (include/qa.h, qa_set_pair_basis).  `precision`: "fp64",
+    "mixed" (double-float storage, FP32-based arithmetic, ~1e-9 of FP64) or
+    "fp32" (complex64 storage, the fast mode).  No GPU is touched.
     """
 
     def __init__(self, model, precision: str = "fp64", pairs: str = "auto"):
         L = load()
         self.model = model
-        self.precision = {"fp64": QA_FP64, "mixed": QA_MIXED}[precision]
+        self.precision = PRECISIONS[precision]
         self._keep = []
         lat = Lattice((C.c_int * 3)(*[int(v) for v in model.n]), int(model.norb), int(model.s_spin))
         hop, inter = self._structs(model)
@@ -316,7 +319,7 @@ class Context(Problem):
         the big tensors are [r][nb][nb][N_k], nb = rho on the reduced basis)."""
         torch = self.torch
         r, no, np_, nk = self.r, self.norb, self.nb, self.nk
-        big_dt = torch.complex128 if self.precision == QA_FP64 else torch.complex64
+        big_dt = {QA_FP64: torch.complex128, QA_MIXED: "df", QA_FP32: torch.complex64}[self.precision]
         shapes = {QA_P_QNU: ((r, np_, np_, nk), big_dt), QA_WC_RTAU: ((r, np_, np_, nk), big_dt),
                   QA_SIGC_KTAU: ((r, no, no, nk), big_dt), QA_SIGC_KIW: ((r, no, no, nk), big_dt),
                   QA_SIGHF_K: ((nk, no, no), torch.complex128),
@@ -326,7 +329,12 @@ class Context(Problem):
             _check(load().qa_get(self.ctx, QA_MU0, C.addressof(v), 8, self._stream()), "qa_get")
             return v.value
         shape, dt = shapes[which]
-        out = torch.empty(shape, dtype=dt, device=self.device)
-        _check(load().qa_get(self.ctx, which, out.data_ptr(), out.numel() * out.element_size(),
+        # double-float complex arrives as four floats (re.hi, re.lo, im.hi, im.lo)
+        raw = torch.empty(shape + (4,), dtype=torch.float32, device=self.device) if dt == "df" else \
+            torch.empty(shape, dtype=dt, device=self.device)
+        _check(load().qa_get(self.ctx, which, raw.data_ptr(), raw.numel() * raw.element_size(),
                              self._stream()), "qa_get")
-        return out
+        if dt == "df":
+            d = raw.double()
+            return torch.complex(d[..., 0] + d[..., 1], d[..., 2] + d[..., 3])
+        return raw

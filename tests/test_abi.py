@@ -132,7 +132,7 @@ def test_pair_basis(name, rho):
     density-density interaction, norb + norb(norb - 1)/2 (one density per orbital
     and one symmetric exchange/pair-hopping combination per orbital pair)."""
     m = wl.config(name)
-    p = qa.Problem(m, "mixed")
+    p = qa.Problem(m, "fp32")
     assert p.rho == rho
     B = p.basis
     assert B.shape == (m.norb ** 2, rho)
@@ -147,10 +147,10 @@ def test_pair_basis(name, rho):
     assert p.reduced == (rho < m.norb ** 2)
     assert not qa.Problem(m, "fp64").reduced
     assert qa.Problem(m, "fp64", pairs="reduced").reduced == (rho < m.norb ** 2)
-    assert not qa.Problem(m, "mixed", pairs="full").reduced
+    assert not qa.Problem(m, "fp32", pairs="full").reduced
     # the reduced workspace is smaller
     if rho < m.norb ** 2:
-        assert qa.Problem(m, "mixed").workspace_size() < qa.Problem(m, "mixed", pairs="full").workspace_size()
+        assert qa.Problem(m, "fp32").workspace_size() < qa.Problem(m, "fp32", pairs="full").workspace_size()
 
 
 def _canonical_pattern(norb):
@@ -170,7 +170,7 @@ def test_pair_basis_canonical_shape(name, canonical):
     the GPU parity tests of these workloads therefore exercise that kernel, and
     graphene's density-density basis exercises the generic term-list kernel."""
     m = wl.config(name)
-    B = qa.Problem(m, "mixed").basis
+    B = qa.Problem(m, "fp32").basis
     supp = [sorted(np.flatnonzero(np.abs(B[:, j]) > 0).tolist()) for j in range(B.shape[1])]
     match = supp == _canonical_pattern(m.norb)
     assert match == canonical
@@ -186,7 +186,7 @@ def test_pair_basis_rank_deficient_block():
     V = np.zeros_like(m.V)
     V[0][1, 1] = V[0][1, 2] = V[0][2, 1] = V[0][2, 2] = 0.7
     m.V = V
-    p = qa.Problem(m, "mixed")
+    p = qa.Problem(m, "fp32")
     assert p.rho == 1 and p.reduced
     b = p.basis[:, 0] * np.sign(p.basis[1, 0].real)
     assert np.allclose(b, [0, 2 ** -0.5, 2 ** -0.5, 0], atol=1e-15)

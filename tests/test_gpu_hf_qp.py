@@ -12,7 +12,7 @@ Quasiparticles: after one GW step from G0 on both sides (their Sigma's agree
 to 1e-10, tests/test_gpu_parity.py), Z, Sigma(0), H_QP and the QP energies are
 compared element by element.  Bounds: FP64 1e-8 relative (the Matsubara
 difference quotient divides by 2 w0 = 2 pi / beta); mixed 1e-4 (Sigma^C(k, i w)
-in complex64 carries 1e-5 relative error, test_gpu_parity.MIXED_BOUND).
+in complex64 carries 1e-5 relative error, test_gpu_parity.FP32_BOUND).
 """
 import functools
 
@@ -140,10 +140,10 @@ def test_qp_fp64(name):
 
 
 @pytest.mark.parametrize("name", ["peierls-5x3x2", "five-orbital-4x3x2", "graphene-6x6"])
-def test_qp_mixed(name):
+def test_qp_fp32(name):
     from paper_2604_22223_gb300 import qa
     m, d, o, ref = oracle_qp(name)
-    ctx = qa.Context(m, "mixed")
+    ctx = qa.Context(m, "fp32")
     ctx.step()
     _compare_qp(ctx.qp(), ref, 1e-4)
 
@@ -168,7 +168,7 @@ def test_paper_graphene_workflow():
     _compare_qp(ctx.qp(), ref, 1e-8)
 
 
-@pytest.mark.parametrize("precision,bound", [("fp64", 1e-8), ("mixed", 1e-4)])
+@pytest.mark.parametrize("precision,bound", [("fp64", 1e-8), ("fp32", 1e-4)])
 def test_paper_five_orbital_step_and_qp(precision, bound):
     """The paper's degenerate five-orbital benchmark model on a 3x3x2 grid."""
     from paper_2604_22223_gb300 import qa
@@ -184,7 +184,7 @@ def test_paper_five_orbital_hf_half_filling():
     particle-hole value mu = 9.5 (tests/test_golden_paper.py)."""
     from paper_2604_22223_gb300 import qa
     m = wl.config("five-orbital-paper-8x8x8")
-    ctx = qa.Context(m, "mixed")
+    ctx = qa.Context(m, "fp32")
     G, mu, n_loc, iters, resid, status = ctx.hf_solve(200, 1e-12, 1.0)
     assert abs(mu - 9.5) <= 1e-10
     # n_loc is the DLR density -G(beta^-) of the HF G (eps = 1e-10 grid at beta Lambda = 2500)
@@ -199,7 +199,7 @@ def test_bench_size_hf_and_qp_properties():
     from paper_2604_22223_gb300 import qa
     m = wl.config("five-orbital-32x32x8")
     res = qp.hf_loop(m, tol=HF_TOL, max_iter=200, mix=1.0)
-    ctx = qa.Context(m, "mixed")
+    ctx = qa.Context(m, "fp32")
     G, mu, n_loc, iters, resid, status = ctx.hf_solve(200, HF_TOL, 1.0)
     assert status == 0 and abs(iters - res["iters"]) <= 1
     assert rel(ctx.get(qa.QA_SIGHF_K).cpu().numpy(), res["sig_hf_k"]) <= 1e-8

@@ -35,12 +35,12 @@ def rel(a, b):
     return float(np.abs(np.asarray(a) - b).max() / max(np.abs(b).max(), 1e-300))
 
 
-def test_largest_grid_fp64_vs_mixed():
+def test_largest_grid_fp64_vs_fp32():
     from paper_2604_22223_gb300 import qa
     m = wl.config("peierls-3x3")
     m.n = (16, 32, 24)                        # N_k = 12288, the largest accepted grid
     out = {}
-    for prec in ("fp64", "mixed"):
+    for prec in ("fp64", "fp32"):
         ctx = qa.Context(m, prec)
         assert ctx.nk == 12288
         G, mu, n_loc, st = ctx.step()
@@ -48,7 +48,7 @@ def test_largest_grid_fp64_vs_mixed():
         out[prec] = (G.cpu().numpy(), mu, n_loc, st["N"])
         del ctx
     G64, mu64, n64, N64 = out["fp64"]
-    G32, mu32, n32, N32 = out["mixed"]
+    G32, mu32, n32, N32 = out["fp32"]
     assert abs(N64 - m.filling) <= 1e-10
     assert np.all(np.isfinite(G64)) and np.all(np.isfinite(G32))
     assert abs(mu32 - mu64) <= 2e-5 * max(1.0, abs(mu64))
@@ -68,7 +68,7 @@ def high_rank():
     return m, d, gw.gw_step(m, d, G0)
 
 
-@pytest.mark.parametrize("prec,bound", [("fp64", 1e-9), ("mixed", 1e-3)])
+@pytest.mark.parametrize("prec,bound", [("fp64", 1e-9), ("fp32", 1e-3)])
 def test_largest_rank_against_oracle(high_rank, prec, bound):
     from paper_2604_22223_gb300 import qa
     m, d, o = high_rank

@@ -23,9 +23,12 @@ FP64 = 1e-10
 # |N - N_target| <= 1e-12; in the graphene semimetal dN/dmu is small at the Dirac
 # points, so mu (and G) carry ~1e-10 of that root tolerance.
 FP64_G = 1e-9
-# Mixed path: FP32 rounding is amplified by the DLR Matsubara -> tau maps (W^C, G);
-# G also inherits the mu root found on FP32 densities and refined by one FP64 step.
-MIXED = {"P_qnu": 2e-6, "WC_Rtau": 2e-4, "sigc_ktau": 2e-4, "sigc_kiw": 2e-5, "sighf": 1e-9,
+# Mixed path (double-float): the stated 1e-7 on Sigma, and on every other output.
+MIXED = 1e-7
+# FP32 path (the fast mode): FP32 rounding is amplified by the DLR Matsubara -> tau
+# maps (W^C, G); G also inherits the mu root found on FP32 densities and refined by
+# one FP64 step.
+FP32 = {"P_qnu": 2e-6, "WC_Rtau": 2e-4, "sigc_ktau": 2e-4, "sigc_kiw": 2e-5, "sighf": 1e-9,
          "G": 1e-4, "mu": 5e-5}
 
 
@@ -61,7 +64,7 @@ def rel(a, b):
 
 
 @pytest.mark.parametrize("name", ["graphene-36x36", "five-orbital-16x16"])
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
 def test_full_step(name, prec):
     from paper_2604_22223_gb300 import qa
     m = wl.config(name)
@@ -80,7 +83,7 @@ def test_full_step(name, prec):
         "mu": abs(mu - o["mu"]) / max(1.0, abs(o["mu"])),
     }
     for k, e in errs.items():
-        bound = (FP64_G if k in ("G", "mu") else FP64) if prec == "fp64" else MIXED[k]
+        bound = {"fp64": FP64_G if k in ("G", "mu") else FP64, "mixed": MIXED, "fp32": FP32[k]}[prec]
         assert e <= bound, (k, e, bound, errs)
 
 
@@ -92,7 +95,7 @@ def bench_oracle():
     return m, d, G0, mu0
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
 def test_benchmark_grid_sampled(bench_oracle, prec):
     import torch
     from paper_2604_22223_gb300 import qa
@@ -115,15 +118,15 @@ def test_benchmark_grid_sampled(bench_oracle, prec):
         if ctx.reduced:
             ref = np.einsum("ai,tab,bj->tij", ctx.basis.conj(), ref, ctx.basis)
         got = P[..., iq].cpu().numpy()
-        assert rel(got, ref) <= (FP64 if prec == "fp64" else MIXED["P_qnu"]), iq
+        assert rel(got, ref) <= {"fp64": FP64, "mixed": MIXED, "fp32": FP32["P_qnu"]}[prec], iq
     # sum rule and filling of the new G
     Gc = G.cpu().numpy()                                  # [r][a][b][k]
     c = np.linalg.solve(d.K_tau(), Gc.reshape(d.r, -1))
     g0p = (d.K_tau(np.array([0.0]))[0] @ c).reshape(m.norb, m.norb, m.nk)
     gbm = (d.K_beta() @ c).reshape(m.norb, m.norb, m.nk)
-    tol = 1e-7 if prec == "fp64" else 1e-3
+    tol = {"fp64": 1e-7, "mixed": 1e-6, "fp32": 1e-3}[prec]
     assert np.abs(g0p + gbm + np.eye(m.norb)[:, :, None]).max() <= tol
-    assert abs(st["N"] - m.filling) <= (1e-11 if prec == "fp64" else 1e-5)
+    assert abs(st["N"] - m.filling) <= (1e-5 if prec == "fp32" else 1e-11)
     # time reversal of a real-hopping model: Sigma^C(-k, tau) = Sigma^C(k, tau)^T
     S = ctx.get(qa.QA_SIGC_KTAU).cpu().numpy()
     mk = lattice.minus_R_index(m.n)
