@@ -376,3 +376,73 @@ def test_hartree_fock_fock_space():
             E_hf = 0.5 * m.s_spin * np.trace((sig_h + sig_f[0]) @ n)
             E_ex = _fock_space_energy(V, C, no)
             assert abs(E_hf - E_ex) <= 1e-12 * max(1.0, abs(E_ex))
+
+
+# ------------------------------------------- explicit-sum forms and the G Dyson step
+
+@pytest.mark.parametrize("name", ["peierls-3x3", "five-orbital-4x3x2"])
+def test_polarization_at_q_matches_real_space_bubble(name):
+    """The explicit k-sum bubble -(s/N) sum_k G_bc(k, tau) G_da(k - q, beta - tau)
+    (Eq. for the polarizability written as a convolution) equals, at every q, the
+    real-space product G(R) G(-R) followed by the FFT R -> q that gw_step uses.
+    A wrong k - q index or pair orientation in either form breaks the agreement
+    (peierls-3x3 has complex hoppings, so G(k) != G(-k))."""
+    m = wl.config(name)
+    d = gw.make_dlr(m)
+    G0, _ = gw.g0(m, d)
+    o = gw.gw_step(m, d, G0)
+    Grefl = gw.reflected(m, d, G0)
+    for iq in range(m.nk):
+        got = gw.polarization_at_q(m, d, G0, iq, Grefl)
+        ref = o["P_qnu"][iq]
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(o["P_qnu"]).max(), iq
+
+
+@pytest.mark.parametrize("name", ["peierls-3x3", "five-orbital-4x3x2"])
+def test_self_energy_at_k_matches_real_space_product(name):
+    """The explicit q-sum -(1/N) sum_q G_bc(k - q, tau) W^C_(ab),(cd)(q, tau) (Eq. for
+    the GW self-energy as a convolution) equals, at every k, the real-space
+    product -G(R) W^C(R) followed by the FFT that gw_step uses."""
+    m = wl.config(name)
+    d = gw.make_dlr(m)
+    G0, _ = gw.g0(m, d)
+    o = gw.gw_step(m, d, G0)
+    scale = np.abs(o["sigc_ktau"]).max()
+    for ik in range(m.nk):
+        got = gw.self_energy_at_k(m, G0, o["WC_qtau"], ik)
+        assert np.abs(got - o["sigc_ktau"][ik]).max() <= 1e-12 * scale, ik
+
+
+def test_dyson_g_with_pole_self_energy_closed_form():
+    """G(k, i w) = (i w + mu - H(k) - Sigma(i w))^-1 (Eq. for the full Green's
+    function) with a frequency-dependent Sigma(i w) = V V^H / (i w - w0) is the
+    upper-left block of the resolvent of the Hermitian matrix
+    M = [[H - mu, V], [V^H, w0]] (Schur complement), so G(k, tau) is the pole sum
+    sum_m U_am U*_bm K(tau, lambda_m) over M's eigenpairs.  Complex, non-commuting
+    H(k) and V make a sign error in Sigma or a transposed Sigma fail."""
+    rng = np.random.default_rng(5)
+    no, nk, beta, mu, w0 = 2, 3, 10.0, 0.3, -0.7
+    d = DLR(beta, 200.0, 1e-12)
+    A = rng.normal(size=(nk, no, no)) + 1j * rng.normal(size=(nk, no, no))
+    Hk = 0.5 * (A + np.conj(np.swapaxes(A, 1, 2)))
+    V = 0.6 * (rng.normal(size=(no, no)) + 1j * rng.normal(size=(no, no)))
+    iw = d.iw()
+    sig = (V @ V.conj().T)[None, None] / (iw[None, :, None, None] - w0)
+    sig = np.broadcast_to(sig, (nk, d.r, no, no))
+    Giw = gw.g_iw(d, Hk, mu, None, sig)
+    Gtau = gw._node_axis_apply(d.K_tau(), gw._node_axis_solve(d.K_iw(), Giw))
+    for k in range(nk):
+        M = np.zeros((2 * no, 2 * no), dtype=np.complex128)
+        M[:no, :no] = Hk[k] - mu * np.eye(no)
+        M[:no, no:] = V
+        M[no:, :no] = V.conj().T
+        M[no:, no:] = w0 * np.eye(no)
+        lam, U = np.linalg.eigh(M)
+        Uo = U[:no]
+        # Matsubara nodes: sum_m U_am U*_bm / (i w - lambda_m)
+        ref_iw = np.einsum("am,nm,bm->nab", Uo, 1.0 / (iw[:, None] - lam[None, :]), Uo.conj())
+        assert np.abs(Giw[k] - ref_iw).max() <= 1e-12 * np.abs(ref_iw).max()
+        # tau nodes: sum_m U_am U*_bm K(tau, lambda_m), K = -k(t, beta lambda)
+        K = -kfun(d.t, beta * lam)                             # [tau, m]
+        ref_tau = np.einsum("am,tm,bm->tab", Uo, K, Uo.conj())
+        assert np.abs(Gtau[k] - ref_tau).max() <= 1e-9 * np.abs(ref_tau).max()
