@@ -133,6 +133,15 @@ struct qa_ctx {
   void* d_tc_Trefl = nullptr;
   void* d_tc_Ttw = nullptr;
   void* d_tc_Twt = nullptr;
+  // tensor-core DLR operands of the accurate mixed path (fixed-point bf16 slices)
+  bool use_oz = false;
+  std::vector<uint8_t> oz_Ttn, oz_Tnt, oz_Trefl, oz_Ttw, oz_Twt;
+  void* d_oz_Ttn = nullptr;
+  void* d_oz_Tnt = nullptr;
+  void* d_oz_Trefl = nullptr;
+  void* d_oz_Ttw = nullptr;
+  void* d_oz_Twt = nullptr;
+  void* d_Pnu = nullptr;          // third big tensor (QA_MIXED): P(q, i nu)
   // pair basis of the big tensors: full (npair) or reduced (rho, qa_basis.cpp)
   int pair_mode = QA_PAIRS_AUTO;
   bool reduced = false;
@@ -350,6 +359,7 @@ size_t layout(qa_ctx* c, char* base) {
   // big tensors last; P must also hold the FP64 V(q) staging of qa_bind
   c->d_P = take(std::max(r * nb2 * nk * es, nk * nb2 * 16));
   c->d_W = take(r * nb2 * nk * es);
+  if (c->precision == QA_MIXED && c->use_oz) c->d_Pnu = take(r * nb2 * nk * es);
   c->nblocks_g = qa::dyson_g_blocks(c->r, c->nk);
   c->d_part = static_cast<double*>(take(2 * static_cast<size_t>(c->nblocks_g) * 8));
   c->d_red = static_cast<double*>(take(2 * 8));
@@ -357,6 +367,13 @@ size_t layout(qa_ctx* c, char* base) {
   c->d_bad = static_cast<long long*>(take(8));
   c->d_nloc = static_cast<double2*>(take(no2 * 16));
   c->d_wq = static_cast<double2*>(take(2 * r * 16));
+  if (c->precision == QA_MIXED && c->use_oz) {
+    c->d_oz_Ttn = take(c->oz_Ttn.size());
+    c->d_oz_Tnt = take(c->oz_Tnt.size());
+    c->d_oz_Trefl = take(c->oz_Trefl.size());
+    c->d_oz_Ttw = take(c->oz_Ttw.size());
+    c->d_oz_Twt = take(c->oz_Twt.size());
+  }
   if (c->precision == QA_FP32 && c->use_tc) {
     c->d_tc_Ttn = take(c->tc_Ttn.size() * 2);
     c->d_tc_Tnt = take(c->tc_Tnt.size() * 2);
@@ -660,8 +677,13 @@ int finish_g(qa_ctx* c, const DevTables& tab, double mu, void* G_out_c128, doubl
   if (is_f64<T>()) {
     QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Twt, c->r, c->r, c->d_Giw, G_out_c128, ncol, st));
   } else if (is_df<T>()) {
-    QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Twt, c->r, c->r, c->d_Giw, c->d_Gt, ncol, st));
-    QA_LAUNCH(c, 1, qa::launch_df_to_c128(c->d_Gt, static_cast<double2*>(G_out_c128), ncol * c->r, st));
+    if (c->use_oz) {
+      // the transform stores complex128 directly
+      QA_LAUNCH(c, 1, qa::launch_dlr_oz(c->d_oz_Twt, c->r, c->d_Giw, G_out_c128, ncol, c->d_err, st, true));
+    } else {
+      QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Twt, c->r, c->r, c->d_Giw, c->d_Gt, ncol, st));
+      QA_LAUNCH(c, 1, qa::launch_df_to_c128(c->d_Gt, static_cast<double2*>(G_out_c128), ncol * c->r, st));
+    }
   } else {
     if (c->use_tc) {
       // the transform stores complex128 directly
@@ -741,8 +763,11 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
                        c->n[1], c->n[2], c->d_sigFR, c->d_SigHF, st, c->d_phV));
   tm.mark();  // 0: HF
   // G(k, beta - tau), real-space G
+  const bool oz = is_df<T>() && c->use_oz;
   if (f32 && c->use_tc)
     QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Trefl, r, Gk, c->d_Grefl, ncs, c->d_err, st));
+  else if (oz)
+    QA_LAUNCH(c, 1, qa::launch_dlr_oz(c->d_oz_Trefl, r, Gk, c->d_Grefl, ncs, c->d_err, st));
   else
     QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Trefl, r, r, Gk, c->d_Grefl, ncs, st));
   QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, +1, Gk, c->d_GR, ncs / nk * r, st));
@@ -764,18 +789,29 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
     QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, -1, c->d_P, c->d_P, ncb / nk * r, st));
   }
   tm.mark();  // 3: FFT R -> q
-  if (f32 && c->use_tc)
-    QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Ttn, r, c->d_P, c->d_P, ncb, c->d_err, st));
-  else
-    QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Ttn, r, r, c->d_P, c->d_P, ncb, st));
-  tm.mark();  // 4: DLR tau -> nu
-  QA_LAUNCH(c, 1, qa::launch_dyson_w<T>(c->d_P, c->d_Vq, c->d_W, r, c->nb, nk, c->d_err, c->d_bad, st,
-                                        &c->dblk));
-  tm.mark();  // 5: Dyson W
-  if (f32 && c->use_tc)
-    QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Tnt, r, c->d_W, c->d_W, ncb, c->d_err, st));
-  else
-    QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Tnt, r, r, c->d_W, c->d_W, ncb, st));
+  if (oz) {
+    // out-of-place tensor-core maps: P(q, tau) [P] -> P(q, i nu) [Pnu] -> W^C(q, i nu) [P]
+    // -> W^C(q, tau) [W]
+    QA_LAUNCH(c, 1, qa::launch_dlr_oz(c->d_oz_Ttn, r, c->d_P, c->d_Pnu, ncb, c->d_err, st));
+    tm.mark();  // 4: DLR tau -> nu
+    QA_LAUNCH(c, 1, qa::launch_dyson_w<T>(c->d_Pnu, c->d_Vq, c->d_P, r, c->nb, nk, c->d_err, c->d_bad, st,
+                                          &c->dblk));
+    tm.mark();  // 5: Dyson W
+    QA_LAUNCH(c, 1, qa::launch_dlr_oz(c->d_oz_Tnt, r, c->d_P, c->d_W, ncb, c->d_err, st));
+  } else {
+    if (f32 && c->use_tc)
+      QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Ttn, r, c->d_P, c->d_P, ncb, c->d_err, st));
+    else
+      QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Ttn, r, r, c->d_P, c->d_P, ncb, st));
+    tm.mark();  // 4: DLR tau -> nu
+    QA_LAUNCH(c, 1, qa::launch_dyson_w<T>(c->d_P, c->d_Vq, c->d_W, r, c->nb, nk, c->d_err, c->d_bad, st,
+                                          &c->dblk));
+    tm.mark();  // 5: Dyson W
+    if (f32 && c->use_tc)
+      QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Tnt, r, c->d_W, c->d_W, ncb, c->d_err, st));
+    else
+      QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Tnt, r, r, c->d_W, c->d_W, ncb, st));
+  }
   tm.mark();  // 6: DLR nu -> tau
   QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, +1, c->d_W, c->d_W, ncb / nk * r, st));
   tm.mark();  // 7: FFT q -> R
@@ -792,6 +828,8 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
   QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, -1, c->d_SigC, c->d_SigC, ncs / nk * r, st));
   if (f32 && c->use_tc)
     QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Ttw, r, c->d_SigC, c->d_SigIw, ncs, c->d_err, st));
+  else if (oz)
+    QA_LAUNCH(c, 1, qa::launch_dlr_oz(c->d_oz_Ttw, r, c->d_SigC, c->d_SigIw, ncs, c->d_err, st));
   else
     QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Ttw, r, r, c->d_SigC, c->d_SigIw, ncs, st));
   tm.mark();  // 9: Sigma -> (k, i w)
@@ -1209,6 +1247,14 @@ int qa_create(const qa_lattice* lat, const qa_hoppings* hop, const qa_interactio
   if (qa::build_dlr(Lambda, eps, &c->grid) != 0) { delete c; return QA_EINVAL; }
   c->r = c->grid.r;
   qa::build_dlr_matrices(c->grid, beta, &c->mats);
+  if (precision == QA_MIXED && qa::dlr_oz_supported(c->r)) {
+    c->use_oz = true;
+    qa::pack_dlr_oz(c->mats.Ttn.data(), c->r, &c->oz_Ttn);
+    qa::pack_dlr_oz(c->mats.Tnt.data(), c->r, &c->oz_Tnt);
+    qa::pack_dlr_oz(c->mats.Trefl.data(), c->r, &c->oz_Trefl);
+    qa::pack_dlr_oz(c->mats.Ttw.data(), c->r, &c->oz_Ttw);
+    qa::pack_dlr_oz(c->mats.Twt.data(), c->r, &c->oz_Twt);
+  }
   if (precision == QA_FP32 && qa::dlr_tc_supported(c->r, nullptr)) {
     const char* env = std::getenv("QA_DLR_SIMT");
     c->use_tc = !(env && env[0] == '1');
@@ -1311,6 +1357,13 @@ int qa_bind(qa_ctx* c, void* workspace, size_t bytes, void* stream) {
     wq.insert(wq.end(), m.wq_m.begin(), m.wq_m.end());
     QA_TRY(upload_c<double>(c->d_wq, wq, st));
     QA_TRY(cudaStreamSynchronize(st));    // wq goes out of scope
+  }
+  if (c->use_oz) {
+    QA_TRY(cudaMemcpyAsync(c->d_oz_Ttn, c->oz_Ttn.data(), c->oz_Ttn.size(), cudaMemcpyHostToDevice, st));
+    QA_TRY(cudaMemcpyAsync(c->d_oz_Tnt, c->oz_Tnt.data(), c->oz_Tnt.size(), cudaMemcpyHostToDevice, st));
+    QA_TRY(cudaMemcpyAsync(c->d_oz_Trefl, c->oz_Trefl.data(), c->oz_Trefl.size(), cudaMemcpyHostToDevice, st));
+    QA_TRY(cudaMemcpyAsync(c->d_oz_Ttw, c->oz_Ttw.data(), c->oz_Ttw.size(), cudaMemcpyHostToDevice, st));
+    QA_TRY(cudaMemcpyAsync(c->d_oz_Twt, c->oz_Twt.data(), c->oz_Twt.size(), cudaMemcpyHostToDevice, st));
   }
   if (c->use_tc) {
     QA_TRY(cudaMemcpyAsync(c->d_tc_Ttn, c->tc_Ttn.data(), c->tc_Ttn.size() * 2, cudaMemcpyHostToDevice, st));
@@ -1471,7 +1524,7 @@ int qa_get(const qa_ctx* c, int which, void* dst, size_t bytes, void* stream) {
   const void* src = nullptr;
   size_t need = 0;
   switch (which) {
-    case QA_P_QNU: src = c->d_P; need = r * nb2 * nk * es; break;
+    case QA_P_QNU: src = c->d_Pnu ? c->d_Pnu : c->d_P; need = r * nb2 * nk * es; break;
     case QA_WC_RTAU: src = c->d_W; need = r * nb2 * nk * es; break;
     case QA_SIGC_KTAU: src = c->d_SigC; need = r * no2 * nk * es; break;
     case QA_SIGC_KIW: src = c->d_SigIw; need = r * no2 * nk * es; break;

@@ -109,6 +109,25 @@ void pack_dlr_tc(const std::complex<double>* T, int r, std::vector<uint16_t>* ds
 cudaError_t launch_dlr_tc(const void* Bsplit, int r, const void* in, void* out, long long ncol,
                           int* err, cudaStream_t st, bool out_c128 = false);
 
+// Accurate DLR transform of double-float (dfc) columns on the tensor cores from
+// fixed-point bf16 slices (qa_dlr_oz.cu); out must not alias in.  The packed
+// operand (pack_dlr_oz) holds, per part of at most 96 output rows of the real
+// embedding, five slices [Nw][Kp] in the canonical layout, then the row
+// exponents.  Supported when 2r <= 192.
+struct DlrOzLayout {
+  int nparts = 0, Kp = 0;
+  int n0[2] = {0, 0}, Nw[2] = {0, 0};
+  long long off[2] = {0, 0};
+  long long rexp_off = 0, bytes = 0;
+  size_t smem = 0;
+};
+DlrOzLayout dlr_oz_layout(int r);
+bool dlr_oz_supported(int r);
+void pack_dlr_oz(const std::complex<double>* T, int r, std::vector<uint8_t>* dst);
+// out_c128: store complex128 instead of double-float.
+cudaError_t launch_dlr_oz(const void* pack, int r, const void* in, void* out, long long ncol,
+                          int* err, cudaStream_t st, bool out_c128 = false);
+
 // Batched 3-D FFT of contiguous lines of N_k points (in place allowed).
 // sign = -1: X(k) = sum_R e^{-ikR} X(R); sign = +1: (1/N_k) sum_k e^{+ikR} X(k).
 // scale > 0 replaces the default factor (1 for sign -1, 1/N_k for sign +1).
