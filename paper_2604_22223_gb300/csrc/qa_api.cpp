@@ -142,6 +142,9 @@ struct qa_ctx {
   void* d_oz_Ttw = nullptr;
   void* d_oz_Twt = nullptr;
   void* d_Pnu = nullptr;          // third big tensor (QA_MIXED): P(q, i nu)
+  int* d_tgo = nullptr;           // Sigma terms regrouped by target entry (QA_MIXED): offsets,
+  void* d_tgi = nullptr;          // (Wt entry, G entry) pairs
+  void* d_tgc = nullptr;          // and double-float coefficients
   // pair basis of the big tensors: full (npair) or reduced (rho, qa_basis.cpp)
   int pair_mode = QA_PAIRS_AUTO;
   bool reduced = false;
@@ -360,6 +363,12 @@ size_t layout(qa_ctx* c, char* base) {
   c->d_P = take(std::max(r * nb2 * nk * es, nk * nb2 * 16));
   c->d_W = take(r * nb2 * nk * es);
   if (c->precision == QA_MIXED && c->use_oz) c->d_Pnu = take(r * nb2 * nk * es);
+  if (c->precision == QA_MIXED) {
+    const size_t cap = term_capacity(c);
+    c->d_tgo = static_cast<int*>(take((no2 + 1) * 4));
+    c->d_tgi = take(cap * 8);
+    c->d_tgc = take(cap * 16);
+  }
   c->nblocks_g = qa::dyson_g_blocks(c->r, c->nk);
   c->d_part = static_cast<double*>(take(2 * static_cast<size_t>(c->nblocks_g) * 8));
   c->d_red = static_cast<double*>(take(2 * 8));
@@ -459,6 +468,27 @@ int upload_interaction(qa_ctx* c, cudaStream_t st) {
       else if (c->precision == QA_MIXED) QA_TRY(upload_c<qa::dfl>(dc[k], tl[k]->coef, st));
       else QA_TRY(upload_c<float>(dc[k], tl[k]->coef, st));
     }
+  }
+  if (c->precision == QA_MIXED) {
+    // the Sigma terms grouped by target entry Sigma_ad (idx >> 8), in list order
+    const qa::PairTerms& ts = c->tsig;
+    const int no2 = c->norb * c->norb, nout = static_cast<int>(ts.off.size()) - 1;
+    std::vector<int> toff(no2 + 1, 0), tidx;
+    std::vector<cd> tcoef;
+    for (int tg = 0; tg < no2; ++tg) {
+      toff[tg] = static_cast<int>(tcoef.size());
+      for (int o = 0; o < nout; ++o)
+        for (int e = ts.off[o]; e < ts.off[o + 1]; ++e)
+          if ((ts.idx[e] >> 8) == tg) {
+            tidx.push_back(o);
+            tidx.push_back(ts.idx[e] & 255);
+            tcoef.push_back(ts.coef[e]);
+          }
+    }
+    toff[no2] = static_cast<int>(tcoef.size());
+    QA_TRY(cudaMemcpyAsync(c->d_tgo, toff.data(), toff.size() * 4, cudaMemcpyHostToDevice, st));
+    QA_TRY(cudaMemcpyAsync(c->d_tgi, tidx.data(), tidx.size() * 4, cudaMemcpyHostToDevice, st));
+    QA_TRY(upload_c<qa::dfl>(c->d_tgc, tcoef, st));
   }
   if (c->reduced) {
     if (c->nV > 0) QA_TRY(upload_c<double>(c->d_sV, c->sV, st));
@@ -794,8 +824,12 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
     // -> W^C(q, tau) [W]
     QA_LAUNCH(c, 1, qa::launch_dlr_oz(c->d_oz_Ttn, r, c->d_P, c->d_Pnu, ncb, c->d_err, st));
     tm.mark();  // 4: DLR tau -> nu
-    QA_LAUNCH(c, 1, qa::launch_dyson_w<T>(c->d_Pnu, c->d_Vq, c->d_P, r, c->nb, nk, c->d_err, c->d_bad, st,
-                                          &c->dblk));
+    if (qa::dyson_w_df_supported(c->nb))
+      QA_LAUNCH(c, 1, qa::launch_dyson_w_df(c->d_Pnu, c->d_Vq, c->d_P, r, c->nb, nk, c->d_err, c->d_bad,
+                                            st, &c->dblk));
+    else
+      QA_LAUNCH(c, 1, qa::launch_dyson_w<T>(c->d_Pnu, c->d_Vq, c->d_P, r, c->nb, nk, c->d_err, c->d_bad,
+                                            st, &c->dblk));
     tm.mark();  // 5: Dyson W
     QA_LAUNCH(c, 1, qa::launch_dlr_oz(c->d_oz_Tnt, r, c->d_P, c->d_W, ncb, c->d_err, st));
   } else {
@@ -818,6 +852,9 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
   if (c->reduced && f32 && c->sig_canon)
     QA_LAUNCH(c, 1, qa::launch_sigma_canonical(c->d_GR, c->d_W, c->tsig.coef.data(), c->sig_canon,
                                                c->d_SigC, r, nk, st));
+  else if (is_df<T>())
+    QA_LAUNCH(c, 1, qa::launch_sigma_target_df(c->d_GR, c->d_W, c->d_tgo, c->d_tgi, c->d_tgc, c->d_SigC,
+                                               r, c->norb, nb2, nk, st));
   else if (c->reduced)
     QA_LAUNCH(c, 1, qa::launch_sigma_reduced<T>(c->d_GR, c->d_W, c->d_tsig, c->d_csig,
                                                 static_cast<int>(c->tsig.idx.size()), c->d_SigC, r,

@@ -1,0 +1,344 @@
+// Screened interaction on the accurate mixed path (paper Eq. for W):
+// W^C = (1 - S P)^-1 S P S per (q, i nu) with P and S(q) given in double-float,
+// as an FP32 solve refined by one double-float residual step (mixed-precision
+// iterative refinement):
+//   1. A = 1 - S P and B = S P S from the FP32 high parts; Gauss-Jordan
+//      elimination of [A | B] with partial pivoting in FP32 gives X0 and
+//      leaves each lane its elimination multipliers;
+//   2. R = B - A X0 = S Z - X0 with Z = P (S + X0), in double-float (every
+//      product split exactly by an FMA, compensated sums);
+//   3. delta = A^-1 R by replaying the recorded elimination on R in FP32;
+//   4. X1 = X0 + delta as a double-float.
+// One step takes the FP32 error cond(A) u to (cond(A) u)^2.  S is block
+// diagonal on the reduced pair basis (the interaction's connected pair
+// components); its rows are kept compactly (BW entries from lo[i]).
+//
+// Layout: 16 lanes per system (lane i = row i), two systems per warp, four
+// warps per block over 8 consecutive q at one nu; the tiles sit in shared
+// memory and move to and from HBM in coalesced runs along q.
+#include "qa_common.cuh"
+
+namespace qa {
+namespace {
+
+constexpr int kDfLanes = 16;
+constexpr int kDfWarps = 4;
+constexpr int kDfSys = kDfWarps * 32 / kDfLanes;      // systems per block
+constexpr int kPS = 17;                               // padded row stride of the 16-wide tiles
+
+__device__ void report_df(int* err, long long* first_bad, int code, long long idx) {
+  atomicCAS(err, 0, code);
+  if (first_bad) atomicMin(reinterpret_cast<unsigned long long*>(first_bad),
+                           static_cast<unsigned long long>(idx));
+}
+
+// double-float accumulator with an unnormalised low part: value = s + e
+struct DfAcc {
+  float s, e;
+};
+__device__ __forceinline__ void acc_add(DfAcc& a, float p) {
+  float t;
+  two_sum(a.s, p, a.s, t);
+  a.e = __fadd_rn(a.e, t);
+}
+// a += x * y (x double-float, y FP32): the product x.hi y split exactly
+__device__ __forceinline__ void acc_fma(DfAcc& a, dfl x, float y) {
+  const float p = __fmul_rn(x.hi, y);
+  const float q = __fmaf_rn(x.hi, y, -p);
+  acc_add(a, p);
+  a.e = __fadd_rn(a.e, __fmaf_rn(x.lo, y, q));
+}
+// a += x * y (both double-float)
+__device__ __forceinline__ void acc_fma(DfAcc& a, dfl x, dfl y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float q = __fmaf_rn(x.hi, y.hi, -p);
+  q = __fmaf_rn(x.hi, y.lo, q);
+  q = __fmaf_rn(x.lo, y.hi, q);
+  acc_add(a, p);
+  a.e = __fadd_rn(a.e, q);
+}
+__device__ __forceinline__ dfl acc_val(const DfAcc& a) { return df_norm(a.s, a.e); }
+
+// re/im accumulators of a complex sum
+struct CAcc {
+  DfAcc re, im;
+};
+__device__ __forceinline__ void cacc_fma(CAcc& a, dfc x, float2 y) {
+  acc_fma(a.re, x.x, y.x);
+  acc_fma(a.re, -x.y, y.y);
+  acc_fma(a.im, x.x, y.y);
+  acc_fma(a.im, x.y, y.x);
+}
+__device__ __forceinline__ void cacc_fma(CAcc& a, dfc x, dfc y) {
+  acc_fma(a.re, x.x, y.x);
+  acc_fma(a.re, -x.y, y.y);
+  acc_fma(a.im, x.x, y.y);
+  acc_fma(a.im, x.y, y.x);
+}
+
+__device__ __forceinline__ float2 hi2(dfc v) { return make_float2(v.x.hi, v.y.hi); }
+
+// NFIX > 0: system size fixed at compile time.  BW: bound of the block width of S.
+template <int NFIX, int BW>
+__global__ void __launch_bounds__(kDfWarps * 32, 3) dyson_w_df_kernel(
+    const dfc* __restrict__ P, const dfc* __restrict__ Vq, dfc* __restrict__ WC, int n_arg, int nk,
+    int* err, long long* first_bad, DysonBlocks blk) {
+  const int n = NFIX > 0 ? NFIX : n_arg;
+  constexpr int M = kDfLanes;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  dfc* Pt = reinterpret_cast<dfc*>(smem_raw);                 // [sys][M][kPS]: P, then Z, then X1
+  dfc* Sc = Pt + kDfSys * M * kPS;                             // [sys][M][BW] rows of S in their block
+  float2* X0 = reinterpret_cast<float2*>(Sc + kDfSys * M * BW);   // [sys][M][kPS]
+  float2* Rb = X0 + kDfSys * M * kPS;                          // [sys][2][2 M] pivot rows
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int l = lane & (M - 1);
+  const int sys = tid / M;
+  const int q0 = blockIdx.x * kDfSys;
+  const int nu = blockIdx.y;
+  const int nn = n * n;
+  const size_t slab = static_cast<size_t>(nu) * nn * nk;
+  // block bounds of row i of S (the whole row when no block structure is known)
+  auto blo = [&](int i) { return blk.nblk > 0 ? static_cast<int>(blk.lo[i]) : 0; };
+  auto bhi = [&](int i) { return blk.nblk > 0 ? static_cast<int>(blk.hi[i]) : n; };
+  // ---- tiles: P (coalesced along q), rows of S
+  for (int idx = tid; idx < kDfSys * M * M; idx += blockDim.x) {
+    const int ss = idx % kDfSys, e = idx / kDfSys;
+    const int i = e / M, j = e - i * M;
+    const int q = q0 + ss;
+    dfc v = dfc{dfl(0.f, 0.f), dfl(0.f, 0.f)};
+    if (i < n && j < n && q < nk) v = ldg_c(P + slab + static_cast<size_t>(i * n + j) * nk + q);
+    Pt[(ss * M + i) * kPS + j] = v;
+  }
+  for (int idx = tid; idx < kDfSys * M * BW; idx += blockDim.x) {
+    const int ss = idx / (M * BW), e = idx - ss * (M * BW);
+    const int i = e / BW, t = e - i * BW;
+    const int q = q0 + ss;
+    dfc v = dfc{dfl(0.f, 0.f), dfl(0.f, 0.f)};
+    if (i < n && q < nk) {
+      const int m = blo(i) + t;
+      if (m < bhi(i)) v = ldg_c(Vq + static_cast<size_t>(q) * nn + i * n + m);
+    }
+    Sc[(ss * M + i) * BW + t] = v;
+  }
+  __syncthreads();
+  const int q = q0 + sys;
+  dfc* Pw = Pt + sys * M * kPS;
+  const dfc* Sw = Sc + sys * M * BW;
+  float2* Xw = X0 + sys * M * kPS;
+  float2* Rw = Rb + sys * 4 * M;
+  const bool row = l < n;
+  const int lo_l = row ? blo(l) : 0, hi_l = row ? bhi(l) : 0;
+
+  // ---- 1. a = row l of S P, b = row l of (S P) S, from the FP32 high parts
+  float2 a[M], b[M];
+#pragma unroll
+  for (int j = 0; j < M; ++j) a[j] = make_float2(0.f, 0.f);
+  for (int m = lo_l; m < hi_l; ++m) {
+    const float2 slm = hi2(Sw[l * BW + (m - lo_l)]);
+#pragma unroll
+    for (int j = 0; j < M; ++j)
+      if (j < n) a[j] = cfma(slm, hi2(Pw[m * kPS + j]), a[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < M; ++j) b[j] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    if (m < n) {
+      const int lo_m = blo(m), hi_m = bhi(m);
+#pragma unroll
+      for (int k = 0; k < M; ++k)
+        if (k >= lo_m && k < hi_m) b[k] = cfma(a[m], hi2(Sw[m * BW + (k - lo_m)]), b[k]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < M; ++j) {
+    a[j].x = (row && j == l ? 1.f : 0.f) - a[j].x;
+    a[j].y = -a[j].y;
+  }
+
+  // ---- Gauss-Jordan on [A | B] in FP32, recording each lane's multipliers
+  bool used = !row;
+  int mypos = -1;
+  float2 dval = make_float2(1.f, 0.f);
+  bool singular = false;
+  float2 frec[M];
+#pragma unroll
+  for (int c = 0; c < M; ++c) {
+    frec[c] = make_float2(0.f, 0.f);
+    if (c < n) {
+      float2* Ra_c = Rw + (c & 1) * 2 * M;
+      float2* Rb_c = Ra_c + M;
+      const float v2 = cabs2(a[c]);
+      unsigned key = used ? 0u : (max(__float_as_uint(v2) & ~0xFu, 0x10u) | (M - 1 - l));
+#pragma unroll
+      for (int o = M / 2; o > 0; o >>= 1) key = max(key, __shfl_xor_sync(0xffffffffu, key, o));
+      const int p = M - 1 - static_cast<int>(key & (M - 1));
+      if (!(__uint_as_float(key & ~0xFu) >= 1e-12f)) singular = true;
+      const bool me = (l == p);
+      if (me) {
+        used = true;
+        mypos = c;
+        dval = a[c];
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+          if (j >= c) Ra_c[j] = a[j];
+          Rb_c[j] = b[j];
+        }
+      }
+      __syncwarp();
+      const float2 apc = Ra_c[c];
+      const float2 f = me ? make_float2(0.f, 0.f) : cmul(a[c], cinv(apc));
+      frec[c] = f;
+#pragma unroll
+      for (int j = 0; j < M; ++j) {
+        if (j > c && j < n) a[j] = cfms(f, Ra_c[j], a[j]);
+        if (j < n) b[j] = cfms(f, Rb_c[j], b[j]);
+      }
+    }
+  }
+  // X0: row mypos of the FP32 solution
+  if (mypos >= 0) {
+    const float2 inv = cinv(dval);
+#pragma unroll
+    for (int j = 0; j < M; ++j) Xw[mypos * kPS + j] = j < n ? cmul(b[j], inv) : make_float2(0.f, 0.f);
+  }
+  __syncwarp();
+
+  // ---- 2. residual R = S Z - X0, Z = P (S + X0), in double-float.  Row l of Z
+  // overwrites row l of P in place, so it is computed whole (columns four at a
+  // time) before any of it is stored; the loops over j stay rolled (the
+  // instruction cache holds them) and read row l of P from shared memory.
+  {
+    dfc zrow[M];
+    for (int k0 = 0; k0 < n; k0 += 4) {
+      CAcc z[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) z[u] = CAcc{{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 1
+      for (int j = 0; j < n; ++j) {
+        const dfc pj = Pw[l * kPS + j];
+        const int lo_j = blo(j), hi_j = bhi(j);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int k = k0 + u;
+          if (k < n) {
+            cacc_fma(z[u], pj, Xw[j * kPS + k]);
+            // P[l][j] S[j][k]: S[j][k] != 0 only when k lies in j's block
+            if (k >= lo_j && k < hi_j) cacc_fma(z[u], pj, Sw[j * BW + (k - lo_j)]);
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+#pragma unroll
+        for (int kk = 0; kk < M; kk += 4)
+          if (kk == k0) zrow[kk + u] = dfc{acc_val(z[u].re), acc_val(z[u].im)};
+      }
+    }
+    __syncwarp();
+    if (row) {
+#pragma unroll
+      for (int k = 0; k < M; ++k)
+        if (k < n) Pw[l * kPS + k] = zrow[k];
+    }
+  }
+  __syncwarp();
+  float2 rres[M];
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
+    rres[k] = make_float2(0.f, 0.f);
+    if (row && k < n) {
+      const float2 x0 = Xw[l * kPS + k];
+      CAcc z = CAcc{{-x0.x, 0.f}, {-x0.y, 0.f}};
+      for (int m = lo_l; m < hi_l; ++m) cacc_fma(z, Sw[l * BW + (m - lo_l)], Pw[m * kPS + k]);
+      rres[k] = make_float2(z.re.s + z.re.e, z.im.s + z.im.e);
+    }
+  }
+  __syncwarp();
+
+  // ---- 3. delta = A^-1 R: the recorded elimination replayed on R
+#pragma unroll
+  for (int c = 0; c < M; ++c) {
+    if (c < n) {
+      float2* Rr = Rw + (c & 1) * 2 * M;
+      if (mypos == c) {
+#pragma unroll
+        for (int j = 0; j < M; ++j) Rr[j] = rres[j];
+      }
+      __syncwarp();
+      const float2 f = frec[c];
+#pragma unroll
+      for (int j = 0; j < M; ++j)
+        if (j < n) rres[j] = cfms(f, Rr[j], rres[j]);
+    }
+  }
+  __syncwarp();
+  // ---- 4. X1 = X0 + delta (row mypos), into the P/Z tile
+  if (mypos >= 0) {
+    const float2 inv = cinv(dval);
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      if (j < n) {
+        const float2 d = cmul(rres[j], inv);
+        const float2 x0 = Xw[mypos * kPS + j];
+        float s, e;
+        two_sum(x0.x, d.x, s, e);
+        const dfl re = df_norm(s, e);
+        two_sum(x0.y, d.y, s, e);
+        const dfl im = df_norm(s, e);
+        Pw[mypos * kPS + j] = dfc{re, im};
+      }
+    }
+  }
+  if (singular && l == 0 && q < nk)
+    report_df(err, first_bad, QA_ESINGULAR_CODE, static_cast<long long>(nu) * nk + q);
+  __syncthreads();
+  for (int idx = tid; idx < kDfSys * nn; idx += blockDim.x) {
+    const int ss = idx % kDfSys, e = idx / kDfSys;
+    const int i = e / n, j = e - i * n;
+    const int qq = q0 + ss;
+    if (qq < nk) {
+      const dfc v = Pt[(ss * M + i) * kPS + j];
+      reinterpret_cast<float4*>(WC)[slab + static_cast<size_t>(e) * nk + qq] =
+          make_float4(v.x.hi, v.x.lo, v.y.hi, v.y.lo);
+    }
+  }
+}
+
+template <int NFIX, int BW>
+cudaError_t launch_df(const void* P, const void* Vq, void* WC, int r, int n, int nk, int* err,
+                      long long* first_bad, cudaStream_t st, const DysonBlocks& blk) {
+  constexpr int M = kDfLanes;
+  const size_t smem = static_cast<size_t>(kDfSys) * M * kPS * sizeof(dfc) +
+                      static_cast<size_t>(kDfSys) * M * BW * sizeof(dfc) +
+                      static_cast<size_t>(kDfSys) * M * kPS * sizeof(float2) +
+                      static_cast<size_t>(kDfSys) * 4 * M * sizeof(float2);
+  auto fn = &dyson_w_df_kernel<NFIX, BW>;
+  cudaError_t e = set_smem(reinterpret_cast<const void*>(fn), smem, true);
+  if (e != cudaSuccess) return e;
+  dim3 grid((nk + kDfSys - 1) / kDfSys, r);
+  fn<<<grid, kDfWarps * 32, smem, st>>>(static_cast<const dfc*>(P), static_cast<const dfc*>(Vq),
+                                        static_cast<dfc*>(WC), n, nk, err, first_bad, blk);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool dyson_w_df_supported(int n) { return n >= 1 && n <= kDfLanes; }
+
+cudaError_t launch_dyson_w_df(const void* P, const void* Vq, void* WC, int r, int n, int nk,
+                              int* err, long long* first_bad, cudaStream_t st,
+                              const DysonBlocks* blk) {
+  if (!dyson_w_df_supported(n) || P == WC) return cudaErrorInvalidValue;
+  DysonBlocks b = blk ? *blk : DysonBlocks{};
+  int bw = 0;
+  for (int i = 0; i < n && b.nblk > 0; ++i) bw = max(bw, static_cast<int>(b.hi[i]) - static_cast<int>(b.lo[i]));
+  if (b.nblk > 0 && bw <= 5) {
+    if (n == 15) return launch_df<15, 5>(P, Vq, WC, r, n, nk, err, first_bad, st, b);
+    return launch_df<0, 5>(P, Vq, WC, r, n, nk, err, first_bad, st, b);
+  }
+  b.nblk = 0;
+  return launch_df<0, kDfLanes>(P, Vq, WC, r, n, nk, err, first_bad, st, b);
+}
+
+}  // namespace qa

@@ -165,6 +165,14 @@ cudaError_t launch_dyson_w(const void* P, const void* Vq, void* WC, int r, int n
                            int* err, long long* first_bad, cudaStream_t st,
                            const DysonBlocks* blk = nullptr);
 
+// Accurate mixed path (qa_dyson_df.cu): W^C from double-float P and S(q), an FP32
+// Gauss-Jordan solve refined by one double-float residual step; n <= 16, out of
+// place.
+bool dyson_w_df_supported(int n);
+cudaError_t launch_dyson_w_df(const void* P, const void* Vq, void* WC, int r, int n, int nk,
+                              int* err, long long* first_bad, cudaStream_t st,
+                              const DysonBlocks* blk = nullptr);
+
 // Sigma^C[t][a][d][R] = -sum_bc G[t][b][c][R] W^C[t][(ab)][(cd)][R]
 template <typename T>
 cudaError_t launch_sigma(const void* GR, const void* WC, void* Sig, int r, int norb, int nk,
@@ -195,6 +203,12 @@ int sigma_canonical_norb(const int* off, const int* idx, int nout, int nterm, in
 // launch_sigma_reduced<float>; coef: the list's norb^4 coefficients (host).
 cudaError_t launch_sigma_canonical(const void* GR, const void* Wt, const std::complex<double>* coef,
                                    int norb, void* Sig, int r, int nk, cudaStream_t st);
+// Sigma in double-float (dfc G, Wt and Sigma; accurate mixed path) from the sigma
+// term lists regrouped by target entry: toff[norb^2 + 1], tidx[nterm] = (Wt entry,
+// G entry) as int2, tcoef[nterm] dfc.  Any pair basis (nout = nb^2 entries of Wt).
+cudaError_t launch_sigma_target_df(const void* GR, const void* Wt, const int* toff, const void* tidx,
+                                   const void* tcoef, void* Sig, int r, int norb, int nout, int nk,
+                                   cudaStream_t st);
 
 // Dyson for G.  prep: Bm[n][a][b][k] = (mu_ref - H(k) - SigHF(k))_ab - SigIw[n][a][b][k]
 // (SigHF FP64 [N_k][norb][norb] and SigIw may be null) and per-block bounds

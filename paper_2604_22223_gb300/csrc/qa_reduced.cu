@@ -318,6 +318,53 @@ cudaError_t launch_sigma_canonical(const void* GR, const void* Wt, const std::co
   }
 }
 
+// ---- Sigma in double-float (accurate mixed path), any pair basis.
+// One thread per (R, target entry Sigma_ad) walks the target's terms
+// Sigma_ad += coef * Wt_o(R) * G_g(R) from a per-target list (the sigma term
+// lists regrouped by target on the host); the block is 32 consecutive R x all
+// targets, so each load is a coalesced run along R and the Wt entries shared by
+// several targets of one R are re-read from L1.  The sum is compensated: every
+// leading FP32 product split exactly by an FMA, the high parts added with
+// TwoSum.  A short loop instead of an unrolled term pattern keeps the code in
+// the instruction cache.
+constexpr int kSigDfR = 32;
+
+__device__ __forceinline__ void df_acc_prod(float& s, float& e, dfl u, dfl v) {
+  const float p = __fmul_rn(u.hi, v.hi);
+  float q = __fmaf_rn(u.hi, v.hi, -p);
+  q = __fmaf_rn(u.hi, v.lo, q);
+  q = __fmaf_rn(u.lo, v.hi, q);
+  float t;
+  two_sum(s, p, s, t);
+  e = __fadd_rn(e, __fadd_rn(t, q));
+}
+
+__global__ void __launch_bounds__(kSigDfR * 25) sigma_target_df_kernel(
+    const dfc* __restrict__ GR, const dfc* __restrict__ Wt, const int* __restrict__ toff,
+    const int2* __restrict__ tidx, const dfc* __restrict__ tcoef, dfc* __restrict__ Sig, int no2,
+    int nout, int nk) {
+  const int R = blockIdx.x * kSigDfR + threadIdx.x;
+  const int tg = threadIdx.y;                 // target entry a * norb + d
+  const int t = blockIdx.y;
+  if (R >= nk || tg >= no2) return;
+  const dfc* g = GR + static_cast<size_t>(t) * no2 * nk + R;
+  const dfc* w = Wt + static_cast<size_t>(t) * nout * nk + R;
+  float rs = 0.f, re = 0.f, is = 0.f, ie = 0.f;
+  const int e1 = toff[tg + 1];
+  for (int e = toff[tg]; e < e1; ++e) {
+    const int2 ix = __ldg(tidx + e);          // (Wt entry, G entry)
+    const dfc cw = cmul(ldg_c(tcoef + e), ldg_c(w + static_cast<size_t>(ix.x) * nk));
+    const dfc gv = ldg_c(g + static_cast<size_t>(ix.y) * nk);
+    df_acc_prod(rs, re, cw.x, gv.x);
+    df_acc_prod(rs, re, -cw.y, gv.y);
+    df_acc_prod(is, ie, cw.x, gv.y);
+    df_acc_prod(is, ie, cw.y, gv.x);
+  }
+  const dfl vr = df_norm(rs, re), vi = df_norm(is, ie);
+  reinterpret_cast<float4*>(Sig)[(static_cast<size_t>(t) * no2 + tg) * nk + R] =
+      make_float4(vr.hi, vr.lo, vi.hi, vi.lo);
+}
+
 template <typename T>
 cudaError_t launch_bubble_reduced(const void* GR, const void* GreflR, const int* mR,
                                   const int* terms, const void* coef, int nterm, void* Pt, int r,
@@ -368,5 +415,18 @@ template cudaError_t launch_bubble_reduced<dfl>(const void*, const void*, const 
                                                 cudaStream_t);
 template cudaError_t launch_sigma_reduced<dfl>(const void*, const void*, const int*, const void*,
                                                int, void*, int, int, int, int, cudaStream_t, int);
+
+cudaError_t launch_sigma_target_df(const void* GR, const void* Wt, const int* toff, const void* tidx,
+                                   const void* tcoef, void* Sig, int r, int norb, int nout, int nk,
+                                   cudaStream_t st) {
+  const int no2 = norb * norb;
+  if (no2 > 25 || r < 1 || r > 65535) return cudaErrorInvalidValue;
+  dim3 block(kSigDfR, no2), grid((nk + kSigDfR - 1) / kSigDfR, r);
+  sigma_target_df_kernel<<<grid, block, 0, st>>>(static_cast<const dfc*>(GR), static_cast<const dfc*>(Wt),
+                                                 toff, static_cast<const int2*>(tidx),
+                                                 static_cast<const dfc*>(tcoef), static_cast<dfc*>(Sig),
+                                                 no2, nout, nk);
+  return cudaGetLastError();
+}
 
 }  // namespace qa
