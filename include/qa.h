@@ -292,6 +292,17 @@ int qa_density(qa_ctx* ctx, const void* G, double* n_out, double* N_total, void*
 int qa_density_static(const qa_ctx* ctx, const void* G, double* n_out, double* N_total,
                       void* stream);
 
+/* qa_fma_probe: arithmetic-rate probe (a measurement utility; the paper has no
+ * counterpart).  Enqueues on `stream` one kernel of 8 blocks per SM x 256
+ * threads in which every thread runs eight independent chains of `iters` fused
+ * multiply-adds in FP64 (precision = QA_FP64) or FP32 (QA_FP32), writing one
+ * value per thread to `out` (device, *out_elems doubles or floats, caller
+ * owned).  *flops receives the kernel's floating-point operations (2 per FMA);
+ * the caller times the launch to obtain the GPU's FMA rate.  out = NULL only
+ * reports *out_elems and *flops.  QA_EINVAL for iters < 1 or another precision. */
+int qa_fma_probe(int precision, int iters, void* out, long long* out_elems, double* flops,
+                 void* stream);
+
 /* Intermediates of the last step / of qa_bind, copied to dst (host or device):
  * element type complex128 for QA_FP64, double-float complex for QA_MIXED (four
  * floats re.hi, re.lo, im.hi, im.lo; value = hi + lo) and complex64 for

@@ -25,10 +25,34 @@ QA_P_QNU, QA_WC_RTAU, QA_SIGC_KTAU, QA_SIGC_KIW, QA_SIGHF_K, QA_G0, QA_HK, QA_MU
 EXPORTED = ["qa_create", "qa_workspace_size", "qa_bind", "qa_get_grid", "qa_get_plan",
             "qa_get_sizes", "qa_gw_step", "qa_density", "qa_density_static", "qa_get",
             "qa_set_timing", "qa_set_mu", "qa_set_params", "qa_gw_backward", "qa_set_pair_basis",
-            "qa_get_pair_basis", "qa_hf_solve", "qa_qp", "qa_destroy", "qa_strerror"]
+            "qa_get_pair_basis", "qa_hf_solve", "qa_qp", "qa_destroy", "qa_strerror",
+            "qa_fma_probe"]
 
 STAGES = ["hartree_fock", "g_to_R", "bubble", "fft_R_to_q", "dlr_tau_to_nu", "dyson_w",
           "dlr_nu_to_tau", "fft_q_to_R", "sigma", "sigma_to_k_iw", "mu_search", "dyson_g"]
+
+
+def fma_rate(precision: str, iters: int = 4096, reps: int = 3):
+    """Measured FMA rate of the current GPU (TFLOP/s, 2 flops per FMA) from
+    qa_fma_probe: the best of `reps` CUDA-event-timed launches after one warm-up."""
+    import torch
+    L = load()
+    prec = PRECISIONS[precision]
+    n, flops = C.c_longlong(), C.c_double()
+    _check(L.qa_fma_probe(prec, iters, None, C.byref(n), C.byref(flops), None), "qa_fma_probe")
+    out = torch.empty(n.value, dtype=torch.float64 if prec == QA_FP64 else torch.float32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    best = None
+    for rep in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _check(L.qa_fma_probe(prec, iters, out.data_ptr(), C.byref(n), C.byref(flops), stream), "qa_fma_probe")
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if rep > 0:
+            best = ms if best is None else min(best, ms)
+    return flops.value / (best * 1e-3) / 1e12, best
 
 
 class QAError(RuntimeError):
@@ -87,6 +111,7 @@ def load(path: str = LIB_PATH):
     L.qa_get_pair_basis.argtypes = [vp, C.POINTER(i), C.POINTER(i), vp]
     L.qa_hf_solve.argtypes = [vp, i, d, d, vp, C.POINTER(d), C.POINTER(i), C.POINTER(d), vp, vp]
     L.qa_qp.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.qa_fma_probe.argtypes = [i, i, vp, C.POINTER(C.c_longlong), C.POINTER(d), vp]
     L.qa_destroy.argtypes = [vp]
     L.qa_destroy.restype = None
     L.qa_strerror.argtypes = [i]
