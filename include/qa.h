@@ -321,6 +321,17 @@ enum {
 };
 int qa_get(const qa_ctx* ctx, int which, void* dst, size_t bytes, void* stream);
 
+/* qa_set_wait_limit: a diagnostics control of the tensor-core DLR kernels (the
+ * paper has no counterpart).  Their producer/consumer pipeline waits on shared
+ * memory barriers, each wait bounded by `polls` polls (default 2^24; polls < 0
+ * restores it).  A wait that runs out takes the kernel's time-out path: the
+ * error word becomes QA_ETIMEOUT (returned by the call), the kernel lets the
+ * tensor-core operations it already issued finish (with the default bound),
+ * releases its tensor memory and returns, so the context stays usable.
+ * polls = 0 makes every pipeline wait give up at once: a way to exercise that
+ * path without any fault.  Host only; takes effect from the next call. */
+int qa_set_wait_limit(qa_ctx* ctx, long long polls);
+
 /* Enable per-stage CUDA-event timing in qa_step_stats (0/1). */
 int qa_set_timing(qa_ctx* ctx, int enable);
 

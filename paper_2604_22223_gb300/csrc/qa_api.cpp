@@ -111,6 +111,7 @@ struct qa_ctx {
   bool timing = false;
   int launches = 0;           // kernels launched by the current call
   bool mu_fixed = false;      // qa_set_mu: use mu_value instead of the search
+  long long wait_limit = -1;  // qa_set_wait_limit: polls of the tensor-core kernels' pipeline waits
   double mu_value = 0.0;
   // adjoint (FP64 contexts only)
   DevTables tH;               // conjugate transposes of the FP64 DLR matrices
@@ -709,7 +710,7 @@ int finish_g(qa_ctx* c, const DevTables& tab, double mu, void* G_out_c128, doubl
   } else if (is_df<T>()) {
     if (c->use_oz) {
       // the transform stores complex128 directly
-      QA_LAUNCH(c, 1, qa::launch_dlr_oz(c->d_oz_Twt, c->r, c->d_Giw, G_out_c128, ncol, c->d_err, st, true));
+      QA_LAUNCH(c, 1, qa::launch_dlr_oz(c->d_oz_Twt, c->r, c->d_Giw, G_out_c128, ncol, c->d_err, st, true, c->wait_limit));
     } else {
       QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Twt, c->r, c->r, c->d_Giw, c->d_Gt, ncol, st));
       QA_LAUNCH(c, 1, qa::launch_df_to_c128(c->d_Gt, static_cast<double2*>(G_out_c128), ncol * c->r, st));
@@ -718,7 +719,7 @@ int finish_g(qa_ctx* c, const DevTables& tab, double mu, void* G_out_c128, doubl
     if (c->use_tc) {
       // the transform stores complex128 directly
       QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Twt, c->r, c->d_Giw, G_out_c128, ncol, c->d_err, st,
-                                        true));
+                                        true, c->wait_limit));
     } else {
       QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Twt, c->r, c->r, c->d_Giw, c->d_Gt, ncol, st));
       QA_LAUNCH(c, 1, qa::launch_c64_to_c128(static_cast<const float2*>(c->d_Gt),
@@ -795,9 +796,9 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
   // G(k, beta - tau), real-space G
   const bool oz = is_df<T>() && c->use_oz;
   if (f32 && c->use_tc)
-    QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Trefl, r, Gk, c->d_Grefl, ncs, c->d_err, st));
+    QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Trefl, r, Gk, c->d_Grefl, ncs, c->d_err, st, false, c->wait_limit));
   else if (oz)
-    QA_LAUNCH(c, 1, qa::launch_dlr_oz(c->d_oz_Trefl, r, Gk, c->d_Grefl, ncs, c->d_err, st));
+    QA_LAUNCH(c, 1, qa::launch_dlr_oz(c->d_oz_Trefl, r, Gk, c->d_Grefl, ncs, c->d_err, st, false, c->wait_limit));
   else
     QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Trefl, r, r, Gk, c->d_Grefl, ncs, st));
   QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, +1, Gk, c->d_GR, ncs / nk * r, st));
@@ -822,7 +823,7 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
   if (oz) {
     // out-of-place tensor-core maps: P(q, tau) [P] -> P(q, i nu) [Pnu] -> W^C(q, i nu) [P]
     // -> W^C(q, tau) [W]
-    QA_LAUNCH(c, 1, qa::launch_dlr_oz(c->d_oz_Ttn, r, c->d_P, c->d_Pnu, ncb, c->d_err, st));
+    QA_LAUNCH(c, 1, qa::launch_dlr_oz(c->d_oz_Ttn, r, c->d_P, c->d_Pnu, ncb, c->d_err, st, false, c->wait_limit));
     tm.mark();  // 4: DLR tau -> nu
     if (qa::dyson_w_df_supported(c->nb))
       QA_LAUNCH(c, 1, qa::launch_dyson_w_df(c->d_Pnu, c->d_Vq, c->d_P, r, c->nb, nk, c->d_err, c->d_bad,
@@ -831,10 +832,10 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
       QA_LAUNCH(c, 1, qa::launch_dyson_w<T>(c->d_Pnu, c->d_Vq, c->d_P, r, c->nb, nk, c->d_err, c->d_bad,
                                             st, &c->dblk));
     tm.mark();  // 5: Dyson W
-    QA_LAUNCH(c, 1, qa::launch_dlr_oz(c->d_oz_Tnt, r, c->d_P, c->d_W, ncb, c->d_err, st));
+    QA_LAUNCH(c, 1, qa::launch_dlr_oz(c->d_oz_Tnt, r, c->d_P, c->d_W, ncb, c->d_err, st, false, c->wait_limit));
   } else {
     if (f32 && c->use_tc)
-      QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Ttn, r, c->d_P, c->d_P, ncb, c->d_err, st));
+      QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Ttn, r, c->d_P, c->d_P, ncb, c->d_err, st, false, c->wait_limit));
     else
       QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Ttn, r, r, c->d_P, c->d_P, ncb, st));
     tm.mark();  // 4: DLR tau -> nu
@@ -842,7 +843,7 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
                                           &c->dblk));
     tm.mark();  // 5: Dyson W
     if (f32 && c->use_tc)
-      QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Tnt, r, c->d_W, c->d_W, ncb, c->d_err, st));
+      QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Tnt, r, c->d_W, c->d_W, ncb, c->d_err, st, false, c->wait_limit));
     else
       QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Tnt, r, r, c->d_W, c->d_W, ncb, st));
   }
@@ -864,9 +865,9 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
   tm.mark();  // 8: Sigma contraction
   QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, -1, c->d_SigC, c->d_SigC, ncs / nk * r, st));
   if (f32 && c->use_tc)
-    QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Ttw, r, c->d_SigC, c->d_SigIw, ncs, c->d_err, st));
+    QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Ttw, r, c->d_SigC, c->d_SigIw, ncs, c->d_err, st, false, c->wait_limit));
   else if (oz)
-    QA_LAUNCH(c, 1, qa::launch_dlr_oz(c->d_oz_Ttw, r, c->d_SigC, c->d_SigIw, ncs, c->d_err, st));
+    QA_LAUNCH(c, 1, qa::launch_dlr_oz(c->d_oz_Ttw, r, c->d_SigC, c->d_SigIw, ncs, c->d_err, st, false, c->wait_limit));
   else
     QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Ttw, r, r, c->d_SigC, c->d_SigIw, ncs, st));
   tm.mark();  // 9: Sigma -> (k, i w)
@@ -896,10 +897,18 @@ int gw_step_impl(qa_ctx* c, const void* G_in, void* G_out, double* mu_out, doubl
     rc = mu_search<T>(c, c->d_SigHF, c->d_SigIw, tab, c->have_mu ? c->mu : c->mu0, &mu, &N,
                       &evals, st);
   }
-  if (rc != QA_OK) return rc;
+  if (rc != QA_OK) {
+    // a device-side failure earlier in the step (a singular Dyson pivot, a
+    // timed-out wait) is the cause of what the search saw: report it first
+    const int herr = check_err(c, stats, st);
+    return herr ? herr : rc;
+  }
   tm.mark();  // 10: mu search
   rc = finish_g<T>(c, tab, mu, G_out, n_out, st);
-  if (rc != QA_OK) return rc;
+  if (rc != QA_OK) {
+    const int herr = check_err(c, stats, st);
+    return herr ? herr : rc;
+  }
   tm.mark();  // 11: Dyson G + G(tau)
   tm.finish(stats);
   c->mu = mu;
@@ -1577,6 +1586,12 @@ int qa_get(const qa_ctx* c, int which, void* dst, size_t bytes, void* stream) {
   if (bytes != need) return QA_EINVAL;
   QA_TRY(cudaMemcpyAsync(dst, src, need, cudaMemcpyDefault, st));
   QA_TRY(cudaStreamSynchronize(st));
+  return QA_OK;
+}
+
+int qa_set_wait_limit(qa_ctx* c, long long polls) {
+  if (!c) return QA_EINVAL;
+  c->wait_limit = polls < 0 ? -1 : polls;
   return QA_OK;
 }
 

@@ -60,6 +60,7 @@ struct OzArgs {
   void* out;               // dfc, or double2 when OUT64
   long long ncol;
   int* err;
+  long long wait_limit;    // polls of each pipeline wait before the time-out path
 };
 
 __device__ __forceinline__ uint32_t pack_hi16(float a, float b) {
@@ -150,12 +151,12 @@ __global__ void __launch_bounds__(kWorkers + 32, 1) dlr_oz_kernel(OzArgs a) {
       bool ok = true;
       for (long long tile = cp; tile < ntiles && ok; tile += cpp, ++tl) {
         if (tl > 0) {
-          if (!tc::mbar_wait(drained, static_cast<uint32_t>((tl - 1) & 1), abort_flag)) { ok = false; break; }
+          if (!tc::mbar_wait(drained, static_cast<uint32_t>((tl - 1) & 1), abort_flag, a.wait_limit)) { ok = false; break; }
           tc::fence_after();
         }
         for (int ch = 0; ch < nchunk; ++ch, ++g) {
           const int b = static_cast<int>(g & 1);
-          if (!tc::mbar_wait(&full[b], static_cast<uint32_t>((g >> 1) & 1), abort_flag)) { ok = false; break; }
+          if (!tc::mbar_wait(&full[b], static_cast<uint32_t>((g >> 1) & 1), abort_flag, a.wait_limit)) { ok = false; break; }
           tc::fence_after();
 #pragma unroll
           for (int lvl = 0; lvl < kOzSlices; ++lvl) {
@@ -194,6 +195,7 @@ __global__ void __launch_bounds__(kWorkers + 32, 1) dlr_oz_kernel(OzArgs a) {
         const long long pcol = tile * kTileM + pm;
         float mx = 0.0f;
         if (pcol < a.ncol) {
+#pragma unroll 4
           for (int l = pq; l < a.r; l += 4) {
             const float4 v = __ldg(reinterpret_cast<const float4*>(a.in + static_cast<long long>(l) * a.ncol + pcol));
             mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.z)));
@@ -209,25 +211,36 @@ __global__ void __launch_bounds__(kWorkers + 32, 1) dlr_oz_kernel(OzArgs a) {
         }
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&prep[tl & 1]);
-        if (!tc::mbar_wait(&prep[tl & 1], static_cast<uint32_t>((tl >> 1) & 1), abort_flag)) { ok = false; break; }
+        if (!tc::mbar_wait(&prep[tl & 1], static_cast<uint32_t>((tl >> 1) & 1), abort_flag, a.wait_limit)) { ok = false; break; }
       }
       const float scale = s_b[(tl & 1) * kTileM + m];
       const long long col = tile * kTileM + m;
       const bool colok = col < a.ncol;
+      // this thread's two values of a chunk; the next chunk's are loaded before
+      // the current one is sliced (one chunk of loads in flight)
+      auto load2 = [&](int ch, dfc* v) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int l = ch * 8 + qt * 2 + e;
+          v[e] = dfc{dfl(0.0f, 0.0f), dfl(0.0f, 0.0f)};
+          if (colok && ch < nchunk && l < a.r) v[e] = ldg_c(a.in + static_cast<long long>(l) * a.ncol + col);
+        }
+      };
+      dfc cur[2], nxt[2];
+      load2(0, cur);
       for (int ch = 0; ch < nchunk; ++ch, ++g) {
         const int b = static_cast<int>(g & 1);
+        load2(ch + 1, nxt);
         if (g >= 2) {
-          const bool w = tc::mbar_wait(&done[b], static_cast<uint32_t>(((g - 2) >> 1) & 1), abort_flag);
+          const bool w = tc::mbar_wait(&done[b], static_cast<uint32_t>(((g - 2) >> 1) & 1), abort_flag, a.wait_limit);
           if (__any_sync(0xffffffffu, !w)) { ok = false; break; }
         }
         float s[4][kOzSlices];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-          const int l = ch * 8 + qt * 2 + e;
-          dfc v = dfc{dfl(0.0f, 0.0f), dfl(0.0f, 0.0f)};
-          if (colok && l < a.r) v = ldg_c(a.in + static_cast<long long>(l) * a.ncol + col);
-          slice5(v.x, scale, s[2 * e]);
-          slice5(v.y, scale, s[2 * e + 1]);
+          slice5(cur[e].x, scale, s[2 * e]);
+          slice5(cur[e].y, scale, s[2 * e + 1]);
+          cur[e] = nxt[e];
         }
 #pragma unroll
         for (int j = 0; j < kOzSlices; ++j) {
@@ -243,7 +256,7 @@ __global__ void __launch_bounds__(kWorkers + 32, 1) dlr_oz_kernel(OzArgs a) {
       if (!ok) break;
       // the tile's MMAs are done once its last chunk's commit has arrived
       {
-        const bool w = tc::mbar_wait(&done[(g - 1) & 1], static_cast<uint32_t>(((g - 1) >> 1) & 1), abort_flag);
+        const bool w = tc::mbar_wait(&done[(g - 1) & 1], static_cast<uint32_t>(((g - 1) >> 1) & 1), abort_flag, a.wait_limit);
         if (__any_sync(0xffffffffu, !w)) { ok = false; break; }
       }
       tc::fence_after();
@@ -376,7 +389,7 @@ void pack_dlr_oz(const std::complex<double>* T, int r, std::vector<uint8_t>* dst
 }
 
 cudaError_t launch_dlr_oz(const void* pack, int r, const void* in, void* out, long long ncol, int* err,
-                          cudaStream_t st, bool out_c128) {
+                          cudaStream_t st, bool out_c128, long long wait_limit) {
   if (!dlr_oz_supported(r) || in == out) return cudaErrorInvalidValue;
   if (ncol <= 0) return cudaSuccess;
   const DlrOzLayout L = dlr_oz_layout(r);
@@ -406,6 +419,7 @@ cudaError_t launch_dlr_oz(const void* pack, int r, const void* in, void* out, lo
   a.out = out;
   a.ncol = ncol;
   a.err = err;
+  a.wait_limit = wait_limit >= 0 ? wait_limit : tc::kWaitLimit;
   fn<<<static_cast<unsigned>(cpp * L.nparts), kWorkers + 32, L.smem, st>>>(a);
   return cudaGetLastError();
 }

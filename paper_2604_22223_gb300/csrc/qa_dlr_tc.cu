@@ -126,6 +126,7 @@ struct TcArgs {
   double2* out64;          // when set, the result is stored here as complex128 instead
   long long ncol;
   int* err;
+  long long wait_limit;    // polls of each pipeline wait before the time-out path
 };
 
 // acc[0..23] += the 24 TMEM columns at taddr (this thread's lane), rounded to
@@ -149,10 +150,10 @@ constexpr int kDepth = 2;               // K-chunks of input in flight per worke
 constexpr int kPrefetch = 16;            // further K-chunks requested into L2 ahead of the ring
 constexpr int kWorkers = 4 * kTcThreads;   // 16 worker warps; warp 16 issues the MMAs
 
-// bounded wait that also gives up once another thread has flagged an abort
+// bounded wait (lim polls) that also gives up once another thread has flagged an abort
 __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity,
-                                                   volatile int* abort_flag) {
-  for (long long i = 0; i < kWaitLimit; ++i) {
+                                                   volatile int* abort_flag, long long lim) {
+  for (long long i = 0; i < lim; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((i & 1023) == 1023 && *abort_flag) return false;
   }
@@ -226,7 +227,7 @@ __global__ void __launch_bounds__(kWorkers + 32, 1) dlr_tc_kernel(TcArgs a) {
       long long g = 0;
       for (; g < nstream; ++g) {
         const int b = static_cast<int>(g & 1);
-        if (!mbar_wait_or_abort(&full[b], static_cast<uint32_t>((g >> 1) & 1), abort_flag)) {
+        if (!mbar_wait_or_abort(&full[b], static_cast<uint32_t>((g >> 1) & 1), abort_flag, a.wait_limit)) {
           *abort_flag = 1;
           break;
         }
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(kWorkers + 32, 1) dlr_tc_kernel(TcArgs a) {
         __syncwarp();
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full[b])) : "memory");
         if (ch > 0) {
-          const bool w = mbar_wait_or_abort(&done[(g - 1) & 1], static_cast<uint32_t>(((g - 1) >> 1) & 1), abort_flag);
+          const bool w = mbar_wait_or_abort(&done[(g - 1) & 1], static_cast<uint32_t>(((g - 1) >> 1) & 1), abort_flag, a.wait_limit);
           if (__any_sync(0xffffffffu, !w)) {          // warp-uniform exit
             *abort_flag = 1;
             ok = false;
@@ -339,7 +340,7 @@ __global__ void __launch_bounds__(kWorkers + 32, 1) dlr_tc_kernel(TcArgs a) {
         }
       }
       if (!ok) break;
-      const bool w = mbar_wait_or_abort(&done[(g - 1) & 1], static_cast<uint32_t>(((g - 1) >> 1) & 1), abort_flag);
+      const bool w = mbar_wait_or_abort(&done[(g - 1) & 1], static_cast<uint32_t>(((g - 1) >> 1) & 1), abort_flag, a.wait_limit);
       if (__any_sync(0xffffffffu, !w)) {
         *abort_flag = 1;
         break;
@@ -423,7 +424,7 @@ void pack_dlr_tc(const std::complex<double>* T, int r, std::vector<uint16_t>* ds
 }
 
 cudaError_t launch_dlr_tc(const void* Bsplit, int r, const void* in, void* out, long long ncol,
-                          int* err, cudaStream_t st, bool out_c128) {
+                          int* err, cudaStream_t st, bool out_c128, long long wait_limit) {
   size_t smem = 0;
   if (!dlr_tc_supported(r, &smem)) return cudaErrorInvalidValue;
   if (ncol <= 0) return cudaSuccess;
@@ -447,6 +448,7 @@ cudaError_t launch_dlr_tc(const void* Bsplit, int r, const void* in, void* out, 
   a.out64 = out_c128 ? reinterpret_cast<double2*>(out) : nullptr;
   a.ncol = ncol;
   a.err = err;
+  a.wait_limit = wait_limit >= 0 ? wait_limit : kWaitLimit;
   fn<<<grid, kWorkers + 32, smem, st>>>(a);
   return cudaGetLastError();
 }

@@ -163,37 +163,44 @@ __global__ void __launch_bounds__(kDfWarps * 32, 3) dyson_w_df_kernel(
   bool singular = false;
   float2 frec[M];
 #pragma unroll
-  for (int c = 0; c < M; ++c) {
-    frec[c] = make_float2(0.f, 0.f);
-    if (c < n) {
-      float2* Ra_c = Rw + (c & 1) * 2 * M;
-      float2* Rb_c = Ra_c + M;
-      const float v2 = cabs2(a[c]);
-      unsigned key = used ? 0u : (max(__float_as_uint(v2) & ~0xFu, 0x10u) | (M - 1 - l));
+  for (int j = 0; j < M; ++j) frec[j] = make_float2(0.f, 0.f);
+  // the column loop stays rolled (small code); register arrays are indexed by c
+  // through compile-time selects
+#pragma unroll 1
+  for (int c = 0; c < n; ++c) {
+    float2* Ra_c = Rw + (c & 1) * 2 * M;
+    float2* Rb_c = Ra_c + M;
+    float2 ac = a[0];
 #pragma unroll
-      for (int o = M / 2; o > 0; o >>= 1) key = max(key, __shfl_xor_sync(0xffffffffu, key, o));
-      const int p = M - 1 - static_cast<int>(key & (M - 1));
-      if (!(__uint_as_float(key & ~0xFu) >= 1e-12f)) singular = true;
-      const bool me = (l == p);
-      if (me) {
-        used = true;
-        mypos = c;
-        dval = a[c];
+    for (int j = 1; j < M; ++j)
+      if (j == c) ac = a[j];
+    const float v2 = cabs2(ac);
+    unsigned key = used ? 0u : (max(__float_as_uint(v2) & ~0xFu, 0x10u) | (M - 1 - l));
 #pragma unroll
-        for (int j = 0; j < M; ++j) {
-          if (j >= c) Ra_c[j] = a[j];
-          Rb_c[j] = b[j];
-        }
-      }
-      __syncwarp();
-      const float2 apc = Ra_c[c];
-      const float2 f = me ? make_float2(0.f, 0.f) : cmul(a[c], cinv(apc));
-      frec[c] = f;
+    for (int o = M / 2; o > 0; o >>= 1) key = max(key, __shfl_xor_sync(0xffffffffu, key, o));
+    const int p = M - 1 - static_cast<int>(key & (M - 1));
+    if (!(__uint_as_float(key & ~0xFu) >= 1e-12f)) singular = true;
+    const bool me = (l == p);
+    if (me) {
+      used = true;
+      mypos = c;
+      dval = ac;
 #pragma unroll
       for (int j = 0; j < M; ++j) {
-        if (j > c && j < n) a[j] = cfms(f, Ra_c[j], a[j]);
-        if (j < n) b[j] = cfms(f, Rb_c[j], b[j]);
+        if (j >= c) Ra_c[j] = a[j];
+        Rb_c[j] = b[j];
       }
+    }
+    __syncwarp();
+    const float2 apc = Ra_c[c];
+    const float2 f = me ? make_float2(0.f, 0.f) : cmul(ac, cinv(apc));
+#pragma unroll
+    for (int j = 0; j < M; ++j)
+      if (j == c) frec[j] = f;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      if (j > c && j < n) a[j] = cfms(f, Ra_c[j], a[j]);
+      if (j < n) b[j] = cfms(f, Rb_c[j], b[j]);
     }
   }
   // X0: row mypos of the FP32 solution
@@ -257,20 +264,21 @@ __global__ void __launch_bounds__(kDfWarps * 32, 3) dyson_w_df_kernel(
   __syncwarp();
 
   // ---- 3. delta = A^-1 R: the recorded elimination replayed on R
+#pragma unroll 1
+  for (int c = 0; c < n; ++c) {
+    float2* Rr = Rw + (c & 1) * 2 * M;
+    if (mypos == c) {
 #pragma unroll
-  for (int c = 0; c < M; ++c) {
-    if (c < n) {
-      float2* Rr = Rw + (c & 1) * 2 * M;
-      if (mypos == c) {
-#pragma unroll
-        for (int j = 0; j < M; ++j) Rr[j] = rres[j];
-      }
-      __syncwarp();
-      const float2 f = frec[c];
-#pragma unroll
-      for (int j = 0; j < M; ++j)
-        if (j < n) rres[j] = cfms(f, Rr[j], rres[j]);
+      for (int j = 0; j < M; ++j) Rr[j] = rres[j];
     }
+    __syncwarp();
+    float2 f = frec[0];
+#pragma unroll
+    for (int j = 1; j < M; ++j)
+      if (j == c) f = frec[j];
+#pragma unroll
+    for (int j = 0; j < M; ++j)
+      if (j < n) rres[j] = cfms(f, Rr[j], rres[j]);
   }
   __syncwarp();
   // ---- 4. X1 = X0 + delta (row mypos), into the P/Z tile

@@ -106,8 +106,9 @@ cudaError_t launch_dlr_apply(const void* Tm, int rows_out, int r, const void* in
 bool dlr_tc_supported(int r, size_t* smem_bytes);
 void pack_dlr_tc(const std::complex<double>* T, int r, std::vector<uint16_t>* dst);
 // out_c128: store the result as complex128 (out must not alias in then).
+// wait_limit: polls of each pipeline mbarrier wait (< 0: the default, 2^24).
 cudaError_t launch_dlr_tc(const void* Bsplit, int r, const void* in, void* out, long long ncol,
-                          int* err, cudaStream_t st, bool out_c128 = false);
+                          int* err, cudaStream_t st, bool out_c128 = false, long long wait_limit = -1);
 
 // Accurate DLR transform of double-float (dfc) columns on the tensor cores from
 // fixed-point bf16 slices (qa_dlr_oz.cu); out must not alias in.  The packed
@@ -126,7 +127,7 @@ bool dlr_oz_supported(int r);
 void pack_dlr_oz(const std::complex<double>* T, int r, std::vector<uint8_t>* dst);
 // out_c128: store complex128 instead of double-float.
 cudaError_t launch_dlr_oz(const void* pack, int r, const void* in, void* out, long long ncol,
-                          int* err, cudaStream_t st, bool out_c128 = false);
+                          int* err, cudaStream_t st, bool out_c128 = false, long long wait_limit = -1);
 
 // Batched 3-D FFT of contiguous lines of N_k points (in place allowed).
 // sign = -1: X(k) = sum_R e^{-ikR} X(R); sign = +1: (1/N_k) sum_k e^{+ikR} X(k).

@@ -26,7 +26,7 @@ EXPORTED = ["qa_create", "qa_workspace_size", "qa_bind", "qa_get_grid", "qa_get_
             "qa_get_sizes", "qa_gw_step", "qa_density", "qa_density_static", "qa_get",
             "qa_set_timing", "qa_set_mu", "qa_set_params", "qa_gw_backward", "qa_set_pair_basis",
             "qa_get_pair_basis", "qa_hf_solve", "qa_qp", "qa_destroy", "qa_strerror",
-            "qa_fma_probe"]
+            "qa_fma_probe", "qa_set_wait_limit"]
 
 STAGES = ["hartree_fock", "g_to_R", "bubble", "fft_R_to_q", "dlr_tau_to_nu", "dyson_w",
           "dlr_nu_to_tau", "fft_q_to_R", "sigma", "sigma_to_k_iw", "mu_search", "dyson_g"]
@@ -112,6 +112,7 @@ def load(path: str = LIB_PATH):
     L.qa_hf_solve.argtypes = [vp, i, d, d, vp, C.POINTER(d), C.POINTER(i), C.POINTER(d), vp, vp]
     L.qa_qp.argtypes = [vp, vp, vp, vp, vp, vp]
     L.qa_fma_probe.argtypes = [i, i, vp, C.POINTER(C.c_longlong), C.POINTER(d), vp]
+    L.qa_set_wait_limit.argtypes = [vp, C.c_longlong]
     L.qa_destroy.argtypes = [vp]
     L.qa_destroy.restype = None
     L.qa_strerror.argtypes = [i]
@@ -256,8 +257,13 @@ class Context(Problem):
     def new_g(self):
         return self.torch.empty(self.g_shape, dtype=self.torch.complex128, device=self.device)
 
-    def step(self, G_in=None, G_out=None, timing: bool = False):
-        """One GW iteration; returns (G_out, mu, n_local [norb, norb] complex, stats dict)."""
+    def set_wait_limit(self, polls=None):
+        """Poll budget of the tensor-core kernels' pipeline waits (None: default)."""
+        _check(load().qa_set_wait_limit(self.ctx, -1 if polls is None else int(polls)), "qa_set_wait_limit")
+
+    def step(self, G_in=None, G_out=None, timing: bool = False, check: bool = True):
+        """One GW iteration; returns (G_out, mu, n_local [norb, norb] complex, stats dict).
+        check=False returns a failing status in stats["call_status"] instead of raising."""
         L = load()
         if G_out is None:
             G_out = self.new_g()
@@ -270,9 +276,10 @@ class Context(Problem):
         st = StepStats()
         status = L.qa_gw_step(self.ctx, None if G_in is None else G_in.data_ptr(), G_out.data_ptr(),
                               C.byref(mu), n.ctypes.data, C.byref(st), self._stream())
-        _check(status, "qa_gw_step")
+        if check:
+            _check(status, "qa_gw_step")
         stats = {"mu": st.mu, "N": st.N, "mu_evals": st.mu_evals, "status": st.status,
-                 "first_bad": st.first_bad, "launches": st.launches}
+                 "first_bad": st.first_bad, "launches": st.launches, "call_status": status}
         if timing:
             stats["stage_ms"] = dict(zip(STAGES, list(st.stage_ms)[:len(STAGES)]))
         return G_out, mu.value, n.view(np.complex128).reshape(self.norb, self.norb), stats

@@ -4,7 +4,12 @@
   P(q, i nu), W^C(R, tau), Sigma^C, Sigma^HF, G and mu against the oracle.
 * The mixed path runs on the reduced pair basis (its default): P is compared
   as B^H P B and W^C expanded as B Wt^C B^H.
-* five-orbital-32x32x8 (the benchmark grid, the launch configuration bench.py
+* peierls-32x32x8 (the benchmark's 32x32x8 grid with the two-orbital Peierls
+  model, which the oracle finishes in about a minute): every element of P(q, i nu),
+  W^C(R, tau), Sigma^C(k, tau), Sigma^C(k, i w), G and mu in all three precisions,
+  so the FFT kernels specialised to the 32x32x8 grid (q -> R, Sigma -> k and the
+  fused bubble) are compared with the oracle element by element.
+* five-orbital-32x32x8 (the benchmark workload, the launch configuration bench.py
   times): G0, mu0 and Sigma^HF in full; P(q, i nu) at sampled q from the
   oracle's explicit k-sum; and properties that hold at any size: the sum rule
   G(0+) + G(beta-) = -1 of the new G, the filling, and Sigma^C(-k, tau) =
@@ -79,6 +84,33 @@ def test_full_step(name, prec):
         "sigc_ktau": rel(ctx.get(qa.QA_SIGC_KTAU).cpu().numpy(), kl(o["sigc_ktau"])),
         "sigc_kiw": rel(ctx.get(qa.QA_SIGC_KIW).cpu().numpy(), kl(o["sigc_kiw"])),
         "sighf": rel(ctx.get(qa.QA_SIGHF_K).cpu().numpy(), o["sig_hf_k"]),
+        "G": rel(G.cpu().numpy(), kl(o["G_ktau"])),
+        "mu": abs(mu - o["mu"]) / max(1.0, abs(o["mu"])),
+    }
+    for k, e in errs.items():
+        bound = {"fp64": FP64_G if k in ("G", "mu") else FP64, "mixed": MIXED, "fp32": FP32[k]}[prec]
+        assert e <= bound, (k, e, bound, errs)
+
+
+@pytest.fixture(scope="module")
+def grid_oracle():
+    m = wl.config("peierls-32x32x8")
+    d = gw.make_dlr(m)
+    G0, mu0 = gw.g0(m, d)
+    return m, d, G0, gw.gw_step(m, d, G0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "fp32"])
+def test_benchmark_grid_elementwise(grid_oracle, prec):
+    from paper_2604_22223_gb300 import qa
+    m, d, G0, o = grid_oracle
+    ctx = qa.Context(m, prec)
+    G, mu, n, st = ctx.step()
+    errs = {
+        "P_qnu": rel(ctx.get(qa.QA_P_QNU).cpu().numpy(), project_P(ctx, kl(o["P_qnu"]))),
+        "WC_Rtau": rel(expand_W(ctx, ctx.get(qa.QA_WC_RTAU).cpu().numpy()), kl(o["WC_Rtau"])),
+        "sigc_ktau": rel(ctx.get(qa.QA_SIGC_KTAU).cpu().numpy(), kl(o["sigc_ktau"])),
+        "sigc_kiw": rel(ctx.get(qa.QA_SIGC_KIW).cpu().numpy(), kl(o["sigc_kiw"])),
         "G": rel(G.cpu().numpy(), kl(o["G_ktau"])),
         "mu": abs(mu - o["mu"]) / max(1.0, abs(o["mu"])),
     }
