@@ -18,6 +18,10 @@ Contents
               Hartree and Fock terms (Eqs. for Sigma^H, Sigma^F), the Dyson
               equation for G, the chemical-potential bisection and the density
               n = -G(beta^-) (Sec. "GW self-consistency").
+  qp.py       Hartree-Fock loop and quasiparticle quantities.
+  free_energy.py  the GW grand potential in the Luttinger-Ward form (named in
+              the paper's introduction, defined here on truncated Matsubara
+              traces) on the input G of one iteration.
 
 Every floating-point quantity is complex128/float64.  Library primitives
 (matrix products, linear solves, eigh) are used as single steps; nothing is
