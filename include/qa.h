@@ -230,6 +230,41 @@ int qa_gw_backward(qa_ctx* ctx, const void* G_in, double mu, const void* Gbar_ou
                    const void* Sigbar, const double* nbar, void* Gbar_in, double* grad_t,
                    double* grad_V, void* stream);
 
+/* qa_free_energy: the GW grand potential per unit cell in the Luttinger-Ward
+ * form, evaluated on the input G of one iteration at fixed chemical potential
+ * `mu` (the paper's introduction names the Luttinger-Ward functional as the
+ * target of a differentiable GW code without writing it down; this is the
+ * reading used, with truncated Matsubara traces):
+ *   Omega = Omega_HF + Omega_dc + Omega_G + Omega_W, parts[] in this order,
+ *   Omega_HF = -(s/(beta N_k)) sum_{k,i} ln(1 + exp(-beta (e_i(k) - mu))), e_i the
+ *              eigenvalues of the Hermitian part of H(k) + Sigma^HF(k);
+ *   Omega_dc = -(1/2)(s/N_k) sum_k Re tr[Sigma^HF(k) n(k)];
+ *   Omega_G  = -(s/(beta N_k)) sum_k sum_{n=-M}^{M-1}
+ *              Re{ln det[1 - G_HF Sigma^C] + tr[Sigma^C G]}(k, i w_n),
+ *              G_HF = (i w_n + mu - H - Sigma^HF)^-1;
+ *   Omega_W  = (1/(2 beta N_k)) sum_q sum_{m=-M}^{M}
+ *              Re{ln det[1 - V(q) P(q, i nu_m)] + tr[V(q) P(q, i nu_m)]},
+ * with Sigma = Sigma^HF + Sigma^C and P computed from G_in as qa_gw_step does,
+ * and Sigma^C, G, P at the uniform frequencies from their DLR expansions.
+ *   G_in   device, G layout complex128, or NULL = G0;
+ *   M      Matsubara cutoff (1 .. 2^20); part of the definition;
+ *   omega  host scalar, parts host [4] (either may be NULL).
+ * FP64 contexts only (QA_EINVAL otherwise); either pair basis.  The first call
+ * for a cutoff allocates the uniform-frequency maps and a scratch (cudaMalloc,
+ * kept until qa_destroy; QA_ENOMEM if it fails); a singular 1 - V P or
+ * Dyson matrix gives QA_ESINGULAR.  Synchronises `stream`. */
+int qa_free_energy(qa_ctx* ctx, const void* G_in, double mu, int M, double* omega, double* parts,
+                   void* stream);
+
+/* qa_free_energy_backward: gradient of omega_bar * Omega (qa_free_energy, same
+ * G_in, mu, M) through the adjoint of the iteration's stages (qa_gw_backward's
+ * chain, with Omega's explicit cotangents added where its terms read Sigma^HF,
+ * n, H, Sigma^C, G, P and V).  Outputs as qa_gw_backward (Gbar_in device,
+ * grad_t and grad_V host; each may be NULL).  FP64 contexts, full pair basis
+ * (QA_ESTATE otherwise).  Synchronises `stream`. */
+int qa_free_energy_backward(qa_ctx* ctx, const void* G_in, double mu, int M, double omega_bar,
+                            void* Gbar_in, double* grad_t, double* grad_V, void* stream);
+
 /* qa_hf_solve: self-consistent Hartree-Fock (paper Sec. "Hartree-Fock
  * self-consistency" and Fig. 3(a), the first stage of the QAssemble workflow).
  * Starting from the Fermi-Dirac density of H0 at its own chemical potential,

@@ -173,8 +173,19 @@ struct qa_ctx {
   QaMailbox* mb = nullptr;        // pinned host mailbox (qa_bind) and its device alias
   QaMailbox* mb_dev = nullptr;
   size_t ws_need = 0;             // workspace bytes of the bound layout
+  // grand potential (qa_free_energy): uniform-frequency maps of cutoff om_M,
+  // fermionic / bosonic chunk rows om_cf / om_cb, and the scratch they use
+  int om_M = 0, om_cf = 0, om_cb = 0;
+  double2* d_omEF = nullptr;      // [2M][r]
+  double2* d_omEFH = nullptr;     // per fermionic chunk: [r][rows] conjugate transpose
+  double2* d_omEB = nullptr;      // [2M+1][r]
+  double2* d_omEBH = nullptr;     // per bosonic chunk: [r][rows]
+  char* d_om = nullptr;           // scratch (allocated on the first qa_free_energy call)
   ~qa_ctx() {
     if (mb) cudaFreeHost(mb);
+    for (void* p : {static_cast<void*>(d_omEF), static_cast<void*>(d_omEFH), static_cast<void*>(d_omEB),
+                    static_cast<void*>(d_omEBH), static_cast<void*>(d_om)})
+      if (p) cudaFree(p);
   }
 };
 
@@ -924,12 +935,216 @@ int gw_step_impl(qa_ctx* c, const void* G_in, void* G_out, double* mu_out, doubl
   return herr;
 }
 
+// ------------------------------------------------ grand potential (FP64)
+
+// Scratch of the grand potential (d_om): eigen-decomposition of H + Sigma^HF,
+// the cotangents collected before the adjoint chain runs, frequency chunks,
+// per-point terms and the four accumulated terms.
+struct OmScratch {
+  double* E;
+  double2* U;
+  double2* abar;      // [norb^2][N_k] cotangent of H + Sigma^HF
+  double2* sig_x;     // [norb^2][N_k] cotangent of Sigma^HF alone
+  double2* nbar_x;    // [norb^2][N_k] cotangent of n(k)
+  double2* sbar_tau;  // [r][norb^2][N_k] cotangent of Sigma^C(k, tau)
+  double2* gbar_tau;  // [r][norb^2][N_k] cotangent of G_in
+  double2* bufS;
+  double2* bufG;
+  double2* bufA;
+  double2* bufP;
+  double2* bufV;
+  double* part;
+  double* acc;        // [4]: Omega_HF, Omega_dc, Omega_G, Omega_W
+};
+
+size_t om_layout(const qa_ctx* c, int cf, int cb, OmScratch* o) {
+  const size_t nk = c->nk, no = c->norb, no2 = no * no, r = c->r;
+  const size_t ncs = no2 * nk, ncb = static_cast<size_t>(c->nb) * c->nb * nk;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t a = off;
+    off += align_up(bytes);
+    return a;
+  };
+  const size_t oE = take(nk * no * 8), oU = take(nk * no2 * 16), oA = take(ncs * 16), oSx = take(ncs * 16),
+               oNx = take(ncs * 16), oSt = take(r * ncs * 16), oGt = take(r * ncs * 16),
+               oBS = take(cf * ncs * 16), oBG = take(cf * ncs * 16), oBA = take(cf * ncs * 16),
+               oBP = take(cb * ncb * 16), oBV = take(cb * ncb * 16),
+               oPart = take(std::max({2 * nk, static_cast<size_t>(cf) * nk, static_cast<size_t>(cb) * nk}) * 8),
+               oAcc = take(4 * 8);
+  if (o) {
+    char* b = c->d_om;
+    o->E = reinterpret_cast<double*>(b + oE);
+    o->U = reinterpret_cast<double2*>(b + oU);
+    o->abar = reinterpret_cast<double2*>(b + oA);
+    o->sig_x = reinterpret_cast<double2*>(b + oSx);
+    o->nbar_x = reinterpret_cast<double2*>(b + oNx);
+    o->sbar_tau = reinterpret_cast<double2*>(b + oSt);
+    o->gbar_tau = reinterpret_cast<double2*>(b + oGt);
+    o->bufS = reinterpret_cast<double2*>(b + oBS);
+    o->bufG = reinterpret_cast<double2*>(b + oBG);
+    o->bufA = reinterpret_cast<double2*>(b + oBA);
+    o->bufP = reinterpret_cast<double2*>(b + oBP);
+    o->bufV = reinterpret_cast<double2*>(b + oBV);
+    o->part = reinterpret_cast<double*>(b + oPart);
+    o->acc = reinterpret_cast<double*>(b + oAcc);
+  }
+  return off;
+}
+
+void om_free(qa_ctx* c) {
+  for (double2** p : {&c->d_omEF, &c->d_omEFH, &c->d_omEB, &c->d_omEBH}) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
+  if (c->d_om) cudaFree(c->d_om);
+  c->d_om = nullptr;
+  c->om_M = 0;
+}
+
+// Uniform-frequency maps of cutoff M (and their per-chunk conjugate
+// transposes) and the scratch, allocated on first use and kept.
+int ensure_omega(qa_ctx* c, int M) {
+  if (c->om_M == M && c->d_om) return QA_OK;
+  om_free(c);
+  std::vector<cd> EF, EB;
+  qa::build_uniform_maps(c->grid, c->beta, M, &EF, &EB);
+  const int r = c->r;
+  const size_t ncs = static_cast<size_t>(c->norb) * c->norb * c->nk;
+  const size_t ncb = static_cast<size_t>(c->nb) * c->nb * c->nk;
+  const size_t cap = static_cast<size_t>(512) << 20;     // bytes of one chunk buffer at most
+  const int cf = static_cast<int>(std::min<size_t>({static_cast<size_t>(2 * M), 256,
+                                                    std::max<size_t>(1, cap / (ncs * 16))}));
+  const int cb = static_cast<int>(std::min<size_t>({static_cast<size_t>(2 * M + 1), 256,
+                                                    std::max<size_t>(1, cap / (ncb * 16))}));
+  auto chunked_h = [r](const std::vector<cd>& A, int rows_all, int ch) {
+    std::vector<cd> H(A.size());
+    for (int j0 = 0; j0 < rows_all; j0 += ch) {
+      const int rows = std::min(ch, rows_all - j0);
+      for (int j = 0; j < r; ++j)
+        for (int i = 0; i < rows; ++i)
+          H[static_cast<size_t>(j0) * r + static_cast<size_t>(j) * rows + i] =
+              std::conj(A[static_cast<size_t>(j0 + i) * r + j]);
+    }
+    return H;
+  };
+  const std::vector<cd> EFH = chunked_h(EF, 2 * M, cf), EBH = chunked_h(EB, 2 * M + 1, cb);
+  struct Up {
+    double2** dst;
+    const std::vector<cd>* src;
+  } ups[4] = {{&c->d_omEF, &EF}, {&c->d_omEFH, &EFH}, {&c->d_omEB, &EB}, {&c->d_omEBH, &EBH}};
+  for (const Up& u : ups) {
+    if (cudaMalloc(reinterpret_cast<void**>(u.dst), u.src->size() * 16) != cudaSuccess) {
+      om_free(c);
+      return QA_ENOMEM;
+    }
+    QA_TRY(cudaMemcpy(*u.dst, u.src->data(), u.src->size() * 16, cudaMemcpyHostToDevice));
+  }
+  if (cudaMalloc(reinterpret_cast<void**>(&c->d_om), om_layout(c, cf, cb, nullptr)) != cudaSuccess) {
+    om_free(c);
+    return QA_ENOMEM;
+  }
+  c->om_M = M;
+  c->om_cf = cf;
+  c->om_cb = cb;
+  return QA_OK;
+}
+
+// The four terms of the grand potential for the G_in whose stages
+// forward_sigma<double> has just computed (Sigma^HF, n, Sigma^C(k, tau),
+// P(q, i nu) in place), into parts[4] on the host.
+int omega_value(qa_ctx* c, const double2* Gin, double mu, double* parts, cudaStream_t st) {
+  OmScratch o;
+  om_layout(c, c->om_cf, c->om_cb, &o);
+  const int r = c->r, no = c->norb, nk = c->nk, nb = c->nb, M = c->om_M;
+  const long long ncs = static_cast<long long>(no) * no * nk, ncb = static_cast<long long>(nb) * nb * nk;
+  const double s = c->nspin, beta = c->beta;
+  QA_TRY(cudaMemsetAsync(o.acc, 0, 4 * sizeof(double), st));
+  QA_LAUNCH(c, 1, qa::launch_hf_eig(c->d_Hk, c->d_SigHF, no, nk, o.E, o.U, st));
+  QA_LAUNCH(c, 1, qa::launch_omega_hf(o.E, o.U, c->d_SigHF, c->d_nk, no, nk, beta, mu, o.part, nullptr, 0.0, st));
+  QA_LAUNCH(c, 1, qa::launch_sum_scalar(o.part, nk, -s / (beta * nk), o.acc, 0, st));
+  QA_LAUNCH(c, 1, qa::launch_sum_scalar(o.part + nk, nk, -0.5 * s / nk, o.acc, 1, st));
+  for (int j0 = 0; j0 < 2 * M; j0 += c->om_cf) {
+    const int rows = std::min(c->om_cf, 2 * M - j0);
+    const double2* E = c->d_omEF + static_cast<size_t>(j0) * r;
+    QA_LAUNCH(c, 1, qa::launch_dlr_apply<double>(E, rows, r, c->d_SigC, o.bufS, ncs, st));
+    QA_LAUNCH(c, 1, qa::launch_dlr_apply<double>(E, rows, r, Gin, o.bufG, ncs, st));
+    QA_LAUNCH(c, 1, qa::launch_omega_g(c->d_Hk, c->d_SigHF, o.bufS, o.bufG, j0 - M, rows, no, nk, beta, mu,
+                                       o.part, nullptr, 0.0, 0.0, c->d_err, st));
+    QA_LAUNCH(c, 1, qa::launch_sum_scalar(o.part, static_cast<long long>(rows) * nk, -s / (beta * nk), o.acc, 2, st));
+  }
+  for (int j0 = 0; j0 < 2 * M + 1; j0 += c->om_cb) {
+    const int rows = std::min(c->om_cb, 2 * M + 1 - j0);
+    QA_LAUNCH(c, 1, qa::launch_dlr_apply<double>(c->d_omEB + static_cast<size_t>(j0) * r, rows, r, c->d_P,
+                                                 o.bufP, ncb, st));
+    QA_LAUNCH(c, 1, qa::launch_omega_w(o.bufP, static_cast<const double2*>(c->d_Vq), nb, nk, rows, o.part,
+                                       nullptr, 0.0, c->d_err, st));
+    QA_LAUNCH(c, 1, qa::launch_sum_scalar(o.part, static_cast<long long>(rows) * nk, 1.0 / (2.0 * beta * nk),
+                                          o.acc, 3, st));
+  }
+  QA_TRY(cudaMemcpyAsync(parts, o.acc, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  QA_TRY(cudaStreamSynchronize(st));
+  return QA_OK;
+}
+
+// Cotangents of the grand potential's explicit dependences, taken before the
+// adjoint chain reuses the forward buffers: abar (H + Sigma^HF), sig_x
+// (Sigma^HF alone), nbar_x (n(k)), sbar_tau (Sigma^C(k, tau)), gbar_tau (G_in).
+int omega_bwd_pre(qa_ctx* c, const double2* Gin, double mu, double wbar, cudaStream_t st) {
+  OmScratch o;
+  om_layout(c, c->om_cf, c->om_cb, &o);
+  const int r = c->r, no = c->norb, nk = c->nk, M = c->om_M;
+  const long long ncs = static_cast<long long>(no) * no * nk;
+  const double s = c->nspin, beta = c->beta, cg = s / (beta * nk);
+  QA_LAUNCH(c, 1, qa::launch_hf_eig(c->d_Hk, c->d_SigHF, no, nk, o.E, o.U, st));
+  QA_LAUNCH(c, 1, qa::launch_omega_hf(o.E, o.U, c->d_SigHF, c->d_nk, no, nk, beta, mu, o.part, o.abar,
+                                      s / nk * wbar, st));
+  QA_LAUNCH(c, 1, qa::launch_herm_scale(c->d_nk, 0, no, nk, -0.5 * s / nk * wbar, o.sig_x, st));
+  QA_LAUNCH(c, 1, qa::launch_herm_scale(c->d_SigHF, 1, no, nk, -0.5 * s / nk * wbar, o.nbar_x, st));
+  QA_TRY(cudaMemsetAsync(o.sbar_tau, 0, static_cast<size_t>(r) * ncs * 16, st));
+  QA_TRY(cudaMemsetAsync(o.gbar_tau, 0, static_cast<size_t>(r) * ncs * 16, st));
+  for (int j0 = 0; j0 < 2 * M; j0 += c->om_cf) {
+    const int rows = std::min(c->om_cf, 2 * M - j0);
+    const double2* E = c->d_omEF + static_cast<size_t>(j0) * r;
+    const double2* EH = c->d_omEFH + static_cast<size_t>(j0) * r;
+    QA_LAUNCH(c, 1, qa::launch_dlr_apply<double>(E, rows, r, c->d_SigC, o.bufS, ncs, st));
+    QA_LAUNCH(c, 1, qa::launch_dlr_apply<double>(E, rows, r, Gin, o.bufG, ncs, st));
+    QA_LAUNCH(c, 1, qa::launch_omega_g(c->d_Hk, c->d_SigHF, o.bufS, o.bufG, j0 - M, rows, no, nk, beta, mu,
+                                       o.part, o.bufA, -cg * wbar, cg * wbar, c->d_err, st));
+    QA_LAUNCH(c, 1, qa::launch_sum_rows(o.bufA, rows, ncs, o.abar, 1, st));
+    QA_LAUNCH(c, 1, qa::launch_dlr_apply<double>(EH, r, rows, o.bufS, o.sbar_tau, ncs, st, 1));
+    QA_LAUNCH(c, 1, qa::launch_dlr_apply<double>(EH, r, rows, o.bufG, o.gbar_tau, ncs, st, 1));
+  }
+  return QA_OK;
+}
+
+// The ring term's cotangents: Pbar(q, i nu_j) += EB^H Pbar_m, Vbar(q) += sum_m
+// (P W P)^H terms; needs P(q, i nu) (d_P) intact.
+int omega_bwd_w(qa_ctx* c, double wbar, double2* Pbar_nu, cudaStream_t st) {
+  OmScratch o;
+  om_layout(c, c->om_cf, c->om_cb, &o);
+  const int r = c->r, nk = c->nk, nb = c->nb, M = c->om_M;
+  const long long ncb = static_cast<long long>(nb) * nb * nk;
+  const double cw = -wbar / (2.0 * c->beta * nk);
+  for (int j0 = 0; j0 < 2 * M + 1; j0 += c->om_cb) {
+    const int rows = std::min(c->om_cb, 2 * M + 1 - j0);
+    QA_LAUNCH(c, 1, qa::launch_dlr_apply<double>(c->d_omEB + static_cast<size_t>(j0) * r, rows, r, c->d_P,
+                                                 o.bufP, ncb, st));
+    QA_LAUNCH(c, 1, qa::launch_omega_w(o.bufP, static_cast<const double2*>(c->d_Vq), nb, nk, rows, o.part,
+                                       o.bufV, cw, c->d_err, st));
+    QA_LAUNCH(c, 1, qa::launch_sum_rows(o.bufV, rows, ncb, reinterpret_cast<double2*>(c->d_Vqbar), 1, st));
+    QA_LAUNCH(c, 1, qa::launch_dlr_apply<double>(c->d_omEBH + static_cast<size_t>(j0) * r, r, rows, o.bufP,
+                                                 Pbar_nu, ncb, st, 1));
+  }
+  return QA_OK;
+}
+
 // Adjoint of one iteration at fixed mu (FP64).  Recomputes the forward
 // stages from G_in (P is recomputed, not stored), then pulls the cotangents
 // back stage by stage (qa_adjoint.cu).
 int gw_backward_impl(qa_ctx* c, const double2* Gin, double mu, const double2* Gbar_out,
                      const double2* Sigbar, const double* nbar, double2* Gbar_in, double* grad_t,
-                     double* grad_V, cudaStream_t st) {
+                     double* grad_V, cudaStream_t st, double wbar = 0.0) {
   const qa::FftDev& fft = c->fft64;
   const int r = c->r, no2 = c->norb * c->norb, nk = c->nk, np2 = c->npair * c->npair;
   const long long ncs = static_cast<long long>(no2) * nk;
@@ -942,6 +1157,12 @@ int gw_backward_impl(qa_ctx* c, const double2* Gin, double mu, const double2* Gb
   StageTimer tm(c, st);
   c->timing = timing;
   if (int rc = forward_sigma<double>(c, Gin, tm, st)) return rc;
+  // grand-potential cotangent (wbar != 0): its explicit terms first
+  OmScratch om{};
+  if (wbar != 0.0) {
+    om_layout(c, c->om_cf, c->om_cb, &om);
+    if (int rc = omega_bwd_pre(c, Gin, mu, wbar, st)) return rc;
+  }
   double2* Giw_bar = static_cast<double2*>(c->d_Giw);
   double2* SigIw_bar = static_cast<double2*>(c->d_Gt);
   double2* Sig_bar = static_cast<double2*>(c->d_SigC);
@@ -960,9 +1181,11 @@ int gw_backward_impl(qa_ctx* c, const double2* Gin, double mu, const double2* Gb
   // Dyson for G
   QA_LAUNCH(c, 1, qa::launch_dyson_g_bwd(c->d_Hk, c->d_SigHF, static_cast<const double2*>(c->d_SigIw),
                                          c->d_iw, mu, r, c->norb, nk, Giw_bar, SigIw_bar, c->d_Sbar, st));
+  if (wbar != 0.0) QA_LAUNCH(c, 1, qa::launch_axpy(c->d_Sbar, om.abar, 1.0, ncs, st));
   // Sigma^C(k, i w) <- Sigma^C(k, tau) <- Sigma^C(R, tau)
   QA_LAUNCH(c, 1, qa::launch_dlr_apply<double>(c->tH.Ttw, r, r, SigIw_bar, Sig_bar, ncs, st));
   if (Sigbar) QA_LAUNCH(c, 1, qa::launch_axpy(Sig_bar, Sigbar, 1.0, ncs * r, st));
+  if (wbar != 0.0) QA_LAUNCH(c, 1, qa::launch_axpy(Sig_bar, om.sbar_tau, 1.0, ncs * r, st));
   QA_LAUNCH(c, 1, qa::launch_fft3d<double>(fft, +1, Sig_bar, Sig_bar, lines_s, st, 1.0));
   // Sigma contraction: Gbar(R) and Wbar(R, tau) (in place over W^C)
   QA_LAUNCH(c, 1, qa::launch_sigma_bwd(static_cast<const double2*>(c->d_GR), Sig_bar, Wbig, c->d_GRbar,
@@ -975,6 +1198,8 @@ int gw_backward_impl(qa_ctx* c, const double2* Gin, double mu, const double2* Gb
   QA_LAUNCH(c, 1, qa::launch_dyson_w_bwd(static_cast<const double2*>(c->d_P),
                                          static_cast<const double2*>(c->d_Vq), Wbig, c->d_Vqbar, r,
                                          c->npair, nk, c->d_err, st));
+  if (wbar != 0.0)
+    if (int rc = omega_bwd_w(c, wbar, Wbig, st)) return rc;
   // P(q, i nu) <- P(q, tau) <- P(R, tau)
   QA_LAUNCH(c, 1, qa::launch_dlr_apply<double>(c->tH.Ttn, r, r, Wbig, Wbig, ncb, st));
   QA_LAUNCH(c, 1, qa::launch_fft3d<double>(fft, +1, Wbig, Wbig, lines_b, st, 1.0));
@@ -988,6 +1213,13 @@ int gw_backward_impl(qa_ctx* c, const double2* Gin, double mu, const double2* Gb
   double2* gin = Gbar_in ? Gbar_in : reinterpret_cast<double2*>(c->d_Gk);
   QA_LAUNCH(c, 1, qa::launch_dlr_apply<double>(c->tH.Trefl, r, r, c->d_GLbar, gin, ncs, st));
   QA_LAUNCH(c, 1, qa::launch_axpy(gin, c->d_GRbar, 1.0, ncs * r, st));
+  if (wbar != 0.0) QA_LAUNCH(c, 1, qa::launch_axpy(gin, om.gbar_tau, 1.0, ncs * r, st));
+  // t(R) = -H(R): tbar(R) = -sum_k e^{+ik.R} Hbar(k)
+  QA_LAUNCH(c, 1, qa::launch_density_R(c->d_Sbar, c->d_hR, c->nH, no2, nullptr, nk, c->n[0], c->n[1],
+                                       c->n[2], c->d_tbar, st));
+  QA_LAUNCH(c, 1, qa::launch_scale(c->d_tbar, -static_cast<double>(nk), static_cast<long long>(c->nH) * no2, st));
+  // Sigma^HF alone carries the grand potential's double-counting term
+  if (wbar != 0.0) QA_LAUNCH(c, 1, qa::launch_axpy(c->d_Sbar, om.sig_x, 1.0, ncs, st));
   // Hartree and Fock: (H, Sigma^HF) bar -> Sigma^H bar, Sigma^F bar(R_v) -> Vbar, nbar
   QA_LAUNCH(c, 1, qa::launch_density_R(c->d_Sbar, c->d_vR, c->nV + 1, no2, nullptr, nk, c->n[0],
                                        c->n[1], c->n[2], c->d_X, st));
@@ -995,11 +1227,8 @@ int gw_backward_impl(qa_ctx* c, const double2* Gin, double mu, const double2* Gb
                                     c->d_VbarHF, c->d_nbarR, st));
   QA_LAUNCH(c, 1, qa::launch_nbar_k(c->d_nbarR, c->d_vR, c->nV + 1, no2, nk, c->n[0], c->n[1],
                                     c->n[2], c->d_nk, st));
+  if (wbar != 0.0) QA_LAUNCH(c, 1, qa::launch_axpy(c->d_nk, om.nbar_x, 1.0, ncs, st));
   QA_LAUNCH(c, 1, qa::launch_dlr_apply<double>(c->tH.dtau, r, 1, c->d_nk, gin, ncs, st, 1));
-  // t(R) = -H(R): tbar(R) = -sum_k e^{+ik.R} Hbar(k)
-  QA_LAUNCH(c, 1, qa::launch_density_R(c->d_Sbar, c->d_hR, c->nH, no2, nullptr, nk, c->n[0], c->n[1],
-                                       c->n[2], c->d_tbar, st));
-  QA_LAUNCH(c, 1, qa::launch_scale(c->d_tbar, -static_cast<double>(nk), static_cast<long long>(c->nH) * no2, st));
   // V(R): sum_q e^{+iq.R} Vbar(q) plus the Hartree/Fock part
   if (c->nV > 0) {
     QA_LAUNCH(c, 1, qa::launch_density_R(reinterpret_cast<const double2*>(c->d_Vqbar), c->d_vR, c->nV,
@@ -1657,6 +1886,42 @@ int qa_gw_backward(qa_ctx* c, const void* G_in, double mu, const void* Gbar_out,
   return gw_backward_impl(c, Gin, mu, static_cast<const double2*>(Gbar_out),
                           static_cast<const double2*>(Sigbar), nbar, static_cast<double2*>(Gbar_in),
                           grad_t, grad_V, static_cast<cudaStream_t>(stream));
+}
+
+int qa_free_energy(qa_ctx* c, const void* G_in, double mu, int M, double* omega, double* parts,
+                   void* stream) {
+  if (!c || M < 1 || M > (1 << 20) || !std::isfinite(mu)) return QA_EINVAL;
+  if (!c->bound) return QA_ESTATE;
+  if (c->precision != QA_FP64) return QA_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (int rc = ensure_omega(c, M)) return rc;
+  const double2* Gin = static_cast<const double2*>(G_in ? G_in : c->d_G0);
+  c->launches = 0;
+  if (int rc = reset_err(c, st)) return rc;
+  const bool timing = c->timing;
+  c->timing = false;
+  StageTimer tm(c, st);
+  c->timing = timing;
+  if (int rc = forward_sigma<double>(c, Gin, tm, st)) return rc;
+  double p[4];
+  if (int rc = omega_value(c, Gin, mu, p, st)) return rc;
+  if (int herr = check_err(c, nullptr, st)) return herr;
+  if (omega) *omega = p[0] + p[1] + p[2] + p[3];
+  if (parts)
+    for (int i = 0; i < 4; ++i) parts[i] = p[i];
+  return QA_OK;
+}
+
+int qa_free_energy_backward(qa_ctx* c, const void* G_in, double mu, int M, double omega_bar,
+                            void* Gbar_in, double* grad_t, double* grad_V, void* stream) {
+  if (!c || M < 1 || M > (1 << 20) || !std::isfinite(mu) || !std::isfinite(omega_bar)) return QA_EINVAL;
+  if (!c->bound) return QA_ESTATE;
+  if (c->precision != QA_FP64) return QA_EINVAL;
+  if (c->reduced) return QA_ESTATE;
+  if (int rc = ensure_omega(c, M)) return rc;
+  const double2* Gin = static_cast<const double2*>(G_in ? G_in : c->d_G0);
+  return gw_backward_impl(c, Gin, mu, nullptr, nullptr, nullptr, static_cast<double2*>(Gbar_in), grad_t,
+                          grad_V, static_cast<cudaStream_t>(stream), omega_bar);
 }
 
 int qa_hf_solve(qa_ctx* c, int max_iter, double tol, double mix, void* G_out, double* mu_out,

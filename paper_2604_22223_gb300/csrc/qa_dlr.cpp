@@ -292,6 +292,38 @@ void build_dlr_matrices(const DlrGrid& g, double beta, DlrMatrices* m) {
   for (int j = 0; j < r; ++j) m->iw[j] = (2.0 * g.nf[j] + 1.0) * M_PI / beta;
 }
 
+// Uniform Matsubara evaluation of the expansions: the fermionic kernel at
+// i w_n times K_tau^-1 (from the tau-node values) and the bosonic kernel at
+// i nu_m times K_B^-1 (from the bosonic-node values), composed in long double.
+void build_uniform_maps(const DlrGrid& g, double beta, int M, std::vector<std::complex<double>>* EF,
+                        std::vector<std::complex<double>>* EB) {
+  const int r = g.r;
+  using ld = long double;
+  const ld b = beta;
+  const ld pi = 3.141592653589793238462643383279502884L;
+  std::vector<cld> Kt(static_cast<size_t>(r) * r), KB(Kt.size());
+  for (int j = 0; j < r; ++j)
+    for (int l = 0; l < r; ++l) {
+      const ld x = g.x[l];
+      Kt[static_cast<size_t>(j) * r + l] = cld(-kernel<ld>(static_cast<ld>(g.t[j]), x), 0);
+      if (g.mb[j] == 0 && g.x[l] == 0.0) KB[static_cast<size_t>(j) * r + l] = cld(-b / 2, 0);
+      else KB[static_cast<size_t>(j) * r + l] = b * std::tanh(x / 2) / cld(-x, 2 * pi * g.mb[j]);
+    }
+  const std::vector<cld> Kti = invert(Kt, r), KBi = invert(KB, r);
+  std::vector<cld> F(static_cast<size_t>(2 * M) * r), B(static_cast<size_t>(2 * M + 1) * r);
+  for (int n = -M; n < M; ++n)
+    for (int l = 0; l < r; ++l)
+      F[static_cast<size_t>(n + M) * r + l] = b / cld(-static_cast<ld>(g.x[l]), (2 * static_cast<ld>(n) + 1) * pi);
+  for (int m = -M; m <= M; ++m)
+    for (int l = 0; l < r; ++l) {
+      const ld x = g.x[l];
+      B[static_cast<size_t>(m + M) * r + l] =
+          (m == 0 && g.x[l] == 0.0) ? cld(-b / 2, 0) : b * std::tanh(x / 2) / cld(-x, 2 * pi * m);
+    }
+  *EF = matmul(F, Kti, 2 * M, r);
+  *EB = matmul(B, KBi, 2 * M + 1, r);
+}
+
 void plan_fft_axis(int L, FftAxisPlan* p, std::vector<int>* pos) {
   p->L = L;
   p->nfac = 0;

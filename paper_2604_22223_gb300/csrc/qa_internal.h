@@ -46,6 +46,11 @@ struct DlrMatrices {
   std::vector<double> iw;                   // w_n values (imaginary parts)
 };
 void build_dlr_matrices(const DlrGrid& g, double beta, DlrMatrices* m);
+// Uniform-frequency evaluation of DLR expansions, physical units, row-major:
+// EF [2M][r]: X(i w_n) = sum_j EF[n+M][j] X(tau_j), n = -M .. M-1;
+// EB [2M+1][r]: X(i nu_m) = sum_j EB[m+M][j] X(i nu_j) (bosonic DLR nodes).
+void build_uniform_maps(const DlrGrid& g, double beta, int M, std::vector<std::complex<double>>* EF,
+                        std::vector<std::complex<double>>* EB);
 
 // ------------------------------------------------------------ pair basis
 // Orthonormal basis B (npair x rho, row-major [A][j]) of the subspace that the
@@ -319,6 +324,33 @@ cudaError_t launch_qp(const double2* Hk, const double2* SigHF, const void* SigIw
                       const double2* wp, const double2* wm, int r, int norb, int nk, double w0,
                       double2* S, double2* Z, double2* S0, double2* Hqp, double* eps, int* err,
                       cudaStream_t st);
+
+// ---- GW grand potential in the Luttinger-Ward form (FP64), qa_free_energy.cu
+// Per k: part[k] = sum_i ln(1 + e^{-beta (E_ki - mu)}), part[nk + k] =
+// Re tr[SigHF(k) n(k)] (n [norb^2][N_k]); nhf (may be null) = scale f(A - mu).
+cudaError_t launch_omega_hf(const double* E, const double2* U, const double2* SigHF,
+                            const double2* nk_in, int norb, int nk, double beta, double mu,
+                            double* part, double2* nhf, double scale, cudaStream_t st);
+// Fermionic-trace terms of rows j = 0..rows-1 (i w_{n0+j}) of S = Sigma^C and G
+// ([rows][norb^2][N_k]): part[j][k]; with abar (may be null) the cotangents
+// S <- cs (G - G_D)^H, G <- cs S^H (in place), abar = ca (G_D - G_HF)^H.
+cudaError_t launch_omega_g(const double2* Hk, const double2* SigHF, double2* S, double2* G, int n0,
+                           int rows, int norb, int nk, double beta, double mu, double* part,
+                           double2* abar, double cs, double ca, int* err, cudaStream_t st);
+// Bosonic-trace terms of rows of P ([rows][nb^2][N_k]) with V(q) ([N_k][nb^2]):
+// part[j][q] = ln|det(1 - V P)| + Re tr[V P]; with vbar (may be null)
+// P <- cw (W - V)^H in place and vbar = cw (P W P)^H, W = (1 - V P)^-1 V.
+cudaError_t launch_omega_w(double2* P, const double2* Vq, int nb, int nk, int rows, double* part,
+                           double2* vbar, double cw, int* err, cudaStream_t st);
+// out[(a,b)][k] = coef conj(in_(b,a)(k)); in [N_k][norb^2] (kmajor) or [norb^2][N_k]
+cudaError_t launch_herm_scale(const double2* in, int kmajor, int norb, int nk, double coef, double2* out,
+                              cudaStream_t st);
+// out[e] (+)= sum_j buf[j][e], j < rows, e < n
+cudaError_t launch_sum_rows(const double2* buf, int rows, long long n, double2* out, int accumulate,
+                            cudaStream_t st);
+// acc[slot] += scale * sum part[0 .. n) (fixed order)
+cudaError_t launch_sum_scalar(const double* part, long long n, double scale, double* acc, int slot,
+                              cudaStream_t st);
 
 // Host copies a density call needs (valid for the context's lifetime).
 int density_tables(const ::qa_ctx* ctx, const std::complex<double>** dtau, int* r, int* norb,

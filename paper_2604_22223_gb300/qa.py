@@ -26,7 +26,7 @@ EXPORTED = ["qa_create", "qa_workspace_size", "qa_bind", "qa_get_grid", "qa_get_
             "qa_get_sizes", "qa_gw_step", "qa_density", "qa_density_static", "qa_get",
             "qa_set_timing", "qa_set_mu", "qa_set_params", "qa_gw_backward", "qa_set_pair_basis",
             "qa_get_pair_basis", "qa_hf_solve", "qa_qp", "qa_destroy", "qa_strerror",
-            "qa_fma_probe", "qa_set_wait_limit"]
+            "qa_fma_probe", "qa_set_wait_limit", "qa_free_energy", "qa_free_energy_backward"]
 
 STAGES = ["hartree_fock", "g_to_R", "bubble", "fft_R_to_q", "dlr_tau_to_nu", "dyson_w",
           "dlr_nu_to_tau", "fft_q_to_R", "sigma", "sigma_to_k_iw", "mu_search", "dyson_g"]
@@ -113,6 +113,8 @@ def load(path: str = LIB_PATH):
     L.qa_qp.argtypes = [vp, vp, vp, vp, vp, vp]
     L.qa_fma_probe.argtypes = [i, i, vp, C.POINTER(C.c_longlong), C.POINTER(d), vp]
     L.qa_set_wait_limit.argtypes = [vp, C.c_longlong]
+    L.qa_free_energy.argtypes = [vp, vp, d, i, C.POINTER(d), vp, vp]
+    L.qa_free_energy_backward.argtypes = [vp, vp, d, i, d, vp, vp, vp, vp]
     L.qa_destroy.argtypes = [vp]
     L.qa_destroy.restype = None
     L.qa_strerror.argtypes = [i]
@@ -308,6 +310,29 @@ class Context(Problem):
         _check(load().qa_gw_backward(self.ctx, ptr(G_in), float(mu), ptr(Gbar_out), ptr(Sigbar),
                                      None if nb is None else nb.ctypes.data, ptr(Gb), gt.ctypes.data,
                                      gV.ctypes.data, self._stream()), "qa_gw_backward")
+        return (Gb, gt.view(np.complex128).reshape(nH, no, no),
+                gV.view(np.complex128)[:nV * npair * npair].reshape(nV, npair, npair))
+
+    def free_energy(self, G_in, mu, M):
+        """GW grand potential of G_in at fixed mu, Matsubara cutoff M (qa_free_energy):
+        (Omega, {omega_hf, omega_dc, omega_g, omega_w})."""
+        om = C.c_double()
+        parts = np.zeros(4)
+        _check(load().qa_free_energy(self.ctx, None if G_in is None else G_in.data_ptr(), float(mu), int(M),
+                                     C.byref(om), parts.ctypes.data, self._stream()), "qa_free_energy")
+        return om.value, dict(zip(("omega_hf", "omega_dc", "omega_g", "omega_w"), parts.tolist()))
+
+    def free_energy_backward(self, G_in, mu, M, omega_bar=1.0, want_gin=True):
+        """Gradient of omega_bar * Omega (qa_free_energy_backward): (Gbar_in, grad_t, grad_V)."""
+        no, npair = self.norb, self.npair
+        nH, nV = len(self.model.hop_R), len(self.model.V_R)
+        gt = np.zeros(2 * nH * no * no)
+        gV = np.zeros(2 * max(nV, 1) * npair * npair)
+        Gb = self.new_g() if want_gin else None
+        _check(load().qa_free_energy_backward(self.ctx, None if G_in is None else G_in.data_ptr(), float(mu),
+                                              int(M), float(omega_bar), None if Gb is None else Gb.data_ptr(),
+                                              gt.ctypes.data, gV.ctypes.data, self._stream()),
+               "qa_free_energy_backward")
         return (Gb, gt.view(np.complex128).reshape(nH, no, no),
                 gV.view(np.complex128)[:nV * npair * npair].reshape(nV, npair, npair))
 

@@ -77,9 +77,11 @@ def test_adjoint_matches_finite_differences(name):
     from paper_2604_22223_gb300 import qa
     model = wl.config(name)
     rng = np.random.default_rng(11)
+    d = gw.make_dlr(model)
+    G0_or, _ = gw.g0(model, d)
+    mu = gw.gw_step(model, d, G0_or)["mu"]   # the oracle's mu, frozen for both sides
     ctx = qa.Context(model, "fp64")
     G0 = ctx.get(qa.QA_G0)
-    _, mu, _, _ = ctx.step(G0)
     ctx.set_mu(mu)                      # frozen mu for the forward evaluations below
     shape = tuple(G0.shape)
     CG = torch.from_numpy(rng.normal(size=shape) + 1j * rng.normal(size=shape)).cuda()
@@ -115,8 +117,6 @@ def test_adjoint_matches_finite_differences(name):
         assert abs(adj[k] - fd[k]) <= TOL * max(1.0, abs(fd[k])), (k, adj[k], fd[k])
 
     # the oracle's FP64 gradient by its own central differences (frozen mu)
-    d = gw.make_dlr(model)
-    G0_or, _ = gw.g0(model, d)
     CGo = np.moveaxis(CG.cpu().numpy(), -1, 0)
     CSo = np.moveaxis(CS.cpu().numpy(), -1, 0)
 
