@@ -51,6 +51,7 @@ struct QaMailbox {
   int err;                  // device error word
   int pad;
   double2 nloc[25];         // local density matrix
+  qa::MuState mus;          // final state of the device-side chemical-potential search
 };
 
 struct qa_ctx {
@@ -181,7 +182,20 @@ struct qa_ctx {
   double2* d_omEB = nullptr;      // [2M+1][r]
   double2* d_omEBH = nullptr;     // per bosonic chunk: [r][rows]
   char* d_om = nullptr;           // scratch (allocated on the first qa_free_energy call)
+  // device-side chemical-potential search: its state and one instantiated graph
+  // (a while-node over [density, update]) per arithmetic, built on first use
+  qa::MuState* d_mus = nullptr;
+  cudaGraphExec_t mu_exec[3] = {nullptr, nullptr, nullptr};
+  void drop_mu_graphs() {
+    for (cudaGraphExec_t& g : mu_exec)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
+  }
   ~qa_ctx() {
+    drop_mu_graphs();
+    if (d_mus) cudaFree(d_mus);
     if (mb) cudaFreeHost(mb);
     for (void* p : {static_cast<void*>(d_omEF), static_cast<void*>(d_omEFH), static_cast<void*>(d_omEB),
                     static_cast<void*>(d_omEBH), static_cast<void*>(d_om)})
@@ -557,109 +571,91 @@ int eval_density(qa_ctx* c, const DevTables& tab, double mu, double* N, double* 
   return QA_OK;
 }
 
-// Chemical potential: the root of N(mu) = filling (N increases with mu).
-// One Newton step from the warm start mu_s (the previous mu) is tried first;
-// otherwise a bracket is found by marching from the better of the two points
-// in the direction of the root with growing steps, clamped to the window
+// The device-side search's graph for arithmetic T: a while-node whose body
+// is [density at the state's mu, update of the state], captured once per
+// context (the pointers it holds are fixed by qa_bind).
+template <typename T>
+int mu_graph(qa_ctx* c, const DevTables& tab, cudaGraphExec_t* out) {
+  const int slot = is_f64<T>() ? 0 : (is_df<T>() ? 1 : 2);
+  if (c->mu_exec[slot]) {
+    *out = c->mu_exec[slot];
+    return QA_OK;
+  }
+  if (!c->d_mus && cudaMalloc(reinterpret_cast<void**>(&c->d_mus), sizeof(qa::MuState)) != cudaSuccess)
+    return QA_ENOMEM;
+  cudaGraph_t g = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  auto fail = [&]() {
+    if (cs) cudaStreamDestroy(cs);
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return QA_ECUDA;
+  };
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) return fail();
+  cudaGraphConditionalHandle cond;
+  if (cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault) != cudaSuccess) return fail();
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = cond;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) != cudaSuccess) return fail();
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return fail();
+  if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+      cudaSuccess)
+    return fail();
+  cudaError_t e1 = qa::launch_dyson_g<T>(c->d_Bm, tab.dw, c->d_iw, 0.0, c->r, c->norb, c->nk, nullptr,
+                                         c->d_part, c->nblocks_g, 0, c->d_err, cs,
+                                         reinterpret_cast<const double*>(c->d_mus));
+  cudaError_t e2 = qa::launch_mu_update(c->d_part, c->nblocks_g, c->d_mus, static_cast<double>(c->nspin),
+                                        c->nk, cond, cs);
+  cudaGraph_t captured = nullptr;
+  cudaError_t e3 = cudaStreamEndCapture(cs, &captured);
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) return fail();
+  cudaStreamDestroy(cs);
+  cs = nullptr;
+  if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) return fail();
+  cudaGraphDestroy(g);
+  c->mu_exec[slot] = ex;
+  *out = ex;
+  return QA_OK;
+}
+
+// Chemical potential: the root of N(mu) = filling (N increases with mu),
+// found on the device (qa_mu.cu): one Newton step from the warm start mu_s
+// (the previous mu); otherwise a bracket by marching from the better of the
+// two points toward the root with growing steps, clamped to the window
 // |mu - mu_s| <= max ||H + Sigma - mu_s|| + 1 + 10/beta outside which N is
-// empty or full; then
-// bisection with Newton steps taken when they stay inside the bracket and
-// at least halve the step before last (safeguarded Newton, "rtsafe").
-// Stop when |N - filling| <= tolN or the bracket (or, on the mixed path
-// whose FP32 density carries ~1e-6 noise, the Newton step) is below tolB.
+// empty or full; then bisection with Newton steps taken when they stay inside
+// the bracket and at least halve the step before last (safeguarded Newton).
+// Stop when |N - filling| <= tolN or the bracket (or, on the FP32 path whose
+// density carries ~1e-6 noise, the Newton step) is below tolB.  The whole
+// search is one graph launch; the host reads its final state once.
 template <typename T>
 int mu_search(qa_ctx* c, const double2* SigHF, const void* SigIw, const DevTables& tab,
               double mu_start, double* mu_out, double* N_out, int* evals, cudaStream_t st) {
   const double mu_s = std::isfinite(mu_start) ? mu_start : 0.0;
-  double bound = 0;
-  if (int rc = prepare_g<T>(c, SigHF, SigIw, mu_s, &bound, st)) return rc;
-  if (!std::isfinite(bound)) return QA_ERANGE;
-  const double wid = bound + 1.0 + 10.0 / c->beta;
-  const double wlo = mu_s - wid, whi = mu_s + wid;
   const double target = c->filling;
   const bool fp64 = !is_f32<T>();     // FP64 or double-float densities
-  // FP32 densities carry ~1e-6 relative noise: stop at that level on the FP32 path
-  const double tolN = (fp64 ? 1e-12 : 2e-6) * std::max(1.0, target);
-  auto tolB = [&](double m) { return (fp64 ? 2e-13 : 2e-7) * std::max(1.0, std::fabs(m)); };
-  int count = 0;
-  double N = 0, dN = 0;
-  auto ev = [&](double m, double* f, double* d) -> int {
-    int rc = eval_density<T>(c, tab, m, &N, &dN, st);
-    ++count;
-    if (rc != QA_OK) return rc;
-    if (!std::isfinite(N)) return QA_ERANGE;
-    *f = N - target;
-    *d = dN;
-    return QA_OK;
-  };
-  double mu = mu_s;
-  double f = 0, d = 0;
-  int rc = ev(mu, &f, &d);
-  if (rc != QA_OK) return rc;
-  // from a warm start one Newton step usually lands within tolerance
-  if (std::fabs(f) > tolN && d > 0 && std::isfinite(f / d) && std::fabs(f / d) < 0.25 * wid) {
-    const double m1 = mu - f / d;
-    double f1 = 0, d1 = 0;
-    rc = ev(m1, &f1, &d1);
-    if (rc != QA_OK) return rc;
-    if (std::fabs(f1) <= tolN) { mu = m1; f = f1; d = d1; }
-    else if (std::fabs(f1) < std::fabs(f)) { mu = m1; f = f1; d = d1; }   // continue from the better point
-  }
-  double lo = mu, hi = mu;
-  if (std::fabs(f) > tolN) {
-    // march toward the root until the sign of N - filling changes
-    double step = (d > 0 && std::isfinite(f / d)) ? 1.5 * std::fabs(f / d) : 1.0;
-    step = std::min(std::max(step, 1e-6), wid);
-    const double dir = f < 0 ? 1.0 : -1.0;
-    double fa = f, a = mu, b = mu, fb = f, db = d;
-    for (int m = 0; m < 64; ++m) {
-      b = a + dir * step;
-      if (b > whi) b = whi;
-      if (b < wlo) b = wlo;
-      rc = ev(b, &fb, &db);
-      if (rc != QA_OK) return rc;
-      if ((fb < 0) != (fa < 0) || std::fabs(fb) <= tolN) break;
-      if (b == whi || b == wlo) return QA_ERANGE;   // filling not reachable in the window
-      a = b;
-      fa = fb;
-      step *= 4.0;
-    }
-    if ((fb < 0) == (fa < 0) && std::fabs(fb) > tolN) return QA_ENOCONV;
-    lo = std::min(a, b);
-    hi = std::max(a, b);
-    // continue from the end with the smaller residual
-    if (std::fabs(fb) < std::fabs(fa)) { mu = b; f = fb; d = db; }
-    else { mu = a; f = fa; }
-    double dx = hi - lo, dxold = dx;
-    for (int it = 0; it < 200 && std::fabs(f) > tolN; ++it) {
-      if (f < 0) lo = std::max(lo, mu); else hi = std::min(hi, mu);
-      if (hi - lo <= tolB(mu)) {
-        mu = 0.5 * (lo + hi);
-        rc = ev(mu, &f, &d);
-        if (rc != QA_OK) return rc;
-        break;
-      }
-      const double cand = mu - f / d;
-      if (!(d > 0) || !std::isfinite(cand) || cand <= lo || cand >= hi ||
-          std::fabs(2.0 * f) > std::fabs(dxold * d)) {
-        dxold = dx;
-        dx = 0.5 * (hi - lo);
-        mu = lo + dx;
-      } else {
-        dxold = dx;
-        dx = f / d;
-        mu = cand;
-        if (!fp64 && std::fabs(dx) <= tolB(mu)) {   // converged to the density noise
-          rc = ev(mu, &f, &d);
-          if (rc != QA_OK) return rc;
-          break;
-        }
-      }
-      rc = ev(mu, &f, &d);
-      if (rc != QA_OK) return rc;
-      if (it == 199 && std::fabs(f) > tolN) return QA_ENOCONV;
-    }
-  }
+  cudaGraphExec_t ex = nullptr;
+  if (int rc = mu_graph<T>(c, tab, &ex)) return rc;
+  c->mu_ref = mu_s;
+  QA_LAUNCH(c, 1, qa::launch_dyson_g_prep<T>(c->d_Hk, SigHF, SigIw, mu_s, c->r, c->norb, c->nk,
+                                             c->d_Bm, c->d_part, c->nblocks_g, st));
+  QA_LAUNCH(c, 1, qa::launch_reduce_pairs(c->d_part, c->nblocks_g, 1, c->d_red, st));
+  QA_LAUNCH(c, 1, qa::launch_mu_init(c->d_mus, c->d_red, mu_s, target, c->beta, fp64 ? 1 : 0, st));
+  QA_TRY(cudaGraphLaunch(ex, st));
+  QA_TRY(cudaMemcpyAsync(&c->mb->mus, c->d_mus, sizeof(qa::MuState), cudaMemcpyDeviceToHost, st));
+  QA_TRY(cudaStreamSynchronize(st));
+  const qa::MuState& ms = c->mb->mus;
+  int count = ms.count;
+  c->launches += 2 * std::max(count, 1);
+  if (ms.status != QA_OK) return ms.status;
+  double mu = ms.mu;
+  double N = ms.N;
   if (!fp64) {
     // one FP64-accurate evaluation at the FP32 root (FP32 inverse refined by a
     // double-float residual step) and a Newton correction: removes the bias
@@ -1596,6 +1592,7 @@ int qa_bind(qa_ctx* c, void* workspace, size_t bytes, void* stream) {
     QA_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->mb_dev), c->mb, 0));
   }
   c->d_red = c->mb_dev->red;
+  c->drop_mu_graphs();          // they hold pointers into the previous workspace
   c->d_err = &c->mb_dev->err;
   c->d_bad = &c->mb_dev->bad;
   c->d_nloc = c->mb_dev->nloc;

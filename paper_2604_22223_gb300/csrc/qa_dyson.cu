@@ -819,21 +819,22 @@ __global__ void __launch_bounds__(256) dyson_g_prep_kernel(const double2* __rest
   if (threadIdx.x == 0) { part[2 * blockIdx.x] = best * no; part[2 * blockIdx.x + 1] = 0.0; }
 }
 
-// G(k, i w_n) = (i w_n + dmu + Bm(k, i w_n))^-1, dmu = mu - mu_ref.
+// G(k, i w_n) = (i w_n + dmu + Bm(k, i w_n))^-1, dmu = mu - mu_ref (with mus:
+// mus[0] - mus[1], the device-side search's current point and reference).
 // mode 0: per-block partial sums of Re(dw_n Tr G) and Re(dw_n Tr G^2) (FP64
 // accumulation of the per-system traces); mode 1: also store G.
 template <typename T, int NO>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) dyson_g_kernel(const cplx<T>* __restrict__ Bm,
                                                       const cplx<T>* __restrict__ dw,
                                                       const double* __restrict__ iw, double dmu,
-                                                      int r, int nk, cplx<T>* Giw, double* part,
-                                                      int mode, int* err) {
+                                                      const double* mus, int r, int nk, cplx<T>* Giw,
+                                                      double* part, int mode, int* err) {
   using V = cplx<T>;
   __shared__ double sh[64];
   const long long total = static_cast<long long>(r) * nk;
   double s1 = 0.0, s2 = 0.0;
   bool bad = false;
-  const T dm = static_cast<T>(dmu);
+  const T dm = static_cast<T>(mus ? mus[0] - mus[1] : dmu);
   for (long long idx = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; idx < total;
        idx += static_cast<long long>(gridDim.x) * blockDim.x) {
     const int n = static_cast<int>(idx / nk);
@@ -938,13 +939,13 @@ cudaError_t launch_dyson_g_prep(const double2* Hk, const double2* SigHF, const v
 template <typename T>
 cudaError_t launch_dyson_g(const void* Bm, const void* dw, const double* iw, double dmu, int r,
                            int norb, int nk, void* Giw, double* part, int nblocks, int mode,
-                           int* err, cudaStream_t st) {
+                           int* err, cudaStream_t st, const double* mus) {
   auto b = reinterpret_cast<const cplx<T>*>(Bm);
   auto d = reinterpret_cast<const cplx<T>*>(dw);
   auto g = reinterpret_cast<cplx<T>*>(Giw);
   switch (norb) {
 #define QA_CASE(NO) \
-    case NO: dyson_g_kernel<T, NO><<<nblocks, 256, 0, st>>>(b, d, iw, dmu, r, nk, g, part, mode, err); break;
+    case NO: dyson_g_kernel<T, NO><<<nblocks, 256, 0, st>>>(b, d, iw, dmu, mus, r, nk, g, part, mode, err); break;
     QA_CASE(1) QA_CASE(2) QA_CASE(3) QA_CASE(4) QA_CASE(5)
 #undef QA_CASE
     default: return cudaErrorInvalidValue;
@@ -982,9 +983,9 @@ template cudaError_t launch_dyson_w<double>(const void*, const void*, void*, int
 template cudaError_t launch_dyson_w<float>(const void*, const void*, void*, int, int, int, int*,
                                            long long*, cudaStream_t, const DysonBlocks*);
 template cudaError_t launch_dyson_g<double>(const void*, const void*, const double*, double, int,
-                                            int, int, void*, double*, int, int, int*, cudaStream_t);
+                                            int, int, void*, double*, int, int, int*, cudaStream_t, const double*);
 template cudaError_t launch_dyson_g<float>(const void*, const void*, const double*, double, int, int,
-                                           int, void*, double*, int, int, int*, cudaStream_t);
+                                           int, void*, double*, int, int, int*, cudaStream_t, const double*);
 template cudaError_t launch_dyson_g_prep<double>(const double2*, const double2*, const void*, double,
                                                  int, int, int, void*, double*, int, cudaStream_t);
 template cudaError_t launch_dyson_g_prep<float>(const double2*, const double2*, const void*, double,
@@ -992,7 +993,7 @@ template cudaError_t launch_dyson_g_prep<float>(const double2*, const double2*, 
 template cudaError_t launch_dyson_w<dfl>(const void*, const void*, void*, int, int, int, int*,
                                          long long*, cudaStream_t, const DysonBlocks*);
 template cudaError_t launch_dyson_g<dfl>(const void*, const void*, const double*, double, int, int,
-                                         int, void*, double*, int, int, int*, cudaStream_t);
+                                         int, void*, double*, int, int, int*, cudaStream_t, const double*);
 template cudaError_t launch_dyson_g_prep<dfl>(const double2*, const double2*, const void*, double,
                                               int, int, int, void*, double*, int, cudaStream_t);
 

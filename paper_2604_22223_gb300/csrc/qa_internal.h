@@ -223,13 +223,34 @@ template <typename T>
 cudaError_t launch_dyson_g_prep(const double2* Hk, const double2* SigHF, const void* SigIw,
                                 double mu_ref, int r, int norb, int nk, void* Bm, double* part,
                                 int nblocks, cudaStream_t st);
-// G = (i w_n + dmu + Bm)^-1 with dmu = mu - mu_ref.  mode 0: per-block partial
-// sums of Re(dw_n Tr G) and Re(dw_n Tr G^2) into part[2*blocks]; mode 1: also
-// store G(k, i w_n) in Giw [r][norb][norb][N_k].
+// G = (i w_n + dmu + Bm)^-1 with dmu = mu - mu_ref (mus non-null: mus[0] -
+// mus[1] read on the device).  mode 0: per-block partial sums of
+// Re(dw_n Tr G) and Re(dw_n Tr G^2) into part[2*blocks]; mode 1: also store
+// G(k, i w_n) in Giw [r][norb][norb][N_k].
 template <typename T>
 cudaError_t launch_dyson_g(const void* Bm, const void* dw, const double* iw, double dmu, int r,
                            int norb, int nk, void* Giw, double* part, int nblocks, int mode,
-                           int* err, cudaStream_t st);
+                           int* err, cudaStream_t st, const double* mus = nullptr);
+
+// State of the device-side chemical-potential search (qa_mu.cu); mu and
+// mu_ref come first (the density kernel reads them).
+struct MuState {
+  double mu, mu_ref;
+  double target, tolN, wid, wlo, whi;
+  double N, dN, f, d, mu0, f0, d0;
+  double a, fa, b, fb, db, step, dir;
+  double lo, hi, dx, dxold;
+  int phase, count, status, it, m, fp64;
+};
+// Start the search at mu_s (the density table Bm folded with mu_ref = mu_s);
+// bound[0]: the bound of ||H + Sigma - mu_s|| that sets the window.
+cudaError_t launch_mu_init(MuState* s, const double* bound, double mu_s, double target, double beta,
+                           int fp64, cudaStream_t st);
+// Reduce the density sums of the last evaluation, advance the search and set
+// the while-node condition `cond` (non-zero while the search goes on).  Only
+// inside a graph with that conditional node.
+cudaError_t launch_mu_update(const double* part, int nblocks, MuState* s, double nspin, int nk,
+                             cudaGraphConditionalHandle cond, cudaStream_t st);
 int dyson_g_blocks(int r, int nk);
 // FP64-accurate density sums (mode 0) at mu with Sigma^C(k, i w) stored as
 // complex64, from FP32 arithmetic: FP32 inverse and one residual correction in
