@@ -625,9 +625,10 @@ int mu_graph(qa_ctx* c, const DevTables& tab, cudaGraphExec_t* out) {
 }
 
 // Chemical potential: the root of N(mu) = filling (N increases with mu),
-// found on the device (qa_mu.cu): one Newton step from the warm start mu_s
-// (the previous mu); otherwise a bracket by marching from the better of the
-// two points toward the root with growing steps, clamped to the window
+// found on the device (qa_mu.cu): Newton steps from the warm start mu_s (the
+// previous mu) while each at least quarters the residual; otherwise a bracket
+// by marching from the better point toward the root with growing steps,
+// clamped to the window
 // |mu - mu_s| <= max ||H + Sigma - mu_s|| + 1 + 10/beta outside which N is
 // empty or full; then bisection with Newton steps taken when they stay inside
 // the bracket and at least halve the step before last (safeguarded Newton).

@@ -240,7 +240,7 @@ struct MuState {
   double N, dN, f, d, mu0, f0, d0;
   double a, fa, b, fb, db, step, dir;
   double lo, hi, dx, dxold;
-  int phase, count, status, it, m, fp64;
+  int phase, count, status, it, m, fp64, nt;
 };
 // Start the search at mu_s (the density table Bm folded with mu_ref = mu_s);
 // bound[0]: the bound of ||H + Sigma - mu_s|| that sets the window.

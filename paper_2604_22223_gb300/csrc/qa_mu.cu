@@ -1,8 +1,9 @@
 // Chemical-potential search on the device (paper Sec. "GW self-consistency":
 // mu is fixed by the filling, N(mu) = (s/N_k) sum_k Tr n(k) = N_target).
 //
-// The search is a safeguarded Newton iteration on N(mu) - N_target: one
-// Newton trial from the warm start, a march with growing steps toward the root
+// The search is a safeguarded Newton iteration on N(mu) - N_target: Newton
+// steps from the warm start while each at least quarters the residual, then
+// (if needed) a march with growing steps toward the root
 // until N - N_target changes sign (inside the window outside which N is empty
 // or full), then bisection with Newton steps taken when they stay inside the
 // bracket and at least halve the step before last.  Its state lives in device
@@ -59,6 +60,19 @@ __device__ void safe_step(MuState* s) {
   s->phase = kPhSafe;
 }
 
+// Newton step from the point just evaluated (kept as the fallback); on the
+// FP32 path a step below the density noise ends the search after one more
+// evaluation.
+__device__ void newton_from(MuState* s, double fv, double dv) {
+  s->mu0 = s->mu;
+  s->f0 = fv;
+  s->d0 = dv;
+  s->nt += 1;
+  const double dx = fv / dv;
+  s->mu = s->mu - dx;
+  s->phase = (!s->fp64 && fabs(dx) <= tol_b(s, s->mu)) ? kPhFinal : kPhNewton;
+}
+
 // From the current point: finish, or start the march toward the root.
 __device__ void march_start(MuState* s) {
   if (!(fabs(s->f) > s->tolN)) { finish(s, 0); return; }
@@ -84,18 +98,27 @@ __device__ void mu_advance(MuState* s, double N, double dN) {
     case kPhStart:
       s->f = fv;
       s->d = dv;
+      s->nt = 0;
       if (fabs(fv) > s->tolN && dv > 0 && isfinite(fv / dv) && fabs(fv / dv) < 0.25 * s->wid) {
-        s->mu0 = s->mu;
-        s->f0 = fv;
-        s->d0 = dv;
-        s->mu = s->mu - fv / dv;
-        s->phase = kPhNewton;
+        newton_from(s, fv, dv);
         return;
       }
       march_start(s);
       return;
     case kPhNewton:
-      if (fabs(fv) <= s->tolN || fabs(fv) < fabs(s->f0)) {
+      if (fabs(fv) <= s->tolN) {
+        s->f = fv;
+        s->d = dv;
+        finish(s, 0);
+        return;
+      }
+      // converging (the residual at least quartered): another Newton step
+      if (fabs(fv) < 0.25 * fabs(s->f0) && s->nt < 6 && dv > 0 && isfinite(fv / dv) &&
+          fabs(fv / dv) < 0.25 * s->wid) {
+        newton_from(s, fv, dv);
+        return;
+      }
+      if (fabs(fv) < fabs(s->f0)) {
         s->f = fv;
         s->d = dv;
       } else {
