@@ -5,8 +5,9 @@
 //   1. A = 1 - S P and B = S P S from the FP32 high parts; Gauss-Jordan
 //      elimination of [A | B] with partial pivoting in FP32 gives X0 and
 //      leaves each lane its elimination multipliers;
-//   2. R = B - A X0 = S Z - X0 with Z = P (S + X0), in double-float (every
-//      product split exactly by an FMA, compensated sums);
+//   2. R = B - A X0 = M Y - X0 with M = S P (double-float) and Y = S + X0,
+//      the n^3 product M Y on the tensor cores from exact fixed-point bf16
+//      slices (warp-level MMA), its levels added in double-float;
 //   3. delta = A^-1 R by replaying the recorded elimination on R in FP32;
 //   4. X1 = X0 + delta as a double-float.
 // One step takes the FP32 error cond(A) u to (cond(A) u)^2.  S is block
@@ -41,13 +42,6 @@ __device__ __forceinline__ void acc_add(DfAcc& a, float p) {
   two_sum(a.s, p, a.s, t);
   a.e = __fadd_rn(a.e, t);
 }
-// a += x * y (x double-float, y FP32): the product x.hi y split exactly
-__device__ __forceinline__ void acc_fma(DfAcc& a, dfl x, float y) {
-  const float p = __fmul_rn(x.hi, y);
-  const float q = __fmaf_rn(x.hi, y, -p);
-  acc_add(a, p);
-  a.e = __fadd_rn(a.e, __fmaf_rn(x.lo, y, q));
-}
 // a += x * y (both double-float)
 __device__ __forceinline__ void acc_fma(DfAcc& a, dfl x, dfl y) {
   const float p = __fmul_rn(x.hi, y.hi);
@@ -63,12 +57,6 @@ __device__ __forceinline__ dfl acc_val(const DfAcc& a) { return df_norm(a.s, a.e
 struct CAcc {
   DfAcc re, im;
 };
-__device__ __forceinline__ void cacc_fma(CAcc& a, dfc x, float2 y) {
-  acc_fma(a.re, x.x, y.x);
-  acc_fma(a.re, -x.y, y.y);
-  acc_fma(a.im, x.x, y.y);
-  acc_fma(a.im, x.y, y.x);
-}
 __device__ __forceinline__ void cacc_fma(CAcc& a, dfc x, dfc y) {
   acc_fma(a.re, x.x, y.x);
   acc_fma(a.re, -x.y, y.y);
@@ -77,6 +65,46 @@ __device__ __forceinline__ void cacc_fma(CAcc& a, dfc x, dfc y) {
 }
 
 __device__ __forceinline__ float2 hi2(dfc v) { return make_float2(v.x.hi, v.y.hi); }
+
+// ---- fixed-point bf16 slices for the residual's tensor-core product
+constexpr int kSl = 5;                                // slices per operand (levels 0..4)
+
+// e with max < 2^e for a row (or column) maximum, clamped so that every grid
+// constant below stays a normal float
+__device__ __forceinline__ int grid_exp(float mx) {
+  const int e = static_cast<int>((__float_as_uint(mx) >> 23) & 0xffu) - 126;
+  return max(-60, min(e, 100));
+}
+// v = hi + lo cut into kSl slices: slice t is the remainder rounded to a
+// multiple of 2^(e-7-8t) (adding and subtracting 1.5 * 2^(e+16-8t) rounds to
+// that grid), an integer of at most 8 bits times the grid, so exact in bf16.
+// The remainder stays exact as the pair (r, lo): r - s is exact because s is
+// a grid multiple no coarser than r's own spacing at the scale of r.
+__device__ __forceinline__ void slice_df(dfl v, int e, float (&s)[kSl]) {
+  float r = v.hi;
+#pragma unroll
+  for (int t = 0; t < kSl; ++t) {
+    const float C = __uint_as_float((static_cast<unsigned>(e + 143 - 8 * t) << 23) | 0x400000u);
+    const float x = __fadd_rn(r, v.lo);
+    const float c = __fsub_rn(__fadd_rn(x, C), C);
+    s[t] = c;
+    r = __fsub_rn(r, c);
+  }
+}
+// two values of at most 8 significant bits as bf16x2 (exact): lo in the low half
+__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
+  unsigned d;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+  return d;
+}
+// c += a b on a 16x8x16 tile (a row-major 16x16, b column-major 16x8), FP32 accumulation
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
 
 // NFIX > 0: system size fixed at compile time.  BW: bound of the block width of S.
 template <int NFIX, int BW>
@@ -211,55 +239,162 @@ __global__ void __launch_bounds__(kDfWarps * 32, 3) dyson_w_df_kernel(
   }
   __syncwarp();
 
-  // ---- 2. residual R = S Z - X0, Z = P (S + X0), in double-float.  Row l of Z
-  // overwrites row l of P in place, so it is computed whole (columns four at a
-  // time) before any of it is stored; the loops over j stay rolled (the
-  // instruction cache holds them) and read row l of P from shared memory.
+  // ---- 2. residual R = B - A X0 = M Y - X0 with M = S P and Y = S + X0, on the
+  // tensor cores.  M and Y are formed in double-float straight into the
+  // register layout of the warp-level MMA (m16n8k16: bf16 operands, FP32
+  // accumulation) and cut into kSl bf16 slices on a fixed-point grid per row of
+  // M and per column of Y (slice t of a row with |M| < 2^e is a multiple of
+  // 2^(e-7-8t) with at most 8 significant bits; Ozaki, Ogita, Oishi & Rump 2012).
+  // Each slice product is exact and every level sum (slice indices t + u = L)
+  // stays below 2^22 units of its grid, so the tensor core's FP32
+  // accumulation of a level is exact; the levels are added in double-float.
+  // The warp's two systems go through this one after the other on all 32
+  // lanes; R lands in the system's P tile (P is not needed after M).
+  __syncwarp();
   {
-    dfc zrow[M];
-    for (int k0 = 0; k0 < n; k0 += 4) {
-      CAcc z[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) z[u] = CAcc{{0.f, 0.f}, {0.f, 0.f}};
+    const int g = lane >> 2, t4 = lane & 3;
+    const int wsys = (tid >> 5) * 2;
 #pragma unroll 1
-      for (int j = 0; j < n; ++j) {
-        const dfc pj = Pw[l * kPS + j];
-        const int lo_j = blo(j), hi_j = bhi(j);
+    for (int h = 0; h < 2; ++h) {
+      const int ss = wsys + h;
+      const dfc* Ps = Pt + ss * M * kPS;
+      const dfc* Ss = Sc + ss * M * BW;
+      const float2* Xs = X0 + ss * M * kPS;
+      float2* Rt = reinterpret_cast<float2*>(Pt + ss * M * kPS);
+      // A operand: M at rows g, g + 8 and columns 2 t4 + {0, 1}, 2 t4 + {8, 9}
+      unsigned ar[kSl][4], ai[kSl][4];
+      {
+        dfc me[2][4];
+        float mx[2] = {0.f, 0.f};
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int k = k0 + u;
-          if (k < n) {
-            cacc_fma(z[u], pj, Xw[j * kPS + k]);
-            // P[l][j] S[j][k]: S[j][k] != 0 only when k lies in j's block
-            if (k >= lo_j && k < hi_j) cacc_fma(z[u], pj, Sw[j * BW + (k - lo_j)]);
+        for (int rh = 0; rh < 2; ++rh) {
+          const int row = g + 8 * rh;
+          const int lo_r = row < n ? blo(row) : 0, hi_r = row < n ? bhi(row) : 0;
+#pragma unroll
+          for (int ci = 0; ci < 4; ++ci) {
+            const int col = 2 * t4 + (ci & 1) + 8 * (ci >> 1);
+            CAcc z = CAcc{{0.f, 0.f}, {0.f, 0.f}};
+            if (col < n)
+              for (int m = lo_r; m < hi_r; ++m) cacc_fma(z, Ss[row * BW + (m - lo_r)], Ps[m * kPS + col]);
+            me[rh][ci] = dfc{acc_val(z.re), acc_val(z.im)};
+            mx[rh] = fmaxf(mx[rh], fmaxf(fabsf(me[rh][ci].x.hi), fabsf(me[rh][ci].y.hi)));
           }
         }
+        int er[2];
+#pragma unroll
+        for (int rh = 0; rh < 2; ++rh) {
+          mx[rh] = fmaxf(mx[rh], __shfl_xor_sync(0xffffffffu, mx[rh], 1));
+          mx[rh] = fmaxf(mx[rh], __shfl_xor_sync(0xffffffffu, mx[rh], 2));
+          er[rh] = grid_exp(mx[rh]);
+        }
+#pragma unroll
+        for (int qr = 0; qr < 4; ++qr) {
+          const int rh = qr & 1, c0 = (qr >> 1) * 2;
+          float s0[kSl], s1[kSl];
+          slice_df(me[rh][c0].x, er[rh], s0);
+          slice_df(me[rh][c0 + 1].x, er[rh], s1);
+#pragma unroll
+          for (int t = 0; t < kSl; ++t) ar[t][qr] = pack_bf16(s0[t], s1[t]);
+          slice_df(me[rh][c0].y, er[rh], s0);
+          slice_df(me[rh][c0 + 1].y, er[rh], s1);
+#pragma unroll
+          for (int t = 0; t < kSl; ++t) ai[t][qr] = pack_bf16(s0[t], s1[t]);
+        }
       }
+      __syncwarp();                       // every lane has read P: R may overwrite it
+#pragma unroll 1
+      for (int nt = 0; nt < 2; ++nt) {
+        // B operand: Y at rows 2 t4 + {0, 1}, 2 t4 + {8, 9} and column g + 8 nt
+        const int col = g + 8 * nt;
+        unsigned br[kSl][2], bi[kSl][2];
+        {
+          dfc ye[4];
+          float my = 0.f;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+          for (int ri = 0; ri < 4; ++ri) {
+            const int j = 2 * t4 + (ri & 1) + 8 * (ri >> 1);
+            dfc y = dfc{dfl(0.f, 0.f), dfl(0.f, 0.f)};
+            if (j < n && col < n) {
+              const float2 x0 = Xs[j * kPS + col];
+              const int lo_j = blo(j), hi_j = bhi(j);
+              dfc sv = dfc{dfl(0.f, 0.f), dfl(0.f, 0.f)};
+              if (col >= lo_j && col < hi_j) sv = Ss[j * BW + (col - lo_j)];
+              float s, e;
+              two_sum(x0.x, sv.x.hi, s, e);
+              y.x = df_norm(s, __fadd_rn(e, sv.x.lo));
+              two_sum(x0.y, sv.y.hi, s, e);
+              y.y = df_norm(s, __fadd_rn(e, sv.y.lo));
+            }
+            ye[ri] = y;
+            my = fmaxf(my, fmaxf(fabsf(y.x.hi), fabsf(y.y.hi)));
+          }
+          my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, 1));
+          my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, 2));
+          const int ey = grid_exp(my);
 #pragma unroll
-        for (int kk = 0; kk < M; kk += 4)
-          if (kk == k0) zrow[kk + u] = dfc{acc_val(z[u].re), acc_val(z[u].im)};
+          for (int qr = 0; qr < 2; ++qr) {
+            float s0[kSl], s1[kSl];
+            slice_df(ye[2 * qr].x, ey, s0);
+            slice_df(ye[2 * qr + 1].x, ey, s1);
+#pragma unroll
+            for (int t = 0; t < kSl; ++t) br[t][qr] = pack_bf16(s0[t], s1[t]);
+            slice_df(ye[2 * qr].y, ey, s0);
+            slice_df(ye[2 * qr + 1].y, ey, s1);
+#pragma unroll
+            for (int t = 0; t < kSl; ++t) bi[t][qr] = pack_bf16(s0[t], s1[t]);
+          }
+        }
+        // level sums: re = Mr Yr - Mi Yi, im = Mr Yi + Mi Yr
+        float acc[kSl][2][4];
+#pragma unroll
+        for (int L = 0; L < kSl; ++L)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[L][0][c] = acc[L][1][c] = 0.f;
+#pragma unroll
+        for (int t = 0; t < kSl; ++t) {
+          unsigned nai[4];
+#pragma unroll
+          for (int qr = 0; qr < 4; ++qr) nai[qr] = ai[t][qr] ^ 0x80008000u;
+#pragma unroll
+          for (int u = 0; u + t < kSl; ++u) {
+            mma_bf16(acc[t + u][0], ar[t], br[u][0], br[u][1]);
+            mma_bf16(acc[t + u][0], nai, bi[u][0], bi[u][1]);
+            mma_bf16(acc[t + u][1], ar[t], bi[u][0], bi[u][1]);
+            mma_bf16(acc[t + u][1], ai[t], br[u][0], br[u][1]);
+          }
+        }
+        // R = (sum of the levels) - X0 at rows g, g + 8 and columns 2 t4 + {0, 1} + 8 nt
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int row = g + 8 * (c >> 1), k = 2 * t4 + (c & 1) + 8 * nt;
+          float2 rv = make_float2(0.f, 0.f);
+          if (row < n && k < n) {
+            const float2 x0 = Xs[row * kPS + k];
+            float v[2];
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+              float s = acc[0][p][c], e = 0.f, tt;
+#pragma unroll
+              for (int L = 1; L < kSl; ++L) {
+                two_sum(s, acc[L][p][c], s, tt);
+                e = __fadd_rn(e, tt);
+              }
+              const dfl z = df_norm(s, e);
+              v[p] = __fadd_rn(__fsub_rn(z.hi, p ? x0.y : x0.x), z.lo);
+            }
+            rv = make_float2(v[0], v[1]);
+          }
+          Rt[row * kPS + k] = rv;
+        }
       }
-    }
-    __syncwarp();
-    if (row) {
-#pragma unroll
-      for (int k = 0; k < M; ++k)
-        if (k < n) Pw[l * kPS + k] = zrow[k];
     }
   }
   __syncwarp();
   float2 rres[M];
+  {
+    const float2* Rt = reinterpret_cast<const float2*>(Pw);
 #pragma unroll
-  for (int k = 0; k < M; ++k) {
-    rres[k] = make_float2(0.f, 0.f);
-    if (row && k < n) {
-      const float2 x0 = Xw[l * kPS + k];
-      CAcc z = CAcc{{-x0.x, 0.f}, {-x0.y, 0.f}};
-      for (int m = lo_l; m < hi_l; ++m) cacc_fma(z, Sw[l * BW + (m - lo_l)], Pw[m * kPS + k]);
-      rres[k] = make_float2(z.re.s + z.re.e, z.im.s + z.im.e);
-    }
+    for (int k = 0; k < M; ++k) rres[k] = (row && k < n) ? Rt[l * kPS + k] : make_float2(0.f, 0.f);
   }
   __syncwarp();
 
