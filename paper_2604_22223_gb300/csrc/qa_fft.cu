@@ -334,6 +334,199 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? (L1C >= 0 ? 3 : 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Line-per-block path for 16-byte elements (FP64 and double-float) on the
+// 32x32x8 and 16x16x8 grids.  A whole line of N_k points stays in shared
+// memory (at 32x32x8 that is one line per SM), so the block runs up to 512
+// threads and each task holds one transform of at most 8 points: an axis of
+// 16 or 32 points is split as L = A * 8 by decimation in frequency (8-point
+// transforms over elements A apart, the twiddles w_L^(n1 k2) from the plan's
+// table, then A-point transforms over adjacent elements), which leaves the
+// axis in digit order, frequency 8 k1 + k2 at position k1 + A k2; the final
+// store maps positions to frequencies.  The code is one small codelet per
+// radix instead of whole 32-point transforms in registers, and the
+// occupancy is 16 warps per SM instead of 8.
+constexpr int kLineMaxThreads = 512;
+
+__host__ __device__ constexpr int pad8(int e) { return e + (e >> 3); }
+
+template <int LL>                      // log2 of an axis length
+struct AxisSplit {
+  static constexpr int steps = LL == 0 ? 0 : (LL <= 3 ? 1 : 2);
+  static constexpr int A = LL <= 3 ? 1 : (1 << (LL - 3));
+};
+
+// frequency held at position p of an axis after its transform
+template <int LL>
+__device__ __forceinline__ int axis_freq(int p) {
+  if constexpr (LL <= 3) {
+    return p;
+  } else {
+    constexpr int A = 1 << (LL - 3);
+    return 8 * (p & (A - 1)) + (p >> (LL - 3));
+  }
+}
+
+// One step along the axis of log2 length LL and log2 stride LS.
+// STEP 0: the whole axis (LL <= 3); 1: 8-point transforms over elements A
+// apart, then the twiddles; 2: A-point transforms over adjacent elements.
+// SRC_G: read the input line in natural order; DST_G: write the output line
+// in natural order (scaled), otherwise in place in shared memory.
+template <typename T, int SIGN, int NTH, int L1, int L2, int L3, int LL, int LS, int STEP, bool SRC_G,
+          bool DST_G>
+__device__ __forceinline__ void line_step(const cplx<T>* __restrict__ src, cplx<T>* __restrict__ dst,
+                                          cplx<T>* buf, const cplx<T>* __restrict__ tw, T scale) {
+  using V = cplx<T>;
+  constexpr int NK = 1 << (L1 + L2 + L3);
+  constexpr int L = 1 << LL, S = 1 << LS;
+  constexpr int A = AxisSplit<LL>::A;
+  constexpr int LR = STEP == 0 ? LL : (STEP == 1 ? 3 : LL - 3);
+  constexpr int R = 1 << LR;
+  constexpr int NT = NK / R;
+  for (int task = threadIdx.x; task < NT; task += NTH) {
+    const int o_lo = task & (S - 1);
+    const int rest = task >> LS;
+    int base, n1 = 0;
+    if constexpr (STEP == 0) {
+      base = (rest << (LL + LS)) + o_lo;
+    } else if constexpr (STEP == 1) {
+      n1 = rest & (A - 1);
+      base = ((rest >> (LL - 3)) << (LL + LS)) + (n1 << LS) + o_lo;
+    } else {
+      base = ((rest >> 3) << (LL + LS)) + ((A * (rest & 7)) << LS) + o_lo;
+    }
+    constexpr int st = STEP == 1 ? A * S : S;
+    V x[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int e = base + j * st;
+      x[brev_bits(j, LR)] = SRC_G ? src[e] : buf[pad8(e)];
+    }
+    fft_regs<V, R, SIGN>(x);
+    if constexpr (STEP == 1) {
+#pragma unroll
+      for (int j = 1; j < R; ++j) x[j] = cmul(x[j], tw_get(tw, (n1 * j) & (L - 1), SIGN));
+    }
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int e = base + j * st;
+      if constexpr (DST_G) {
+        const int p3 = e & ((1 << L3) - 1), p2 = (e >> L3) & ((1 << L2) - 1), p1 = e >> (L2 + L3);
+        const int f = (axis_freq<L1>(p1) << (L2 + L3)) + (axis_freq<L2>(p2) << L3) + axis_freq<L3>(p3);
+        dst[f] = cscale(x[j], scale);
+      } else {
+        buf[pad8(e)] = x[j];
+      }
+    }
+  }
+}
+
+template <typename T, int SIGN, int NTH, int L1, int L2, int L3, int LL, int LS, bool SRC_G, bool DST_G>
+__device__ __forceinline__ void line_axis(const cplx<T>* src, cplx<T>* dst, cplx<T>* buf,
+                                          const cplx<T>* tw, T scale) {
+  if constexpr (AxisSplit<LL>::steps == 1) {
+    line_step<T, SIGN, NTH, L1, L2, L3, LL, LS, 0, SRC_G, DST_G>(src, dst, buf, tw, scale);
+  } else if constexpr (AxisSplit<LL>::steps == 2) {
+    line_step<T, SIGN, NTH, L1, L2, L3, LL, LS, 1, SRC_G, false>(src, dst, buf, tw, scale);
+    __syncthreads();
+    line_step<T, SIGN, NTH, L1, L2, L3, LL, LS, 2, false, DST_G>(src, dst, buf, tw, scale);
+  }
+}
+
+template <typename T, bool BUB, int SIGN, int L1, int L2, int L3>
+__global__ void __launch_bounds__(((1 << (L1 + L2 + L3)) / 8 < kLineMaxThreads ? (1 << (L1 + L2 + L3)) / 8
+                                                                                 : kLineMaxThreads),
+                                  1)
+    fft3d_line_kernel(FftDev p, const cplx<T>* in, cplx<T>* out, T scale, BubbleSrc bs) {
+  using V = cplx<T>;
+  constexpr int NK = 1 << (L1 + L2 + L3);
+  constexpr int NTH = NK / 8 < kLineMaxThreads ? NK / 8 : kLineMaxThreads;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* tc = reinterpret_cast<V*>(smem_raw);                 // [bs.mt] term coefficients (BUB)
+  int* ti = reinterpret_cast<int*>(tc + (BUB ? bs.mt : 0));
+  V* buf = reinterpret_cast<V*>(ti + (BUB ? bs.mt : 0));
+  const int tid = threadIdx.x;
+  const long long gl = blockIdx.x;
+  const V* twg = reinterpret_cast<const V*>(p.tw);
+  if (BUB) {
+    const V* GR = reinterpret_cast<const V*>(bs.GR);
+    const V* GL = reinterpret_cast<const V*>(bs.GL);
+    const V* cf = reinterpret_cast<const V*>(bs.coef);
+    const int tau = static_cast<int>(gl / bs.nout), o = static_cast<int>(gl - static_cast<long long>(tau) * bs.nout);
+    const int e0 = bs.terms[o], nt = bs.terms[o + 1] - e0;
+    for (int e = tid; e < nt; e += NTH) {
+      tc[e] = cf[e0 + e];
+      ti[e] = bs.terms[bs.nout + 1 + e0 + e];
+    }
+    __syncthreads();
+    const V* gt = GR + static_cast<size_t>(tau) * bs.no2 * NK;
+    const V* lt = GL + static_cast<size_t>(tau) * bs.no2 * NK;
+    // four points per thread at a time: eight loads in flight per term
+    for (int eb = tid; eb < NK; eb += 4 * NTH) {
+      int mr[4];
+      V acc[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = eb + u * NTH;
+        mr[u] = e < NK ? bs.mR[e] : 0;
+        acc[u] = cmk<V>(0, 0);
+      }
+      for (int v = 0; v < nt; ++v) {
+        const int id = ti[v];
+        const V c = tc[v];
+        const V* g1 = gt + static_cast<size_t>(id & 255) * NK;
+        const V* g2 = lt + static_cast<size_t>(id >> 8) * NK;
+        V xv[4], yv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int e = eb + u * NTH;
+          xv[u] = e < NK ? g1[e] : cmk<V>(0, 0);
+          yv[u] = e < NK ? g2[mr[u]] : cmk<V>(0, 0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] = cfma(c, cmul(xv[u], yv[u]), acc[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = eb + u * NTH;
+        if (e < NK) buf[pad8(e)] = acc[u];
+      }
+    }
+    __syncthreads();
+  }
+  const V* src = in + gl * NK;
+  V* dst = out + gl * NK;
+  constexpr bool h3 = L3 > 0, h2 = L2 > 0, h1 = L1 > 0;
+  if constexpr (h3) {
+    line_axis<T, SIGN, NTH, L1, L2, L3, L3, 0, !BUB, !h2 && !h1>(src, dst, buf, twg + p.tw_off[2], scale);
+    if constexpr (h2 || h1) __syncthreads();
+  }
+  if constexpr (h2) {
+    line_axis<T, SIGN, NTH, L1, L2, L3, L2, L3, !BUB && !h3, !h1>(src, dst, buf, twg + p.tw_off[1], scale);
+    if constexpr (h1) __syncthreads();
+  }
+  if constexpr (h1) {
+    line_axis<T, SIGN, NTH, L1, L2, L3, L1, L2 + L3, !BUB && !h3 && !h2, true>(src, dst, buf,
+                                                                              twg + p.tw_off[0], scale);
+  }
+}
+
+template <typename T, bool BUB, int L1, int L2, int L3>
+cudaError_t launch_fft3d_line(const FftDev& plan, int sign, const void* in, void* out, long long nlines,
+                              cudaStream_t st, T sc, const BubbleSrc& bs) {
+  constexpr int NK = 1 << (L1 + L2 + L3);
+  constexpr int NTH = NK / 8 < kLineMaxThreads ? NK / 8 : kLineMaxThreads;
+  const size_t extra = BUB ? static_cast<size_t>(bs.mt) * (sizeof(cplx<T>) + sizeof(int)) : 0;
+  const size_t smem = static_cast<size_t>(pad8(NK)) * sizeof(cplx<T>) + extra;
+  auto fn = sign > 0 ? &fft3d_line_kernel<T, BUB, 1, L1, L2, L3> : &fft3d_line_kernel<T, BUB, -1, L1, L2, L3>;
+  cudaError_t e = set_smem(reinterpret_cast<const void*>(fn), smem, true);
+  if (e != cudaSuccess) return e;
+  if (nlines > 0x7fffffffLL) return cudaErrorInvalidValue;
+  fn<<<static_cast<unsigned>(nlines), NTH, smem, st>>>(plan, reinterpret_cast<const cplx<T>*>(in),
+                                                       reinterpret_cast<cplx<T>*>(out), sc, bs);
+  return cudaGetLastError();
+}
+
 bool reg_axis_ok(int L, int maxL) {
   return L >= 1 && L <= maxL && (L & (L - 1)) == 0;
 }
@@ -359,6 +552,11 @@ cudaError_t launch_fft3d_reg(const FftDev& plan, int sign, const void* in, void*
   const size_t smem = static_cast<size_t>(lpb) * line_sz * sizeof(cplx<T>) + extra;
   const int vec = BUB ? 0 : aligned16(in);
   const int l1 = ilog2(plan.n[0]), l2 = ilog2(plan.n[1]), l3 = ilog2(plan.n[2]);
+  if constexpr (sizeof(cplx<T>) == 16) {
+    // one line per block (16-byte elements)
+    if (l1 == 5 && l2 == 5 && l3 == 3) return launch_fft3d_line<T, BUB, 5, 5, 3>(plan, sign, in, out, nlines, st, sc, bs);
+    if (l1 == 4 && l2 == 4 && l3 == 3) return launch_fft3d_line<T, BUB, 4, 4, 3>(plan, sign, in, out, nlines, st, sc, bs);
+  }
   auto fn = sign > 0 ? &fft3d_reg_kernel<T, BUB, 1, -1, -1, -1> : &fft3d_reg_kernel<T, BUB, -1, -1, -1, -1>;
   if (l1 == 5 && l2 == 5 && l3 == 3)          // 32 x 32 x 8
     fn = sign > 0 ? &fft3d_reg_kernel<T, BUB, 1, 5, 5, 3> : &fft3d_reg_kernel<T, BUB, -1, 5, 5, 3>;
