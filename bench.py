@@ -189,9 +189,15 @@ def stage_costs(ctx, prec):
     if prec == "mixed":
         # Dyson-W: FP32 formation (S P, S P S over the blocks of S), Gauss-Jordan on
         # [A | B] and the replay on R (FP32 complex multiply-adds, 4 instructions);
-        # the residual Z = P (S + X0) and R = S Z in double-float
+        # the residual R = M Y - X0: M = S P in double-float (48 per complex
+        # multiply-add over the non-zeros of S), Y = S + X0, five bf16 slices of
+        # both (4 instructions per slice and real value, one pack per two) and the
+        # double-float sum of the five level results (4 TwoSums and a renormalisation
+        # per real output, 30); the slice products themselves run on the tensor
+        # cores (15 slice pairs x 4 real 16x16x16 products per system, not counted here)
         f32c = 2 * n * sb + sum((n - 1) * ((n - 1 - c) + n) for c in range(n)) + n * (n - 1) * n
-        dyson = (r * nk * (4 * f32c + 40 * n ** 3 + 48 * 2 * n * sb), "df")
+        dyson = (r * nk * (4 * f32c + 48 * n * sb + 2 * (2 * n * n) * (5 * 4 + 3) + 2 * n * n * 30
+                           + 10 * n * n), "df")
         kp = (2 * r + 15) // 16 * 16
         dlr = (15 * 2 * (nb * nb * nk) * kp * kp, "tensor")      # 15 slice products, M x N x K
         fft = (60 * X * lg, "df")                                # ~60 per point and radix-2 stage
@@ -615,7 +621,29 @@ def run_ours(args):
     del ctx, Gd_in, Gd_out, Gh_out
     torch.cuda.empty_cache()
 
-    def other(prec, pairs, K):
+    def adjoint_timing(c):
+        """One qa_gw_backward at the forward's mu (after one untimed call): the
+        adjoint of a step from G0 with a seeded random cotangent of the new G."""
+        G0 = c.get(qa.QA_G0).clone()
+        _, mu_f, _, _ = c.step(G0, c.new_g())
+        gen = torch.Generator(device=dev).manual_seed(2604222230)
+        Gbar = torch.randn(c.g_shape + (2,), dtype=torch.float64, device=dev, generator=gen)
+        Gbar = torch.view_as_complex(Gbar)
+        c.backward(G0, mu_f, Gbar_out=Gbar)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        c.backward(G0, mu_f, Gbar_out=Gbar)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = max_over_ranks(pg, e0.elapsed_time(e1), dev)
+        return {"ms": ms, "what": "qa_gw_backward (FP64, full pair basis, mu frozen at the forward's "
+                                  "value, LU factors of 1 - VP kept by its forward recompute): cotangent "
+                                  "of the new G in; G_in, t(R) and V(R) cotangents out",
+                "forward_plus_adjoint_ms": None}
+
+    def other(prec, pairs, K, adjoint=False):
         c = qa.Context(model, prec, device=str(dev), pairs=pairs)
         ms, stg, _, _, _ = timed(c, K, 1)
         ms = max_over_ranks(pg, ms, dev)
@@ -623,6 +651,9 @@ def run_ours(args):
                "pair_basis": "reduced rho=%d" % c.rho if c.reduced else "full npair=%d" % c.npair,
                "stage_ms": stg, "roofline": roofline(c, prec, stg, pk),
                "iteration_hbm_frac": iteration_bytes(c, prec) / (ms / K * 1e-3) / 1e9 / pk["hbm_gbs"]}
+        if adjoint:
+            out["adjoint"] = adjoint_timing(c)
+            out["adjoint"]["forward_plus_adjoint_ms"] = out["ms_per_step"] + out["adjoint"]["ms"]
         del c
         torch.cuda.empty_cache()
         return out
@@ -637,7 +668,7 @@ def run_ours(args):
     table1 = paper_table1(qa, wl, dev, pg, world, timed)
     fp32 = other("fp32", "auto", args.other_steps)
     full_mixed = other("mixed", "full", 2)
-    fp64 = other("fp64", "full", args.fp64_steps)
+    fp64 = other("fp64", "full", args.fp64_steps, adjoint=not args.no_adjoint)
     fp64_red = other("fp64", "reduced", args.fp64_steps)
     acc = accuracy_check(qa, wl, dev)
     if rank != 0:
@@ -751,6 +782,7 @@ def main():
     ap.add_argument("--other-steps", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -223,8 +223,9 @@ int qa_set_params(qa_ctx* ctx, const qa_hoppings* hop, const qa_interaction* int
  * The forward stages are recomputed from G_in (nothing is kept from an earlier
  * step), so an unrolled loop checkpoints only its G's and mu's.  Adjoints:
  * FFT -> inverse FFT, DLR map -> conjugate transpose, Dyson -> -G^H Gbar G^H,
- * W Dyson -> Pbar = W^H Wbar W^H, Vbar = (1-VP)^-H Wbar (1+PW)^H - Wbar, reusing
- * one LU per (q, i nu).  Needs the full pair basis (QA_ESTATE otherwise).
+ * W Dyson -> Pbar = W^H Wbar W^H, Vbar = (1-VP)^-H Wbar (1+PW)^H - Wbar, with the
+ * LU factors of 1 - VP that the recomputed forward W Dyson solve keeps (one per
+ * (q, i nu), in the workspace).  Needs the full pair basis (QA_ESTATE otherwise).
  * Synchronises `stream`. */
 int qa_gw_backward(qa_ctx* ctx, const void* G_in, double mu, const void* Gbar_out,
                    const void* Sigbar, const double* nbar, void* Gbar_in, double* grad_t,

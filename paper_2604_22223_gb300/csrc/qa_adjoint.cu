@@ -9,7 +9,8 @@
 //   Sigma^C_ad = -sum_bc G_bc W^C_(ab),(cd)                      (GW self-energy)
 //       Gbar_bc = -sum_ad conj(W^C_(ab),(cd)) Sigmabar_ad;  W^C bar = -Sigmabar_ad conj(G_bc)
 //   W = (1 - V P)^-1 V, W^C = W - V                             (screened interaction)
-//       Pbar = W^H Wbar W^H;  Vbar = (1 - VP)^-H Wbar (1 + P W)^H - Wbar
+//       Pbar = W^H Wbar W^H;  Vbar = (1 - VP)^-H Wbar (1 + P W)^H - Wbar,
+//       with the LU factors of 1 - VP kept by the forward recompute
 //   P_(ab),(cd) = -s G_bc(R) G_da(-R, beta - tau)                (polarizability)
 //       Gbar_bc(R) = -s sum_ad conj(G_da(-R)) Pbar;  Gbar_da(-R) = -s sum_bc conj(G_bc(R)) Pbar
 // The mu of the forward step is held fixed.
@@ -306,7 +307,9 @@ __device__ void wsolve_h(const double2* LU, const int* perm, double2* B, int n, 
 __global__ void __launch_bounds__(kWarpsB * 32) dyson_w_bwd_kernel(const double2* __restrict__ P,
                                                                   const double2* __restrict__ Vq,
                                                                   double2* Wb, double* Vqbar,
-                                                                  int n, int nk, int* err) {
+                                                                  int n, int nk, int* err,
+                                                                  const double2* __restrict__ lu,
+                                                                  const unsigned char* __restrict__ piv) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int q = blockIdx.x * kWarpsB + w;
@@ -330,14 +333,25 @@ __global__ void __launch_bounds__(kWarpsB * 32) dyson_w_bwd_kernel(const double2
     S2[i * ld + j] = Wb[base + static_cast<size_t>(e) * nk];
   }
   __syncwarp();
-  wmm<false, false>(S1, S0, S3, n, ld, lane);           // S3 = V P
-  for (int e = lane; e < n * n; e += 32) {
-    int i = e / n, j = e - i * n;
-    double2 v = S3[i * ld + j];
-    S3[i * ld + j] = make_double2((i == j ? 1.0 : 0.0) - v.x, -v.y);   // A = 1 - V P
+  bool singular = false;
+  if (lu) {
+    // the forward step's factors of A = 1 - V P (its singular pivots were reported there)
+    for (int e = lane; e < n * n; e += 32) {
+      int i = e / n, j = e - i * n;
+      S3[i * ld + j] = lu[base + static_cast<size_t>(e) * nk];
+    }
+    for (int c = lane; c < n; c += 32) perm[c] = piv[(static_cast<size_t>(nu) * n + c) * nk + q];
+    __syncwarp();
+  } else {
+    wmm<false, false>(S1, S0, S3, n, ld, lane);           // S3 = V P
+    for (int e = lane; e < n * n; e += 32) {
+      int i = e / n, j = e - i * n;
+      double2 v = S3[i * ld + j];
+      S3[i * ld + j] = make_double2((i == j ? 1.0 : 0.0) - v.x, -v.y);   // A = 1 - V P
+    }
+    __syncwarp();
+    singular = wlu(S3, perm, n, ld, lane);
   }
-  __syncwarp();
-  bool singular = wlu(S3, perm, n, ld, lane);
   for (int e = lane; e < n * n; e += 32) {
     int i = e / n, j = e - i * n;
     S4[i * ld + j] = S1[i * ld + j];
@@ -495,14 +509,16 @@ cudaError_t launch_bubble_bwd(const double2* GR, const double2* GL, const int* m
 }
 
 cudaError_t launch_dyson_w_bwd(const double2* P, const double2* Vq, double2* Wb, double* Vqbar,
-                               int r, int npair, int nk, int* err, cudaStream_t st) {
+                               int r, int npair, int nk, int* err, cudaStream_t st,
+                               const double2* lu, const unsigned char* piv) {
+  if (lu && !piv) return cudaErrorInvalidValue;
   if (npair > kMaxN) return cudaErrorInvalidValue;
   const size_t smem = static_cast<size_t>(kWarpsB) * 5 * npair * (npair + 1) * sizeof(double2) +
                       kWarpsB * kMaxN * sizeof(int);
   cudaError_t e = set_smem(reinterpret_cast<const void*>(&dyson_w_bwd_kernel), smem);
   if (e != cudaSuccess) return e;
   dim3 grid((nk + kWarpsB - 1) / kWarpsB, r);
-  dyson_w_bwd_kernel<<<grid, kWarpsB * 32, smem, st>>>(P, Vq, Wb, Vqbar, npair, nk, err);
+  dyson_w_bwd_kernel<<<grid, kWarpsB * 32, smem, st>>>(P, Vq, Wb, Vqbar, npair, nk, err, lu, piv);
   return cudaGetLastError();
 }
 

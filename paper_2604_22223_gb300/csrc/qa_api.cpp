@@ -126,6 +126,9 @@ struct qa_ctx {
   double2* d_tbar = nullptr;
   double2* d_Vbar = nullptr;
   double2* d_nbar = nullptr;
+  void* d_lu = nullptr;           // LU factors of 1 - V P (full-basis FP64 contexts)
+  unsigned char* d_piv = nullptr; // their pivot rows [r][npair][N_k]
+  bool keep_lu = false;           // the next FP64 forward keeps them (set by the adjoint)
   int nH_user = 0;
   // tensor-core DLR operands (QA_FP32 contexts)
   bool use_tc = false;
@@ -443,6 +446,10 @@ size_t layout(qa_ctx* c, char* base) {
     c->d_tbar = static_cast<double2*>(take(std::max(1, c->nH) * no2 * 16));
     c->d_Vbar = static_cast<double2*>(take(std::max(1, c->nV) * np2 * 16));
     c->d_nbar = static_cast<double2*>(take(no2 * 16));
+    if (!c->reduced) {
+      c->d_lu = take(r * np2 * nk * 16);
+      c->d_piv = static_cast<unsigned char*>(take(r * c->npair * nk));
+    }
   }
   return off;
 }
@@ -847,8 +854,9 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
     else
       QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Ttn, r, r, c->d_P, c->d_P, ncb, st));
     tm.mark();  // 4: DLR tau -> nu
+    const bool keep = is_f64<T>() && c->keep_lu && c->d_lu;
     QA_LAUNCH(c, 1, qa::launch_dyson_w<T>(c->d_P, c->d_Vq, c->d_W, r, c->nb, nk, c->d_err, c->d_bad, st,
-                                          &c->dblk));
+                                          &c->dblk, keep ? c->d_lu : nullptr, keep ? c->d_piv : nullptr));
     tm.mark();  // 5: Dyson W
     if (f32 && c->use_tc)
       QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Tnt, r, c->d_W, c->d_W, ncb, c->d_err, st, false, c->wait_limit));
@@ -1153,7 +1161,10 @@ int gw_backward_impl(qa_ctx* c, const double2* Gin, double mu, const double2* Gb
   c->timing = false;
   StageTimer tm(c, st);
   c->timing = timing;
-  if (int rc = forward_sigma<double>(c, Gin, tm, st)) return rc;
+  c->keep_lu = true;
+  const int frc = forward_sigma<double>(c, Gin, tm, st);
+  c->keep_lu = false;
+  if (frc) return frc;
   // grand-potential cotangent (wbar != 0): its explicit terms first
   OmScratch om{};
   if (wbar != 0.0) {
@@ -1194,7 +1205,8 @@ int gw_backward_impl(qa_ctx* c, const double2* Gin, double mu, const double2* Gb
   QA_TRY(cudaMemsetAsync(c->d_Vqbar, 0, static_cast<size_t>(ncb) * 16, st));
   QA_LAUNCH(c, 1, qa::launch_dyson_w_bwd(static_cast<const double2*>(c->d_P),
                                          static_cast<const double2*>(c->d_Vq), Wbig, c->d_Vqbar, r,
-                                         c->npair, nk, c->d_err, st));
+                                         c->npair, nk, c->d_err, st,
+                                         static_cast<const double2*>(c->d_lu), c->d_piv));
   if (wbar != 0.0)
     if (int rc = omega_bwd_w(c, wbar, Wbig, st)) return rc;
   // P(q, i nu) <- P(q, tau) <- P(R, tau)
@@ -1900,7 +1912,10 @@ int qa_free_energy(qa_ctx* c, const void* G_in, double mu, int M, double* omega,
   c->timing = false;
   StageTimer tm(c, st);
   c->timing = timing;
-  if (int rc = forward_sigma<double>(c, Gin, tm, st)) return rc;
+  c->keep_lu = true;
+  const int frc = forward_sigma<double>(c, Gin, tm, st);
+  c->keep_lu = false;
+  if (frc) return frc;
   double p[4];
   if (int rc = omega_value(c, Gin, mu, p, st)) return rc;
   if (int herr = check_err(c, nullptr, st)) return herr;

@@ -38,7 +38,8 @@ template <typename T, bool VPV>
 __global__ void __launch_bounds__(kWarpsW * 32) dyson_w_kernel(const cplx<T>* __restrict__ P,
                                                                const cplx<T>* __restrict__ Vq,
                                                                cplx<T>* WC, int n, int nk,
-                                                               int* err, long long* first_bad) {
+                                                               int* err, long long* first_bad,
+                                                               cplx<T>* lu, unsigned char* piv) {
   using V = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -106,8 +107,10 @@ __global__ void __launch_bounds__(kWarpsW * 32) dyson_w_kernel(const cplx<T>* __
     }
     const int p = idx;
     if (val < Tiny<T>::v || !(val == val)) singular = true;
+    if (lu && lane == 0) piv[(static_cast<size_t>(nu) * n + c) * nk + q] = static_cast<unsigned char>(p);
     if (p != c && lane < n) {
-      if (lane >= c) {
+      // whole rows when the factors are kept (columns < c then hold multipliers)
+      if (lane >= c || lu) {
         V tmp = A[c * ld + lane]; A[c * ld + lane] = A[p * ld + lane]; A[p * ld + lane] = tmp;
       }
       V tmp = Bm[c * ld + lane]; Bm[c * ld + lane] = Bm[p * ld + lane]; Bm[p * ld + lane] = tmp;
@@ -115,6 +118,7 @@ __global__ void __launch_bounds__(kWarpsW * 32) dyson_w_kernel(const cplx<T>* __
     __syncwarp();
     if (lane > c && lane < n) {
       V l = cmul(A[lane * ld + c], cinv(A[c * ld + c]));
+      if (lu) A[lane * ld + c] = l;
       for (int j = c + 1; j < n; ++j) A[lane * ld + j] = cfms(l, A[c * ld + j], A[lane * ld + j]);
       for (int j = 0; j < n; ++j) Bm[lane * ld + j] = cfms(l, Bm[c * ld + j], Bm[lane * ld + j]);
     }
@@ -134,6 +138,7 @@ __global__ void __launch_bounds__(kWarpsW * 32) dyson_w_kernel(const cplx<T>* __
     V x = Bm[i * ld + j];
     if (!VPV) x = csub(x, Vqq[e]);
     out[static_cast<size_t>(e) * nk] = x;
+    if (lu) lu[(static_cast<size_t>(nu) * nn + e) * nk + q] = A[i * ld + j];
   }
   if (singular && lane == 0) report(err, first_bad, QA_ESINGULAR_CODE, static_cast<long long>(nu) * nk + q);
 }
@@ -904,8 +909,9 @@ int dyson_g_blocks(int r, int nk) {
 template <typename T>
 cudaError_t launch_dyson_w(const void* P, const void* Vq, void* WC, int r, int npair, int nk,
                            int* err, long long* first_bad, cudaStream_t st,
-                           const DysonBlocks* blk) {
+                           const DysonBlocks* blk, void* lu, unsigned char* piv) {
   if (npair > kMaxPair) return cudaErrorInvalidValue;
+  if (lu && (sizeof(T) != 8 || !piv)) return cudaErrorInvalidValue;
   if (sizeof(T) == 4) {
     // register-row kernel: W^C = (1 - V P)^-1 V P V directly
     if (npair <= 4) return launch_dyson_w_tile<4>(P, Vq, WC, r, npair, nk, err, first_bad, st, blk);
@@ -922,7 +928,8 @@ cudaError_t launch_dyson_w(const void* P, const void* Vq, void* WC, int r, int n
   dim3 grid((nk + kWarpsW - 1) / kWarpsW, r);
   fn<<<grid, kWarpsW * 32, smem, st>>>(reinterpret_cast<const cplx<T>*>(P),
                                        reinterpret_cast<const cplx<T>*>(Vq),
-                                       reinterpret_cast<cplx<T>*>(WC), npair, nk, err, first_bad);
+                                       reinterpret_cast<cplx<T>*>(WC), npair, nk, err, first_bad,
+                                       reinterpret_cast<cplx<T>*>(lu), piv);
   return cudaGetLastError();
 }
 
@@ -979,9 +986,9 @@ cudaError_t launch_reduce_pairs(const double* part, int n, int op_max, double* o
 }
 
 template cudaError_t launch_dyson_w<double>(const void*, const void*, void*, int, int, int, int*,
-                                            long long*, cudaStream_t, const DysonBlocks*);
+                                            long long*, cudaStream_t, const DysonBlocks*, void*, unsigned char*);
 template cudaError_t launch_dyson_w<float>(const void*, const void*, void*, int, int, int, int*,
-                                           long long*, cudaStream_t, const DysonBlocks*);
+                                           long long*, cudaStream_t, const DysonBlocks*, void*, unsigned char*);
 template cudaError_t launch_dyson_g<double>(const void*, const void*, const double*, double, int,
                                             int, int, void*, double*, int, int, int*, cudaStream_t, const double*);
 template cudaError_t launch_dyson_g<float>(const void*, const void*, const double*, double, int, int,
@@ -991,7 +998,7 @@ template cudaError_t launch_dyson_g_prep<double>(const double2*, const double2*,
 template cudaError_t launch_dyson_g_prep<float>(const double2*, const double2*, const void*, double,
                                                 int, int, int, void*, double*, int, cudaStream_t);
 template cudaError_t launch_dyson_w<dfl>(const void*, const void*, void*, int, int, int, int*,
-                                         long long*, cudaStream_t, const DysonBlocks*);
+                                         long long*, cudaStream_t, const DysonBlocks*, void*, unsigned char*);
 template cudaError_t launch_dyson_g<dfl>(const void*, const void*, const double*, double, int, int,
                                          int, void*, double*, int, int, int*, cudaStream_t, const double*);
 template cudaError_t launch_dyson_g_prep<dfl>(const double2*, const double2*, const void*, double,

@@ -165,11 +165,14 @@ struct DysonBlocks {
 
 // W^C(q, i nu) from P(q, i nu) and V(q): per (nu, q) system of size npair.  blk
 // (optional, FP32 systems of size <= 16): V(q)'s block structure, used to skip
-// its zero blocks in V P and V P V.
+// its zero blocks in V P and V P V.  lu, piv (optional, FP64 only): keep the
+// LU factors of 1 - V P (row-pivoted, unit L below the diagonal; layout of P)
+// and the pivot row of each column ([r][npair][N_k] bytes) for the adjoint.
 template <typename T>
 cudaError_t launch_dyson_w(const void* P, const void* Vq, void* WC, int r, int npair, int nk,
                            int* err, long long* first_bad, cudaStream_t st,
-                           const DysonBlocks* blk = nullptr);
+                           const DysonBlocks* blk = nullptr, void* lu = nullptr,
+                           unsigned char* piv = nullptr);
 
 // Accurate mixed path (qa_dyson_df.cu): W^C from double-float P and S(q), an FP32
 // Gauss-Jordan solve refined by one double-float residual step; n <= 16, out of
@@ -308,8 +311,11 @@ cudaError_t launch_sigma_bwd(const double2* GR, const double2* SigbarR, double2*
 cudaError_t launch_bubble_bwd(const double2* GR, const double2* GL, const int* mR,
                               const double2* Pbar, double2* GRbar, double2* GLbar, int r, int norb,
                               int nk, double s, cudaStream_t st);
+// lu, piv (may be NULL): the factors kept by launch_dyson_w for the same P and
+// V; without them the kernel factorises 1 - V P itself.
 cudaError_t launch_dyson_w_bwd(const double2* P, const double2* Vq, double2* Wb, double* Vqbar,
-                               int r, int npair, int nk, int* err, cudaStream_t st);
+                               int r, int npair, int nk, int* err, cudaStream_t st,
+                               const double2* lu = nullptr, const unsigned char* piv = nullptr);
 cudaError_t launch_hf_bwd(const double2* VR, const double2* nR, const double2* X, int nV, int norb,
                           double s, int nk, double2* VbarHF, double2* nbarR, cudaStream_t st);
 cudaError_t launch_nbar_k(const double2* nbarR, const int* R, int nV1, int np, int nk, int n1,
