@@ -638,9 +638,10 @@ def run_ours(args):
         e1.record()
         torch.cuda.synchronize()
         ms = max_over_ranks(pg, e0.elapsed_time(e1), dev)
-        return {"ms": ms, "what": "qa_gw_backward (FP64, full pair basis, mu frozen at the forward's "
+        return {"ms": ms, "what": "qa_gw_backward (FP64, %s pair basis, mu frozen at the forward's "
                                   "value, LU factors of 1 - VP kept by its forward recompute): cotangent "
-                                  "of the new G in; G_in, t(R) and V(R) cotangents out",
+                                  "of the new G in; G_in, t(R) and V(R) cotangents out"
+                                  % ("reduced" if c.reduced else "full"),
                 "forward_plus_adjoint_ms": None}
 
     def other(prec, pairs, K, adjoint=False):
@@ -669,7 +670,7 @@ def run_ours(args):
     fp32 = other("fp32", "auto", args.other_steps)
     full_mixed = other("mixed", "full", 2)
     fp64 = other("fp64", "full", args.fp64_steps, adjoint=not args.no_adjoint)
-    fp64_red = other("fp64", "reduced", args.fp64_steps)
+    fp64_red = other("fp64", "reduced", args.fp64_steps, adjoint=not args.no_adjoint)
     acc = accuracy_check(qa, wl, dev)
     if rank != 0:
         return

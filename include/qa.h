@@ -154,7 +154,7 @@ int qa_create(const qa_lattice* lat, const qa_hoppings* hop, const qa_interactio
  * contraction that the paper proposes for the O(N_orb^4) polarizability (Sec.
  * "Results", five-orbital benchmark).  QA_PAIRS_REDUCED takes effect when
  * 0 < rho < npair and the contraction term lists have at most 4096 entries;
- * otherwise the full basis is used.  qa_gw_backward needs the full basis. */
+ * otherwise the full basis is used.  qa_free_energy_backward needs the full basis. */
 int qa_set_pair_basis(qa_ctx* ctx, int mode);
 
 /* The interaction subspace: *rho its dimension, *active 1 when the big tensors
@@ -225,7 +225,12 @@ int qa_set_params(qa_ctx* ctx, const qa_hoppings* hop, const qa_interaction* int
  * FFT -> inverse FFT, DLR map -> conjugate transpose, Dyson -> -G^H Gbar G^H,
  * W Dyson -> Pbar = W^H Wbar W^H, Vbar = (1-VP)^-H Wbar (1+PW)^H - Wbar, with the
  * LU factors of 1 - VP that the recomputed forward W Dyson solve keeps (one per
- * (q, i nu), in the workspace).  Needs the full pair basis (QA_ESTATE otherwise).
+ * (q, i nu), in the workspace).  Either pair basis: on the reduced one the
+ * bubble and self-energy adjoints walk the forward's term lists, the Dyson
+ * adjoint runs in the rho-dimensional subspace (S = B^H V B) and grad_V is
+ * B Sbar B^H plus the Hartree-Fock part; on the subspace (Pi grad_V Pi,
+ * Pi = B B^H, the directions in which V can move without changing the
+ * subspace) it equals the full basis' gradient.
  * Synchronises `stream`. */
 int qa_gw_backward(qa_ctx* ctx, const void* G_in, double mu, const void* Gbar_out,
                    const void* Sigbar, const double* nbar, void* Gbar_in, double* grad_t,

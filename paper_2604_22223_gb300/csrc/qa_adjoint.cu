@@ -201,6 +201,96 @@ __global__ void __launch_bounds__(128) bubble_bwd_kernel(const double2* __restri
     }
 }
 
+// ------------------------------------------ reduced pair basis (term lists)
+// The reduced basis replaces the explicit (ab),(cd) sums by the host term
+// lists of the forward kernels: per reduced entry o = (i, j) the terms
+// (coefficient c, indices) with
+//   Pt_o(R)      += c G_g1(R, tau) G^refl_g2(-R, beta - tau)   (bubble, idx = g1 | g2 << 8)
+//   Sigma_t(R)   += c G_g(R, tau) Wt^C_o(R, tau)                 (self-energy, idx = g | t << 8)
+// and their adjoints  x_bar += conj(c y) z_bar  for every product z = c x y.
+// One thread per (tau_j, R); the per-thread vectors of norb^2 values sit in
+// shared memory (indexed at run time by the term lists).
+constexpr int kTermThreads = 64;
+
+__global__ void __launch_bounds__(kTermThreads) sigma_bwd_terms_kernel(
+    const double2* __restrict__ GR, const double2* __restrict__ SigbarR, double2* W, double2* GRbar,
+    const int* __restrict__ terms, const double2* __restrict__ coef, int nb2, int no2, int nk) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* sg = reinterpret_cast<double2*>(smem_raw);          // [no2][threads]
+  double2* ssb = sg + no2 * kTermThreads;
+  double2* sgb = ssb + no2 * kTermThreads;
+  const int t = blockIdx.x;
+  const int R = blockIdx.y * kTermThreads + threadIdx.x;
+  const int th = threadIdx.x;
+  const bool ok = R < nk;
+  for (int e = 0; e < no2; ++e) {
+    const size_t at = (static_cast<size_t>(t) * no2 + e) * nk + R;
+    sg[e * kTermThreads + th] = ok ? GR[at] : make_double2(0, 0);
+    ssb[e * kTermThreads + th] = ok ? SigbarR[at] : make_double2(0, 0);
+    sgb[e * kTermThreads + th] = make_double2(0, 0);
+  }
+  if (ok) {
+    const int* idx = terms + nb2 + 1;
+    double2* Wt = W + static_cast<size_t>(t) * nb2 * nk + R;
+    for (int o = 0; o < nb2; ++o) {
+      const double2 w = Wt[static_cast<size_t>(o) * nk];
+      double2 wb = make_double2(0, 0);
+      for (int e = terms[o]; e < terms[o + 1]; ++e) {
+        const int g = idx[e] & 255, tg = idx[e] >> 8;
+        const double2 c = coef[e], sb = ssb[tg * kTermThreads + th];
+        wb = cfma(cconj(cmul(c, sg[g * kTermThreads + th])), sb, wb);
+        sgb[g * kTermThreads + th] = cfma(cconj(cmul(c, w)), sb, sgb[g * kTermThreads + th]);
+      }
+      Wt[static_cast<size_t>(o) * nk] = wb;
+    }
+    for (int e = 0; e < no2; ++e)
+      GRbar[(static_cast<size_t>(t) * no2 + e) * nk + R] = sgb[e * kTermThreads + th];
+  }
+}
+
+__global__ void __launch_bounds__(kTermThreads) bubble_bwd_terms_kernel(
+    const double2* __restrict__ GR, const double2* __restrict__ GL, const int* __restrict__ mR,
+    const double2* __restrict__ Pbar, double2* GRbar, double2* GLbar, const int* __restrict__ terms,
+    const double2* __restrict__ coef, int nb2, int no2, int nk) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* sgr = reinterpret_cast<double2*>(smem_raw);         // [no2][threads]
+  double2* sgl = sgr + no2 * kTermThreads;
+  double2* sgrb = sgl + no2 * kTermThreads;
+  double2* sglb = sgrb + no2 * kTermThreads;
+  const int t = blockIdx.x;
+  const int R = blockIdx.y * kTermThreads + threadIdx.x;
+  const int th = threadIdx.x;
+  const bool ok = R < nk;
+  const int mr = ok ? mR[R] : 0;
+  for (int e = 0; e < no2; ++e) {
+    const size_t row = (static_cast<size_t>(t) * no2 + e) * nk;
+    sgr[e * kTermThreads + th] = ok ? GR[row + R] : make_double2(0, 0);
+    sgl[e * kTermThreads + th] = ok ? GL[row + mr] : make_double2(0, 0);
+    sgrb[e * kTermThreads + th] = ok ? GRbar[row + R] : make_double2(0, 0);
+    sglb[e * kTermThreads + th] = make_double2(0, 0);
+  }
+  if (ok) {
+    const int* idx = terms + nb2 + 1;
+    const double2* Pt = Pbar + static_cast<size_t>(t) * nb2 * nk + R;
+    for (int o = 0; o < nb2; ++o) {
+      const double2 pb = Pt[static_cast<size_t>(o) * nk];
+      for (int e = terms[o]; e < terms[o + 1]; ++e) {
+        const int g1 = idx[e] & 255, g2 = idx[e] >> 8;
+        const double2 c = coef[e];
+        sgrb[g1 * kTermThreads + th] =
+            cfma(cconj(cmul(c, sgl[g2 * kTermThreads + th])), pb, sgrb[g1 * kTermThreads + th]);
+        sglb[g2 * kTermThreads + th] =
+            cfma(cconj(cmul(c, sgr[g1 * kTermThreads + th])), pb, sglb[g2 * kTermThreads + th]);
+      }
+    }
+    for (int e = 0; e < no2; ++e) {
+      const size_t row = (static_cast<size_t>(t) * no2 + e) * nk;
+      GRbar[row + R] = sgrb[e * kTermThreads + th];
+      GLbar[row + mr] = sglb[e * kTermThreads + th];
+    }
+  }
+}
+
 // --------------------------------------------------------------- Dyson W
 constexpr int kWarpsB = 4;
 constexpr int kMaxN = 25;
@@ -505,6 +595,33 @@ cudaError_t launch_bubble_bwd(const double2* GR, const double2* GL, const int* m
 #undef QA_CASE
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sigma_bwd_terms(const double2* GR, const double2* SigbarR, double2* W, double2* GRbar,
+                                   const int* terms, const double2* coef, int r, int nb2, int norb, int nk,
+                                   cudaStream_t st) {
+  const int no2 = norb * norb;
+  if (no2 > 256) return cudaErrorInvalidValue;
+  const size_t smem = static_cast<size_t>(3) * no2 * kTermThreads * sizeof(double2);
+  cudaError_t e = set_smem(reinterpret_cast<const void*>(&sigma_bwd_terms_kernel), smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(r, (nk + kTermThreads - 1) / kTermThreads);
+  sigma_bwd_terms_kernel<<<grid, kTermThreads, smem, st>>>(GR, SigbarR, W, GRbar, terms, coef, nb2, no2, nk);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bubble_bwd_terms(const double2* GR, const double2* GL, const int* mR, const double2* Pbar,
+                                    double2* GRbar, double2* GLbar, const int* terms, const double2* coef,
+                                    int r, int nb2, int norb, int nk, cudaStream_t st) {
+  const int no2 = norb * norb;
+  if (no2 > 256) return cudaErrorInvalidValue;
+  const size_t smem = static_cast<size_t>(4) * no2 * kTermThreads * sizeof(double2);
+  cudaError_t e = set_smem(reinterpret_cast<const void*>(&bubble_bwd_terms_kernel), smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(r, (nk + kTermThreads - 1) / kTermThreads);
+  bubble_bwd_terms_kernel<<<grid, kTermThreads, smem, st>>>(GR, GL, mR, Pbar, GRbar, GLbar, terms, coef, nb2,
+                                                            no2, nk);
   return cudaGetLastError();
 }
 

@@ -100,6 +100,7 @@ struct qa_ctx {
   void* d_Gt = nullptr;       // G(k, tau) / n(k) scratch (sized for FP64)
   void* d_P = nullptr;
   void* d_W = nullptr;
+  float* d_colscale = nullptr;  // per-column slice grids of the tensor-core DLR maps (mixed)
   double* d_part = nullptr;
   double* d_red = nullptr;
   int* d_err = nullptr;
@@ -391,7 +392,10 @@ size_t layout(qa_ctx* c, char* base) {
   // big tensors last; P must also hold the FP64 V(q) staging of qa_bind
   c->d_P = take(std::max(r * nb2 * nk * es, nk * nb2 * 16));
   c->d_W = take(r * nb2 * nk * es);
-  if (c->precision == QA_MIXED && c->use_oz) c->d_Pnu = take(r * nb2 * nk * es);
+  if (c->precision == QA_MIXED && c->use_oz) {
+    c->d_Pnu = take(r * nb2 * nk * es);
+    c->d_colscale = static_cast<float*>(take(std::max(nb2, no2) * nk * 4));
+  }
   if (c->precision == QA_MIXED) {
     const size_t cap = term_capacity(c);
     c->d_tgo = static_cast<int*>(take((no2 + 1) * 4));
@@ -446,10 +450,8 @@ size_t layout(qa_ctx* c, char* base) {
     c->d_tbar = static_cast<double2*>(take(std::max(1, c->nH) * no2 * 16));
     c->d_Vbar = static_cast<double2*>(take(std::max(1, c->nV) * np2 * 16));
     c->d_nbar = static_cast<double2*>(take(no2 * 16));
-    if (!c->reduced) {
-      c->d_lu = take(r * np2 * nk * 16);
-      c->d_piv = static_cast<unsigned char*>(take(r * c->npair * nk));
-    }
+    c->d_lu = take(r * nb2 * nk * 16);
+    c->d_piv = static_cast<unsigned char*>(take(r * c->nb * nk));
   }
   return off;
 }
@@ -725,7 +727,7 @@ int finish_g(qa_ctx* c, const DevTables& tab, double mu, void* G_out_c128, doubl
   } else if (is_df<T>()) {
     if (c->use_oz) {
       // the transform stores complex128 directly
-      QA_LAUNCH(c, 1, qa::launch_dlr_oz(c->d_oz_Twt, c->r, c->d_Giw, G_out_c128, ncol, c->d_err, st, true, c->wait_limit));
+      QA_LAUNCH(c, 2, qa::launch_dlr_oz(c->d_oz_Twt, c->r, c->d_Giw, G_out_c128, ncol, c->d_err, st, true, c->wait_limit, c->d_colscale));
     } else {
       QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Twt, c->r, c->r, c->d_Giw, c->d_Gt, ncol, st));
       QA_LAUNCH(c, 1, qa::launch_df_to_c128(c->d_Gt, static_cast<double2*>(G_out_c128), ncol * c->r, st));
@@ -813,7 +815,7 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
   if (f32 && c->use_tc)
     QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Trefl, r, Gk, c->d_Grefl, ncs, c->d_err, st, false, c->wait_limit));
   else if (oz)
-    QA_LAUNCH(c, 1, qa::launch_dlr_oz(c->d_oz_Trefl, r, Gk, c->d_Grefl, ncs, c->d_err, st, false, c->wait_limit));
+    QA_LAUNCH(c, 2, qa::launch_dlr_oz(c->d_oz_Trefl, r, Gk, c->d_Grefl, ncs, c->d_err, st, false, c->wait_limit, c->d_colscale));
   else
     QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Trefl, r, r, Gk, c->d_Grefl, ncs, st));
   QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, +1, Gk, c->d_GR, ncs / nk * r, st));
@@ -838,7 +840,7 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
   if (oz) {
     // out-of-place tensor-core maps: P(q, tau) [P] -> P(q, i nu) [Pnu] -> W^C(q, i nu) [P]
     // -> W^C(q, tau) [W]
-    QA_LAUNCH(c, 1, qa::launch_dlr_oz(c->d_oz_Ttn, r, c->d_P, c->d_Pnu, ncb, c->d_err, st, false, c->wait_limit));
+    QA_LAUNCH(c, 2, qa::launch_dlr_oz(c->d_oz_Ttn, r, c->d_P, c->d_Pnu, ncb, c->d_err, st, false, c->wait_limit, c->d_colscale));
     tm.mark();  // 4: DLR tau -> nu
     if (qa::dyson_w_df_supported(c->nb))
       QA_LAUNCH(c, 1, qa::launch_dyson_w_df(c->d_Pnu, c->d_Vq, c->d_P, r, c->nb, nk, c->d_err, c->d_bad,
@@ -847,7 +849,7 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
       QA_LAUNCH(c, 1, qa::launch_dyson_w<T>(c->d_Pnu, c->d_Vq, c->d_P, r, c->nb, nk, c->d_err, c->d_bad,
                                             st, &c->dblk));
     tm.mark();  // 5: Dyson W
-    QA_LAUNCH(c, 1, qa::launch_dlr_oz(c->d_oz_Tnt, r, c->d_P, c->d_W, ncb, c->d_err, st, false, c->wait_limit));
+    QA_LAUNCH(c, 2, qa::launch_dlr_oz(c->d_oz_Tnt, r, c->d_P, c->d_W, ncb, c->d_err, st, false, c->wait_limit, c->d_colscale));
   } else {
     if (f32 && c->use_tc)
       QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Ttn, r, c->d_P, c->d_P, ncb, c->d_err, st, false, c->wait_limit));
@@ -883,7 +885,7 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
   if (f32 && c->use_tc)
     QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Ttw, r, c->d_SigC, c->d_SigIw, ncs, c->d_err, st, false, c->wait_limit));
   else if (oz)
-    QA_LAUNCH(c, 1, qa::launch_dlr_oz(c->d_oz_Ttw, r, c->d_SigC, c->d_SigIw, ncs, c->d_err, st, false, c->wait_limit));
+    QA_LAUNCH(c, 2, qa::launch_dlr_oz(c->d_oz_Ttw, r, c->d_SigC, c->d_SigIw, ncs, c->d_err, st, false, c->wait_limit, c->d_colscale));
   else
     QA_LAUNCH(c, 1, qa::launch_dlr_apply<T>(tab.Ttw, r, r, c->d_SigC, c->d_SigIw, ncs, st));
   tm.mark();  // 9: Sigma -> (k, i w)
@@ -1151,10 +1153,11 @@ int gw_backward_impl(qa_ctx* c, const double2* Gin, double mu, const double2* Gb
                      const double2* Sigbar, const double* nbar, double2* Gbar_in, double* grad_t,
                      double* grad_V, cudaStream_t st, double wbar = 0.0) {
   const qa::FftDev& fft = c->fft64;
-  const int r = c->r, no2 = c->norb * c->norb, nk = c->nk, np2 = c->npair * c->npair;
+  // big tensors in the context's pair basis: nb = npair (full) or rho (reduced)
+  const int r = c->r, no2 = c->norb * c->norb, nk = c->nk, np2 = c->npair * c->npair, nb2 = c->nb * c->nb;
   const long long ncs = static_cast<long long>(no2) * nk;
-  const long long ncb = static_cast<long long>(np2) * nk;
-  const long long lines_s = static_cast<long long>(no2) * r, lines_b = static_cast<long long>(np2) * r;
+  const long long ncb = static_cast<long long>(nb2) * nk;
+  const long long lines_s = static_cast<long long>(no2) * r, lines_b = static_cast<long long>(nb2) * r;
   c->launches = 0;
   if (int rc = reset_err(c, st)) return rc;
   bool timing = c->timing;
@@ -1196,8 +1199,13 @@ int gw_backward_impl(qa_ctx* c, const double2* Gin, double mu, const double2* Gb
   if (wbar != 0.0) QA_LAUNCH(c, 1, qa::launch_axpy(Sig_bar, om.sbar_tau, 1.0, ncs * r, st));
   QA_LAUNCH(c, 1, qa::launch_fft3d<double>(fft, +1, Sig_bar, Sig_bar, lines_s, st, 1.0));
   // Sigma contraction: Gbar(R) and Wbar(R, tau) (in place over W^C)
-  QA_LAUNCH(c, 1, qa::launch_sigma_bwd(static_cast<const double2*>(c->d_GR), Sig_bar, Wbig, c->d_GRbar,
-                                       r, c->norb, nk, st));
+  if (c->reduced)
+    QA_LAUNCH(c, 1, qa::launch_sigma_bwd_terms(static_cast<const double2*>(c->d_GR), Sig_bar, Wbig, c->d_GRbar,
+                                               c->d_tsig, static_cast<const double2*>(c->d_csig), r, nb2,
+                                               c->norb, nk, st));
+  else
+    QA_LAUNCH(c, 1, qa::launch_sigma_bwd(static_cast<const double2*>(c->d_GR), Sig_bar, Wbig, c->d_GRbar,
+                                         r, c->norb, nk, st));
   // W^C(R, tau) <- W^C(q, tau) <- W^C(q, i nu)
   QA_LAUNCH(c, 1, qa::launch_fft3d<double>(fft, -1, Wbig, Wbig, lines_b, st, 1.0 / nk));
   QA_LAUNCH(c, 1, qa::launch_dlr_apply<double>(c->tH.Tnt, r, r, Wbig, Wbig, ncb, st));
@@ -1205,7 +1213,7 @@ int gw_backward_impl(qa_ctx* c, const double2* Gin, double mu, const double2* Gb
   QA_TRY(cudaMemsetAsync(c->d_Vqbar, 0, static_cast<size_t>(ncb) * 16, st));
   QA_LAUNCH(c, 1, qa::launch_dyson_w_bwd(static_cast<const double2*>(c->d_P),
                                          static_cast<const double2*>(c->d_Vq), Wbig, c->d_Vqbar, r,
-                                         c->npair, nk, c->d_err, st,
+                                         c->nb, nk, c->d_err, st,
                                          static_cast<const double2*>(c->d_lu), c->d_piv));
   if (wbar != 0.0)
     if (int rc = omega_bwd_w(c, wbar, Wbig, st)) return rc;
@@ -1213,9 +1221,15 @@ int gw_backward_impl(qa_ctx* c, const double2* Gin, double mu, const double2* Gb
   QA_LAUNCH(c, 1, qa::launch_dlr_apply<double>(c->tH.Ttn, r, r, Wbig, Wbig, ncb, st));
   QA_LAUNCH(c, 1, qa::launch_fft3d<double>(fft, +1, Wbig, Wbig, lines_b, st, 1.0));
   // bubble
-  QA_LAUNCH(c, 1, qa::launch_bubble_bwd(static_cast<const double2*>(c->d_GR),
-                                        static_cast<const double2*>(c->d_Grefl), c->d_mR, Wbig,
-                                        c->d_GRbar, c->d_GLbar, r, c->norb, nk, c->nspin, st));
+  if (c->reduced)
+    QA_LAUNCH(c, 1, qa::launch_bubble_bwd_terms(static_cast<const double2*>(c->d_GR),
+                                                static_cast<const double2*>(c->d_Grefl), c->d_mR, Wbig,
+                                                c->d_GRbar, c->d_GLbar, c->d_tbub,
+                                                static_cast<const double2*>(c->d_cbub), r, nb2, c->norb, nk, st));
+  else
+    QA_LAUNCH(c, 1, qa::launch_bubble_bwd(static_cast<const double2*>(c->d_GR),
+                                          static_cast<const double2*>(c->d_Grefl), c->d_mR, Wbig,
+                                          c->d_GRbar, c->d_GLbar, r, c->norb, nk, c->nspin, st));
   // G(R) <- G(k) and G(-R, beta - tau) <- G(k, beta - tau) <- G(k, tau)
   QA_LAUNCH(c, 1, qa::launch_fft3d<double>(fft, -1, c->d_GRbar, c->d_GRbar, lines_s, st, 1.0 / nk));
   QA_LAUNCH(c, 1, qa::launch_fft3d<double>(fft, -1, c->d_GLbar, c->d_GLbar, lines_s, st, 1.0 / nk));
@@ -1238,20 +1252,51 @@ int gw_backward_impl(qa_ctx* c, const double2* Gin, double mu, const double2* Gb
                                     c->n[2], c->d_nk, st));
   if (wbar != 0.0) QA_LAUNCH(c, 1, qa::launch_axpy(c->d_nk, om.nbar_x, 1.0, ncs, st));
   QA_LAUNCH(c, 1, qa::launch_dlr_apply<double>(c->tH.dtau, r, 1, c->d_nk, gin, ncs, st, 1));
-  // V(R): sum_q e^{+iq.R} Vbar(q) plus the Hartree/Fock part
+  // V(R): sum_q e^{+iq.R} Vbar(q) plus the Hartree/Fock part.  On the reduced
+  // basis the Dyson adjoint gives the cotangent of S(q) = B^H V(q) B, so
+  // Vbar(R) = B Sbar(R) B^H (on the host: nV small matrices).
   if (c->nV > 0) {
     QA_LAUNCH(c, 1, qa::launch_density_R(reinterpret_cast<const double2*>(c->d_Vqbar), c->d_vR, c->nV,
-                                         np2, nullptr, nk, c->n[0], c->n[1], c->n[2], c->d_Vbar, st));
-    QA_LAUNCH(c, 1, qa::launch_scale(c->d_Vbar, static_cast<double>(nk), static_cast<long long>(c->nV) * np2, st));
-    QA_LAUNCH(c, 1, qa::launch_axpy(c->d_Vbar, c->d_VbarHF, 1.0, static_cast<long long>(c->nV) * np2, st));
+                                         nb2, nullptr, nk, c->n[0], c->n[1], c->n[2], c->d_Vbar, st));
+    QA_LAUNCH(c, 1, qa::launch_scale(c->d_Vbar, static_cast<double>(nk), static_cast<long long>(c->nV) * nb2, st));
+    if (!c->reduced)
+      QA_LAUNCH(c, 1, qa::launch_axpy(c->d_Vbar, c->d_VbarHF, 1.0, static_cast<long long>(c->nV) * np2, st));
   }
   if (grad_t)
     QA_TRY(cudaMemcpyAsync(grad_t, c->d_tbar, static_cast<size_t>(c->nH_user) * no2 * 16,
                            cudaMemcpyDeviceToHost, st));
-  if (grad_V && c->nV > 0)
-    QA_TRY(cudaMemcpyAsync(grad_V, c->d_Vbar, static_cast<size_t>(c->nV) * np2 * 16,
-                           cudaMemcpyDeviceToHost, st));
+  std::vector<cd> sbar, vhf;
+  if (grad_V && c->nV > 0) {
+    if (c->reduced) {
+      sbar.resize(static_cast<size_t>(c->nV) * nb2);
+      vhf.resize(static_cast<size_t>(c->nV) * np2);
+      QA_TRY(cudaMemcpyAsync(sbar.data(), c->d_Vbar, sbar.size() * 16, cudaMemcpyDeviceToHost, st));
+      QA_TRY(cudaMemcpyAsync(vhf.data(), c->d_VbarHF, vhf.size() * 16, cudaMemcpyDeviceToHost, st));
+    } else {
+      QA_TRY(cudaMemcpyAsync(grad_V, c->d_Vbar, static_cast<size_t>(c->nV) * np2 * 16,
+                             cudaMemcpyDeviceToHost, st));
+    }
+  }
   QA_TRY(cudaStreamSynchronize(st));
+  if (grad_V && c->nV > 0 && c->reduced) {
+    const int np = c->npair, rho = c->rho;
+    cd* gv = reinterpret_cast<cd*>(grad_V);
+    for (int v = 0; v < c->nV; ++v)
+      for (int A = 0; A < np; ++A)
+        for (int Bq = 0; Bq < np; ++Bq) {
+          cd acc = vhf[(static_cast<size_t>(v) * np + A) * np + Bq];
+          for (int i = 0; i < rho; ++i) {
+            const cd bai = c->basis[static_cast<size_t>(A) * rho + i];
+            if (bai == cd(0, 0)) continue;
+            for (int j = 0; j < rho; ++j) {
+              const cd bbj = c->basis[static_cast<size_t>(Bq) * rho + j];
+              if (bbj == cd(0, 0)) continue;
+              acc += bai * sbar[(static_cast<size_t>(v) * rho + i) * rho + j] * std::conj(bbj);
+            }
+          }
+          gv[(static_cast<size_t>(v) * np + A) * np + Bq] = acc;
+        }
+  }
   return check_err(c, nullptr, st);
 }
 
@@ -1891,7 +1936,6 @@ int qa_gw_backward(qa_ctx* c, const void* G_in, double mu, const void* Gbar_out,
   if (!c) return QA_EINVAL;
   if (!c->bound) return QA_ESTATE;
   if (c->precision != QA_FP64 || !std::isfinite(mu)) return QA_EINVAL;
-  if (c->reduced) return QA_ESTATE;
   const double2* Gin = static_cast<const double2*>(G_in ? G_in : c->d_G0);
   return gw_backward_impl(c, Gin, mu, static_cast<const double2*>(Gbar_out),
                           static_cast<const double2*>(Sigbar), nbar, static_cast<double2*>(Gbar_in),

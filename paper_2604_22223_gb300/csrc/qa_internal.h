@@ -130,9 +130,11 @@ struct DlrOzLayout {
 DlrOzLayout dlr_oz_layout(int r);
 bool dlr_oz_supported(int r);
 void pack_dlr_oz(const std::complex<double>* T, int r, std::vector<uint8_t>* dst);
-// out_c128: store complex128 instead of double-float.
+// out_c128: store complex128 instead of double-float.  colscale: device scratch of
+// ncol floats (the per-column slice grid, written by a streaming pass that this
+// call launches first: two kernels per call).
 cudaError_t launch_dlr_oz(const void* pack, int r, const void* in, void* out, long long ncol,
-                          int* err, cudaStream_t st, bool out_c128 = false, long long wait_limit = -1);
+                          int* err, cudaStream_t st, bool out_c128, long long wait_limit, float* colscale);
 
 // Batched 3-D FFT of contiguous lines of N_k points (in place allowed).
 // sign = -1: X(k) = sum_R e^{-ikR} X(R); sign = +1: (1/N_k) sum_k e^{+ikR} X(k).
@@ -311,6 +313,14 @@ cudaError_t launch_sigma_bwd(const double2* GR, const double2* SigbarR, double2*
 cudaError_t launch_bubble_bwd(const double2* GR, const double2* GL, const int* mR,
                               const double2* Pbar, double2* GRbar, double2* GLbar, int r, int norb,
                               int nk, double s, cudaStream_t st);
+// Reduced pair basis: adjoints of the term-list bubble and self-energy
+// (terms: off[nb2 + 1] then idx[]; coef complex128), one thread per (tau, R).
+cudaError_t launch_sigma_bwd_terms(const double2* GR, const double2* SigbarR, double2* W, double2* GRbar,
+                                   const int* terms, const double2* coef, int r, int nb2, int norb, int nk,
+                                   cudaStream_t st);
+cudaError_t launch_bubble_bwd_terms(const double2* GR, const double2* GL, const int* mR, const double2* Pbar,
+                                    double2* GRbar, double2* GLbar, const int* terms, const double2* coef,
+                                    int r, int nb2, int norb, int nk, cudaStream_t st);
 // lu, piv (may be NULL): the factors kept by launch_dyson_w for the same P and
 // V; without them the kernel factorises 1 - V P itself.
 cudaError_t launch_dyson_w_bwd(const double2* P, const double2* Vq, double2* Wb, double* Vqbar,
