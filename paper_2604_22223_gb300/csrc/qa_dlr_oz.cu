@@ -61,6 +61,7 @@ struct OzArgs {
   long long ncol;
   int* err;
   long long wait_limit;    // polls of each pipeline wait before the time-out path
+  const float* colscale;   // 2^(8 - b_c) per column (col_scale_kernel)
 };
 
 __device__ __forceinline__ uint32_t pack_hi16(float a, float b) {
@@ -190,25 +191,11 @@ __global__ void __launch_bounds__(kWorkers + 32, 1) dlr_oz_kernel(OzArgs a) {
     long long g = 0, tl = 0;
     bool ok = true;
     for (long long tile = cp; tile < ntiles && ok; tile += cpp, ++tl) {
-      // column exponents: 2^(b_c) >= 2 max |x| over the column's 2r values
+      // column scales 2^(8 - b_c), 2^(b_c) >= 2 max |x| over the column's 2r values
+      // (computed by col_scale_kernel in one streaming pass before this launch)
       {
         const long long pcol = tile * kTileM + pm;
-        float mx = 0.0f;
-        if (pcol < a.ncol) {
-#pragma unroll 4
-          for (int l = pq; l < a.r; l += 4) {
-            const float4 v = __ldg(reinterpret_cast<const float4*>(a.in + static_cast<long long>(l) * a.ncol + pcol));
-            mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.z)));
-          }
-        }
-        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-        mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
-        if (pq == 0) {
-          int e = 0;
-          if (mx > 0.0f) frexpf(mx * 2.000004f, &e);          // 2^e > 2 max (1 + 2^-19)
-          e = max(e, -100);                                    // keeps 2^(8 - e) a finite float
-          s_b[(tl & 1) * kTileM + pm] = ldexpf(1.0f, 8 - e);
-        }
+        if (pq == 0) s_b[(tl & 1) * kTileM + pm] = pcol < a.ncol ? __ldg(a.colscale + pcol) : 1.0f;
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&prep[tl & 1]);
         if (!tc::mbar_wait(&prep[tl & 1], static_cast<uint32_t>((tl >> 1) & 1), abort_flag, a.wait_limit)) { ok = false; break; }
@@ -312,6 +299,25 @@ __global__ void __launch_bounds__(kWorkers + 32, 1) dlr_oz_kernel(OzArgs a) {
   if (warp == 0) tc::tmem_dealloc(taddr, kTmemCols);
 }
 
+// 2^(8 - b_c) per column c of in [r][ncol] (double-float complex), with 2^(b_c) > 2 max over
+// the column's 2r real values of |high part| (1 + 2^-19), b_c >= -100: the fixed-point grid of
+// the column's slices.  Consecutive threads read consecutive columns (coalesced).
+__global__ void __launch_bounds__(256) col_scale_kernel(const dfc* __restrict__ in, int r, long long ncol,
+                                                        float* __restrict__ scale) {
+  for (long long c = blockIdx.x * 256LL + threadIdx.x; c < ncol; c += static_cast<long long>(gridDim.x) * 256) {
+    float mx = 0.0f;
+#pragma unroll 8
+    for (int l = 0; l < r; ++l) {
+      const float4 v = __ldg(reinterpret_cast<const float4*>(in + static_cast<long long>(l) * ncol + c));
+      mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.z)));
+    }
+    int e = 0;
+    if (mx > 0.0f) frexpf(mx * 2.000004f, &e);
+    e = max(e, -100);
+    scale[c] = ldexpf(1.0f, 8 - e);
+  }
+}
+
 uint16_t bf16_of_int(long double v) {
   const float f = static_cast<float>(v);           // an integer of at most 8 significant bits
   uint32_t u;
@@ -389,9 +395,15 @@ void pack_dlr_oz(const std::complex<double>* T, int r, std::vector<uint8_t>* dst
 }
 
 cudaError_t launch_dlr_oz(const void* pack, int r, const void* in, void* out, long long ncol, int* err,
-                          cudaStream_t st, bool out_c128, long long wait_limit) {
-  if (!dlr_oz_supported(r) || in == out) return cudaErrorInvalidValue;
+                          cudaStream_t st, bool out_c128, long long wait_limit, float* colscale) {
+  if (!dlr_oz_supported(r) || in == out || !colscale) return cudaErrorInvalidValue;
   if (ncol <= 0) return cudaSuccess;
+  {
+    const long long nb = std::min<long long>((ncol + 255) / 256, 152LL * 8);
+    col_scale_kernel<<<static_cast<unsigned>(nb), 256, 0, st>>>(static_cast<const dfc*>(in), r, ncol, colscale);
+    cudaError_t e0 = cudaGetLastError();
+    if (e0 != cudaSuccess) return e0;
+  }
   const DlrOzLayout L = dlr_oz_layout(r);
   auto fn = out_c128 ? &dlr_oz_kernel<true> : &dlr_oz_kernel<false>;
   cudaError_t e = set_smem(reinterpret_cast<const void*>(fn), L.smem, true);
@@ -420,6 +432,7 @@ cudaError_t launch_dlr_oz(const void* pack, int r, const void* in, void* out, lo
   a.ncol = ncol;
   a.err = err;
   a.wait_limit = wait_limit >= 0 ? wait_limit : tc::kWaitLimit;
+  a.colscale = colscale;
   fn<<<static_cast<unsigned>(cpp * L.nparts), kWorkers + 32, L.smem, st>>>(a);
   return cudaGetLastError();
 }

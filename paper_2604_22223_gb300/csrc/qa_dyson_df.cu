@@ -26,6 +26,12 @@ constexpr int kDfLanes = 16;
 constexpr int kDfWarps = 4;
 constexpr int kDfSys = kDfWarps * 32 / kDfLanes;      // systems per block
 constexpr int kPS = 17;                               // padded row stride of the 16-wide tiles
+// per-system strides of the shared tiles, padded so that the same entry of
+// consecutive systems (the coalesced tile loads and stores, and the two
+// systems of a warp) falls in different banks
+constexpr int kSysP = kDfLanes * kPS + 1;             // P / Z / X1 tile, dfc
+constexpr int kSysX = kDfLanes * kPS + 2;             // X0 tile, float2
+constexpr int kSysR = 4 * kDfLanes + 2;               // pivot rows, float2
 
 __device__ void report_df(int* err, long long* first_bad, int code, long long idx) {
   atomicCAS(err, 0, code);
@@ -114,10 +120,11 @@ __global__ void __launch_bounds__(kDfWarps * 32, 3) dyson_w_df_kernel(
   const int n = NFIX > 0 ? NFIX : n_arg;
   constexpr int M = kDfLanes;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  dfc* Pt = reinterpret_cast<dfc*>(smem_raw);                 // [sys][M][kPS]: P, then Z, then X1
-  dfc* Sc = Pt + kDfSys * M * kPS;                             // [sys][M][BW] rows of S in their block
-  float2* X0 = reinterpret_cast<float2*>(Sc + kDfSys * M * BW);   // [sys][M][kPS]
-  float2* Rb = X0 + kDfSys * M * kPS;                          // [sys][2][2 M] pivot rows
+  constexpr int kSysS = M * BW + 1;
+  dfc* Pt = reinterpret_cast<dfc*>(smem_raw);                 // [sys][M][kPS]: P, then R, then X1
+  dfc* Sc = Pt + kDfSys * kSysP;                               // [sys][M][BW] rows of S in their block
+  float2* X0 = reinterpret_cast<float2*>(Sc + kDfSys * kSysS);   // [sys][M][kPS]
+  float2* Rb = X0 + kDfSys * kSysX;                            // [sys][2][2 M] pivot rows
   const int tid = threadIdx.x, lane = tid & 31;
   const int l = lane & (M - 1);
   const int sys = tid / M;
@@ -135,7 +142,7 @@ __global__ void __launch_bounds__(kDfWarps * 32, 3) dyson_w_df_kernel(
     const int q = q0 + ss;
     dfc v = dfc{dfl(0.f, 0.f), dfl(0.f, 0.f)};
     if (i < n && j < n && q < nk) v = ldg_c(P + slab + static_cast<size_t>(i * n + j) * nk + q);
-    Pt[(ss * M + i) * kPS + j] = v;
+    Pt[ss * kSysP + i * kPS + j] = v;
   }
   for (int idx = tid; idx < kDfSys * M * BW; idx += blockDim.x) {
     const int ss = idx / (M * BW), e = idx - ss * (M * BW);
@@ -146,14 +153,14 @@ __global__ void __launch_bounds__(kDfWarps * 32, 3) dyson_w_df_kernel(
       const int m = blo(i) + t;
       if (m < bhi(i)) v = ldg_c(Vq + static_cast<size_t>(q) * nn + i * n + m);
     }
-    Sc[(ss * M + i) * BW + t] = v;
+    Sc[ss * kSysS + i * BW + t] = v;
   }
   __syncthreads();
   const int q = q0 + sys;
-  dfc* Pw = Pt + sys * M * kPS;
-  const dfc* Sw = Sc + sys * M * BW;
-  float2* Xw = X0 + sys * M * kPS;
-  float2* Rw = Rb + sys * 4 * M;
+  dfc* Pw = Pt + sys * kSysP;
+  const dfc* Sw = Sc + sys * kSysS;
+  float2* Xw = X0 + sys * kSysX;
+  float2* Rw = Rb + sys * kSysR;
   const bool row = l < n;
   const int lo_l = row ? blo(l) : 0, hi_l = row ? bhi(l) : 0;
 
@@ -257,10 +264,10 @@ __global__ void __launch_bounds__(kDfWarps * 32, 3) dyson_w_df_kernel(
 #pragma unroll 1
     for (int h = 0; h < 2; ++h) {
       const int ss = wsys + h;
-      const dfc* Ps = Pt + ss * M * kPS;
-      const dfc* Ss = Sc + ss * M * BW;
-      const float2* Xs = X0 + ss * M * kPS;
-      float2* Rt = reinterpret_cast<float2*>(Pt + ss * M * kPS);
+      const dfc* Ps = Pt + ss * kSysP;
+      const dfc* Ss = Sc + ss * kSysS;
+      const float2* Xs = X0 + ss * kSysX;
+      float2* Rt = reinterpret_cast<float2*>(Pt + ss * kSysP);
       // A operand: M at rows g, g + 8 and columns 2 t4 + {0, 1}, 2 t4 + {8, 9}
       unsigned ar[kSl][4], ai[kSl][4];
       {
@@ -441,7 +448,7 @@ __global__ void __launch_bounds__(kDfWarps * 32, 3) dyson_w_df_kernel(
     const int i = e / n, j = e - i * n;
     const int qq = q0 + ss;
     if (qq < nk) {
-      const dfc v = Pt[(ss * M + i) * kPS + j];
+      const dfc v = Pt[ss * kSysP + i * kPS + j];
       reinterpret_cast<float4*>(WC)[slab + static_cast<size_t>(e) * nk + qq] =
           make_float4(v.x.hi, v.x.lo, v.y.hi, v.y.lo);
     }
@@ -452,10 +459,10 @@ template <int NFIX, int BW>
 cudaError_t launch_df(const void* P, const void* Vq, void* WC, int r, int n, int nk, int* err,
                       long long* first_bad, cudaStream_t st, const DysonBlocks& blk) {
   constexpr int M = kDfLanes;
-  const size_t smem = static_cast<size_t>(kDfSys) * M * kPS * sizeof(dfc) +
-                      static_cast<size_t>(kDfSys) * M * BW * sizeof(dfc) +
-                      static_cast<size_t>(kDfSys) * M * kPS * sizeof(float2) +
-                      static_cast<size_t>(kDfSys) * 4 * M * sizeof(float2);
+  const size_t smem = static_cast<size_t>(kDfSys) * kSysP * sizeof(dfc) +
+                      static_cast<size_t>(kDfSys) * (M * BW + 1) * sizeof(dfc) +
+                      static_cast<size_t>(kDfSys) * kSysX * sizeof(float2) +
+                      static_cast<size_t>(kDfSys) * kSysR * sizeof(float2);
   auto fn = &dyson_w_df_kernel<NFIX, BW>;
   cudaError_t e = set_smem(reinterpret_cast<const void*>(fn), smem, true);
   if (e != cudaSuccess) return e;
