@@ -160,6 +160,7 @@ struct qa_ctx {
   int nb = 1;                     // size of the big-tensor matrices (npair or rho)
   std::vector<cd> basis;          // [npair][rho]
   std::vector<cd> sV;             // [nV][rho][rho] = B^H V(R) B
+  bool s_real = false;            // S(q) real for all q: every S(R) real with S(-R) = S(R)
   qa::PairTerms tbub, tsig;
   int* d_tbub = nullptr;          // off + idx
   void* d_cbub = nullptr;         // coefficients (compute precision)
@@ -528,6 +529,22 @@ int upload_interaction(qa_ctx* c, cudaStream_t st) {
   if (c->reduced) {
     if (c->nV > 0) QA_TRY(upload_c<double>(c->d_sV, c->sV, st));
     src = c->d_sV;
+    // S(q) = sum_R S(R) e^{-iq.R} is real when every S(R) is real and S(-R) = S(R)
+    const size_t nb2s = static_cast<size_t>(nb2);
+    bool real = c->nV > 0;
+    for (int v = 0; v < c->nV && real; ++v) {
+      int w = -1;
+      for (int u = 0; u < c->nV && w < 0; ++u)
+        if (c->vR[3 * u] == -c->vR[3 * v] && c->vR[3 * u + 1] == -c->vR[3 * v + 1] &&
+            c->vR[3 * u + 2] == -c->vR[3 * v + 2])
+          w = u;
+      if (w < 0) { real = false; break; }
+      for (size_t e = 0; e < nb2s && real; ++e) {
+        const cd a = c->sV[v * nb2s + e], b = c->sV[w * nb2s + e];
+        if (a.imag() != 0.0 || a != b) real = false;
+      }
+    }
+    c->s_real = real;
   }
   if (c->precision == QA_FP64) {
     QA_LAUNCH(c, 1, qa::launch_ft_table(c->d_vR, src, c->nV, nb2, nullptr, c->nk, c->n[0], c->n[1],
@@ -844,7 +861,7 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
     tm.mark();  // 4: DLR tau -> nu
     if (qa::dyson_w_df_supported(c->nb))
       QA_LAUNCH(c, 1, qa::launch_dyson_w_df(c->d_Pnu, c->d_Vq, c->d_P, r, c->nb, nk, c->d_err, c->d_bad,
-                                            st, &c->dblk));
+                                            st, &c->dblk, c->s_real));
     else
       QA_LAUNCH(c, 1, qa::launch_dyson_w<T>(c->d_Pnu, c->d_Vq, c->d_P, r, c->nb, nk, c->d_err, c->d_bad,
                                             st, &c->dblk));

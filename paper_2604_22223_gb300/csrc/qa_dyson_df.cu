@@ -70,7 +70,17 @@ __device__ __forceinline__ void cacc_fma(CAcc& a, dfc x, dfc y) {
   acc_fma(a.im, x.y, y.x);
 }
 
+// a += x * y with x real (a double-float), y complex
+__device__ __forceinline__ void cacc_fma(CAcc& a, dfl x, dfc y) {
+  acc_fma(a.re, x, y.x);
+  acc_fma(a.im, x, y.y);
+}
+
 __device__ __forceinline__ float2 hi2(dfc v) { return make_float2(v.x.hi, v.y.hi); }
+// c + s b, s real
+__device__ __forceinline__ float2 rfma(float s, float2 b, float2 c) {
+  return make_float2(fmaf(s, b.x, c.x), fmaf(s, b.y, c.y));
+}
 
 // ---- fixed-point bf16 slices for the residual's tensor-core product
 constexpr int kSl = 5;                                // slices per operand (levels 0..4)
@@ -113,7 +123,8 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], 
 }
 
 // NFIX > 0: system size fixed at compile time.  BW: bound of the block width of S.
-template <int NFIX, int BW>
+// RS: S(q) is real (real S(R) with S(-R) = S(R)): its products take half the work.
+template <int NFIX, int BW, bool RS>
 __global__ void __launch_bounds__(kDfWarps * 32, 3) dyson_w_df_kernel(
     const dfc* __restrict__ P, const dfc* __restrict__ Vq, dfc* __restrict__ WC, int n_arg, int nk,
     int* err, long long* first_bad, DysonBlocks blk) {
@@ -172,7 +183,7 @@ __global__ void __launch_bounds__(kDfWarps * 32, 3) dyson_w_df_kernel(
     const float2 slm = hi2(Sw[l * BW + (m - lo_l)]);
 #pragma unroll
     for (int j = 0; j < M; ++j)
-      if (j < n) a[j] = cfma(slm, hi2(Pw[m * kPS + j]), a[j]);
+      if (j < n) a[j] = RS ? rfma(slm.x, hi2(Pw[m * kPS + j]), a[j]) : cfma(slm, hi2(Pw[m * kPS + j]), a[j]);
   }
 #pragma unroll
   for (int j = 0; j < M; ++j) b[j] = make_float2(0.f, 0.f);
@@ -182,7 +193,8 @@ __global__ void __launch_bounds__(kDfWarps * 32, 3) dyson_w_df_kernel(
       const int lo_m = blo(m), hi_m = bhi(m);
 #pragma unroll
       for (int k = 0; k < M; ++k)
-        if (k >= lo_m && k < hi_m) b[k] = cfma(a[m], hi2(Sw[m * BW + (k - lo_m)]), b[k]);
+        if (k >= lo_m && k < hi_m)
+          b[k] = RS ? rfma(Sw[m * BW + (k - lo_m)].x.hi, a[m], b[k]) : cfma(a[m], hi2(Sw[m * BW + (k - lo_m)]), b[k]);
     }
   }
 #pragma unroll
@@ -282,7 +294,12 @@ __global__ void __launch_bounds__(kDfWarps * 32, 3) dyson_w_df_kernel(
             const int col = 2 * t4 + (ci & 1) + 8 * (ci >> 1);
             CAcc z = CAcc{{0.f, 0.f}, {0.f, 0.f}};
             if (col < n)
-              for (int m = lo_r; m < hi_r; ++m) cacc_fma(z, Ss[row * BW + (m - lo_r)], Ps[m * kPS + col]);
+              for (int m = lo_r; m < hi_r; ++m) {
+                if (RS)
+                  cacc_fma(z, Ss[row * BW + (m - lo_r)].x, Ps[m * kPS + col]);
+                else
+                  cacc_fma(z, Ss[row * BW + (m - lo_r)], Ps[m * kPS + col]);
+              }
             me[rh][ci] = dfc{acc_val(z.re), acc_val(z.im)};
             mx[rh] = fmaxf(mx[rh], fmaxf(fabsf(me[rh][ci].x.hi), fabsf(me[rh][ci].y.hi)));
           }
@@ -455,7 +472,7 @@ __global__ void __launch_bounds__(kDfWarps * 32, 3) dyson_w_df_kernel(
   }
 }
 
-template <int NFIX, int BW>
+template <int NFIX, int BW, bool RS>
 cudaError_t launch_df(const void* P, const void* Vq, void* WC, int r, int n, int nk, int* err,
                       long long* first_bad, cudaStream_t st, const DysonBlocks& blk) {
   constexpr int M = kDfLanes;
@@ -463,7 +480,7 @@ cudaError_t launch_df(const void* P, const void* Vq, void* WC, int r, int n, int
                       static_cast<size_t>(kDfSys) * (M * BW + 1) * sizeof(dfc) +
                       static_cast<size_t>(kDfSys) * kSysX * sizeof(float2) +
                       static_cast<size_t>(kDfSys) * kSysR * sizeof(float2);
-  auto fn = &dyson_w_df_kernel<NFIX, BW>;
+  auto fn = &dyson_w_df_kernel<NFIX, BW, RS>;
   cudaError_t e = set_smem(reinterpret_cast<const void*>(fn), smem, true);
   if (e != cudaSuccess) return e;
   dim3 grid((nk + kDfSys - 1) / kDfSys, r);
@@ -478,17 +495,19 @@ bool dyson_w_df_supported(int n) { return n >= 1 && n <= kDfLanes; }
 
 cudaError_t launch_dyson_w_df(const void* P, const void* Vq, void* WC, int r, int n, int nk,
                               int* err, long long* first_bad, cudaStream_t st,
-                              const DysonBlocks* blk) {
+                              const DysonBlocks* blk, bool real_s) {
   if (!dyson_w_df_supported(n) || P == WC) return cudaErrorInvalidValue;
   DysonBlocks b = blk ? *blk : DysonBlocks{};
   int bw = 0;
   for (int i = 0; i < n && b.nblk > 0; ++i) bw = max(bw, static_cast<int>(b.hi[i]) - static_cast<int>(b.lo[i]));
   if (b.nblk > 0 && bw <= 5) {
-    if (n == 15) return launch_df<15, 5>(P, Vq, WC, r, n, nk, err, first_bad, st, b);
-    return launch_df<0, 5>(P, Vq, WC, r, n, nk, err, first_bad, st, b);
+    if (n == 15)
+      return real_s ? launch_df<15, 5, true>(P, Vq, WC, r, n, nk, err, first_bad, st, b)
+                    : launch_df<15, 5, false>(P, Vq, WC, r, n, nk, err, first_bad, st, b);
+    return launch_df<0, 5, false>(P, Vq, WC, r, n, nk, err, first_bad, st, b);
   }
   b.nblk = 0;
-  return launch_df<0, kDfLanes>(P, Vq, WC, r, n, nk, err, first_bad, st, b);
+  return launch_df<0, kDfLanes, false>(P, Vq, WC, r, n, nk, err, first_bad, st, b);
 }
 
 }  // namespace qa

@@ -180,9 +180,10 @@ cudaError_t launch_dyson_w(const void* P, const void* Vq, void* WC, int r, int n
 // Gauss-Jordan solve refined by one double-float residual step; n <= 16, out of
 // place.
 bool dyson_w_df_supported(int n);
+// real_s: S(q) is real for every q (its imaginary parts are not read).
 cudaError_t launch_dyson_w_df(const void* P, const void* Vq, void* WC, int r, int n, int nk,
                               int* err, long long* first_bad, cudaStream_t st,
-                              const DysonBlocks* blk = nullptr);
+                              const DysonBlocks* blk = nullptr, bool real_s = false);
 
 // Sigma^C[t][a][d][R] = -sum_bc G[t][b][c][R] W^C[t][(ab)][(cd)][R]
 template <typename T>
