@@ -164,6 +164,21 @@ def s_block_sizes(ctx):
     return [roots.count(roots[i]) for i in range(rho)]
 
 
+def s_is_real(ctx):
+    """S(q) = B^H V(q) B is real when every S(R) is real with S(-R) = S(R) (the
+    test the library applies to take its real-S Dyson-W variant)."""
+    import numpy as np
+    m = ctx.model
+    B = ctx.basis if ctx.reduced else np.eye(ctx.npair)
+    S = [B.conj().T @ V @ B for V in np.asarray(m.V)]
+    idx = {tuple(R): i for i, R in enumerate(np.asarray(m.V_R))}
+    for i, R in enumerate(np.asarray(m.V_R)):
+        j = idx.get(tuple(-R))
+        if j is None or np.any(S[i].imag != 0) or np.any(S[i] != S[j]):
+            return False
+    return len(S) > 0
+
+
 def stage_costs(ctx, prec):
     """Algorithmic bytes and arithmetic per launch of each big-tensor stage.
 
@@ -195,8 +210,10 @@ def stage_costs(ctx, prec):
         # double-float sum of the five level results (4 TwoSums and a renormalisation
         # per real output, 30); the slice products themselves run on the tensor
         # cores (15 slice pairs x 4 real 16x16x16 products per system, not counted here)
+        # (with a real S(q), M = S P takes two real products per entry instead of four)
         f32c = 2 * n * sb + sum((n - 1) * ((n - 1 - c) + n) for c in range(n)) + n * (n - 1) * n
-        dyson = (r * nk * (4 * f32c + 48 * n * sb + 2 * (2 * n * n) * (5 * 4 + 3) + 2 * n * n * 30
+        mform = 24 if (ctx.reduced and n == 15 and s_is_real(ctx)) else 48
+        dyson = (r * nk * (4 * f32c + mform * n * sb + 2 * (2 * n * n) * (5 * 4 + 3) + 2 * n * n * 30
                            + 10 * n * n), "df")
         kp = (2 * r + 15) // 16 * 16
         dlr = (15 * 2 * (nb * nb * nk) * kp * kp, "tensor")      # 15 slice products, M x N x K

@@ -67,7 +67,9 @@ enum {
   QA_ERANGE = 5,      /* non-finite values or spectrum outside the DLR window */
   QA_ETIMEOUT = 6,    /* a bounded device wait ran out                       */
   QA_ECUDA = 7,       /* a CUDA runtime call failed                          */
-  QA_ESTATE = 8       /* call out of order (e.g. step before qa_bind)        */
+  QA_ESTATE = 8,      /* call out of order (e.g. step before qa_bind)        */
+  QA_EBOUNDS = 9      /* an index-map gather out of range (only in a library
+                         built with QA_CHECK_BOUNDS; the access was skipped)  */
 };
 
 /* arithmetic of the GPU path */

@@ -91,5 +91,53 @@ def build(verbose: bool = False) -> str:
     return LIB
 
 
+# The translation units whose index-map gathers (the -R map and the pair-basis
+# term lists) carry bounds checks when compiled with QA_CHECK_BOUNDS.
+CHECKED_UNITS = ("qa_fft.cu", "qa_reduced.cu")
+LIB_CHECKED = os.path.join(PKG, "libqa_checked.so")
+BUILD_CHECKED = os.path.join(PKG, "_build_checked")
+
+
+def build_checked(verbose: bool = False) -> str:
+    """libqa_checked.so: libqa.so with CHECKED_UNITS recompiled with -DQA_CHECK_BOUNDS
+    (an out-of-range gather index then reports QA_EBOUNDS instead of reading out of
+    bounds).  A diagnostic build for tests; the product library is libqa.so."""
+    build(verbose)
+    stamp_file = os.path.join(BUILD_CHECKED, "stamp")
+    stamp = _stamp() + "checked"
+    if os.path.exists(LIB_CHECKED) and os.path.exists(stamp_file) and open(stamp_file).read() == stamp:
+        return LIB_CHECKED
+    os.makedirs(BUILD_CHECKED, exist_ok=True)
+    nvcc = _nvcc()
+    objs, jobs = [], []
+    for src in _sources():
+        if not src.endswith((".cu", ".cpp")):
+            continue
+        name = os.path.basename(src)
+        if name in CHECKED_UNITS:
+            obj = os.path.join(BUILD_CHECKED, name + ".o")
+            jobs.append([nvcc] + CUFLAGS + ["-DQA_CHECK_BOUNDS", "-c", src, "-o", obj])
+            objs.append(obj)
+        else:
+            objs.append(os.path.join(BUILD, name + ".o"))
+
+    def run(cmd):
+        p = subprocess.run(cmd, capture_output=True, text=True)
+        if p.returncode != 0:
+            raise RuntimeError("compile failed: %s\n%s%s" % (" ".join(cmd), p.stdout, p.stderr))
+
+    with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+        list(ex.map(run, jobs))
+    tmp = LIB_CHECKED + ".tmp"
+    cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
+    p = subprocess.run(cmd, capture_output=True, text=True)
+    if p.returncode != 0:
+        raise RuntimeError("link failed: %s\n%s%s" % (" ".join(cmd), p.stdout, p.stderr))
+    os.replace(tmp, LIB_CHECKED)
+    with open(stamp_file, "w") as fh:
+        fh.write(stamp)
+    return LIB_CHECKED
+
+
 if __name__ == "__main__":
     print(build(verbose=True))

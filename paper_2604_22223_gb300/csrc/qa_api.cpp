@@ -161,6 +161,7 @@ struct qa_ctx {
   std::vector<cd> basis;          // [npair][rho]
   std::vector<cd> sV;             // [nV][rho][rho] = B^H V(R) B
   bool s_real = false;            // S(q) real for all q: every S(R) real with S(-R) = S(R)
+  bool tsig_real = false;         // every Sigma term coefficient real
   qa::PairTerms tbub, tsig;
   int* d_tbub = nullptr;          // off + idx
   void* d_cbub = nullptr;         // coefficients (compute precision)
@@ -522,6 +523,9 @@ int upload_interaction(qa_ctx* c, cudaStream_t st) {
           }
     }
     toff[no2] = static_cast<int>(tcoef.size());
+    c->tsig_real = true;
+    for (const cd& v : tcoef)
+      if (v.imag() != 0.0) c->tsig_real = false;
     QA_TRY(cudaMemcpyAsync(c->d_tgo, toff.data(), toff.size() * 4, cudaMemcpyHostToDevice, st));
     QA_TRY(cudaMemcpyAsync(c->d_tgi, tidx.data(), tidx.size() * 4, cudaMemcpyHostToDevice, st));
     QA_TRY(upload_c<qa::dfl>(c->d_tgc, tcoef, st));
@@ -842,7 +846,8 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
     // bubble and R -> q transform in one pass (the bubble stage reads as 0)
     tm.mark();  // 2: bubble
     QA_LAUNCH(c, 1, qa::launch_fft3d_bubble<T>(fft, c->d_GR, c->d_Grefl, c->d_mR, c->d_tbub, c->d_cbub,
-                                               max_terms_per_entry(c->tbub), nb2, c->norb, c->d_P, r, st));
+                                               max_terms_per_entry(c->tbub), nb2, c->norb, c->d_P, r, st,
+                                               c->d_err));
   } else {
     if (c->reduced)
       QA_LAUNCH(c, 1, qa::launch_bubble_reduced<T>(c->d_GR, c->d_Grefl, c->d_mR, c->d_tbub, c->d_cbub,
@@ -890,7 +895,7 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
                                                c->d_SigC, r, nk, st));
   else if (is_df<T>())
     QA_LAUNCH(c, 1, qa::launch_sigma_target_df(c->d_GR, c->d_W, c->d_tgo, c->d_tgi, c->d_tgc, c->d_SigC,
-                                               r, c->norb, nb2, nk, st));
+                                               r, c->norb, nb2, nk, st, c->d_err, c->tsig_real));
   else if (c->reduced)
     QA_LAUNCH(c, 1, qa::launch_sigma_reduced<T>(c->d_GR, c->d_W, c->d_tsig, c->d_csig,
                                                 static_cast<int>(c->tsig.idx.size()), c->d_SigC, r,
@@ -1509,6 +1514,7 @@ const char* qa_strerror(int s) {
     case QA_ETIMEOUT: return "device wait timed out";
     case QA_ECUDA: return "CUDA runtime error";
     case QA_ESTATE: return "call out of order";
+    case QA_EBOUNDS: return "index-map gather out of range (bounds-checked build)";
     default: return "unknown status";
   }
 }

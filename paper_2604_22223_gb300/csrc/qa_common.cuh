@@ -9,6 +9,19 @@
 
 namespace qa {
 
+// Bounds checks of the index-map gathers (the -R map and the pair-basis term
+// lists), compiled in only with QA_CHECK_BOUNDS: an index outside [0, n)
+// records QA_EBOUNDS in the error word and the gather reads index 0 instead.
+#ifdef QA_CHECK_BOUNDS
+__device__ __forceinline__ int qa_index(int i, int n, int* err) {
+  if (i >= 0 && i < n) return i;
+  if (err) atomicCAS(err, 0, QA_EBOUNDS_CODE);
+  return 0;
+}
+#else
+__device__ __forceinline__ int qa_index(int i, int, int*) { return i; }
+#endif
+
 template <typename T> struct CplxOf;
 template <> struct CplxOf<double> { using type = double2; };
 template <> struct CplxOf<float> { using type = float2; };

@@ -15,6 +15,8 @@
 // registers, from a per-step table of the mu-independent part.  The density
 // N(mu) = (s/N_k) sum_{k,n} Re(dw_n Tr G) and its derivative
 // -(s/N_k) sum Re(dw_n Tr G^2) are accumulated in FP64.
+#include <type_traits>
+
 #include "qa_common.cuh"
 
 namespace qa {
@@ -829,7 +831,7 @@ __global__ void __launch_bounds__(256) dyson_g_prep_kernel(const double2* __rest
 // mode 0: per-block partial sums of Re(dw_n Tr G) and Re(dw_n Tr G^2) (FP64
 // accumulation of the per-system traces); mode 1: also store G.
 template <typename T, int NO>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) dyson_g_kernel(const cplx<T>* __restrict__ Bm,
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 || std::is_same<T, dfl>::value) ? 2 : 1) dyson_g_kernel(const cplx<T>* __restrict__ Bm,
                                                       const cplx<T>* __restrict__ dw,
                                                       const double* __restrict__ iw, double dmu,
                                                       const double* mus, int r, int nk, cplx<T>* Giw,

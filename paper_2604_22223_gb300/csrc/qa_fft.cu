@@ -26,6 +26,7 @@ struct BubbleSrc {
   int nout;
   int no2;
   int mt;                 // term capacity of the shared-memory lists (multiple of 4)
+  int* err;               // error word (bounds-checked builds)
 };
 
 template <typename V>
@@ -254,14 +255,14 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? (L1C >= 0 ? 3 : 
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int e = e0 + u * kFftThreads;
-          mr[u] = e < nk ? bs.mR[e] : 0;
+          mr[u] = e < nk ? qa_index(bs.mR[e], nk, bs.err) : 0;
           acc[u] = cmk<V>(0, 0);
         }
         for (int v = 0; v < nt; ++v) {
           const int id = ti[v];
           const V c = tc[v];
-          const V* g1 = gt + static_cast<size_t>(id & 255) * nk;
-          const V* g2 = lt + static_cast<size_t>(id >> 8) * nk;
+          const V* g1 = gt + static_cast<size_t>(qa_index(id & 255, bs.no2, bs.err)) * nk;
+          const V* g2 = lt + static_cast<size_t>(qa_index(id >> 8, bs.no2, bs.err)) * nk;
           V x[8], y[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
@@ -468,14 +469,14 @@ __global__ void __launch_bounds__(((1 << (L1 + L2 + L3)) / 8 < kLineMaxThreads ?
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int e = eb + u * NTH;
-        mr[u] = e < NK ? bs.mR[e] : 0;
+        mr[u] = e < NK ? qa_index(bs.mR[e], NK, bs.err) : 0;
         acc[u] = cmk<V>(0, 0);
       }
       for (int v = 0; v < nt; ++v) {
         const int id = ti[v];
         const V c = tc[v];
-        const V* g1 = gt + static_cast<size_t>(id & 255) * NK;
-        const V* g2 = lt + static_cast<size_t>(id >> 8) * NK;
+        const V* g1 = gt + static_cast<size_t>(qa_index(id & 255, bs.no2, bs.err)) * NK;
+        const V* g2 = lt + static_cast<size_t>(qa_index(id >> 8, bs.no2, bs.err)) * NK;
         V xv[4], yv[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -578,10 +579,10 @@ bool fft3d_bubble_supported(const FftDev& plan) { return reg_plan_ok(plan); }
 template <typename T>
 cudaError_t launch_fft3d_bubble(const FftDev& plan, const void* GR, const void* GreflR,
                                 const int* mR, const int* terms, const void* coef, int max_terms,
-                                int nout, int norb, void* out, int r, cudaStream_t st) {
+                                int nout, int norb, void* out, int r, cudaStream_t st, int* err) {
   if (!reg_plan_ok(plan) || max_terms > kMaxLineTerms || norb * norb > 256) return cudaErrorInvalidValue;
   const int mt = (max_terms + 3) / 4 * 4;            // keeps the line buffer aligned
-  BubbleSrc bs{GR, GreflR, mR, terms, coef, nout, norb * norb, mt < 4 ? 4 : mt};
+  BubbleSrc bs{GR, GreflR, mR, terms, coef, nout, norb * norb, mt < 4 ? 4 : mt, err};
   return launch_fft3d_reg<T, true>(plan, -1, nullptr, out, static_cast<long long>(nout) * r, st,
                                    static_cast<T>(1), bs);
 }
@@ -609,10 +610,10 @@ cudaError_t launch_fft3d(const FftDev& plan, int sign, const void* in, void* out
 
 template cudaError_t launch_fft3d_bubble<double>(const FftDev&, const void*, const void*, const int*,
                                                  const int*, const void*, int, int, int, void*, int,
-                                                 cudaStream_t);
+                                                 cudaStream_t, int*);
 template cudaError_t launch_fft3d_bubble<float>(const FftDev&, const void*, const void*, const int*,
                                                 const int*, const void*, int, int, int, void*, int,
-                                                cudaStream_t);
+                                                cudaStream_t, int*);
 template cudaError_t launch_fft3d<double>(const FftDev&, int, const void*, void*, long long,
                                           cudaStream_t, double);
 template cudaError_t launch_fft3d<float>(const FftDev&, int, const void*, void*, long long,
@@ -621,6 +622,6 @@ template cudaError_t launch_fft3d<dfl>(const FftDev&, int, const void*, void*, l
                                        cudaStream_t, double);
 template cudaError_t launch_fft3d_bubble<dfl>(const FftDev&, const void*, const void*, const int*,
                                               const int*, const void*, int, int, int, void*, int,
-                                              cudaStream_t);
+                                              cudaStream_t, int*);
 
 }  // namespace qa

@@ -18,6 +18,7 @@ struct dfl;   // double-float real (qa_df.cuh); complex arrays of it are dfc
 // Device-side copy of the public status code for a singular pivot.
 constexpr int QA_ESINGULAR_CODE = 3;
 constexpr int QA_ETIMEOUT_CODE = 6;
+constexpr int QA_EBOUNDS_CODE = 9;
 
 // ------------------------------------------------------------------- DLR
 // Discrete Lehmann representation (Kaye, Chen & Parcollet, PRB 105, 235115
@@ -151,7 +152,7 @@ bool fft3d_bubble_supported(const FftDev& plan);
 template <typename T>
 cudaError_t launch_fft3d_bubble(const FftDev& plan, const void* GR, const void* GreflR,
                                 const int* mR, const int* terms, const void* coef, int max_terms,
-                                int nout, int norb, void* out, int r, cudaStream_t st);
+                                int nout, int norb, void* out, int r, cudaStream_t st, int* err = nullptr);
 
 // P[t][(ab)][(cd)][R] = -s G[t][b][c][R] Grefl[t][d][a][mR[R]]
 template <typename T>
@@ -220,7 +221,7 @@ cudaError_t launch_sigma_canonical(const void* GR, const void* Wt, const std::co
 // G entry) as int2, tcoef[nterm] dfc.  Any pair basis (nout = nb^2 entries of Wt).
 cudaError_t launch_sigma_target_df(const void* GR, const void* Wt, const int* toff, const void* tidx,
                                    const void* tcoef, void* Sig, int r, int norb, int nout, int nk,
-                                   cudaStream_t st);
+                                   cudaStream_t st, int* err = nullptr, bool real_coef = false);
 
 // Dyson for G.  prep: Bm[n][a][b][k] = (mu_ref - H(k) - SigHF(k))_ab - SigIw[n][a][b][k]
 // (SigHF FP64 [N_k][norb][norb] and SigIw may be null) and per-block bounds

@@ -339,10 +339,13 @@ __device__ __forceinline__ void df_acc_prod(float& s, float& e, dfl u, dfl v) {
   e = __fadd_rn(e, __fadd_rn(t, q));
 }
 
+// RC: every term coefficient is real (a real pair basis), so c Wt takes two
+// double-float products instead of a complex one.
+template <bool RC>
 __global__ void __launch_bounds__(kSigDfR * 25) sigma_target_df_kernel(
     const dfc* __restrict__ GR, const dfc* __restrict__ Wt, const int* __restrict__ toff,
     const int2* __restrict__ tidx, const dfc* __restrict__ tcoef, dfc* __restrict__ Sig, int no2,
-    int nout, int nk) {
+    int nout, int nk, int* err) {
   const int R = blockIdx.x * kSigDfR + threadIdx.x;
   const int tg = threadIdx.y;                 // target entry a * norb + d
   const int t = blockIdx.y;
@@ -353,8 +356,9 @@ __global__ void __launch_bounds__(kSigDfR * 25) sigma_target_df_kernel(
   const int e1 = toff[tg + 1];
   for (int e = toff[tg]; e < e1; ++e) {
     const int2 ix = __ldg(tidx + e);          // (Wt entry, G entry)
-    const dfc cw = cmul(ldg_c(tcoef + e), ldg_c(w + static_cast<size_t>(ix.x) * nk));
-    const dfc gv = ldg_c(g + static_cast<size_t>(ix.y) * nk);
+    const dfc cf = ldg_c(tcoef + e), wv = ldg_c(w + static_cast<size_t>(qa_index(ix.x, nout, err)) * nk);
+    const dfc cw = RC ? dfc{cf.x * wv.x, cf.x * wv.y} : cmul(cf, wv);
+    const dfc gv = ldg_c(g + static_cast<size_t>(qa_index(ix.y, no2, err)) * nk);
     df_acc_prod(rs, re, cw.x, gv.x);
     df_acc_prod(rs, re, -cw.y, gv.y);
     df_acc_prod(is, ie, cw.x, gv.y);
@@ -418,14 +422,15 @@ template cudaError_t launch_sigma_reduced<dfl>(const void*, const void*, const i
 
 cudaError_t launch_sigma_target_df(const void* GR, const void* Wt, const int* toff, const void* tidx,
                                    const void* tcoef, void* Sig, int r, int norb, int nout, int nk,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, int* err, bool real_coef) {
   const int no2 = norb * norb;
   if (no2 > 25 || r < 1 || r > 65535) return cudaErrorInvalidValue;
   dim3 block(kSigDfR, no2), grid((nk + kSigDfR - 1) / kSigDfR, r);
-  sigma_target_df_kernel<<<grid, block, 0, st>>>(static_cast<const dfc*>(GR), static_cast<const dfc*>(Wt),
+  auto fn = real_coef ? &sigma_target_df_kernel<true> : &sigma_target_df_kernel<false>;
+  fn<<<grid, block, 0, st>>>(static_cast<const dfc*>(GR), static_cast<const dfc*>(Wt),
                                                  toff, static_cast<const int2*>(tidx),
                                                  static_cast<const dfc*>(tcoef), static_cast<dfc*>(Sig),
-                                                 no2, nout, nk);
+                                                 no2, nout, nk, err);
   return cudaGetLastError();
 }
 

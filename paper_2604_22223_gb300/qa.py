@@ -83,11 +83,15 @@ class StepStats(C.Structure):
 _lib = None
 
 
-def load(path: str = LIB_PATH):
-    """Load libqa.so and declare the ABI; raises if it was not built."""
+def load(path: str = None):
+    """Load libqa.so and declare the ABI; raises if it was not built.  The
+    environment variable QA_LIB names another build of the same ABI (the
+    bounds-checked libqa_checked.so), read at the first load of a process."""
     global _lib
     if _lib is not None:
         return _lib
+    if path is None:
+        path = os.environ.get("QA_LIB") or LIB_PATH
     if not os.path.exists(path):
         raise RuntimeError("libqa.so not found at %s: run paper_2604_22223_gb300.build()" % path)
     L = C.CDLL(path)
