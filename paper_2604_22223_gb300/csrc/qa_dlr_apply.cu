@@ -6,6 +6,8 @@
 // Each block stages TILE columns x r nodes in shared memory (one HBM read),
 // then every thread produces RB output rows of one column from registers.
 // The tile is fully loaded before any write, so in == out is allowed.
+#include <algorithm>
+
 #include "qa_common.cuh"
 
 namespace qa {
@@ -56,10 +58,31 @@ __global__ void __launch_bounds__(256) dlr_apply_kernel(const cplx<T>* __restric
 
 }  // namespace
 
+// One output row (a weighted sum over the nodes, e.g. the density weights):
+// one thread per column, the weights broadcast from L1.
+template <typename T>
+__global__ void __launch_bounds__(256) node_sum_kernel(const cplx<T>* __restrict__ w, int r,
+                                                       const cplx<T>* __restrict__ in, cplx<T>* out,
+                                                       long long ncol, int accumulate) {
+  for (long long c = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; c < ncol;
+       c += static_cast<long long>(gridDim.x) * blockDim.x) {
+    cplx<T> acc = cmk<cplx<T>>(0, 0);
+    for (int l = 0; l < r; ++l) acc = cfma(ldg_c(w + l), ldg_c(in + static_cast<long long>(l) * ncol + c), acc);
+    out[c] = accumulate ? cadd(out[c], acc) : acc;
+  }
+}
+
 template <typename T>
 cudaError_t launch_dlr_apply(const void* Tm, int rows_out, int r, const void* in, void* out,
                              long long ncol, cudaStream_t st, int accumulate) {
   if (ncol <= 0 || rows_out <= 0) return cudaSuccess;
+  if (rows_out == 1) {
+    const long long nb = std::min<long long>((ncol + 255) / 256, 152LL * 16);
+    node_sum_kernel<T><<<static_cast<unsigned>(nb), 256, 0, st>>>(
+        reinterpret_cast<const cplx<T>*>(Tm), r, reinterpret_cast<const cplx<T>*>(in),
+        reinterpret_cast<cplx<T>*>(out), ncol, accumulate);
+    return cudaGetLastError();
+  }
   constexpr int TILE = sizeof(cplx<T>) >= 16 ? 32 : 64;
   constexpr int RB = 4;
   size_t smem = static_cast<size_t>(r) * TILE * sizeof(cplx<T>);

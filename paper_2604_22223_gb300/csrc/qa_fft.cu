@@ -167,6 +167,30 @@ __device__ __forceinline__ V tw_mul(int j, V v) {
   return cmul(cmk<V>(cos64(j), SIGN * sin64(j)), v);
 }
 
+// Butterfly sums.  For double-float values the sum is left unnormalised: the
+// exact sum of the high parts (TwoSum) with the low parts and its error added
+// into the low word, which keeps hi + lo exact up to the low word's rounding
+// (~2^-48 of the operands) and saves the renormalisation (3 of 11 instructions
+// per add); products (the twiddles) read both words and renormalise, and the
+// kernels renormalise every value they store to global memory.
+template <typename V>
+__device__ __forceinline__ V bf_add(V a, V b) { return cadd(a, b); }
+template <typename V>
+__device__ __forceinline__ V bf_sub(V a, V b) { return csub(a, b); }
+__device__ __forceinline__ dfl add_unnorm(dfl a, dfl b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  return dfl(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+template <>
+__device__ __forceinline__ dfc bf_add<dfc>(dfc a, dfc b) {
+  return dfc{add_unnorm(a.x, b.x), add_unnorm(a.y, b.y)};
+}
+template <>
+__device__ __forceinline__ dfc bf_sub<dfc>(dfc a, dfc b) {
+  return dfc{add_unnorm(a.x, -b.x), add_unnorm(a.y, -b.y)};
+}
+
 // In-register radix-2 transform of length L (input in bit-reversed order,
 // output in natural order): X_f = sum_j x_j exp(SIGN 2 pi i f j / L).
 template <typename V, int L, int SIGN>
@@ -179,8 +203,8 @@ __device__ __forceinline__ void fft_regs(V (&x)[L]) {
       for (int s0 = 0; s0 < L; s0 += m) {
         const V u = x[s0 + k];
         const V t = tw_mul<V, SIGN>(k * (64 / m), x[s0 + k + m / 2]);
-        x[s0 + k] = cadd(u, t);
-        x[s0 + k + m / 2] = csub(u, t);
+        x[s0 + k] = bf_add(u, t);
+        x[s0 + k + m / 2] = bf_sub(u, t);
       }
     }
   }

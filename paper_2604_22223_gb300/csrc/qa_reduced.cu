@@ -327,7 +327,7 @@ cudaError_t launch_sigma_canonical(const void* GR, const void* Wt, const std::co
 // leading FP32 product split exactly by an FMA, the high parts added with
 // TwoSum.  A short loop instead of an unrolled term pattern keeps the code in
 // the instruction cache.
-constexpr int kSigDfR = 32;
+constexpr int kSigDfR = 16;
 
 __device__ __forceinline__ void df_acc_prod(float& s, float& e, dfl u, dfl v) {
   const float p = __fmul_rn(u.hi, v.hi);
