@@ -185,39 +185,31 @@ __global__ void __launch_bounds__(kWorkers + 32, 1) dlr_oz_kernel(OzArgs a) {
     const uint32_t lane_base = static_cast<uint32_t>(32 * (warp & 3)) << 16;
     const uint32_t roff = static_cast<uint32_t>(m >> 3) * 256 + static_cast<uint32_t>(m & 7) * 16 +
                           static_cast<uint32_t>(qt >> 1) * 128 + static_cast<uint32_t>(qt & 1) * 8;
-    // pre-pass mapping: warp w owns rows 8w .. 8w + 7, four lanes per row
-    const int pm = 8 * warp + (lane >> 2), pq = lane & 3;
     const int cq = Nw / 4;                                     // accumulator columns per thread
     long long g = 0, tl = 0;
     bool ok = true;
-    for (long long tile = cp; tile < ntiles && ok; tile += cpp, ++tl) {
-      // column scales 2^(8 - b_c), 2^(b_c) >= 2 max |x| over the column's 2r values
-      // (computed by col_scale_kernel in one streaming pass before this launch)
-      {
-        const long long pcol = tile * kTileM + pm;
-        if (pq == 0) s_b[(tl & 1) * kTileM + pm] = pcol < a.ncol ? __ldg(a.colscale + pcol) : 1.0f;
-        __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&prep[tl & 1]);
-        if (!tc::mbar_wait(&prep[tl & 1], static_cast<uint32_t>((tl >> 1) & 1), abort_flag, a.wait_limit)) { ok = false; break; }
-      }
-      const float scale = s_b[(tl & 1) * kTileM + m];
-      const long long col = tile * kTileM + m;
-      const bool colok = col < a.ncol;
-      // this thread's two values of a chunk; the next chunk's are loaded before
-      // the current one is sliced (one chunk of loads in flight)
-      auto load2 = [&](int ch, dfc* v) {
+    // this thread's two values of chunk ch of the column cl
+    auto load2 = [&](int ch, long long cl, bool cok, dfc* v) {
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const int l = ch * 8 + qt * 2 + e;
-          v[e] = dfc{dfl(0.0f, 0.0f), dfl(0.0f, 0.0f)};
-          if (colok && ch < nchunk && l < a.r) v[e] = ldg_c(a.in + static_cast<long long>(l) * a.ncol + col);
-        }
-      };
-      dfc cur[2], nxt[2];
-      load2(0, cur);
+      for (int e = 0; e < 2; ++e) {
+        const int l = ch * 8 + qt * 2 + e;
+        v[e] = dfc{dfl(0.0f, 0.0f), dfl(0.0f, 0.0f)};
+        if (cok && ch < nchunk && l < a.r) v[e] = ldg_c(a.in + static_cast<long long>(l) * a.ncol + cl);
+      }
+    };
+    // the column, its slice grid 2^(8 - b_c) (col_scale_kernel) and the first chunk of
+    // a tile are fetched before the previous tile's accumulators are drained, so
+    // these loads fly during the drain
+    long long col = static_cast<long long>(cp) * kTileM + m;
+    bool colok = cp < ntiles && col < a.ncol;
+    float scale = colok ? __ldg(a.colscale + col) : 1.0f;
+    dfc cur[2], nxt[2];
+    load2(0, col, colok, cur);
+    for (long long tile = cp; tile < ntiles && ok; tile += cpp, ++tl) {
+      // the next chunk's values are loaded before the current one is sliced
       for (int ch = 0; ch < nchunk; ++ch, ++g) {
         const int b = static_cast<int>(g & 1);
-        load2(ch + 1, nxt);
+        load2(ch + 1, col, colok, nxt);
         if (g >= 2) {
           const bool w = tc::mbar_wait(&done[b], static_cast<uint32_t>(((g - 2) >> 1) & 1), abort_flag, a.wait_limit);
           if (__any_sync(0xffffffffu, !w)) { ok = false; break; }
@@ -246,6 +238,12 @@ __global__ void __launch_bounds__(kWorkers + 32, 1) dlr_oz_kernel(OzArgs a) {
         const bool w = tc::mbar_wait(&done[(g - 1) & 1], static_cast<uint32_t>(((g - 1) >> 1) & 1), abort_flag, a.wait_limit);
         if (__any_sync(0xffffffffu, !w)) { ok = false; break; }
       }
+      // the next tile's column, grid and first chunk
+      const long long ntile = tile + cpp;
+      const long long col_n = ntile * kTileM + m;
+      const bool colok_n = ntile < ntiles && col_n < a.ncol;
+      const float scale_n = colok_n ? __ldg(a.colscale + col_n) : 1.0f;
+      load2(0, col_n, colok_n, cur);
       tc::fence_after();
       const float oscale = 0x1p-16f / scale * 256.0f;          // 2^(b_c - 16)
       for (int c4 = qt * cq; c4 < (qt + 1) * cq; c4 += 4) {
@@ -284,6 +282,9 @@ __global__ void __launch_bounds__(kWorkers + 32, 1) dlr_oz_kernel(OzArgs a) {
       tc::fence_before();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(drained);
+      col = col_n;
+      colok = colok_n;
+      scale = scale_n;
     }
     if (!ok) *abort_flag = 1;
   }
