@@ -162,6 +162,7 @@ struct qa_ctx {
   std::vector<cd> sV;             // [nV][rho][rho] = B^H V(R) B
   bool s_real = false;            // S(q) real for all q: every S(R) real with S(-R) = S(R)
   bool tsig_real = false;         // every Sigma term coefficient real
+  bool tbub_real = false;         // every bubble term coefficient real
   qa::PairTerms tbub, tsig;
   int* d_tbub = nullptr;          // off + idx
   void* d_cbub = nullptr;         // coefficients (compute precision)
@@ -493,6 +494,9 @@ int upload_interaction(qa_ctx* c, cudaStream_t st) {
   const int nb2 = c->nb * c->nb;
   const double2* src = c->d_vV;
   {
+    c->tbub_real = true;
+    for (const cd& v : c->tbub.coef)
+      if (v.imag() != 0.0) c->tbub_real = false;
     const qa::PairTerms* tl[2] = {&c->tbub, &c->tsig};
     int* di[2] = {c->d_tbub, c->d_tsig};
     void* dc[2] = {c->d_cbub, c->d_csig};
@@ -847,7 +851,7 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
     tm.mark();  // 2: bubble
     QA_LAUNCH(c, 1, qa::launch_fft3d_bubble<T>(fft, c->d_GR, c->d_Grefl, c->d_mR, c->d_tbub, c->d_cbub,
                                                max_terms_per_entry(c->tbub), nb2, c->norb, c->d_P, r, st,
-                                               c->d_err));
+                                               c->d_err, c->tbub_real));
   } else {
     if (c->reduced)
       QA_LAUNCH(c, 1, qa::launch_bubble_reduced<T>(c->d_GR, c->d_Grefl, c->d_mR, c->d_tbub, c->d_cbub,

@@ -211,9 +211,10 @@ __global__ void __launch_bounds__(kDfWarps * 32, 3) dyson_w_df_kernel(
   float2 frec[M];
 #pragma unroll
   for (int j = 0; j < M; ++j) frec[j] = make_float2(0.f, 0.f);
-  // the column loop stays rolled (small code); register arrays are indexed by c
-  // through compile-time selects
-#pragma unroll 1
+  // with a compile-time size the column loop is unrolled (every register index
+  // and predicate a constant); otherwise it stays rolled and the register arrays
+  // are indexed by c through compile-time selects
+#pragma unroll(NFIX > 0 ? NFIX : 1)
   for (int c = 0; c < n; ++c) {
     float2* Ra_c = Rw + (c & 1) * 2 * M;
     float2* Rb_c = Ra_c + M;
@@ -423,7 +424,7 @@ __global__ void __launch_bounds__(kDfWarps * 32, 3) dyson_w_df_kernel(
   __syncwarp();
 
   // ---- 3. delta = A^-1 R: the recorded elimination replayed on R
-#pragma unroll 1
+#pragma unroll(NFIX > 0 ? NFIX : 1)
   for (int c = 0; c < n; ++c) {
     float2* Rr = Rw + (c & 1) * 2 * M;
     if (mypos == c) {

@@ -27,6 +27,7 @@ struct BubbleSrc {
   int no2;
   int mt;                 // term capacity of the shared-memory lists (multiple of 4)
   int* err;               // error word (bounds-checked builds)
+  int real_coef;          // every coefficient is real: c x y as x (c y), c y a real scaling
 };
 
 template <typename V>
@@ -295,7 +296,8 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? (L1C >= 0 ? 3 : 
             y[u] = e < nk ? g2[mr[u]] : cmk<V>(0, 0);
           }
 #pragma unroll
-          for (int u = 0; u < 8; ++u) acc[u] = cfma(c, cmul(x[u], y[u]), acc[u]);
+          for (int u = 0; u < 8; ++u)
+            acc[u] = bs.real_coef ? cfma(x[u], cscale(y[u], c.x), acc[u]) : cfma(c, cmul(x[u], y[u]), acc[u]);
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
@@ -509,7 +511,8 @@ __global__ void __launch_bounds__(((1 << (L1 + L2 + L3)) / 8 < kLineMaxThreads ?
           yv[u] = e < NK ? g2[mr[u]] : cmk<V>(0, 0);
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc[u] = cfma(c, cmul(xv[u], yv[u]), acc[u]);
+        for (int u = 0; u < 4; ++u)
+          acc[u] = bs.real_coef ? cfma(xv[u], cscale(yv[u], c.x), acc[u]) : cfma(c, cmul(xv[u], yv[u]), acc[u]);
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -603,10 +606,11 @@ bool fft3d_bubble_supported(const FftDev& plan) { return reg_plan_ok(plan); }
 template <typename T>
 cudaError_t launch_fft3d_bubble(const FftDev& plan, const void* GR, const void* GreflR,
                                 const int* mR, const int* terms, const void* coef, int max_terms,
-                                int nout, int norb, void* out, int r, cudaStream_t st, int* err) {
+                                int nout, int norb, void* out, int r, cudaStream_t st, int* err,
+                                bool real_coef) {
   if (!reg_plan_ok(plan) || max_terms > kMaxLineTerms || norb * norb > 256) return cudaErrorInvalidValue;
   const int mt = (max_terms + 3) / 4 * 4;            // keeps the line buffer aligned
-  BubbleSrc bs{GR, GreflR, mR, terms, coef, nout, norb * norb, mt < 4 ? 4 : mt, err};
+  BubbleSrc bs{GR, GreflR, mR, terms, coef, nout, norb * norb, mt < 4 ? 4 : mt, err, real_coef ? 1 : 0};
   return launch_fft3d_reg<T, true>(plan, -1, nullptr, out, static_cast<long long>(nout) * r, st,
                                    static_cast<T>(1), bs);
 }
@@ -634,10 +638,10 @@ cudaError_t launch_fft3d(const FftDev& plan, int sign, const void* in, void* out
 
 template cudaError_t launch_fft3d_bubble<double>(const FftDev&, const void*, const void*, const int*,
                                                  const int*, const void*, int, int, int, void*, int,
-                                                 cudaStream_t, int*);
+                                                 cudaStream_t, int*, bool);
 template cudaError_t launch_fft3d_bubble<float>(const FftDev&, const void*, const void*, const int*,
                                                 const int*, const void*, int, int, int, void*, int,
-                                                cudaStream_t, int*);
+                                                cudaStream_t, int*, bool);
 template cudaError_t launch_fft3d<double>(const FftDev&, int, const void*, void*, long long,
                                           cudaStream_t, double);
 template cudaError_t launch_fft3d<float>(const FftDev&, int, const void*, void*, long long,
@@ -646,6 +650,6 @@ template cudaError_t launch_fft3d<dfl>(const FftDev&, int, const void*, void*, l
                                        cudaStream_t, double);
 template cudaError_t launch_fft3d_bubble<dfl>(const FftDev&, const void*, const void*, const int*,
                                               const int*, const void*, int, int, int, void*, int,
-                                              cudaStream_t, int*);
+                                              cudaStream_t, int*, bool);
 
 }  // namespace qa

@@ -152,7 +152,8 @@ bool fft3d_bubble_supported(const FftDev& plan);
 template <typename T>
 cudaError_t launch_fft3d_bubble(const FftDev& plan, const void* GR, const void* GreflR,
                                 const int* mR, const int* terms, const void* coef, int max_terms,
-                                int nout, int norb, void* out, int r, cudaStream_t st, int* err = nullptr);
+                                int nout, int norb, void* out, int r, cudaStream_t st, int* err = nullptr,
+                                bool real_coef = false);
 
 // P[t][(ab)][(cd)][R] = -s G[t][b][c][R] Grefl[t][d][a][mR[R]]
 template <typename T>
