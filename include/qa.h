@@ -80,8 +80,10 @@ enum {
                          and computed from FP32 instructions: error-free FP32
                          transformations for the FFTs, products and small
                          solves, the Dyson solve for W in FP32 refined by one
-                         double-float residual step, and the DLR maps on the
-                         tensor cores from fixed-point bf16 slices; FP64 for
+                         residual step (its dense product on the tensor cores
+                         from exact fixed-point bf16 slices, the rest in
+                         double-float), and the DLR maps on the tensor cores
+                         from fixed-point bf16 slices; FP64 for
                          the DLR matrices, the chemical potential and density
                          sums.  Agrees with QA_FP64 to ~1e-9 relative.       */
   QA_FP32 = 2         /* complex64 storage of P, W^C and the G/Sigma stages,

@@ -98,7 +98,9 @@ template <> __device__ __forceinline__ double2 from_d2<double2>(double2 a) { ret
 template <> __device__ __forceinline__ float2 from_d2<float2>(double2 a) {
   return make_float2(static_cast<float>(a.x), static_cast<float>(a.y));
 }
-template <> __device__ __forceinline__ dfc from_d2<dfc>(double2 a) { return dfc{dfl(a.x), dfl(a.y)}; }
+template <> __device__ __forceinline__ dfc from_d2<dfc>(double2 a) {
+  return dfc{df_from_bits(a.x), df_from_bits(a.y)};
+}
 
 // exp(sign * 2 pi i * (sum_d (i_d R_d mod N_d) / N_d)) in FP64; the integer
 // reduction keeps the phase argument exact for any R.

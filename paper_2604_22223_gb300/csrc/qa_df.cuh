@@ -40,6 +40,27 @@ struct __align__(16) dfc {
   dfl x, y;
 };
 
+// d as hi + lo from its bit pattern with FP32-rate integer and float operations
+// (GB300 runs FP64 conversions at the FP64 rate): hi = d truncated to 24
+// significant bits, lo = the remaining 29 mantissa bits rounded to 24, so
+// |hi + lo - d| <= 2^-47 |d| and 0 <= lo/hi < 2^-23.  Zero takes (0, 0); other
+// magnitudes outside [2^-74, 2^100) and non-finite values take the FP64 conversion.
+__device__ __forceinline__ dfl df_from_bits(double d) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(d));
+  const int e = static_cast<int>((b >> 52) & 0x7ffu);
+  if (e < 1023 - 74 || e >= 1023 + 100) {
+    if ((b << 1) == 0ull) return dfl(0.0f, 0.0f);
+    return dfl(d);
+  }
+  const unsigned sign = static_cast<unsigned>(b >> 32) & 0x80000000u;
+  const float hi = __uint_as_float(sign | (static_cast<unsigned>(e - 1023 + 127) << 23) |
+                                   static_cast<unsigned>((b >> 29) & 0x7fffffu));
+  // the low 29 bits weigh 2^(e - 1075): as a float, biased exponent e - 948 (>= 1 here)
+  const float sc = __uint_as_float(static_cast<unsigned>(e - 948) << 23);
+  const float lo = __fmul_rn(__uint2float_rn(static_cast<unsigned>(b & 0x1fffffffu)), sc);
+  return dfl(hi, sign ? -lo : lo);
+}
+
 // s + e = a + b exactly (Knuth)
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
