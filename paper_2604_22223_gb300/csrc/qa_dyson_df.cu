@@ -423,8 +423,9 @@ __global__ void __launch_bounds__(kDfWarps * 32, 3) dyson_w_df_kernel(
   }
   __syncwarp();
 
-  // ---- 3. delta = A^-1 R: the recorded elimination replayed on R
-#pragma unroll(NFIX > 0 ? NFIX : 1)
+  // ---- 3. delta = A^-1 R: the recorded elimination replayed on R (rolled: the
+  // instruction cache holds the unrolled elimination above)
+#pragma unroll 1
   for (int c = 0; c < n; ++c) {
     float2* Rr = Rw + (c & 1) * 2 * M;
     if (mypos == c) {
