@@ -490,3 +490,58 @@ def test_bubble_of_interacting_pole_sum(name):
             T = np.einsum("kmbc,kmda->abcd", A, c[kp])
             ref = m.s_spin * T.reshape(no * no, no * no) / m.nk
             assert np.abs(P[iq, j] - ref).max() <= 1e-8 * scale, (iq, j)
+
+
+def test_screened_interaction_tau_by_direct_matsubara_sum():
+    """W^C(q, tau) of the oracle (the DLR fit of W^C(q, i nu) on the bosonic nodes,
+    evaluated at the tau nodes; Eq. for the screened interaction with the static V
+    removed before the i nu -> tau step) against the direct bosonic sum
+      W^C(q, tau) = (1/beta) sum_m exp(-i nu_m tau) W^C(q, i nu_m),  |m| <= M,
+    with W^C = (1 - V P)^-1 V P V at every nu_m and P(q, i nu_m) the exact Matsubara
+    sum over G0's pole form (as in the bubble pins).  W^C decays like T1/(i nu) +
+    T2/(i nu)^2 (T1 = V A1 V, T2 = -V A2 V + V A1 V A1 V from P = A1/(i nu) -
+    A2/(i nu)^2 + ...); these tails are summed in closed form,
+      (1/beta) sum_{m != 0} exp(-i nu_m tau) / (i nu_m)   = tau/beta - 1/2,
+      (1/beta) sum_{m != 0} exp(-i nu_m tau) / (i nu_m)^2 = -(beta/2) B_2(tau/beta),
+    B_2(x) = x^2 - x + 1/6, and the rest converges as 1/M^2.  Complex hoppings
+    (peierls-3x3) keep every pair entry independent."""
+    m = wl.config("peierls-3x3")
+    d = gw.make_dlr(m)
+    G0, _ = gw.g0(m, d)
+    o = gw.gw_step(m, d, G0)
+    c = gw._node_axis_solve(d.K_tau(), G0)
+    Vq = lattice.V_q(m)
+    beta, no = m.beta, m.norb
+    npair = no * no
+    w = d.omega
+    f = fermi(beta * w)
+    Dlm = w[None, :] - w[:, None]
+    num = f[None, :] - f[:, None]
+    M = 3000
+    mm = np.arange(-M, M + 1)
+    nu = 2j * np.pi * mm / beta
+    nz = mm != 0
+    taus = d.tau_abs()
+    x = taus / beta
+    S1 = x - 0.5
+    S2 = -(beta / 2) * (x * x - x + 1.0 / 6.0)
+    ph = np.exp(-np.outer(taus, nu))
+    pts = lattice.grid_points(m.n)
+    scale = np.abs(o["WC_qtau"]).max()
+    for iq in range(m.nk):
+        kp = _grid_index(m.n, pts - pts[iq])
+        den = nu[:, None, None] + Dlm[None]
+        small = np.abs(den) < 1e-12
+        frac = np.where(small, (-beta * f[:, None] * (1 - f[:, None]))[None], num[None] / np.where(small, 1.0, den))
+        P = m.s_spin * np.einsum("vkmbc,kmda->vabcd", np.einsum("klbc,vlm->vkmbc", c, frac),
+                                 c[kp]).reshape(len(nu), npair, npair) / m.nk
+        A1 = m.s_spin * np.einsum("klbc,lm,kmda->abcd", c, num, c[kp]).reshape(npair, npair) / m.nk
+        A2 = m.s_spin * np.einsum("klbc,lm,kmda->abcd", c, num * Dlm, c[kp]).reshape(npair, npair) / m.nk
+        V = Vq[iq]
+        VP = np.einsum("ab,vbc->vac", V, P)
+        W = np.linalg.solve(np.eye(npair)[None] - VP, np.einsum("vab,bc->vac", VP, V))
+        T1 = V @ A1 @ V
+        T2 = -V @ A2 @ V + V @ A1 @ V @ A1 @ V
+        W[nz] -= T1[None] / nu[nz, None, None] + T2[None] / nu[nz, None, None] ** 2
+        Wt = np.einsum("tv,vab->tab", ph, W) / beta + S1[:, None, None] * T1[None] + S2[:, None, None] * T2[None]
+        assert np.abs(Wt - o["WC_qtau"][iq]).max() <= 1e-6 * scale, iq
