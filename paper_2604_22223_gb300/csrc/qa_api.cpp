@@ -101,6 +101,7 @@ struct qa_ctx {
   void* d_P = nullptr;
   void* d_W = nullptr;
   float* d_colscale = nullptr;  // per-column slice grids of the tensor-core DLR maps (mixed)
+  unsigned char* d_ozcode = nullptr;  // [r][nb^2 N_k] grid codes of a big-tensor map's input (mixed)
   double* d_part = nullptr;
   double* d_red = nullptr;
   int* d_err = nullptr;
@@ -398,6 +399,7 @@ size_t layout(qa_ctx* c, char* base) {
   if (c->precision == QA_MIXED && c->use_oz) {
     c->d_Pnu = take(r * nb2 * nk * es);
     c->d_colscale = static_cast<float*>(take(std::max(nb2, no2) * nk * 4));
+    c->d_ozcode = static_cast<unsigned char*>(take(r * nb2 * nk));
   }
   if (c->precision == QA_MIXED) {
     const size_t cap = term_capacity(c);
@@ -846,12 +848,14 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
   QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, +1, Gk, c->d_GR, ncs / nk * r, st));
   QA_LAUNCH(c, 1, qa::launch_fft3d<T>(fft, +1, c->d_Grefl, c->d_Grefl, ncs / nk * r, st));
   tm.mark();  // 1: G -> R
+  bool p_codes = false;   // the bubble stage stored the grid codes of P(q, tau)
   if (qa::fft3d_bubble_supported(fft) && max_terms_per_entry(c->tbub) <= 640) {
     // bubble and R -> q transform in one pass (the bubble stage reads as 0)
     tm.mark();  // 2: bubble
     QA_LAUNCH(c, 1, qa::launch_fft3d_bubble<T>(fft, c->d_GR, c->d_Grefl, c->d_mR, c->d_tbub, c->d_cbub,
                                                max_terms_per_entry(c->tbub), nb2, c->norb, c->d_P, r, st,
-                                               c->d_err, c->tbub_real));
+                                               c->d_err, c->tbub_real, oz ? c->d_ozcode : nullptr));
+    p_codes = oz && qa::fft3d_bubble_codes(fft);
   } else {
     if (c->reduced)
       QA_LAUNCH(c, 1, qa::launch_bubble_reduced<T>(c->d_GR, c->d_Grefl, c->d_mR, c->d_tbub, c->d_cbub,
@@ -866,16 +870,21 @@ int forward_sigma(qa_ctx* c, const double2* Gin, StageTimer& tm, cudaStream_t st
   if (oz) {
     // out-of-place tensor-core maps: P(q, tau) [P] -> P(q, i nu) [Pnu] -> W^C(q, i nu) [P]
     // -> W^C(q, tau) [W]
-    QA_LAUNCH(c, 2, qa::launch_dlr_oz(c->d_oz_Ttn, r, c->d_P, c->d_Pnu, ncb, c->d_err, st, false, c->wait_limit, c->d_colscale));
+    // (the slice grids of both maps come from the grid codes their producers store,
+    // where those producers write them)
+    QA_LAUNCH(c, 2, qa::launch_dlr_oz(c->d_oz_Ttn, r, c->d_P, c->d_Pnu, ncb, c->d_err, st, false, c->wait_limit,
+                                      c->d_colscale, p_codes ? c->d_ozcode : nullptr));
     tm.mark();  // 4: DLR tau -> nu
-    if (qa::dyson_w_df_supported(c->nb))
+    const bool w_codes = qa::dyson_w_df_supported(c->nb);
+    if (w_codes)
       QA_LAUNCH(c, 1, qa::launch_dyson_w_df(c->d_Pnu, c->d_Vq, c->d_P, r, c->nb, nk, c->d_err, c->d_bad,
-                                            st, &c->dblk, c->s_real));
+                                            st, &c->dblk, c->s_real, c->d_ozcode));
     else
       QA_LAUNCH(c, 1, qa::launch_dyson_w<T>(c->d_Pnu, c->d_Vq, c->d_P, r, c->nb, nk, c->d_err, c->d_bad,
                                             st, &c->dblk));
     tm.mark();  // 5: Dyson W
-    QA_LAUNCH(c, 2, qa::launch_dlr_oz(c->d_oz_Tnt, r, c->d_P, c->d_W, ncb, c->d_err, st, false, c->wait_limit, c->d_colscale));
+    QA_LAUNCH(c, 2, qa::launch_dlr_oz(c->d_oz_Tnt, r, c->d_P, c->d_W, ncb, c->d_err, st, false, c->wait_limit,
+                                      c->d_colscale, w_codes ? c->d_ozcode : nullptr));
   } else {
     if (f32 && c->use_tc)
       QA_LAUNCH(c, 1, qa::launch_dlr_tc(c->d_tc_Ttn, r, c->d_P, c->d_P, ncb, c->d_err, st, false, c->wait_limit));

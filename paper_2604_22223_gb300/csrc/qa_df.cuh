@@ -183,4 +183,17 @@ __device__ __forceinline__ double2 to_c64d(dfc a) {
   return make_double2(static_cast<double>(a.x), static_cast<double>(a.y));
 }
 
+// Slice-grid code of one double-float complex value for the tensor-core DLR maps:
+// 0 for a zero value, else max(e, -100) + 101, where e is the binary exponent of
+// x = 2.000004 max(|re.hi|, |im.hi|) in frexp's convention (2^(e-1) <= x < 2^e;
+// for a normal x, its biased exponent - 126; a subnormal x clamps to -100).  The
+// scaling and the exponent are both monotone in the magnitude, so the largest
+// code over a column decodes to the exponent of the column's largest value.
+__device__ __forceinline__ unsigned oz_grid_code(dfc v) {
+  const float m = fmaxf(fabsf(v.x.hi), fabsf(v.y.hi));
+  if (m == 0.0f) return 0u;
+  const int be = static_cast<int>((__float_as_uint(m * 2.000004f) >> 23) & 0xffu);
+  return static_cast<unsigned>(max(be - 126, -100) + 101);
+}
+
 }  // namespace qa

@@ -61,7 +61,7 @@ struct OzArgs {
   long long ncol;
   int* err;
   long long wait_limit;    // polls of each pipeline wait before the time-out path
-  const float* colscale;   // 2^(8 - b_c) per column (col_scale_kernel)
+  const float* colscale;   // 2^(8 - b_c) per column (col_scale_kernel or col_scale_code_kernel)
 };
 
 __device__ __forceinline__ uint32_t pack_hi16(float a, float b) {
@@ -319,6 +319,41 @@ __global__ void __launch_bounds__(256) col_scale_kernel(const dfc* __restrict__ 
   }
 }
 
+// 2^(8 - b_c) from a column's largest grid code b (0: an all-zero column, b_c = 0)
+__device__ __forceinline__ float code_scale(unsigned b) {
+  const int e = b == 0 ? 0 : static_cast<int>(b) - 101;
+  return ldexpf(1.0f, 8 - e);
+}
+
+// The same grids from the one-byte codes that the producing kernel stored beside
+// each value (oz_grid_code; code [r][ncol]): the largest code of a column decodes
+// to the exponent col_scale_kernel would find, so the two give identical scales
+// while this pass reads one byte per value instead of sixteen.
+__global__ void __launch_bounds__(256) col_scale_code_kernel(const uint8_t* __restrict__ code, int r,
+                                                             long long ncol, float* __restrict__ scale) {
+  for (long long c = blockIdx.x * 256LL + threadIdx.x; c < ncol; c += static_cast<long long>(gridDim.x) * 256) {
+    unsigned mx = 0;
+#pragma unroll 8
+    for (int l = 0; l < r; ++l) mx = max(mx, static_cast<unsigned>(__ldg(code + static_cast<long long>(l) * ncol + c)));
+    scale[c] = code_scale(mx);
+  }
+}
+
+// col_scale_code_kernel for ncol a multiple of 4 (code and scale 16-byte aligned):
+// four columns per thread, one 32-bit load per node and a bytewise maximum
+__global__ void __launch_bounds__(256) col_scale_code4_kernel(const uint8_t* __restrict__ code, int r,
+                                                              long long ncol, float* __restrict__ scale) {
+  const long long nc4 = ncol >> 2;
+  const unsigned* __restrict__ c4 = reinterpret_cast<const unsigned*>(code);
+  for (long long c = blockIdx.x * 256LL + threadIdx.x; c < nc4; c += static_cast<long long>(gridDim.x) * 256) {
+    unsigned mx = 0;
+#pragma unroll 8
+    for (int l = 0; l < r; ++l) mx = __vmaxu4(mx, __ldg(c4 + static_cast<long long>(l) * nc4 + c));
+    reinterpret_cast<float4*>(scale)[c] = make_float4(code_scale(mx & 0xffu), code_scale((mx >> 8) & 0xffu),
+                                                      code_scale((mx >> 16) & 0xffu), code_scale(mx >> 24));
+  }
+}
+
 uint16_t bf16_of_int(long double v) {
   const float f = static_cast<float>(v);           // an integer of at most 8 significant bits
   uint32_t u;
@@ -396,12 +431,21 @@ void pack_dlr_oz(const std::complex<double>* T, int r, std::vector<uint8_t>* dst
 }
 
 cudaError_t launch_dlr_oz(const void* pack, int r, const void* in, void* out, long long ncol, int* err,
-                          cudaStream_t st, bool out_c128, long long wait_limit, float* colscale) {
+                          cudaStream_t st, bool out_c128, long long wait_limit, float* colscale,
+                          const uint8_t* code) {
   if (!dlr_oz_supported(r) || in == out || !colscale) return cudaErrorInvalidValue;
   if (ncol <= 0) return cudaSuccess;
   {
     const long long nb = std::min<long long>((ncol + 255) / 256, 152LL * 8);
-    col_scale_kernel<<<static_cast<unsigned>(nb), 256, 0, st>>>(static_cast<const dfc*>(in), r, ncol, colscale);
+    const bool v4 = (ncol & 3) == 0 && (reinterpret_cast<uintptr_t>(code) & 15) == 0 &&
+                    (reinterpret_cast<uintptr_t>(colscale) & 15) == 0;
+    if (code && v4)
+      col_scale_code4_kernel<<<static_cast<unsigned>(std::min<long long>((ncol / 4 + 255) / 256, 152LL * 8)), 256,
+                               0, st>>>(code, r, ncol, colscale);
+    else if (code)
+      col_scale_code_kernel<<<static_cast<unsigned>(nb), 256, 0, st>>>(code, r, ncol, colscale);
+    else
+      col_scale_kernel<<<static_cast<unsigned>(nb), 256, 0, st>>>(static_cast<const dfc*>(in), r, ncol, colscale);
     cudaError_t e0 = cudaGetLastError();
     if (e0 != cudaSuccess) return e0;
   }

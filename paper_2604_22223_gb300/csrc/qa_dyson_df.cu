@@ -127,7 +127,7 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], 
 template <int NFIX, int BW, bool RS>
 __global__ void __launch_bounds__(kDfWarps * 32, 3) dyson_w_df_kernel(
     const dfc* __restrict__ P, const dfc* __restrict__ Vq, dfc* __restrict__ WC, int n_arg, int nk,
-    int* err, long long* first_bad, DysonBlocks blk) {
+    int* err, long long* first_bad, DysonBlocks blk, unsigned char* __restrict__ code) {
   const int n = NFIX > 0 ? NFIX : n_arg;
   constexpr int M = kDfLanes;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -468,15 +468,16 @@ __global__ void __launch_bounds__(kDfWarps * 32, 3) dyson_w_df_kernel(
     const int qq = q0 + ss;
     if (qq < nk) {
       const dfc v = Pt[ss * kSysP + i * kPS + j];
-      reinterpret_cast<float4*>(WC)[slab + static_cast<size_t>(e) * nk + qq] =
-          make_float4(v.x.hi, v.x.lo, v.y.hi, v.y.lo);
+      const size_t o = slab + static_cast<size_t>(e) * nk + qq;
+      reinterpret_cast<float4*>(WC)[o] = make_float4(v.x.hi, v.x.lo, v.y.hi, v.y.lo);
+      if (code) code[o] = static_cast<unsigned char>(oz_grid_code(v));
     }
   }
 }
 
 template <int NFIX, int BW, bool RS>
 cudaError_t launch_df(const void* P, const void* Vq, void* WC, int r, int n, int nk, int* err,
-                      long long* first_bad, cudaStream_t st, const DysonBlocks& blk) {
+                      long long* first_bad, cudaStream_t st, const DysonBlocks& blk, unsigned char* code) {
   constexpr int M = kDfLanes;
   const size_t smem = static_cast<size_t>(kDfSys) * kSysP * sizeof(dfc) +
                       static_cast<size_t>(kDfSys) * (M * BW + 1) * sizeof(dfc) +
@@ -487,7 +488,7 @@ cudaError_t launch_df(const void* P, const void* Vq, void* WC, int r, int n, int
   if (e != cudaSuccess) return e;
   dim3 grid((nk + kDfSys - 1) / kDfSys, r);
   fn<<<grid, kDfWarps * 32, smem, st>>>(static_cast<const dfc*>(P), static_cast<const dfc*>(Vq),
-                                        static_cast<dfc*>(WC), n, nk, err, first_bad, blk);
+                                        static_cast<dfc*>(WC), n, nk, err, first_bad, blk, code);
   return cudaGetLastError();
 }
 
@@ -497,19 +498,19 @@ bool dyson_w_df_supported(int n) { return n >= 1 && n <= kDfLanes; }
 
 cudaError_t launch_dyson_w_df(const void* P, const void* Vq, void* WC, int r, int n, int nk,
                               int* err, long long* first_bad, cudaStream_t st,
-                              const DysonBlocks* blk, bool real_s) {
+                              const DysonBlocks* blk, bool real_s, unsigned char* code) {
   if (!dyson_w_df_supported(n) || P == WC) return cudaErrorInvalidValue;
   DysonBlocks b = blk ? *blk : DysonBlocks{};
   int bw = 0;
   for (int i = 0; i < n && b.nblk > 0; ++i) bw = max(bw, static_cast<int>(b.hi[i]) - static_cast<int>(b.lo[i]));
   if (b.nblk > 0 && bw <= 5) {
     if (n == 15)
-      return real_s ? launch_df<15, 5, true>(P, Vq, WC, r, n, nk, err, first_bad, st, b)
-                    : launch_df<15, 5, false>(P, Vq, WC, r, n, nk, err, first_bad, st, b);
-    return launch_df<0, 5, false>(P, Vq, WC, r, n, nk, err, first_bad, st, b);
+      return real_s ? launch_df<15, 5, true>(P, Vq, WC, r, n, nk, err, first_bad, st, b, code)
+                    : launch_df<15, 5, false>(P, Vq, WC, r, n, nk, err, first_bad, st, b, code);
+    return launch_df<0, 5, false>(P, Vq, WC, r, n, nk, err, first_bad, st, b, code);
   }
   b.nblk = 0;
-  return launch_df<0, kDfLanes, false>(P, Vq, WC, r, n, nk, err, first_bad, st, b);
+  return launch_df<0, kDfLanes, false>(P, Vq, WC, r, n, nk, err, first_bad, st, b, code);
 }
 
 }  // namespace qa

@@ -28,6 +28,7 @@ struct BubbleSrc {
   int mt;                 // term capacity of the shared-memory lists (multiple of 4)
   int* err;               // error word (bounds-checked builds)
   int real_coef;          // every coefficient is real: c x y as x (c y), c y a real scaling
+  unsigned char* code;    // grid codes of the stored values, like out (double-float line kernel)
 };
 
 template <typename V>
@@ -398,11 +399,13 @@ __device__ __forceinline__ int axis_freq(int p) {
 // STEP 0: the whole axis (LL <= 3); 1: 8-point transforms over elements A
 // apart, then the twiddles; 2: A-point transforms over adjacent elements.
 // SRC_G: read the input line in natural order; DST_G: write the output line
-// in natural order (scaled), otherwise in place in shared memory.
+// in natural order (scaled), otherwise in place in shared memory; cd (double-float
+// only, optional): the line's grid codes, one byte per stored value.
 template <typename T, int SIGN, int NTH, int L1, int L2, int L3, int LL, int LS, int STEP, bool SRC_G,
           bool DST_G>
 __device__ __forceinline__ void line_step(const cplx<T>* __restrict__ src, cplx<T>* __restrict__ dst,
-                                          cplx<T>* buf, const cplx<T>* __restrict__ tw, T scale) {
+                                          cplx<T>* buf, const cplx<T>* __restrict__ tw, T scale,
+                                          unsigned char* __restrict__ cd) {
   using V = cplx<T>;
   constexpr int NK = 1 << (L1 + L2 + L3);
   constexpr int L = 1 << LL, S = 1 << LS;
@@ -440,7 +443,11 @@ __device__ __forceinline__ void line_step(const cplx<T>* __restrict__ src, cplx<
       if constexpr (DST_G) {
         const int p3 = e & ((1 << L3) - 1), p2 = (e >> L3) & ((1 << L2) - 1), p1 = e >> (L2 + L3);
         const int f = (axis_freq<L1>(p1) << (L2 + L3)) + (axis_freq<L2>(p2) << L3) + axis_freq<L3>(p3);
-        dst[f] = cscale(x[j], scale);
+        const V v = cscale(x[j], scale);
+        dst[f] = v;
+        if constexpr (std::is_same<T, dfl>::value) {
+          if (cd) cd[f] = static_cast<unsigned char>(oz_grid_code(v));
+        }
       } else {
         buf[pad8(e)] = x[j];
       }
@@ -450,13 +457,13 @@ __device__ __forceinline__ void line_step(const cplx<T>* __restrict__ src, cplx<
 
 template <typename T, int SIGN, int NTH, int L1, int L2, int L3, int LL, int LS, bool SRC_G, bool DST_G>
 __device__ __forceinline__ void line_axis(const cplx<T>* src, cplx<T>* dst, cplx<T>* buf,
-                                          const cplx<T>* tw, T scale) {
+                                          const cplx<T>* tw, T scale, unsigned char* cd) {
   if constexpr (AxisSplit<LL>::steps == 1) {
-    line_step<T, SIGN, NTH, L1, L2, L3, LL, LS, 0, SRC_G, DST_G>(src, dst, buf, tw, scale);
+    line_step<T, SIGN, NTH, L1, L2, L3, LL, LS, 0, SRC_G, DST_G>(src, dst, buf, tw, scale, cd);
   } else if constexpr (AxisSplit<LL>::steps == 2) {
-    line_step<T, SIGN, NTH, L1, L2, L3, LL, LS, 1, SRC_G, false>(src, dst, buf, tw, scale);
+    line_step<T, SIGN, NTH, L1, L2, L3, LL, LS, 1, SRC_G, false>(src, dst, buf, tw, scale, cd);
     __syncthreads();
-    line_step<T, SIGN, NTH, L1, L2, L3, LL, LS, 2, false, DST_G>(src, dst, buf, tw, scale);
+    line_step<T, SIGN, NTH, L1, L2, L3, LL, LS, 2, false, DST_G>(src, dst, buf, tw, scale, cd);
   }
 }
 
@@ -524,18 +531,19 @@ __global__ void __launch_bounds__(((1 << (L1 + L2 + L3)) / 8 < kLineMaxThreads ?
   }
   const V* src = in + gl * NK;
   V* dst = out + gl * NK;
+  unsigned char* cd = BUB && bs.code ? bs.code + gl * NK : nullptr;
   constexpr bool h3 = L3 > 0, h2 = L2 > 0, h1 = L1 > 0;
   if constexpr (h3) {
-    line_axis<T, SIGN, NTH, L1, L2, L3, L3, 0, !BUB, !h2 && !h1>(src, dst, buf, twg + p.tw_off[2], scale);
+    line_axis<T, SIGN, NTH, L1, L2, L3, L3, 0, !BUB, !h2 && !h1>(src, dst, buf, twg + p.tw_off[2], scale, cd);
     if constexpr (h2 || h1) __syncthreads();
   }
   if constexpr (h2) {
-    line_axis<T, SIGN, NTH, L1, L2, L3, L2, L3, !BUB && !h3, !h1>(src, dst, buf, twg + p.tw_off[1], scale);
+    line_axis<T, SIGN, NTH, L1, L2, L3, L2, L3, !BUB && !h3, !h1>(src, dst, buf, twg + p.tw_off[1], scale, cd);
     if constexpr (h1) __syncthreads();
   }
   if constexpr (h1) {
     line_axis<T, SIGN, NTH, L1, L2, L3, L1, L2 + L3, !BUB && !h3 && !h2, true>(src, dst, buf,
-                                                                              twg + p.tw_off[0], scale);
+                                                                              twg + p.tw_off[0], scale, cd);
   }
 }
 
@@ -603,14 +611,22 @@ cudaError_t launch_fft3d_reg(const FftDev& plan, int sign, const void* in, void*
 
 bool fft3d_bubble_supported(const FftDev& plan) { return reg_plan_ok(plan); }
 
+// the grids on which 16-byte lines take fft3d_line_kernel (the kernel that writes codes)
+bool fft3d_bubble_codes(const FftDev& plan) {
+  if (!reg_plan_ok(plan)) return false;
+  const int l1 = ilog2(plan.n[0]), l2 = ilog2(plan.n[1]), l3 = ilog2(plan.n[2]);
+  return (l1 == 5 && l2 == 5 && l3 == 3) || (l1 == 4 && l2 == 4 && l3 == 3);
+}
+
 template <typename T>
 cudaError_t launch_fft3d_bubble(const FftDev& plan, const void* GR, const void* GreflR,
                                 const int* mR, const int* terms, const void* coef, int max_terms,
                                 int nout, int norb, void* out, int r, cudaStream_t st, int* err,
-                                bool real_coef) {
+                                bool real_coef, unsigned char* code) {
   if (!reg_plan_ok(plan) || max_terms > kMaxLineTerms || norb * norb > 256) return cudaErrorInvalidValue;
   const int mt = (max_terms + 3) / 4 * 4;            // keeps the line buffer aligned
-  BubbleSrc bs{GR, GreflR, mR, terms, coef, nout, norb * norb, mt < 4 ? 4 : mt, err, real_coef ? 1 : 0};
+  BubbleSrc bs{GR, GreflR, mR, terms, coef, nout, norb * norb, mt < 4 ? 4 : mt, err, real_coef ? 1 : 0,
+               std::is_same<T, dfl>::value ? code : nullptr};
   return launch_fft3d_reg<T, true>(plan, -1, nullptr, out, static_cast<long long>(nout) * r, st,
                                    static_cast<T>(1), bs);
 }
@@ -638,10 +654,10 @@ cudaError_t launch_fft3d(const FftDev& plan, int sign, const void* in, void* out
 
 template cudaError_t launch_fft3d_bubble<double>(const FftDev&, const void*, const void*, const int*,
                                                  const int*, const void*, int, int, int, void*, int,
-                                                 cudaStream_t, int*, bool);
+                                                 cudaStream_t, int*, bool, unsigned char*);
 template cudaError_t launch_fft3d_bubble<float>(const FftDev&, const void*, const void*, const int*,
                                                 const int*, const void*, int, int, int, void*, int,
-                                                cudaStream_t, int*, bool);
+                                                cudaStream_t, int*, bool, unsigned char*);
 template cudaError_t launch_fft3d<double>(const FftDev&, int, const void*, void*, long long,
                                           cudaStream_t, double);
 template cudaError_t launch_fft3d<float>(const FftDev&, int, const void*, void*, long long,
@@ -650,6 +666,6 @@ template cudaError_t launch_fft3d<dfl>(const FftDev&, int, const void*, void*, l
                                        cudaStream_t, double);
 template cudaError_t launch_fft3d_bubble<dfl>(const FftDev&, const void*, const void*, const int*,
                                               const int*, const void*, int, int, int, void*, int,
-                                              cudaStream_t, int*, bool);
+                                              cudaStream_t, int*, bool, unsigned char*);
 
 }  // namespace qa

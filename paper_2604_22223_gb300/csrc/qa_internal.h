@@ -133,9 +133,12 @@ bool dlr_oz_supported(int r);
 void pack_dlr_oz(const std::complex<double>* T, int r, std::vector<uint8_t>* dst);
 // out_c128: store complex128 instead of double-float.  colscale: device scratch of
 // ncol floats (the per-column slice grid, written by a streaming pass that this
-// call launches first: two kernels per call).
+// call launches first: two kernels per call).  code (optional, [r][ncol] bytes):
+// the grid codes (oz_grid_code) that the kernel producing `in` stored beside it;
+// the pass then reads them instead of the values.
 cudaError_t launch_dlr_oz(const void* pack, int r, const void* in, void* out, long long ncol,
-                          int* err, cudaStream_t st, bool out_c128, long long wait_limit, float* colscale);
+                          int* err, cudaStream_t st, bool out_c128, long long wait_limit, float* colscale,
+                          const uint8_t* code = nullptr);
 
 // Batched 3-D FFT of contiguous lines of N_k points (in place allowed).
 // sign = -1: X(k) = sum_R e^{-ikR} X(R); sign = +1: (1/N_k) sum_k e^{+ikR} X(k).
@@ -148,12 +151,16 @@ cudaError_t launch_fft3d(const FftDev& plan, int sign, const void* in, void* out
 // fft3d_bubble_supported): line (t, o) of out = FFT over R of
 // sum_{terms of o} coef G[t][g1][R] Grefl[t][g2][mR[R]] (term lists as for
 // launch_bubble_reduced, at most max_terms terms per output, <= 640).
+// code (optional, double-float only): [r][nout N_k] bytes, the grid code of every
+// stored value (oz_grid_code), written where fft3d_bubble_codes(plan) holds and
+// left untouched otherwise.
 bool fft3d_bubble_supported(const FftDev& plan);
+bool fft3d_bubble_codes(const FftDev& plan);
 template <typename T>
 cudaError_t launch_fft3d_bubble(const FftDev& plan, const void* GR, const void* GreflR,
                                 const int* mR, const int* terms, const void* coef, int max_terms,
                                 int nout, int norb, void* out, int r, cudaStream_t st, int* err = nullptr,
-                                bool real_coef = false);
+                                bool real_coef = false, unsigned char* code = nullptr);
 
 // P[t][(ab)][(cd)][R] = -s G[t][b][c][R] Grefl[t][d][a][mR[R]]
 template <typename T>
@@ -182,10 +189,12 @@ cudaError_t launch_dyson_w(const void* P, const void* Vq, void* WC, int r, int n
 // Gauss-Jordan solve refined by one double-float residual step; n <= 16, out of
 // place.
 bool dyson_w_df_supported(int n);
-// real_s: S(q) is real for every q (its imaginary parts are not read).
+// real_s: S(q) is real for every q (its imaginary parts are not read).  code
+// (optional): [r][n^2 N_k] bytes, the grid code of every stored value (oz_grid_code).
 cudaError_t launch_dyson_w_df(const void* P, const void* Vq, void* WC, int r, int n, int nk,
                               int* err, long long* first_bad, cudaStream_t st,
-                              const DysonBlocks* blk = nullptr, bool real_s = false);
+                              const DysonBlocks* blk = nullptr, bool real_s = false,
+                              unsigned char* code = nullptr);
 
 // Sigma^C[t][a][d][R] = -sum_bc G[t][b][c][R] W^C[t][(ab)][(cd)][R]
 template <typename T>
