@@ -332,8 +332,8 @@ int qa_density(qa_ctx* ctx, const void* G, double* n_out, double* N_total, void*
  * fit up to N_k = 10,480).  All calls
  * on a device share that array and it keeps the last call's contents: calls
  * whose GPU work overlaps (other streams or threads) race and give wrong
- * results.  The first call on a device looks up the array's address; make that
- * call before any stream capture.  Synchronises `stream`. */
+ * results.  The first call on a device looks up the array's address.
+ * Synchronises `stream`. */
 int qa_density_static(const qa_ctx* ctx, const void* G, double* n_out, double* N_total,
                       void* stream);
 

@@ -16,8 +16,7 @@
 //   * calls whose GPU work overlaps (two streams, or two host threads on one
 //     device without ordering) race on the array and give wrong results;
 //   * the first call on a device looks up the array's device address with
-//     cudaGetSymbolAddress (with that device current); make that first call
-//     before any stream capture.
+//     cudaGetSymbolAddress (with that device current).
 #include <mutex>
 #include <vector>
 
